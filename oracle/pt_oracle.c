@@ -1,0 +1,524 @@
+/*
+ * pt_oracle.c -- plain, slow, single-threaded CPU oracle.
+ *
+ * TEST INFRASTRUCTURE.  Only tests/, __graft_entry__.smoke() and bench.py's
+ * CPU-baseline leg may load this library.  It shares no code, header, table or
+ * constant generator with the CUDA path: everything below is written out again
+ * from the definitions it cites.
+ *
+ * What it computes (arXiv:1605.03607, "Practical engineering of hard
+ * spin-glass instances"):
+ *   - the Ising cost H = sum_<ij> J_ij s_i s_j over the couplers of the
+ *     Chimera graph, minimised over s_i = +-1 (Eq. 1; graph of Appendix A,
+ *     Fig. 8: L x L unit cells of K_{4,4});
+ *   - parallel tempering (Sec. II): N_T copies at inverse temperatures
+ *     beta_0 > beta_1 > ... (slot 0 coldest), independent Metropolis sweeps,
+ *     then a temperature-exchange sweep over neighbouring pairs with the
+ *     detailed-balance acceptance min(1, exp((beta_p - beta_{p+1})(E_p - E_{p+1})));
+ *     a sweep is a full-lattice Metropolis sweep (Sec. III.B, EMCS definition);
+ *   - the hardness figure of merit "time to solution" (Sec. II) in the form
+ *     used here: the lower median over independent PT runs of the first sweep
+ *     at which a run reaches the target energy;
+ *   - one step of random adaptive optimisation (Algorithm 1): perturb one
+ *     coupler, re-measure TTS, keep the change if TTS increased, otherwise keep
+ *     it with probability exp(-beta_RAO |dTTS|) (greedy when beta_RAO = inf).
+ *
+ * Readings where the paper is silent (all fixed identically on both sides):
+ *   - spin index i = 8*(r*L + c) + 4*u + k (u = 0 vertical, u = 1 horizontal);
+ *     edge order: intra-cell (cell-major, k, k'), then vertical inter-cell
+ *     (r, c, k), then horizontal inter-cell (r, c, k);
+ *   - sweep = colour 0 spins then colour 1 spins, colour (r + c + u) mod 2
+ *     (the two sides of the bipartite graph), each colour in index order;
+ *   - Metropolis on the integer k = -s_i h_i (dE = 2k): accept if k <= 0,
+ *     else if u < thr[slot][k] with thr = floor(exp(-2 k beta) 2^32) built in
+ *     FP64 (acceptance exact to 2^-32);
+ *   - exchange after every `exchange_every`-th sweep, pairs p = 0..N_T-2 in
+ *     ascending order (chained swaps allowed); energies of one instance differ
+ *     by even numbers, d = E_{p+1} - E_p = 2h: accept if h <= 0, else if
+ *     h <= H_p and u < xthr[p][h] = floor(exp(-2 h (beta_p - beta_{p+1})) 2^32);
+ *     configurations are swapped whole (this oracle keeps no permutation);
+ *   - random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11),
+ *     key = (seed, uid), counter (sweep, run<<16 | slot, group, kind) with
+ *     kind 0 Metropolis (group = i>>2, word i&3), 1 exchange (group = p>>2,
+ *     word p&3, slot field 0), 2 initial spins (sweep 0; s = -1 if the word's
+ *     top bit is set), 3 engineering draws (counter (step, proposal, 0, 3)).
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+#define OR_KMAX 18           /* max |h_i| = 6 neighbours x |J| <= 3 */
+#define OR_HMAX (1 << 22)    /* cap on the exchange table length per pair */
+
+/* ------------------------------------------------------------------ */
+/* Philox4x32-10, written from its published definition (SC'11).       */
+/* ------------------------------------------------------------------ */
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {                 /* Weyl key schedule between rounds */
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static uint32_t draw(uint32_t seed, uint32_t uid, uint32_t c0, uint32_t c1,
+                     uint32_t c2, uint32_t c3, int word)
+{
+    uint32_t ctr[4] = {c0, c1, c2, c3}, key[2] = {seed, uid}, out[4];
+    or_philox4x32_10(ctr, key, out);
+    return out[word];
+}
+
+/* ------------------------------------------------------------------ */
+/* Chimera graph (Appendix A, Fig. 8).                                 */
+/* ------------------------------------------------------------------ */
+static int spin_index(int L, int r, int c, int u, int k) { return 8 * (r * L + c) + 4 * u + k; }
+
+int or_chimera_n_edges(int L) { return 16 * L * L + 8 * L * (L - 1); }
+
+/* Fills ei/ej (capacity or_chimera_n_edges(L)); returns the edge count. */
+int or_chimera_edges(int L, int32_t *ei, int32_t *ej)
+{
+    int e = 0;
+    for (int r = 0; r < L; ++r)                       /* intra-cell K_{4,4} */
+        for (int c = 0; c < L; ++c)
+            for (int k = 0; k < 4; ++k)
+                for (int kp = 0; kp < 4; ++kp) {
+                    ei[e] = spin_index(L, r, c, 0, k);
+                    ej[e] = spin_index(L, r, c, 1, kp);
+                    ++e;
+                }
+    for (int r = 0; r + 1 < L; ++r)                   /* vertical: (r,c,0,k)-(r+1,c,0,k) */
+        for (int c = 0; c < L; ++c)
+            for (int k = 0; k < 4; ++k) {
+                ei[e] = spin_index(L, r, c, 0, k);
+                ej[e] = spin_index(L, r + 1, c, 0, k);
+                ++e;
+            }
+    for (int r = 0; r < L; ++r)                       /* horizontal: (r,c,1,k)-(r,c+1,1,k) */
+        for (int c = 0; c + 1 < L; ++c)
+            for (int k = 0; k < 4; ++k) {
+                ei[e] = spin_index(L, r, c, 1, k);
+                ej[e] = spin_index(L, r, c + 1, 1, k);
+                ++e;
+            }
+    return e;
+}
+
+int or_spin_colour(int L, int i)
+{
+    int cell = i >> 3, r = cell / L, c = cell % L, u = (i >> 2) & 1;
+    return (r + c + u) & 1;
+}
+
+/* Eq. 1: H = sum over couplers of J_e s_i s_j. */
+int32_t or_energy(int L, const int8_t *J, const int8_t *s)
+{
+    int E = or_chimera_n_edges(L);
+    int32_t *ei = malloc(sizeof(int32_t) * E), *ej = malloc(sizeof(int32_t) * E);
+    or_chimera_edges(L, ei, ej);
+    int64_t H = 0;
+    for (int e = 0; e < E; ++e) H += (int64_t)J[e] * s[ei[e]] * s[ej[e]];
+    free(ei); free(ej);
+    return (int32_t)H;
+}
+
+/* Neighbour lists: for spin i, up to 6 (neighbour, J) pairs. */
+typedef struct { int n; int32_t nb[6]; int8_t Jn[6]; } nbr_list;
+
+static nbr_list *build_neighbours(int L, const int8_t *J)
+{
+    int N = 8 * L * L, E = or_chimera_n_edges(L);
+    int32_t *ei = malloc(sizeof(int32_t) * E), *ej = malloc(sizeof(int32_t) * E);
+    or_chimera_edges(L, ei, ej);
+    nbr_list *nl = calloc((size_t)N, sizeof(nbr_list));
+    for (int e = 0; e < E; ++e) {
+        nbr_list *a = &nl[ei[e]], *b = &nl[ej[e]];
+        a->nb[a->n] = ej[e]; a->Jn[a->n] = J[e]; a->n++;
+        b->nb[b->n] = ei[e]; b->Jn[b->n] = J[e]; b->n++;
+    }
+    free(ei); free(ej);
+    return nl;
+}
+
+/* ------------------------------------------------------------------ */
+/* Acceptance tables, FP64 on the host.                                */
+/* ------------------------------------------------------------------ */
+static uint32_t prob_to_u32(double p)
+{
+    double x = floor(ldexp(p, 32));
+    if (x >= 4294967295.0) return 0xFFFFFFFFu;
+    if (x <= 0.0) return 0u;
+    return (uint32_t)x;
+}
+
+/* thr[t*(OR_KMAX+1) + k] = floor(exp(-2 k beta_t) 2^32) for k = 1..OR_KMAX; entry 0 unused (0). */
+void or_metropolis_thresholds(int n_temps, const double *betas, uint32_t *thr)
+{
+    for (int t = 0; t < n_temps; ++t) {
+        thr[t * (OR_KMAX + 1)] = 0;
+        for (int k = 1; k <= OR_KMAX; ++k)
+            thr[t * (OR_KMAX + 1) + k] = prob_to_u32(exp(-2.0 * (double)k * betas[t]));
+    }
+}
+
+/* Length H_p of pair p's exchange table: the largest h with a nonzero entry. */
+static int exchange_len(double dbeta)
+{
+    int h = 0;
+    while (h < OR_HMAX && prob_to_u32(exp(-2.0 * (double)(h + 1) * dbeta)) != 0) ++h;
+    return h;
+}
+
+/* Ragged exchange tables: pair p owns entries off[p] .. off[p+1]-1 for h = 1..H_p.
+ * Returns the total length (needs off of n_temps entries).  table may be NULL
+ * to query the size.  Returns -1 if the ladder is not strictly descending. */
+int64_t or_exchange_thresholds(int n_temps, const double *betas, int64_t *off, uint32_t *table)
+{
+    int64_t total = 0;
+    for (int p = 0; p + 1 < n_temps; ++p) {
+        double dbeta = betas[p] - betas[p + 1];
+        if (!(dbeta > 0.0)) return -1;
+        int H = exchange_len(dbeta);
+        if (off) off[p] = total;
+        if (table)
+            for (int h = 1; h <= H; ++h)
+                table[total + h - 1] = prob_to_u32(exp(-2.0 * (double)h * dbeta));
+        total += H;
+    }
+    if (off && n_temps > 0) off[n_temps - 1] = total;
+    return total;
+}
+
+/* ------------------------------------------------------------------ */
+/* Parallel tempering.                                                  */
+/* State arrays (slot order; configurations are swapped physically):   */
+/*   spins[(run*NT + slot)*N + i], E[run*NT + slot],                    */
+/*   best[run], first[run], macc[run*NT + slot] (accepted flips),       */
+/*   xacc[run*(NT-1) + p] (accepted exchanges of pair p).              */
+/* ------------------------------------------------------------------ */
+void or_pt_init_spins(int L, int n_temps, int n_runs, uint32_t seed, uint32_t uid, int8_t *spins)
+{
+    int N = 8 * L * L;
+    for (int run = 0; run < n_runs; ++run)
+        for (int t = 0; t < n_temps; ++t)
+            for (int i = 0; i < N; ++i) {
+                uint32_t w = draw(seed, uid, 0u, ((uint32_t)run << 16) | (uint32_t)t,
+                                  (uint32_t)(i >> 2), 2u, i & 3);
+                spins[((size_t)run * n_temps + t) * N + i] = (w >> 31) ? -1 : 1;
+            }
+}
+
+/* Full energies; best = min over slots of each run, first = 0. */
+void or_pt_start(int L, const int8_t *J, int n_temps, int n_runs, const int8_t *spins,
+                 int32_t *E, int32_t *best, int32_t *first)
+{
+    int N = 8 * L * L;
+    for (int run = 0; run < n_runs; ++run) {
+        int32_t m = INT32_MAX;
+        for (int t = 0; t < n_temps; ++t) {
+            int32_t e = or_energy(L, J, spins + ((size_t)run * n_temps + t) * N);
+            E[run * n_temps + t] = e;
+            if (e < m) m = e;
+        }
+        best[run] = m;
+        first[run] = 0;
+    }
+}
+
+typedef struct {
+    int L, N, NT, R;
+    uint32_t seed, uid;
+    nbr_list *nl;
+    uint32_t *thr;
+    int64_t *xoff;
+    uint32_t *xthr;
+} pt_ctx;
+
+static int ctx_open(pt_ctx *cx, int L, const int8_t *J, int n_temps, const double *betas,
+                    int n_runs, uint32_t seed, uint32_t uid)
+{
+    cx->L = L; cx->N = 8 * L * L; cx->NT = n_temps; cx->R = n_runs;
+    cx->seed = seed; cx->uid = uid;
+    cx->nl = build_neighbours(L, J);
+    cx->thr = malloc(sizeof(uint32_t) * (size_t)n_temps * (OR_KMAX + 1));
+    or_metropolis_thresholds(n_temps, betas, cx->thr);
+    cx->xoff = malloc(sizeof(int64_t) * (size_t)(n_temps > 0 ? n_temps : 1));
+    int64_t tot = or_exchange_thresholds(n_temps, betas, NULL, NULL);
+    if (tot < 0) return -1;
+    cx->xthr = malloc(sizeof(uint32_t) * (size_t)(tot > 0 ? tot : 1));
+    or_exchange_thresholds(n_temps, betas, cx->xoff, cx->xthr);
+    return 0;
+}
+
+static void ctx_close(pt_ctx *cx)
+{
+    free(cx->nl); free(cx->thr); free(cx->xoff); free(cx->xthr);
+}
+
+/* One full-lattice Metropolis sweep of one copy (colour 0 then colour 1). */
+static void metropolis_sweep(const pt_ctx *cx, int run, int slot, uint32_t sweep,
+                             int8_t *s, int32_t *E, uint64_t *macc)
+{
+    const uint32_t *thr = cx->thr + (size_t)slot * (OR_KMAX + 1);
+    for (int colour = 0; colour < 2; ++colour)
+        for (int i = 0; i < cx->N; ++i) {
+            if (or_spin_colour(cx->L, i) != colour) continue;
+            const nbr_list *nb = &cx->nl[i];
+            int h = 0;
+            for (int a = 0; a < nb->n; ++a) h += nb->Jn[a] * s[nb->nb[a]];
+            int k = -s[i] * h;                         /* dE = 2k */
+            uint32_t u = draw(cx->seed, cx->uid, sweep,
+                              ((uint32_t)run << 16) | (uint32_t)slot,
+                              (uint32_t)(i >> 2), 0u, i & 3);
+            int accept = (k <= 0) || (u < thr[k]);
+            if (accept) {
+                s[i] = (int8_t)-s[i];
+                *E += 2 * k;
+                *macc += 1;
+            }
+        }
+}
+
+/* One exchange sweep of one run: pairs p = 0..NT-2 in ascending order. */
+static void exchange_pass(const pt_ctx *cx, int run, uint32_t sweep, int8_t *spins_run,
+                          int32_t *E_run, uint64_t *xacc_run)
+{
+    int N = cx->N;
+    int8_t *tmp = malloc((size_t)N);
+    for (int p = 0; p + 1 < cx->NT; ++p) {
+        int32_t d = E_run[p + 1] - E_run[p];          /* always even */
+        int32_t h = d / 2;
+        uint32_t u = draw(cx->seed, cx->uid, sweep, (uint32_t)run << 16,
+                          (uint32_t)(p >> 2), 1u, p & 3);
+        int accept;
+        if (h <= 0) accept = 1;
+        else {
+            int64_t H = cx->xoff[p + 1] - cx->xoff[p];
+            accept = (h <= H) && (u < cx->xthr[cx->xoff[p] + h - 1]);
+        }
+        if (accept) {
+            memcpy(tmp, spins_run + (size_t)p * N, (size_t)N);
+            memcpy(spins_run + (size_t)p * N, spins_run + (size_t)(p + 1) * N, (size_t)N);
+            memcpy(spins_run + (size_t)(p + 1) * N, tmp, (size_t)N);
+            int32_t e = E_run[p]; E_run[p] = E_run[p + 1]; E_run[p + 1] = e;
+            xacc_run[p] += 1;
+        }
+    }
+    free(tmp);
+}
+
+/* Runs sweeps sweep0+1 .. sweep0+n_sweeps in place.  After each sweep s the
+ * per-run best energy / first sweep are updated, then, if exchange_every > 0
+ * and s % exchange_every == 0, one exchange sweep with counter sweep = s. */
+int or_pt_sweeps(int L, const int8_t *J, int n_temps, const double *betas, int n_runs,
+                 uint32_t seed, uint32_t uid, int8_t *spins, int32_t *E, int32_t *best,
+                 int32_t *first, uint64_t *macc, uint64_t *xacc, uint32_t sweep0,
+                 int n_sweeps, int exchange_every)
+{
+    pt_ctx cx;
+    if (ctx_open(&cx, L, J, n_temps, betas, n_runs, seed, uid) != 0) { ctx_close(&cx); return -1; }
+    int N = cx.N;
+    for (int run = 0; run < n_runs; ++run) {
+        int8_t *sr = spins + (size_t)run * n_temps * N;
+        int32_t *Er = E + (size_t)run * n_temps;
+        for (int step = 1; step <= n_sweeps; ++step) {
+            uint32_t s = sweep0 + (uint32_t)step;
+            for (int t = 0; t < n_temps; ++t)
+                metropolis_sweep(&cx, run, t, s, sr + (size_t)t * N, &Er[t],
+                                 &macc[(size_t)run * n_temps + t]);
+            int32_t m = INT32_MAX;
+            for (int t = 0; t < n_temps; ++t) if (Er[t] < m) m = Er[t];
+            if (m < best[run]) { best[run] = m; first[run] = (int32_t)s; }
+            if (exchange_every > 0 && s % (uint32_t)exchange_every == 0)
+                exchange_pass(&cx, run, s, sr, Er, xacc + (size_t)run * (n_temps > 1 ? n_temps - 1 : 0));
+        }
+    }
+    ctx_close(&cx);
+    return 0;
+}
+
+/* One standalone exchange sweep of every run with counter sweep = `sweep`. */
+int or_pt_exchange(int L, const int8_t *J, int n_temps, const double *betas, int n_runs,
+                   uint32_t seed, uint32_t uid, int8_t *spins, int32_t *E, uint64_t *xacc,
+                   uint32_t sweep)
+{
+    pt_ctx cx;
+    if (ctx_open(&cx, L, J, n_temps, betas, n_runs, seed, uid) != 0) { ctx_close(&cx); return -1; }
+    for (int run = 0; run < n_runs; ++run)
+        exchange_pass(&cx, run, sweep, spins + (size_t)run * n_temps * cx.N,
+                      E + (size_t)run * n_temps, xacc + (size_t)run * (n_temps > 1 ? n_temps - 1 : 0));
+    ctx_close(&cx);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Time to solution.                                                    */
+/* target == INT32_MAX means "the best energy any run found".           */
+/* Run r hits if best[r] <= target and first[r] <= horizon; the TTS is  */
+/* the ceil(R/2)-th smallest hit time (lower median), misses counting   */
+/* as +inf; if that is +inf the instance is unsolved, TTS = horizon+1.  */
+/* ------------------------------------------------------------------ */
+void or_tts(int n_runs, const int32_t *best, const int32_t *first, int32_t target,
+            int32_t horizon, int32_t *tts, int32_t *n_hit, int32_t *target_used)
+{
+    if (target == INT32_MAX) {
+        target = INT32_MAX;
+        for (int r = 0; r < n_runs; ++r) if (best[r] < target) target = best[r];
+    }
+    int64_t *v = malloc(sizeof(int64_t) * (size_t)(n_runs > 0 ? n_runs : 1));
+    int hits = 0;
+    const int64_t INF = INT64_MAX;
+    for (int r = 0; r < n_runs; ++r) {
+        int hit = best[r] <= target && first[r] <= horizon;
+        v[r] = hit ? first[r] : INF;
+        hits += hit;
+    }
+    /* insertion sort: plain and obviously correct */
+    for (int a = 1; a < n_runs; ++a) {
+        int64_t x = v[a]; int b = a - 1;
+        while (b >= 0 && v[b] > x) { v[b + 1] = v[b]; --b; }
+        v[b + 1] = x;
+    }
+    int m = (n_runs + 1) / 2;                 /* ceil(R/2), 1-based rank */
+    int64_t med = n_runs > 0 ? v[m - 1] : INF;
+    *tts = (med == INF) ? horizon + 1 : (int32_t)med;
+    *n_hit = hits;
+    *target_used = target;
+    free(v);
+}
+
+/* A full TTS evaluation of one instance: fresh runs keyed by (seed, uid),
+ * pass_mult*S sweeps, target = best energy of the pass, horizon S. */
+int or_tts_eval(int L, const int8_t *J, int n_temps, const double *betas, int n_runs,
+                uint32_t seed, uint32_t uid, int32_t S, int32_t pass_mult, int exchange_every,
+                int32_t *tts, int32_t *n_hit, int32_t *target)
+{
+    int N = 8 * L * L;
+    size_t nrep = (size_t)n_runs * n_temps;
+    int8_t *spins = malloc(nrep * N);
+    int32_t *E = malloc(sizeof(int32_t) * nrep);
+    int32_t *best = malloc(sizeof(int32_t) * n_runs), *first = malloc(sizeof(int32_t) * n_runs);
+    uint64_t *macc = calloc(nrep, sizeof(uint64_t));
+    uint64_t *xacc = calloc((size_t)n_runs * (n_temps > 1 ? n_temps - 1 : 1), sizeof(uint64_t));
+    or_pt_init_spins(L, n_temps, n_runs, seed, uid, spins);
+    or_pt_start(L, J, n_temps, n_runs, spins, E, best, first);
+    int rc = or_pt_sweeps(L, J, n_temps, betas, n_runs, seed, uid, spins, E, best, first,
+                          macc, xacc, 0u, S * pass_mult, exchange_every);
+    if (rc == 0) or_tts(n_runs, best, first, INT32_MAX, S, tts, n_hit, target);
+    free(spins); free(E); free(best); free(first); free(macc); free(xacc);
+    return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* Random adaptive optimisation (Algorithm 1).                          */
+/* Proposal j of step t: one Philox call, key (seed, base_uid), counter */
+/* (t, j, 0, 3): word 0 picks the coupler e = floor(w0 E / 2^32), word  */
+/* 1 picks the new value among the five allowed values other than the   */
+/* current one (floor(w1 5 / 2^32) into the ascending list), word 2 is  */
+/* the candidate's PT key uid, word 3 the Boltzmann-acceptance uniform. */
+/* ------------------------------------------------------------------ */
+static const int8_t OR_JVALS[6] = {-3, -2, -1, 1, 2, 3};
+
+void or_engineer_draw(int L, const int8_t *J, uint32_t seed, uint32_t base_uid, uint32_t step,
+                      uint32_t proposal, int32_t *edge, int32_t *value, uint32_t *cand_uid,
+                      uint32_t *u_accept)
+{
+    uint32_t ctr[4] = {step, proposal, 0u, 3u}, key[2] = {seed, base_uid}, w[4];
+    or_philox4x32_10(ctr, key, w);
+    uint32_t E = (uint32_t)or_chimera_n_edges(L);
+    int e = (int)(((uint64_t)w[0] * E) >> 32);
+    int pick = (int)(((uint64_t)w[1] * 5u) >> 32);
+    int8_t allowed[5]; int na = 0;
+    for (int a = 0; a < 6; ++a) if (OR_JVALS[a] != J[e] && na < 5) allowed[na++] = OR_JVALS[a];
+    *edge = e;
+    *value = allowed[pick];
+    *cand_uid = w[2];
+    *u_accept = w[3];
+}
+
+/* Runs n_steps RAO steps t = step0 .. step0+n_steps-1 on J (in place).
+ * tts_cur: in = TTS of the current J (if < 0 it is measured with uid = base_uid);
+ * out = TTS of the final J.  beta_rao < 0 means greedy (beta = inf).
+ * direction +1 maximises TTS (hard instances), -1 minimises it (Sec. III.A).
+ * Per-step log arrays (length n_steps) may be NULL. */
+int or_engineer_run(int L, int8_t *J, int n_temps, const double *betas, int n_runs,
+                    uint32_t seed, uint32_t base_uid, int32_t S, int32_t pass_mult,
+                    int exchange_every, uint32_t step0, int n_steps, double beta_rao,
+                    int direction, int32_t *tts_cur,
+                    int32_t *log_edge, int32_t *log_old, int32_t *log_new,
+                    int32_t *log_tts, int32_t *log_accept)
+{
+    int32_t cur = *tts_cur, nh, tg;
+    if (cur < 0) {
+        int rc = or_tts_eval(L, J, n_temps, betas, n_runs, seed, base_uid, S, pass_mult,
+                             exchange_every, &cur, &nh, &tg);
+        if (rc) return rc;
+    }
+    for (int a = 0; a < n_steps; ++a) {
+        uint32_t t = step0 + (uint32_t)a;
+        int32_t e, v; uint32_t cuid, uacc;
+        or_engineer_draw(L, J, seed, base_uid, t, 0u, &e, &v, &cuid, &uacc);
+        int8_t old = J[e];
+        J[e] = (int8_t)v;
+        int32_t tn;
+        int rc = or_tts_eval(L, J, n_temps, betas, n_runs, seed, cuid, S, pass_mult,
+                             exchange_every, &tn, &nh, &tg);
+        if (rc) { J[e] = old; return rc; }
+        int64_t gain = (int64_t)direction * ((int64_t)tn - (int64_t)cur);
+        int accept = gain > 0;
+        if (!accept && beta_rao >= 0.0) {
+            double dt = fabs((double)tn - (double)cur);
+            accept = uacc < prob_to_u32(exp(-beta_rao * dt));
+        }
+        if (accept) cur = tn; else J[e] = old;
+        if (log_edge) log_edge[a] = e;
+        if (log_old) log_old[a] = old;
+        if (log_new) log_new[a] = v;
+        if (log_tts) log_tts[a] = tn;
+        if (log_accept) log_accept[a] = accept;
+    }
+    *tts_cur = cur;
+    return 0;
+}
+
+/* Exact ground-state energy by enumeration of the colour-0 spins: on the
+ * bipartite Chimera graph the colour-1 spins are then independent, each
+ * contributing -|h_i|.  Feasible while colour 0 has <= 24 spins (L <= 2). */
+int32_t or_ground_energy_bipartite(int L, const int8_t *J)
+{
+    int N = 8 * L * L;
+    nbr_list *nl = build_neighbours(L, J);
+    int idx0[64], n0 = 0;
+    for (int i = 0; i < N; ++i) if (or_spin_colour(L, i) == 0) idx0[n0++] = i;
+    int8_t *s = calloc((size_t)N, 1);
+    int32_t bestE = INT32_MAX;
+    for (uint64_t m = 0; m < (1ull << n0); ++m) {
+        for (int a = 0; a < n0; ++a) s[idx0[a]] = ((m >> a) & 1) ? -1 : 1;
+        int32_t e = 0;
+        for (int i = 0; i < N; ++i) {
+            if (or_spin_colour(L, i) != 1) continue;
+            int h = 0;
+            for (int a = 0; a < nl[i].n; ++a) h += nl[i].Jn[a] * s[nl[i].nb[a]];
+            e -= h < 0 ? -h : h;
+        }
+        if (e < bestE) bestE = e;
+    }
+    free(s); free(nl);
+    return bestE;
+}

@@ -1,0 +1,360 @@
+"""Pins of the CPU oracle against facts fixed outside it (no GPU needed).
+
+Each test checks the oracle against something other than itself: published
+known-answer vectors, closed forms, exhaustive enumeration, exact Boltzmann
+statistics, or an exact symmetry of Eq. 1.
+"""
+import itertools
+import math
+import os
+from decimal import Decimal, getcontext
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------
+# Philox4x32-10: published known-answer vectors (Salmon et al., SC'11).
+# --------------------------------------------------------------------------
+def test_philox_known_answers():
+    n = 0
+    for line in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        w = [int(x, 16) for x in line.split()]
+        out = oracle.philox4x32_10(w[0:4], w[4:6])
+        assert list(out) == w[6:10]
+        n += 1
+    assert n == 3
+
+
+# --------------------------------------------------------------------------
+# Chimera graph (Appendix A, Fig. 8): independent predicate-based adjacency.
+# --------------------------------------------------------------------------
+def _coords(L, i):
+    cell, rem = divmod(i, 8)
+    r, c = divmod(cell, L)
+    u, k = divmod(rem, 4)
+    return r, c, u, k
+
+
+def _adjacent(L, i, j):
+    r1, c1, u1, k1 = _coords(L, i)
+    r2, c2, u2, k2 = _coords(L, j)
+    if (r1, c1) == (r2, c2):
+        return u1 != u2                                    # K_{4,4} inside a cell
+    if u1 == u2 == 0 and c1 == c2 and abs(r1 - r2) == 1 and k1 == k2:
+        return True                                        # vertical qubits couple along columns
+    if u1 == u2 == 1 and r1 == r2 and abs(c1 - c2) == 1 and k1 == k2:
+        return True                                        # horizontal qubits couple along rows
+    return False
+
+
+@pytest.mark.parametrize("L", [1, 2, 3, 4, 8])
+def test_chimera_edges_match_predicate(L):
+    ei, ej = oracle.chimera_edges(L)
+    assert len(ei) == W.chimera_n_edges(L) == 16 * L * L + 8 * L * (L - 1)
+    got = {(min(a, b), max(a, b)) for a, b in zip(ei, ej)}
+    assert len(got) == len(ei)                             # no duplicates
+    N = 8 * L * L
+    if L <= 4:
+        want = {(i, j) for i in range(N) for j in range(i + 1, N) if _adjacent(L, i, j)}
+        assert got == want
+    deg = np.bincount(np.concatenate([ei, ej]), minlength=N)
+    assert deg.max() == {1: 4, 2: 5}.get(L, 6)          # every spin of C_2 sits on the boundary
+    if L >= 3:                                             # interior cells: every spin has degree 6
+        for i in range(N):
+            r, c, u, k = _coords(L, i)
+            if 0 < r < L - 1 and 0 < c < L - 1:
+                assert deg[i] == 6
+
+
+@pytest.mark.parametrize("L", [1, 4, 8])
+def test_colouring_is_bipartition(L):
+    ei, ej = oracle.chimera_edges(L)
+    col = oracle.spin_colours(L)
+    assert np.all(col[ei] != col[ej])
+    for i in range(8 * L * L):                             # vertical (r+c)%2, horizontal (r+c+1)%2
+        r, c, u, k = _coords(L, i)
+        assert col[i] == ((r + c) % 2 if u == 0 else (r + c + 1) % 2)
+
+
+# --------------------------------------------------------------------------
+# Eq. 1 energy: dense matrix form, enumeration, symmetries.
+# --------------------------------------------------------------------------
+def _dense_J(L, J):
+    N = 8 * L * L
+    ei, ej = oracle.chimera_edges(L)
+    A = np.zeros((N, N), np.int64)
+    A[ei, ej] = J
+    A[ej, ei] = J
+    return A
+
+
+def test_energy_matches_quadratic_form():
+    rng = np.random.default_rng(3)
+    for L in (1, 2, 4):
+        J = W.random_couplers(L, 11, L)
+        A = _dense_J(L, J)
+        for _ in range(20):
+            s = np.where(rng.integers(0, 2, 8 * L * L) == 0, -1, 1).astype(np.int8)
+            assert oracle.energy(L, J, s) == int(s.astype(np.int64) @ A @ s) // 2
+            assert oracle.energy(L, J, s) == oracle.energy(L, J, -s)   # global flip
+
+
+def test_ground_state_enumeration_single_cell():
+    for uid in range(5):
+        J = W.random_couplers(1, 5, uid)
+        states = np.array(list(itertools.product([-1, 1], repeat=8)), np.int8)
+        E = [oracle.energy(1, J, s) for s in states]
+        assert min(E) == oracle.ground_energy_bipartite(1, J)
+
+
+def test_gauge_maps_energy():
+    L = 4
+    rng = np.random.default_rng(7)
+    J = W.random_couplers(L, 2, 0)
+    ei, ej = oracle.chimera_edges(L)
+    g = np.where(rng.integers(0, 2, 8 * L * L) == 0, -1, 1).astype(np.int8)
+    Jg = (g[ei] * g[ej] * J).astype(np.int8)
+    for _ in range(10):
+        s = np.where(rng.integers(0, 2, 8 * L * L) == 0, -1, 1).astype(np.int8)
+        assert oracle.energy(L, Jg, g * s) == oracle.energy(L, J, s)
+
+
+# --------------------------------------------------------------------------
+# Acceptance tables: exact values at high precision.
+# --------------------------------------------------------------------------
+def _exact_u32(x_exponent: Decimal) -> tuple[int, Decimal]:
+    v = (x_exponent.exp()) * (Decimal(2) ** 32)
+    return int(v), v - int(v)
+
+
+def test_metropolis_thresholds_exact():
+    getcontext().prec = 60
+    betas = W.beta_ladder(48, 0.05, 5.0)
+    thr = oracle.metropolis_thresholds(betas)
+    assert thr.shape == (48, 19)
+    for t, b in enumerate(betas):
+        for k in range(1, 19):
+            want, frac = _exact_u32(-2 * k * Decimal(float(b)))
+            if Decimal("1e-6") < frac < 1 - Decimal("1e-6"):
+                assert int(thr[t, k]) == want, (t, k)
+        assert np.all(np.diff(thr[t, 1:].astype(np.int64)) <= 0)
+
+
+def test_exchange_thresholds_exact():
+    getcontext().prec = 60
+    betas = W.beta_ladder(16, 0.1, 3.0)
+    off, table = oracle.exchange_thresholds(betas)
+    for p in range(15):
+        db = float(betas[p]) - float(betas[p + 1])
+        seg = table[off[p]:off[p + 1]]
+        H = len(seg)
+        # H_p is the last h whose floor(exp(-2 h db) 2^32) is nonzero
+        assert 2 * H * db <= 32 * math.log(2) + 1e-9 < 2 * (H + 1) * db + 1e-9
+        assert np.all(seg > 0) and np.all(np.diff(seg.astype(np.int64)) <= 0)
+        for h in (1, 2, H // 2 + 1, H):
+            want, frac = _exact_u32(-2 * h * Decimal(db))
+            if Decimal("1e-6") < frac < 1 - Decimal("1e-6"):
+                assert int(seg[h - 1]) == want
+    with pytest.raises(ValueError):
+        oracle.exchange_thresholds(np.array([1.0, 1.0]))
+
+
+# --------------------------------------------------------------------------
+# Monte Carlo: incremental energy, exact Boltzmann statistics, gauge, GS.
+# --------------------------------------------------------------------------
+def test_incremental_energy_equals_recompute():
+    L = 4
+    J = W.random_couplers(L, 9, 1)
+    st = oracle.PTState(L, J, W.beta_ladder(8, 0.1, 3.0), 3, seed=9, uid=1)
+    assert np.array_equal(st.E, st.full_energies())
+    for _ in range(5):
+        st.sweeps(37, exchange_every=1)
+        assert np.array_equal(st.E, st.full_energies())
+    assert st.macc.sum() > 0 and st.xacc.sum() > 0
+    assert np.all(st.best <= st.E.min(axis=1))
+
+
+def _boltzmann(L, J, beta):
+    states = np.array(list(itertools.product([-1, 1], repeat=8 * L * L)), np.int8)
+    E = np.array([oracle.energy(L, J, s) for s in states], np.float64)
+    w = np.exp(-beta * (E - E.min()))
+    return states, E, w / w.sum()
+
+
+def _state_index(spins):
+    bits = (spins < 0).astype(np.int64)          # state order of itertools.product([-1, 1])
+    return bits @ (1 << np.arange(bits.shape[-1] - 1, -1, -1))
+
+
+def test_single_temperature_boltzmann_histogram():
+    """A single K_{4,4} cell at one beta: the chain samples exp(-beta E)/Z."""
+    L, beta, R = 1, 0.35, 64
+    J = W.random_couplers(L, 21, 0)
+    _, _, p = _boltzmann(L, J, beta)
+    st = oracle.PTState(L, J, np.array([beta]), R, seed=21, uid=3)
+    counts = np.zeros(256)
+    for _ in range(3000):
+        st.sweeps(1, exchange_every=0)
+        np.add.at(counts, _state_index(st.spins[:, 0, :]), 1)
+    n = counts.sum()
+    chi2 = np.sum((counts - n * p) ** 2 / (n * p))
+    assert chi2 / 255 < 3.0, chi2 / 255
+    # a halved acceptance exponent (a plausible slip) is rejected by the same test
+    _, _, p_wrong = _boltzmann(L, J, beta / 2)
+    chi2_wrong = np.sum((counts - n * p_wrong) ** 2 / (n * p_wrong))
+    assert chi2_wrong / 255 > 10 * max(chi2 / 255, 1.0)
+
+
+def test_two_temperature_exchange_boltzmann():
+    """PT with two slots: each slot must sample the Boltzmann law of its own beta
+    (Sec. II: swaps obey detailed balance).  beta_0 is cold enough that it mixes
+    only through exchanges with the hot slot."""
+    L, R = 1, 64
+    betas = np.array([1.1, 0.25])
+    J = W.random_couplers(L, 31, 0)
+    _, Es, p0 = _boltzmann(L, J, betas[0])
+    _, _, p1 = _boltzmann(L, J, betas[1])
+    st = oracle.PTState(L, J, betas, R, seed=31, uid=5)
+    c0 = np.zeros(256)
+    c1 = np.zeros(256)
+    for _ in range(3000):
+        st.sweeps(1, exchange_every=1)
+        np.add.at(c0, _state_index(st.spins[:, 0, :]), 1)
+        np.add.at(c1, _state_index(st.spins[:, 1, :]), 1)
+    assert np.array_equal(st.E, st.full_energies())
+    for c, p in ((c0, p0), (c1, p1)):
+        n = c.sum()
+        # compare energy-level distributions (robust at the cold slot)
+        levels = np.unique(Es)
+        obs = np.array([c[Es == e].sum() for e in levels]) / n
+        exp_ = np.array([p[Es == e].sum() for e in levels])
+        keep = exp_ > 1e-3
+        assert np.max(np.abs(obs[keep] - exp_[keep])) < 0.02
+    assert st.xacc.sum() > 0
+
+
+def test_gauge_invariance_maps_trajectory():
+    """J_ij -> g_i g_j J_ij with s -> g s maps every dE, acceptance and energy exactly."""
+    L, R = 4, 3
+    betas = W.beta_ladder(6, 0.2, 2.5)
+    J = W.random_couplers(L, 41, 0)
+    ei, ej = oracle.chimera_edges(L)
+    colours = oracle.spin_colours(L)
+    for g in (np.where(np.random.default_rng(1).integers(0, 2, 8 * L * L) == 0, -1, 1),
+              np.where(colours == 0, 1, -1),              # bipartition gauge: J -> -J
+              -np.ones(8 * L * L, np.int64)):             # global flip
+        g = g.astype(np.int8)
+        Jg = (g[ei] * g[ej] * J).astype(np.int8)
+        a = oracle.PTState(L, J, betas, R, seed=41, uid=2)
+        b = oracle.PTState(L, Jg, betas, R, seed=41, uid=2, spins=a.spins * g)
+        for _ in range(3):
+            a.sweeps(50, exchange_every=1)
+            b.sweeps(50, exchange_every=1)
+            assert np.array_equal(b.spins, a.spins * g)
+            assert np.array_equal(a.E, b.E)
+            assert np.array_equal(a.best, b.best) and np.array_equal(a.first, b.first)
+            assert np.array_equal(a.macc, b.macc) and np.array_equal(a.xacc, b.xacc)
+        if np.all(g == np.where(colours == 0, 1, -1)):
+            assert np.array_equal(Jg, -J)
+
+
+def test_pt_finds_exact_ground_state_two_by_two():
+    L = 2
+    for uid in range(3):
+        J = W.random_couplers(L, 51, uid)
+        gs = oracle.ground_energy_bipartite(L, J)
+        st = oracle.PTState(L, J, W.beta_ladder(8, 0.1, 3.0), 8, seed=51, uid=uid)
+        st.sweeps(2000, exchange_every=1)
+        assert np.all(st.best == gs)
+        assert np.all(st.best >= gs) and np.all(st.E >= gs)
+
+
+def test_exchange_standalone_matches_fused():
+    L = 4
+    J = W.random_couplers(L, 61, 0)
+    betas = W.beta_ladder(10, 0.1, 3.0)
+    a = oracle.PTState(L, J, betas, 2, seed=61, uid=0)
+    b = oracle.PTState(L, J, betas, 2, seed=61, uid=0)
+    for _ in range(20):
+        a.sweeps(1, exchange_every=1)
+        b.sweeps(1, exchange_every=0)
+        b.exchange()
+    assert np.array_equal(a.spins, b.spins) and np.array_equal(a.xacc, b.xacc)
+
+
+# --------------------------------------------------------------------------
+# TTS: hand-constructed arrays.
+# --------------------------------------------------------------------------
+def test_tts_lower_median_closed_form():
+    best = np.array([-10, -10, -10, -8, -10, -9, -10, -10], np.int32)
+    first = np.array([50, 7, 900, 3, 20, 4, 100, 60], np.int32)
+    # target = -10: hits at 50, 7, 900, 20, 100, 60 -> sorted 7,20,50,60,100,900,inf,inf; 4th = 60
+    assert oracle.tts(best, first, oracle.TARGET_BEST, 1000) == (60, 6, -10)
+    # horizon 55 drops 900,100,60 -> 7,20,50,inf.. ; 4th is inf -> unsolved = 56
+    assert oracle.tts(best, first, oracle.TARGET_BEST, 55) == (56, 3, -10)
+    # explicit looser target -9 also counts the run that found -9
+    assert oracle.tts(best, first, -9, 1000) == (50, 7, -9)
+    # odd R: ceil(3/2) = 2nd smallest
+    assert oracle.tts(np.array([-2, -2, -2], np.int32), np.array([5, 1, 9], np.int32)) [0] == 5
+    # R = 1
+    assert oracle.tts(np.array([-4], np.int32), np.array([0], np.int32), oracle.TARGET_BEST, 10) == (0, 1, -4)
+
+
+def test_tts_eval_is_prefix_of_longer_pass():
+    """The 4x-pass reading: first[] of a run is a prefix property of its trajectory."""
+    L = 4
+    J = W.random_couplers(L, 71, 0)
+    betas = W.beta_ladder(8, 0.1, 3.0)
+    t4 = oracle.tts_eval(L, J, betas, 6, 71, 9, 256, 4, 1)
+    st = oracle.PTState(L, J, betas, 6, seed=71, uid=9)
+    st.sweeps(1024, 1)
+    assert t4 == oracle.tts(st.best, st.first, oracle.TARGET_BEST, 256)
+
+
+# --------------------------------------------------------------------------
+# RAO (Algorithm 1).
+# --------------------------------------------------------------------------
+def test_engineer_draw_rules():
+    L = 4
+    J = W.random_couplers(L, 81, 0)
+    seen_edges = set()
+    for t in range(400):
+        e, v, cu, ua = oracle.engineer_draw(L, J, 81, 0, t)
+        assert 0 <= e < len(J) and v != J[e] and v in (-3, -2, -1, 1, 2, 3)
+        seen_edges.add(e)
+    assert len(seen_edges) > 200
+    assert oracle.engineer_draw(L, J, 81, 0, 5) == oracle.engineer_draw(L, J, 81, 0, 5)
+
+
+def test_engineer_run_replay_and_monotone():
+    L = 4
+    cfg = W.CONFIGS["c4_tiny"]
+    J0 = W.random_couplers(L, cfg["seed"], 0)
+    betas = W.beta_ladder(8, 0.1, 3.0)
+    args = (L, J0, betas, 4, cfg["seed"], 0, 256, 1, 1, 1, 12)
+    Ja, ta, la = oracle.engineer_run(*args)
+    Jb, tb, lb = oracle.engineer_run(*args)
+    assert ta == tb and np.array_equal(Ja, Jb)
+    assert all(np.array_equal(la[k], lb[k]) for k in la)
+    t0 = oracle.tts_eval(L, J0, betas, 4, cfg["seed"], 0, 256, 1, 1)[0]
+    cur = t0
+    J = J0.copy()
+    for a in range(12):
+        if la["accept"][a]:
+            assert la["tts"][a] > cur                       # greedy: strictly harder
+            cur = la["tts"][a]
+            J[la["edge"][a]] = la["new"][a]
+        assert la["old"][a] != la["new"][a]
+    assert cur == ta and np.array_equal(J, Ja) and ta >= t0
+    # split run (resume from the logged state) equals the straight run
+    J1, t1, _ = oracle.engineer_run(L, J0, betas, 4, cfg["seed"], 0, 256, 1, 1, 1, 5)
+    J2, t2, _ = oracle.engineer_run(L, J1, betas, 4, cfg["seed"], 0, 256, 1, 1, 6, 7, tts_cur=t1)
+    assert t2 == ta and np.array_equal(J2, Ja)
