@@ -1,0 +1,330 @@
+"""Benchmark: PT-TTS hardness evaluation inside the RAO loop on GB300.
+
+Workload (one instance per GPU): Chimera C_8 (N = 512, 1472 couplers), J
+uniform on {+-1, +-2, +-3}, 32 temperatures geometric in beta [0.1, 4], 64
+independent PT runs, TTS horizon S = 2^16 sweeps with the target taken from a
+4x longer pass of the same runs (2^18 sweeps per evaluation), exchange every
+sweep.  A step is one call of the engineering loop's public entry point
+engineer_run(t, K, K): K consecutive RAO steps (Algorithm 1), whose K candidate
+instances are PT-evaluated as one batched launch sequence (extra batches when a
+candidate is kept early).
+
+Reported: spin-flip attempts/s (value, device time), PT-TTS evaluations/s and
+RAO steps/s, the end-to-end number through the same C-ABI call, the roofline
+of the dominant kernel (pt_sweep_kernel, integer-issue bound), the CPU oracle
+on a bounded sample, and SM clocks sampled during the timed region.
+
+--impl reference times the CPU oracle (plain C, one thread) on a bounded
+sample of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "spin flips/s & PT-TTS evals/s; log-TTS gain per GPU-s, surrogate vs plain"
+UNIT = "spin-flip attempts/s"
+
+# Algorithmic integer operations per spin-flip attempt (counted from the
+# method, not from the compiled code):
+#   Philox4x32-10, 1/4 call per attempt: 10 rounds x (2 widening multiplies,
+#     2 three-input xors, 2 key-schedule adds) / 4            = 15
+#   local field over 6 neighbours: 6 multiply-adds            =  6
+#   k = -s_i h_i                                              =  1
+#   acceptance: clamp, table load, 2 compares, or             =  5
+#   flip, energy and accept-count updates                     =  3
+#   spin loads (4 words per 4 spins) and store (1 per 4)      =  1.25
+OPS_PER_ATTEMPT = 31.25
+# Integer issue peak per SM and clock: 4 sub-partitions x 32 lanes.
+INT_LANES_PER_SM_CLK = 128
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("gloo", rank=rank, world_size=ws)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, x):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(ws, x):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def workload():
+    cfg = W.CONFIGS["c8_single"]
+    return cfg
+
+
+def oracle_sample(cfg, sweeps, runs):
+    """CPU oracle on a bounded sample: `runs` runs x all slots x `sweeps` sweeps."""
+    import oracle
+    oracle.build()
+    J = W.random_couplers(cfg["L"], cfg["seed"], 0)
+    betas = W.beta_ladder(cfg["n_temps"], cfg["beta_min"], cfg["beta_max"])
+    st = oracle.PTState(cfg["L"], J, betas, runs, cfg["seed"], 0)
+    t0 = time.perf_counter()
+    st.sweeps(sweeps, cfg["exchange_every"])
+    dt = time.perf_counter() - t0
+    attempts = sweeps * runs * cfg["n_temps"] * 8 * cfg["L"] ** 2
+    return attempts / dt, attempts, dt
+
+
+def run_reference(args):
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    cfg = workload()
+    sweeps, runs = 32, cfg["n_runs"]
+    for _ in range(args.warmup):
+        oracle_sample(cfg, 4, runs)
+    tot_att, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        _, att, dt = oracle_sample(cfg, sweeps, runs)
+        tot_att += att
+        tot_t += dt
+    v = tot_att / tot_t
+    per_eval = cfg["sweeps"] * cfg["pass_mult"] * cfg["n_runs"] * cfg["n_temps"] * 8 * cfg["L"] ** 2
+    sample = f"{runs} runs x {cfg['n_temps']} slots x {sweeps} sweeps of the C_8 instance per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": "c8_single: C_8 N=512, 32 temps beta [0.1,4], 64 runs, S=2^16, 4x target pass",
+                   "sample": sample},
+        "pt_tts_evals_per_s": v / per_eval,
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu(args):
+    import torch
+
+    ws, rank, local = dist_setup()
+    import paper_1605_03607_gb300 as P
+    from paper_1605_03607_gb300 import build as B
+    B.build()
+    P.select_device(local)
+    torch.cuda.set_device(local)
+    cfg = workload()
+    L, NT, R, S, pm = cfg["L"], cfg["n_temps"], cfg["n_runs"], cfg["sweeps"], cfg["pass_mult"]
+    N = 8 * L * L
+    spec = args.speculation
+    uid = rank                                       # weak scaling: one instance per GPU
+    J = W.random_couplers(L, cfg["seed"], uid)
+    betas = W.beta_ladder(NT, cfg["beta_min"], cfg["beta_max"])
+    stream = torch.cuda.current_stream()
+    h = P.PTHandle(L, J, betas, R, cfg["seed"], uid, stream=stream.cuda_stream)
+    if args.schedule:
+        h.set_schedule(*[int(x) for x in args.schedule.split(",")])
+    h.set_timing(True)
+    h.engineer_begin(S=S, pass_mult=pm, exchange_every=cfg["exchange_every"], base_uid=uid)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")   # > 129 MB L2
+    step = 0
+    for _ in range(args.warmup):
+        h.engineer_run(step, spec, spec)
+        step += spec
+    h.eval_stats(reset=True)
+    h.set_timing(True)
+    n0 = h.launch_count()
+    sampler = ClockSampler(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    sampler.start()
+    dev_ms, wall_s = 0.0, 0.0
+    accepted = 0
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        e0.record(stream)
+        res = h.engineer_run(step, spec, spec)
+        e1.record(stream)
+        e1.synchronize()
+        wall_s += time.perf_counter() - w0
+        dev_ms += e0.elapsed_time(e1)
+        accepted += int(res["accepted"].sum())
+        step += spec
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = sampler.stop()
+    launches = h.launch_count() - n0
+    evals, batches, eval_ms = h.eval_stats()
+    sweep_ms, sweep_launches = h.sweep_timing_total()
+    attempts = evals * R * NT * N * S * pm
+    t_dev = max_over_ranks(ws, dev_ms / 1e3)
+    t_wall = max_over_ranks(ws, wall_s)
+    tot_attempts = sum_over_ranks(ws, attempts)
+    tot_evals = sum_over_ranks(ws, evals)
+    tot_steps = sum_over_ranks(ws, args.steps * spec)
+    peaks, peak_kind = load_peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peak_ops = sms * INT_LANES_PER_SM_CLK * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    achieved_ops = attempts * OPS_PER_ATTEMPT / (sweep_ms / 1e3) if sweep_ms > 0 else 0.0
+    # h2d per step: packed candidate couplers + instance descriptors; d2h: 3 ints per candidate
+    h2d = batches / max(args.steps, 1) * (spec * (L * L * 16 * 4) + spec * 128)
+    d2h = batches / max(args.steps, 1) * spec * 12
+    if rank != 0:
+        h.close()
+        return 0
+    cpu = None
+    if ws == 1 and not args.no_cpu:
+        v, att, dt = oracle_sample(cfg, args.cpu_sweeps, R)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{R} runs x {NT} slots x {args.cpu_sweeps} sweeps of the C_8 instance "
+                         f"({att:.3g} attempts, {dt:.1f} s, one thread)"}
+    line = {
+        "metric": METRIC, "value": tot_attempts / t_dev, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": "c8_single: C_8 N=512 (1472 couplers, J in {+-1,+-2,+-3}), 32 temps "
+                               "beta geometric [0.1,4], 64 PT runs, S=2^16, target from 4x pass, "
+                               "exchange every sweep",
+                   "step": f"engineer_run: {spec} RAO steps, candidates evaluated in batches of {spec}",
+                   "speculation": spec, "schedule": list(h.schedule()), "l2": "flushed between steps",
+                   "parallelism": f"{ws} independent instance(s), one per GPU"},
+        "pt_tts_evals_per_s": tot_evals / t_dev,
+        "rao_steps_per_s": tot_steps / t_dev,
+        "accepted_moves": accepted,
+        "e2e": {"value": tot_attempts / t_wall, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "pt_tts_evals_per_s": tot_evals / t_wall},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
+                     "unit": "Tops/s (int32 issue)", "frac": achieved_ops / peak_ops if peak_ops else None,
+                     "traffic": None, "kernel": "pt_sweep_kernel",
+                     "ops_per_attempt": OPS_PER_ATTEMPT,
+                     "avg_launch_ms": sweep_ms / max(sweep_launches, 1), "launches": sweep_launches,
+                     "peak_source": f"{sms} SMs x {INT_LANES_PER_SM_CLK} lanes x "
+                                    f"{peaks.get('sm_max_mhz', 2070.0)} MHz ({peak_kind} max clock)"},
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+    }
+    print(json.dumps(line))
+    h.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--speculation", type=int, default=8)
+    ap.add_argument("--schedule", default="", help="slot_parallel,runs_per_cta,sweeps_per_launch")
+    ap.add_argument("--cpu-sweeps", type=int, default=256)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gb300":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

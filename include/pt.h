@@ -1,0 +1,234 @@
+/*
+ * pt.h -- C ABI of the GB300 parallel-tempering hardness engine.
+ *
+ * Method: "Practical engineering of hard spin-glass instances" (Marshall,
+ * Martin-Mayor, Hen; arXiv:1605.03607).  An instance is a coupler vector J on
+ * the ideal Chimera graph C_L (Appendix A, Fig. 8: L x L unit cells of K_{4,4},
+ * N = 8 L^2 spins).  Its cost is the Ising energy H = sum_<ij> J_ij s_i s_j,
+ * minimised over s_i = +-1 (Eq. 1, no fields).  Its hardness is measured by
+ * parallel tempering (Sec. II: N_T copies at fixed temperatures, Metropolis
+ * updates, neighbour temperature swaps obeying detailed balance) as a time to
+ * solution in sweeps (Sec. II "TTS"), and the random adaptive optimisation
+ * loop (Algorithm 1) perturbs one coupler at a time and keeps a perturbation
+ * when the instance got harder.
+ *
+ * Conventions (all functions):
+ *   - Every function returns PT_OK (0) or a PT_ERR_* code; on error the handle
+ *     is unchanged unless stated, and pt_last_error() describes the failure.
+ *   - Handles are opaque.  The library owns all device memory it allocates.
+ *     Caller arrays are host pointers, read or written during the call only;
+ *     nothing is retained after a call returns.
+ *   - `stream` is a cudaStream_t (NULL: the library creates its own
+ *     non-blocking stream).  Calls that return results synchronise that stream
+ *     only, never the whole device.
+ *   - Spin index i = 8 (r L + c) + 4 u + k with cell row r, column c in [0, L),
+ *     u = 0 (vertical) / 1 (horizontal), k in [0, 4).  Coupler order: the 16
+ *     intra-cell couplers of each cell (cell-major, then k of the vertical
+ *     spin, then k of the horizontal spin), then the vertical inter-cell
+ *     couplers (r, c, 0, k)-(r+1, c, 0, k) ordered by (r, c, k), then the
+ *     horizontal ones (r, c, 1, k)-(r, c+1, 1, k) ordered by (r, c, k):
+ *     16 L^2 + 8 L (L - 1) couplers.  J values must lie in [-3, 3].
+ *   - Temperature slots t = 0 .. N_T-1 hold inverse temperatures beta_t,
+ *     strictly descending (slot 0 is the coldest).
+ *   - Random numbers are Philox4x32-10 (Salmon et al., SC'11) with key
+ *     (seed, uid) and counter (sweep, run << 16 | slot, group, kind): kind 0
+ *     Metropolis (group = i >> 2, word i & 3), 1 exchange (group = p >> 2,
+ *     word p & 3, slot field 0), 2 initial spins, 3 engineering draws.
+ */
+#ifndef GB300_PT_H
+#define GB300_PT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PT_OK 0
+#define PT_ERR_ARG 1      /* invalid argument (sizes, ranges, ladder order, NULL) */
+#define PT_ERR_CUDA 2     /* a CUDA runtime call failed; the handle should be destroyed */
+#define PT_ERR_TIMEOUT 3  /* a bounded device wait gave up */
+#define PT_ERR_OOM 4      /* device or host allocation failed */
+#define PT_ERR_STATE 5    /* call not valid in the handle's current state */
+
+#define PT_TARGET_BEST INT32_MAX   /* pt_tts target: the best energy any run found */
+#define PT_KMAX 18                 /* largest |local field| = 6 neighbours x |J| <= 3 */
+
+typedef struct pt_handle pt_handle;
+
+/* Message for the last failure on `h` (or of the last failed pt_create when
+ * h is NULL).  Static storage owned by the library; never NULL. */
+const char *pt_last_error(const pt_handle *h);
+
+/* Creates one instance with n_runs independent PT runs of n_temps slots
+ * (Sec. II).  J: n_edges int8 couplers in the order above (n_edges must equal
+ * 16 L^2 + 8 L (L - 1)); betas: n_temps doubles, strictly descending, > 0.
+ * Builds on the host, in FP64, the Metropolis table thr[t][k] =
+ * floor(exp(-2 k beta_t) 2^32) (k = 1..18) and the exchange tables
+ * xthr[p][h] = floor(exp(-2 h (beta_p - beta_{p+1})) 2^32) (h = 1..H_p, H_p
+ * the last nonzero entry), then draws the initial spins of every (run, slot)
+ * from the kind-2 stream of (seed, instance_uid).  Limits: 1 <= L <= 16,
+ * 1 <= n_temps <= 64, 1 <= n_runs <= 1024.  Errors: PT_ERR_ARG, PT_ERR_OOM,
+ * PT_ERR_CUDA (no handle is returned). */
+int pt_create(pt_handle **h, int32_t chimera_L, const int8_t *J, int32_t n_edges,
+              const double *betas, int32_t n_temps, int32_t n_runs, uint32_t seed,
+              uint32_t instance_uid, void *stream);
+
+/* Frees every device and host resource of h (NULL is ignored). */
+void pt_destroy(pt_handle *h);
+
+/* Fresh runs: redraws the initial spins from (seed, instance_uid), identity
+ * slot-to-configuration map, full energies, best = min over slots, first = 0,
+ * zero acceptance counters, sweep counter 0. */
+int pt_reset(pt_handle *h, uint32_t instance_uid);
+
+/* Replaces every configuration (host int8 +-1 array [n_runs][n_temps][N] in
+ * slot order), then proceeds as pt_reset without redrawing spins (the sweep
+ * counter is kept).  Used for gauge checks and resumption.  PT_ERR_ARG if a
+ * value is not +-1. */
+int pt_set_spins(pt_handle *h, const int8_t *spins);
+
+/* Performs sweeps s = sweep+1 .. sweep+n_sweeps.  Each sweep is a full-lattice
+ * checkerboard Metropolis sweep of every copy (colour (r + c + u) mod 2 = 0
+ * first; Sec. III.B "full-lattice Metropolis sweeps"), then the per-run best
+ * energy / first sweep update, then, when exchange_every > 0 and
+ * s % exchange_every == 0, one exchange sweep over pairs p = 0..N_T-2 in
+ * ascending order with acceptance min(1, exp((beta_p - beta_{p+1})
+ * (E_p - E_{p+1}))) (Sec. II, detailed balance).  0 <= n_sweeps <= 2^24. */
+int pt_sweep(pt_handle *h, int32_t n_sweeps, int32_t exchange_every);
+
+/* One standalone exchange sweep with counter sweep = the current sweep count
+ * (identical to the exchange pt_sweep performs after that sweep). */
+int pt_exchange(pt_handle *h);
+
+/* Copies the state to host arrays (any may be NULL):
+ *   spins [n_runs][n_temps][N] in slot order, E [n_runs][n_temps] slot order,
+ *   perm  [n_runs][n_temps]    configuration buffer held by each slot,
+ *   best, first [n_runs]       lowest energy seen and the sweep it was first seen,
+ *   macc  [n_runs][n_temps]    accepted Metropolis flips per slot,
+ *   xacc  [n_runs][n_temps-1]  accepted exchanges per pair,
+ *   sweep                      sweeps performed since the last reset. */
+int pt_get_state(pt_handle *h, int8_t *spins, int32_t *E, uint8_t *perm, int32_t *best,
+                 int32_t *first, uint64_t *macc, uint64_t *xacc, uint64_t *sweep);
+
+/* Time to solution from the current state (Sec. II "TTS"): target T =
+ * E_target, or the lowest best energy over runs when E_target ==
+ * PT_TARGET_BEST.  Run r hits when best[r] <= T and first[r] <= horizon; the
+ * TTS is the ceil(R/2)-th smallest hit sweep (misses count as +inf) or
+ * horizon + 1 ("unsolved") when fewer than ceil(R/2) runs hit.  The reduction
+ * runs on the device.  Outputs are host pointers (n_hit, target_used may be
+ * NULL). */
+int pt_tts(pt_handle *h, int32_t E_target, int32_t horizon, int32_t *tts, int32_t *n_hit,
+           int32_t *target_used);
+
+/* A full PT-TTS evaluation: pt_reset(uid), pass_mult * S sweeps with exchange
+ * every `exchange_every` sweeps, then pt_tts(PT_TARGET_BEST, horizon = S).
+ * With pass_mult = 4 the target is the best energy of a 4x longer pass of the
+ * same runs and only hits within the first S sweeps count. */
+int pt_tts_eval(pt_handle *h, uint32_t uid, int32_t S, int32_t pass_mult,
+                int32_t exchange_every, int32_t *tts, int32_t *n_hit, int32_t *target);
+
+/* Sets coupler `edge` to `value` (|value| <= 3), recomputes the energies of
+ * the current configurations and restarts the best/first record from them
+ * (best = min over slots, first = current sweep). */
+int pt_set_coupler(pt_handle *h, int32_t edge, int8_t value);
+
+/* Copies the current couplers (n_edges int8) to the host. */
+int pt_get_couplers(pt_handle *h, int8_t *J);
+
+/* Copies the host-built acceptance tables: thr [n_temps][PT_KMAX + 1] (entry
+ * k = 0 unused), xoff [n_temps] (pair p owns xthr[xoff[p] .. xoff[p+1]-1] for
+ * h = 1..H_p), xthr (capacity xthr_cap entries; may be NULL to query), and the
+ * total exchange-table length in *xthr_len. */
+int pt_get_tables(const pt_handle *h, uint32_t *thr, int64_t *xoff, uint32_t *xthr,
+                  int64_t xthr_cap, int64_t *xthr_len);
+
+/* Random adaptive optimisation (Algorithm 1). */
+typedef struct {
+    int32_t S;               /* TTS horizon in sweeps */
+    int32_t pass_mult;       /* target pass length = pass_mult * S */
+    int32_t exchange_every;  /* sweeps between exchange sweeps */
+    int32_t direction;       /* +1: maximise TTS (hard instances); -1: minimise (easy) */
+    double beta_rao;         /* < 0: greedy (keep only strict improvements); else
+                                also keep a worse move with prob. exp(-beta |dTTS|) */
+} pt_rule;
+
+typedef struct {
+    int32_t edge, old_value, new_value;
+    int32_t tts_old, tts_new, accepted;
+    uint32_t cand_uid;
+} pt_step_result;
+
+/* Starts a loop on the handle's current couplers: measures their TTS with
+ * uid = base_uid (pt_tts_eval) and stores rule, base_uid and that TTS. */
+int engineer_begin(pt_handle *h, const pt_rule *rule, uint32_t base_uid, int32_t *tts0);
+
+/* One RAO step t: draws a coupler e = floor(w0 E / 2^32) and a new value
+ * (floor(w1 5 / 2^32)-th of the five allowed values other than J_e, ascending)
+ * from Philox key (seed, base_uid), counter (t, 0, 0, 3); evaluates the
+ * candidate with uid = w2; keeps it if direction * (TTS' - TTS) > 0, or else
+ * if beta_rao >= 0 and w3 < floor(exp(-beta_rao |TTS' - TTS|) 2^32).
+ * Requires engineer_begin. */
+int engineer_step(pt_handle *h, uint32_t step, pt_step_result *out);
+
+/* n_steps consecutive steps t = step0 .. step0+n_steps-1 with results
+ * identical to n_steps engineer_step calls.  Up to `speculation` (1..16)
+ * candidates are drawn against the current couplers and evaluated in one
+ * batched launch; every candidate after the first kept one is discarded and
+ * redrawn.  out: n_steps results (may be NULL). */
+int engineer_run(pt_handle *h, uint32_t step0, int32_t n_steps, int32_t speculation,
+                 pt_step_result *out);
+
+/* Current loop state: TTS of the current couplers. */
+int engineer_current_tts(const pt_handle *h, int32_t *tts);
+
+/* Checkpoint of the complete PT state and couplers.  With buf == NULL only
+ * *len is set; otherwise *len must be at least that size. */
+int pt_checkpoint(pt_handle *h, void *buf, size_t *len);
+
+/* Restores a checkpoint made by a handle with the same L, n_temps, n_runs and
+ * ladder.  PT_ERR_ARG on a size or shape mismatch. */
+int pt_restore(pt_handle *h, const void *buf, size_t len);
+
+/* Launch schedule (results are identical for every valid choice):
+ * slot_parallel = temperature slots one CTA processes concurrently per run
+ * (threads per run = slot_parallel * L^2, a multiple of 32, <= 1024),
+ * runs_per_cta = runs sharing one CTA, sweeps_per_launch = sweeps per kernel
+ * launch.  0 keeps the current value. */
+int pt_set_schedule(pt_handle *h, int32_t slot_parallel, int32_t runs_per_cta,
+                    int32_t sweeps_per_launch);
+int pt_get_schedule(const pt_handle *h, int32_t *slot_parallel, int32_t *runs_per_cta,
+                    int32_t *sweeps_per_launch);
+
+/* Makes `device` the current device of the calling host thread for the
+ * library's CUDA runtime (handles created afterwards live there).  Errors:
+ * PT_ERR_ARG (index out of range), PT_ERR_CUDA; failures are reported by
+ * pt_last_error(NULL). */
+int pt_select_device(int32_t device);
+
+/* Number of kernels this handle has launched so far. */
+uint64_t pt_launch_count(const pt_handle *h);
+
+/* Enables (on != 0) or disables CUDA-event timing of every sweep-kernel
+ * launch, and zeroes the cumulative totals of pt_sweep_timing_total. */
+int pt_set_timing(pt_handle *h, int on);
+
+/* Cumulative device time (ms) and count of the timed sweep-kernel launches
+ * since the last pt_set_timing. */
+int pt_sweep_timing_total(const pt_handle *h, double *ms, uint64_t *launches);
+
+/* Accounting of full PT-TTS evaluations (pt_tts_eval, engineer_*): instances
+ * evaluated, batched evaluation rounds, and their device time in ms (CUDA
+ * events from the first kernel of a round to its TTS reduction).  reset != 0
+ * zeroes the counters after reading them. */
+int pt_eval_stats(pt_handle *h, uint64_t *evals, uint64_t *batches, double *device_ms, int reset);
+
+/* Device time of the sweep-kernel launches of the last pt_sweep/pt_tts_eval
+ * call, summed (ms, CUDA events on the handle's stream), and their count. */
+int pt_last_sweep_timing(const pt_handle *h, double *ms, int32_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,263 @@
+"""ctypes binding of ``libpt_gb300.so`` (the C ABI declared in include/pt.h).
+
+Argument marshalling only: every step of the PT path runs in the library's
+CUDA kernels.  There is no CPU fallback; loading fails loudly when the library
+has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpt_gb300.so")
+
+PT_OK, PT_ERR_ARG, PT_ERR_CUDA, PT_ERR_TIMEOUT, PT_ERR_OOM, PT_ERR_STATE = range(6)
+PT_TARGET_BEST = 2**31 - 1
+PT_KMAX = 18
+
+_ERRNAMES = {1: "PT_ERR_ARG", 2: "PT_ERR_CUDA", 3: "PT_ERR_TIMEOUT", 4: "PT_ERR_OOM", 5: "PT_ERR_STATE"}
+
+
+class PTError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class pt_rule(C.Structure):
+    _fields_ = [("S", C.c_int32), ("pass_mult", C.c_int32), ("exchange_every", C.c_int32),
+                ("direction", C.c_int32), ("beta_rao", C.c_double)]
+
+
+class pt_step_result(C.Structure):
+    _fields_ = [("edge", C.c_int32), ("old_value", C.c_int32), ("new_value", C.c_int32),
+                ("tts_old", C.c_int32), ("tts_new", C.c_int32), ("accepted", C.c_int32),
+                ("cand_uid", C.c_uint32)]
+
+
+# (name, restype, argtypes) of every entry point declared in include/pt.h
+_VP = C.c_void_p
+_I32P = C.POINTER(C.c_int32)
+SIGNATURES = [
+    ("pt_last_error", C.c_char_p, [_VP]),
+    ("pt_create", C.c_int, [C.POINTER(_VP), C.c_int32, _VP, C.c_int32, _VP, C.c_int32, C.c_int32,
+                            C.c_uint32, C.c_uint32, _VP]),
+    ("pt_destroy", None, [_VP]),
+    ("pt_reset", C.c_int, [_VP, C.c_uint32]),
+    ("pt_set_spins", C.c_int, [_VP, _VP]),
+    ("pt_sweep", C.c_int, [_VP, C.c_int32, C.c_int32]),
+    ("pt_exchange", C.c_int, [_VP]),
+    ("pt_get_state", C.c_int, [_VP] + [_VP] * 8),
+    ("pt_tts", C.c_int, [_VP, C.c_int32, C.c_int32, _I32P, _I32P, _I32P]),
+    ("pt_tts_eval", C.c_int, [_VP, C.c_uint32, C.c_int32, C.c_int32, C.c_int32, _I32P, _I32P, _I32P]),
+    ("pt_set_coupler", C.c_int, [_VP, C.c_int32, C.c_int8]),
+    ("pt_get_couplers", C.c_int, [_VP, _VP]),
+    ("pt_get_tables", C.c_int, [_VP, _VP, _VP, _VP, C.c_int64, C.POINTER(C.c_int64)]),
+    ("engineer_begin", C.c_int, [_VP, C.POINTER(pt_rule), C.c_uint32, _I32P]),
+    ("engineer_step", C.c_int, [_VP, C.c_uint32, C.POINTER(pt_step_result)]),
+    ("engineer_run", C.c_int, [_VP, C.c_uint32, C.c_int32, C.c_int32, C.POINTER(pt_step_result)]),
+    ("engineer_current_tts", C.c_int, [_VP, _I32P]),
+    ("pt_checkpoint", C.c_int, [_VP, _VP, C.POINTER(C.c_size_t)]),
+    ("pt_restore", C.c_int, [_VP, _VP, C.c_size_t]),
+    ("pt_set_schedule", C.c_int, [_VP, C.c_int32, C.c_int32, C.c_int32]),
+    ("pt_get_schedule", C.c_int, [_VP, _I32P, _I32P, _I32P]),
+    ("pt_launch_count", C.c_uint64, [_VP]),
+    ("pt_select_device", C.c_int, [C.c_int32]),
+    ("pt_set_timing", C.c_int, [_VP, C.c_int]),
+    ("pt_last_sweep_timing", C.c_int, [_VP, C.POINTER(C.c_double), _I32P]),
+    ("pt_sweep_timing_total", C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_uint64)]),
+    ("pt_eval_stats", C.c_int, [_VP, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64),
+                                C.POINTER(C.c_double), C.c_int]),
+]
+
+_lib = None
+
+
+def load():
+    """Loads the in-tree library (build it first with paper_1605_03607_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() (no CPU fallback exists)")
+        lib = C.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def select_device(device):
+    """Current device of the library's CUDA runtime for this host thread."""
+    _check(load().pt_select_device(int(device)), None)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _check(rc, h=None):
+    if rc != PT_OK:
+        msg = load().pt_last_error(h)
+        raise PTError(rc, msg.decode() if msg else "")
+
+
+class PTHandle:
+    """One instance, n_runs PT runs of len(betas) slots on the GPU (owner of a pt_handle)."""
+
+    def __init__(self, L, J, betas, n_runs, seed, uid, stream=None):
+        lib = load()
+        self.L = int(L)
+        self.N = 8 * self.L * self.L
+        J = np.ascontiguousarray(J, np.int8)
+        betas = np.ascontiguousarray(betas, np.float64)
+        self.NT = len(betas)
+        self.R = int(n_runs)
+        self.n_edges = len(J)
+        h = C.c_void_p()
+        rc = lib.pt_create(C.byref(h), self.L, _ptr(J), self.n_edges, _ptr(betas), self.NT, self.R,
+                           int(seed) & 0xFFFFFFFF, int(uid) & 0xFFFFFFFF,
+                           None if stream is None else C.c_void_p(stream))
+        _check(rc, None)
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().pt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- PT
+    def reset(self, uid):
+        _check(load().pt_reset(self.h, int(uid) & 0xFFFFFFFF), self.h)
+
+    def set_spins(self, spins):
+        s = np.ascontiguousarray(spins, np.int8).reshape(self.R, self.NT, self.N)
+        _check(load().pt_set_spins(self.h, _ptr(s)), self.h)
+
+    def sweep(self, n, exchange_every=1):
+        _check(load().pt_sweep(self.h, int(n), int(exchange_every)), self.h)
+
+    def exchange(self):
+        _check(load().pt_exchange(self.h), self.h)
+
+    def state(self):
+        spins = np.zeros((self.R, self.NT, self.N), np.int8)
+        E = np.zeros((self.R, self.NT), np.int32)
+        perm = np.zeros((self.R, self.NT), np.uint8)
+        best = np.zeros(self.R, np.int32)
+        first = np.zeros(self.R, np.int32)
+        macc = np.zeros((self.R, self.NT), np.uint64)
+        xacc = np.zeros((self.R, max(self.NT - 1, 1)), np.uint64)
+        sweep = np.zeros(1, np.uint64)
+        _check(load().pt_get_state(self.h, _ptr(spins), _ptr(E), _ptr(perm), _ptr(best), _ptr(first),
+                                   _ptr(macc), _ptr(xacc), _ptr(sweep)), self.h)
+        return dict(spins=spins, E=E, perm=perm, best=best, first=first, macc=macc, xacc=xacc,
+                    sweep=int(sweep[0]))
+
+    def tts(self, target=PT_TARGET_BEST, horizon=None):
+        if horizon is None:
+            horizon = self.state()["sweep"]
+        t, n, tg = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(load().pt_tts(self.h, int(target), int(horizon), C.byref(t), C.byref(n), C.byref(tg)), self.h)
+        return t.value, n.value, tg.value
+
+    def tts_eval(self, uid, S, pass_mult=1, exchange_every=1):
+        t, n, tg = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(load().pt_tts_eval(self.h, int(uid) & 0xFFFFFFFF, int(S), int(pass_mult),
+                                  int(exchange_every), C.byref(t), C.byref(n), C.byref(tg)), self.h)
+        return t.value, n.value, tg.value
+
+    def set_coupler(self, edge, value):
+        _check(load().pt_set_coupler(self.h, int(edge), int(value)), self.h)
+
+    def couplers(self):
+        J = np.zeros(self.n_edges, np.int8)
+        _check(load().pt_get_couplers(self.h, _ptr(J)), self.h)
+        return J
+
+    def tables(self):
+        n = C.c_int64()
+        _check(load().pt_get_tables(self.h, None, None, None, 0, C.byref(n)), self.h)
+        thr = np.zeros((self.NT, PT_KMAX + 1), np.uint32)
+        xoff = np.zeros(self.NT, np.int64)
+        xthr = np.zeros(max(n.value, 1), np.uint32)
+        _check(load().pt_get_tables(self.h, _ptr(thr), _ptr(xoff), _ptr(xthr), len(xthr), C.byref(n)), self.h)
+        return thr, xoff, xthr[:n.value]
+
+    # -- RAO (Algorithm 1)
+    def engineer_begin(self, S, pass_mult=1, exchange_every=1, base_uid=0, beta_rao=-1.0, direction=1):
+        rule = pt_rule(int(S), int(pass_mult), int(exchange_every), int(direction), float(beta_rao))
+        t = C.c_int32()
+        _check(load().engineer_begin(self.h, C.byref(rule), int(base_uid) & 0xFFFFFFFF, C.byref(t)), self.h)
+        return t.value
+
+    def engineer_run(self, step0, n_steps, speculation=1):
+        out = (pt_step_result * max(n_steps, 1))()
+        _check(load().engineer_run(self.h, int(step0) & 0xFFFFFFFF, int(n_steps), int(speculation), out), self.h)
+        keys = ("edge", "old_value", "new_value", "tts_old", "tts_new", "accepted", "cand_uid")
+        return {k: np.array([getattr(out[i], k) for i in range(n_steps)], np.int64) for k in keys}
+
+    def engineer_step(self, step):
+        return self.engineer_run(step, 1, 1)
+
+    def engineer_tts(self):
+        t = C.c_int32()
+        _check(load().engineer_current_tts(self.h, C.byref(t)), self.h)
+        return t.value
+
+    # -- checkpoint / schedule / accounting
+    def checkpoint(self):
+        n = C.c_size_t()
+        _check(load().pt_checkpoint(self.h, None, C.byref(n)), self.h)
+        buf = np.zeros(n.value, np.uint8)
+        _check(load().pt_checkpoint(self.h, _ptr(buf), C.byref(n)), self.h)
+        return buf
+
+    def restore(self, buf):
+        buf = np.ascontiguousarray(buf, np.uint8)
+        _check(load().pt_restore(self.h, _ptr(buf), len(buf)), self.h)
+
+    def set_schedule(self, slot_parallel=0, runs_per_cta=0, sweeps_per_launch=0):
+        _check(load().pt_set_schedule(self.h, int(slot_parallel), int(runs_per_cta), int(sweeps_per_launch)), self.h)
+
+    def schedule(self):
+        a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(load().pt_get_schedule(self.h, C.byref(a), C.byref(b), C.byref(c)), self.h)
+        return a.value, b.value, c.value
+
+    def launch_count(self):
+        return int(load().pt_launch_count(self.h))
+
+    def set_timing(self, on=True):
+        _check(load().pt_set_timing(self.h, 1 if on else 0), self.h)
+
+    def sweep_timing_total(self):
+        ms, n = C.c_double(), C.c_uint64()
+        _check(load().pt_sweep_timing_total(self.h, C.byref(ms), C.byref(n)), self.h)
+        return ms.value, int(n.value)
+
+    def eval_stats(self, reset=False):
+        e, b, ms = C.c_uint64(), C.c_uint64(), C.c_double()
+        _check(load().pt_eval_stats(self.h, C.byref(e), C.byref(b), C.byref(ms), 1 if reset else 0), self.h)
+        return int(e.value), int(b.value), ms.value
+
+    def last_sweep_timing(self):
+        ms, n = C.c_double(), C.c_int32()
+        _check(load().pt_last_sweep_timing(self.h, C.byref(ms), C.byref(n)), self.h)
+        return ms.value, n.value

@@ -1,0 +1,985 @@
+// pt_capi.cu -- host runtime and C ABI (include/pt.h) of the GB300 PT engine.
+//
+// The host side does only what has to happen on the host: argument checks,
+// FP64 acceptance tables (the Metropolis rule of Sec. II and the exchange rule
+// with detailed balance), repacking the couplers into the kernels' layout,
+// the random draws of Algorithm 1 (one Philox4x32-10 call per step), and the
+// accept/reject bookkeeping of the engineering loop.  Every sweep, energy and
+// TTS reduction runs in the kernels of pt_kernels.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/pt.h"
+#include "pt_internal.h"
+#include "pt_kernels.h"
+
+using namespace ptg;
+
+namespace {
+
+std::mutex g_err_mu;
+std::string g_create_err = "no error";
+
+// ------------------------------------------------------------------------
+// Host Philox4x32-10 for the engineering draws (Salmon et al., SC'11).
+// ------------------------------------------------------------------------
+void philox_host(const uint32_t in[4], uint32_t k0, uint32_t k1, uint32_t out[4])
+{
+    uint32_t c0 = in[0], c1 = in[1], c2 = in[2], c3 = in[3];
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        c1 = (uint32_t)p1;
+        c3 = (uint32_t)p0;
+        c0 = n0;
+        c2 = n2;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+uint32_t to_u32_threshold(double p)
+{
+    const double x = std::floor(std::ldexp(p, 32));
+    if (x >= 4294967295.0) return 0xFFFFFFFFu;
+    if (x <= 0.0) return 0u;
+    return (uint32_t)x;
+}
+
+int n_edges_of(int L) { return 16 * L * L + 8 * L * (L - 1); }
+
+// Coupler index helpers for the documented edge order.
+int intra_edge(int L, int cell, int kv, int kh) { (void)L; return 16 * cell + 4 * kv + kh; }
+int vert_edge(int L, int r, int c, int k) { return 16 * L * L + (r * L + c) * 4 + k; }
+int horiz_edge(int L, int r, int c, int k) { return 16 * L * L + 4 * L * (L - 1) + (r * (L - 1) + c) * 4 + k; }
+
+uint32_t pack4(int b0, int b1, int b2, int b3)
+{
+    return (uint32_t)(uint8_t)(int8_t)b0 | ((uint32_t)(uint8_t)(int8_t)b1 << 8) |
+           ((uint32_t)(uint8_t)(int8_t)b2 << 16) | ((uint32_t)(uint8_t)(int8_t)b3 << 24);
+}
+
+// Kernel layout of the couplers (see InstDesc): per (cell, colour), 4 words of
+// negated intra-cell couplers and 4 words of negated inter-cell couplers.
+void pack_couplers(int L, const int8_t* J, uint32_t* jw)
+{
+    for (int r = 0; r < L; ++r)
+        for (int c = 0; c < L; ++c) {
+            const int cell = r * L + c;
+            for (int col = 0; col < 2; ++col) {
+                const int u = (r + c + col) & 1;
+                uint32_t* w = jw + (cell * 2 + col) * 8;
+                for (int k = 0; k < 4; ++k) {
+                    int b[4];
+                    for (int kp = 0; kp < 4; ++kp)
+                        b[kp] = -(u == 0 ? J[intra_edge(L, cell, k, kp)] : J[intra_edge(L, cell, kp, k)]);
+                    w[k] = pack4(b[0], b[1], b[2], b[3]);
+                }
+                int jm[4], jp[4];
+                for (int k = 0; k < 4; ++k) {
+                    if (u == 0) {
+                        jm[k] = r >= 1 ? -J[vert_edge(L, r - 1, c, k)] : 0;
+                        jp[k] = r + 1 < L ? -J[vert_edge(L, r, c, k)] : 0;
+                    } else {
+                        jm[k] = c >= 1 ? -J[horiz_edge(L, r, c - 1, k)] : 0;
+                        jp[k] = c + 1 < L ? -J[horiz_edge(L, r, c, k)] : 0;
+                    }
+                }
+                w[4] = pack4(jm[0], jp[0], 0, 0);
+                w[5] = pack4(0, 0, jm[1], jp[1]);
+                w[6] = pack4(jm[2], jp[2], 0, 0);
+                w[7] = pack4(0, 0, jm[3], jp[3]);
+            }
+        }
+}
+
+void build_neighbours(int L, int16_t* nbr)
+{
+    for (int r = 0; r < L; ++r)
+        for (int c = 0; c < L; ++c) {
+            const int cell = r * L + c;
+            for (int col = 0; col < 2; ++col) {
+                const int u = (r + c + col) & 1;
+                int m = cell, p = cell;
+                if (u == 0) {
+                    if (r >= 1) m = (r - 1) * L + c;
+                    if (r + 1 < L) p = (r + 1) * L + c;
+                } else {
+                    if (c >= 1) m = r * L + c - 1;
+                    if (c + 1 < L) p = r * L + c + 1;
+                }
+                nbr[(cell * 2 + col) * 2 + 0] = (int16_t)m;
+                nbr[(cell * 2 + col) * 2 + 1] = (int16_t)p;
+            }
+        }
+}
+
+struct Tables {
+    std::vector<uint32_t> thr;     // [NT][KT]
+    std::vector<int64_t> xoff;     // [NT]
+    std::vector<uint32_t> xthr;
+    std::vector<float> xhint;      // [NT-1]
+};
+
+// Returns an empty string or the reason the ladder is rejected.
+std::string build_tables(int NT, const double* betas, Tables& tb)
+{
+    tb.thr.assign((size_t)NT * KT, 0u);
+    for (int t = 0; t < NT; ++t) {
+        tb.thr[(size_t)t * KT] = 0xFFFFFFFFu;   // k <= 0 always accepts; entry unused for decisions
+        for (int k = 1; k < KT; ++k)
+            tb.thr[(size_t)t * KT + k] = to_u32_threshold(std::exp(-2.0 * (double)k * betas[t]));
+    }
+    tb.xoff.assign((size_t)NT, 0);
+    tb.xthr.clear();
+    tb.xhint.assign((size_t)(NT > 1 ? NT - 1 : 1), 0.f);
+    for (int p = 0; p + 1 < NT; ++p) {
+        const double db = betas[p] - betas[p + 1];
+        tb.xoff[p] = (int64_t)tb.xthr.size();
+        tb.xhint[p] = (float)(std::log(2.0) / (2.0 * db));
+        for (int64_t h = 1;; ++h) {
+            const uint32_t v = to_u32_threshold(std::exp(-2.0 * (double)h * db));
+            if (v == 0u) break;
+            if (h > (1 << 22)) return "exchange table longer than 2^22 entries (beta gap too small)";
+            if (!tb.xthr.empty() && h > 1 && v > tb.xthr.back())
+                return "exchange table not monotone (host libm)";
+            tb.xthr.push_back(v);
+        }
+    }
+    if (NT > 0) tb.xoff[NT - 1] = (int64_t)tb.xthr.size();
+    if (tb.xthr.size() > (size_t)INT32_MAX / 2) return "exchange tables too large";
+    return "";
+}
+
+// A set of instances of one shape (L, NT, R) sharing one ladder.
+struct Group {
+    int L = 0, NT = 0, R = 0, n_inst = 0;
+    int8_t* spins = nullptr;
+    int32_t* E = nullptr;
+    uint8_t* perm = nullptr;
+    int32_t *best = nullptr, *first = nullptr;
+    unsigned long long *macc = nullptr, *xacc = nullptr;
+    uint32_t* jw = nullptr;          // [n_inst][L2][2][8]
+    InstDesc* d_desc = nullptr;
+    int2* d_items = nullptr;
+    Bundle* d_bundles = nullptr;
+    int32_t* d_tts = nullptr;        // [n_inst][3]
+    int* d_queue = nullptr;
+    std::vector<InstDesc> desc;
+    std::vector<Bundle> bundles;
+    int block = 0, smem = 0;
+    uint64_t sweep = 0;
+};
+
+}  // namespace
+
+struct pt_handle {
+    int L = 0, NT = 0, R = 0, N = 0, n_edges = 0;
+    uint32_t seed = 0, uid = 0;
+    std::vector<int8_t> J;
+    std::vector<double> betas;
+    Tables tb;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    // device tables shared by every group of this handle
+    uint32_t* d_thr = nullptr;
+    int32_t* d_xoff = nullptr;
+    uint32_t* d_xthr = nullptr;
+    float* d_xhint = nullptr;
+    int16_t* d_nbr = nullptr;
+    Group main, cand;
+    int sp = 0, ipc = 0, spl = 4096;
+    uint64_t launches = 0;
+    // timing of sweep launches
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;
+    int ev_used = 0;
+    double last_ms = 0.0;
+    int last_launches = 0;
+    double total_ms = 0.0;
+    uint64_t total_launches = 0;
+    // evaluation accounting (every batched PT-TTS evaluation)
+    uint64_t evals = 0, batches = 0;
+    double eval_ms = 0.0;
+    cudaEvent_t eb0 = nullptr, eb1 = nullptr;
+    // engineering loop
+    bool eng = false;
+    pt_rule rule{};
+    uint32_t base_uid = 0;
+    int32_t tts_cur = 0;
+    std::string err = "no error";
+};
+
+namespace {
+
+int fail(pt_handle* h, int code, const std::string& msg)
+{
+    if (h) h->err = msg;
+    else {
+        std::lock_guard<std::mutex> g(g_err_mu);
+        g_create_err = msg;
+    }
+    return code;
+}
+
+int cuda_fail(pt_handle* h, cudaError_t e, const char* what)
+{
+    return fail(h, e == cudaErrorMemoryAllocation ? PT_ERR_OOM : PT_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                        \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(T** p, size_t n)
+{
+    return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (n ? n : 1));
+}
+
+void free_group(Group& g)
+{
+    cudaFree(g.spins); cudaFree(g.E); cudaFree(g.perm); cudaFree(g.best); cudaFree(g.first);
+    cudaFree(g.macc); cudaFree(g.xacc); cudaFree(g.jw); cudaFree(g.d_desc); cudaFree(g.d_items);
+    cudaFree(g.d_bundles); cudaFree(g.d_tts); cudaFree(g.d_queue);
+    g = Group();
+}
+
+// Default schedule: about 256 threads per run, a multiple of 32.
+void default_schedule(int L, int NT, int R, int& sp, int& ipc)
+{
+    const int L2 = L * L;
+    sp = std::max(1, 256 / L2);
+    if (sp > NT) sp = NT;
+    while ((sp * L2) % 32 != 0) ++sp;
+    const int tpi = sp * L2;
+    ipc = std::max(1, 512 / tpi);
+    if (ipc > R) ipc = R;
+    while (ipc > 1 && bundle_smem_bytes(L, NT, ipc) > 110 * 1024) --ipc;
+}
+
+int check_schedule(pt_handle* h, int L, int NT, int sp, int ipc)
+{
+    const int L2 = L * L;
+    if (sp < 1 || ipc < 1) return fail(h, PT_ERR_ARG, "schedule values must be >= 1");
+    if ((sp * L2) % 32 != 0) return fail(h, PT_ERR_ARG, "slot_parallel * L^2 must be a multiple of 32");
+    if (sp * L2 * ipc > MAX_THREADS) return fail(h, PT_ERR_ARG, "more than 1024 threads per CTA");
+    if (bundle_smem_bytes(L, NT, ipc) > 227 * 1024) return fail(h, PT_ERR_ARG, "shared memory above 227 KB");
+    return PT_OK;
+}
+
+int group_alloc(pt_handle* h, Group& g, int n_inst)
+{
+    g.L = h->L; g.NT = h->NT; g.R = h->R; g.n_inst = n_inst;
+    const size_t reps = (size_t)n_inst * h->R * h->NT;
+    const size_t runs = (size_t)n_inst * h->R;
+    const size_t npair = (size_t)(h->NT > 1 ? h->NT - 1 : 1);
+    CK(dalloc(&g.spins, reps * h->N), "cudaMalloc spins");
+    CK(dalloc(&g.E, reps), "cudaMalloc E");
+    CK(dalloc(&g.perm, reps), "cudaMalloc perm");
+    CK(dalloc(&g.best, runs), "cudaMalloc best");
+    CK(dalloc(&g.first, runs), "cudaMalloc first");
+    CK(dalloc(&g.macc, reps), "cudaMalloc macc");
+    CK(dalloc(&g.xacc, runs * npair), "cudaMalloc xacc");
+    CK(dalloc(&g.jw, (size_t)n_inst * h->L * h->L * 16), "cudaMalloc jw");
+    CK(dalloc(&g.d_desc, (size_t)n_inst), "cudaMalloc desc");
+    CK(dalloc(&g.d_items, runs), "cudaMalloc items");
+    CK(dalloc(&g.d_tts, (size_t)n_inst * 3), "cudaMalloc tts");
+    CK(dalloc(&g.d_queue, 1), "cudaMalloc queue");
+    g.desc.resize(n_inst);
+    for (int i = 0; i < n_inst; ++i) {
+        InstDesc& d = g.desc[i];
+        const size_t r0 = (size_t)i * h->R;
+        d.L = h->L; d.NT = h->NT; d.R = h->R; d.n_xpairs = h->NT - 1;
+        d.seed = h->seed; d.uid = h->uid;
+        d.jw = g.jw + (size_t)i * h->L * h->L * 16;
+        d.nbr = h->d_nbr; d.thr = h->d_thr; d.xoff = h->d_xoff; d.xthr = h->d_xthr; d.xhint = h->d_xhint;
+        d.spins = g.spins + r0 * h->NT * h->N;
+        d.E = g.E + r0 * h->NT;
+        d.perm = g.perm + r0 * h->NT;
+        d.best = g.best + r0;
+        d.first = g.first + r0;
+        d.macc = g.macc + r0 * h->NT;
+        d.xacc = g.xacc + r0 * npair;
+    }
+    std::vector<int2> items(runs);
+    for (int i = 0; i < n_inst; ++i)
+        for (int r = 0; r < h->R; ++r) items[(size_t)i * h->R + r] = make_int2(i, r);
+    CK(cudaMemcpyAsync(g.d_items, items.data(), sizeof(int2) * runs, cudaMemcpyHostToDevice, h->stream), "upload items");
+    return PT_OK;
+}
+
+int group_schedule(pt_handle* h, Group& g)
+{
+    g.bundles.clear();
+    const int L2 = g.L * g.L;
+    for (int i = 0; i < g.n_inst; ++i)
+        for (int r = 0; r < g.R; r += h->ipc) {
+            Bundle b;
+            b.inst = i; b.run0 = r; b.nitems = std::min(h->ipc, g.R - r); b.sp = h->sp;
+            g.bundles.push_back(b);
+        }
+    g.block = h->sp * L2 * h->ipc;
+    g.smem = (int)bundle_smem_bytes(g.L, g.NT, h->ipc);
+    cudaFree(g.d_bundles);
+    g.d_bundles = nullptr;
+    CK(dalloc(&g.d_bundles, g.bundles.size()), "cudaMalloc bundles");
+    CK(cudaMemcpyAsync(g.d_bundles, g.bundles.data(), sizeof(Bundle) * g.bundles.size(),
+                       cudaMemcpyHostToDevice, h->stream), "upload bundles");
+    CK(set_sweep_smem_limit(227 * 1024), "cudaFuncSetAttribute");
+    return PT_OK;
+}
+
+int upload_desc(pt_handle* h, Group& g)
+{
+    CK(cudaMemcpyAsync(g.d_desc, g.desc.data(), sizeof(InstDesc) * g.desc.size(),
+                       cudaMemcpyHostToDevice, h->stream), "upload desc");
+    return PT_OK;
+}
+
+int upload_couplers(pt_handle* h, Group& g, int inst, const int8_t* J)
+{
+    std::vector<uint32_t> jw((size_t)h->L * h->L * 16);
+    pack_couplers(h->L, J, jw.data());
+    CK(cudaMemcpyAsync(g.jw + (size_t)inst * jw.size(), jw.data(), sizeof(uint32_t) * jw.size(),
+                       cudaMemcpyHostToDevice, h->stream), "upload couplers");
+    // the pageable source must stay alive until the copy is done
+    CK(cudaStreamSynchronize(h->stream), "sync after coupler upload");
+    return PT_OK;
+}
+
+int group_reset(pt_handle* h, Group& g, bool draw)
+{
+    CK(launch_init(g.d_desc, g.d_items, g.n_inst * g.R, draw, h->stream), "init kernel");
+    CK(launch_energy(g.d_desc, g.d_items, g.n_inst * g.R, 0, h->stream), "energy kernel");
+    h->launches += 2;
+    g.sweep = 0;
+    return PT_OK;
+}
+
+int ensure_events(pt_handle* h, int n)
+{
+    while ((int)h->ev.size() < n) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e), "cudaEventCreate");
+        h->ev.push_back(e);
+    }
+    return PT_OK;
+}
+
+int group_sweeps(pt_handle* h, Group& g, int64_t n, int xevery)
+{
+    const int nl = (int)((n + h->spl - 1) / h->spl);
+    if (h->timing) {
+        int rc = ensure_events(h, 2 * nl);
+        if (rc) return rc;
+    }
+    int64_t done = 0;
+    int li = 0;
+    while (done < n) {
+        const int chunk = (int)std::min<int64_t>(h->spl, n - done);
+        if (h->timing) CK(cudaEventRecord(h->ev[2 * li], h->stream), "event");
+        CK(launch_sweeps(g.d_desc, g.d_bundles, (int)g.bundles.size(), (int)g.bundles.size(), g.block,
+                         g.smem, (uint32_t)g.sweep, chunk, xevery, 0, nullptr, h->stream),
+           "sweep kernel");
+        if (h->timing) CK(cudaEventRecord(h->ev[2 * li + 1], h->stream), "event");
+        ++h->launches;
+        ++li;
+        g.sweep += (uint64_t)chunk;
+        done += chunk;
+    }
+    h->ev_used = h->timing ? li : 0;
+    h->last_launches = li;
+    return PT_OK;
+}
+
+int collect_timing(pt_handle* h)
+{
+    if (!h->timing) return PT_OK;
+    CK(cudaStreamSynchronize(h->stream), "sync for timing");
+    double ms = 0.0;
+    for (int i = 0; i < h->ev_used; ++i) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, h->ev[2 * i], h->ev[2 * i + 1]), "event time");
+        ms += t;
+    }
+    h->last_ms = ms;
+    h->total_ms += ms;
+    h->total_launches += (uint64_t)h->ev_used;
+    return PT_OK;
+}
+
+int group_tts(pt_handle* h, Group& g, int32_t target, int32_t horizon, std::vector<int32_t>& out)
+{
+    CK(launch_tts(g.d_desc, g.n_inst, target, horizon, g.d_tts, h->stream), "tts kernel");
+    ++h->launches;
+    out.assign((size_t)g.n_inst * 3, 0);
+    CK(cudaMemcpyAsync(out.data(), g.d_tts, sizeof(int32_t) * out.size(), cudaMemcpyDeviceToHost,
+                       h->stream), "download tts");
+    CK(cudaStreamSynchronize(h->stream), "sync tts");
+    return PT_OK;
+}
+
+// Full evaluation of every instance of g: fresh runs, pass_mult*S sweeps, TTS at horizon S.
+int group_eval(pt_handle* h, Group& g, int32_t S, int32_t pass_mult, int32_t xevery,
+               std::vector<int32_t>& out)
+{
+    int rc;
+    if (!h->eb0) {
+        CK(cudaEventCreate(&h->eb0), "cudaEventCreate");
+        CK(cudaEventCreate(&h->eb1), "cudaEventCreate");
+    }
+    if ((rc = upload_desc(h, g))) return rc;
+    CK(cudaEventRecord(h->eb0, h->stream), "event");
+    if ((rc = group_reset(h, g, true))) return rc;
+    if ((rc = group_sweeps(h, g, (int64_t)S * pass_mult, xevery))) return rc;
+    CK(launch_tts(g.d_desc, g.n_inst, PT_TARGET_BEST, S, g.d_tts, h->stream), "tts kernel");
+    ++h->launches;
+    CK(cudaEventRecord(h->eb1, h->stream), "event");
+    out.assign((size_t)g.n_inst * 3, 0);
+    CK(cudaMemcpyAsync(out.data(), g.d_tts, sizeof(int32_t) * out.size(), cudaMemcpyDeviceToHost,
+                       h->stream), "download tts");
+    CK(cudaStreamSynchronize(h->stream), "sync eval");
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->eb0, h->eb1), "event time");
+    h->eval_ms += ms;
+    h->evals += (uint64_t)g.n_inst;
+    h->batches += 1;
+    return collect_timing(h);
+}
+
+// Draw of proposal j for step t against couplers J (Algorithm 1, one perturbed edge).
+void engineer_draw(const pt_handle* h, const int8_t* J, uint32_t step, uint32_t proposal,
+                   int32_t& edge, int32_t& value, uint32_t& uid, uint32_t& uacc)
+{
+    static const int8_t vals[6] = {-3, -2, -1, 1, 2, 3};
+    const uint32_t ctr[4] = {step, proposal, 0u, 3u};
+    uint32_t w[4];
+    philox_host(ctr, h->seed, h->base_uid, w);
+    edge = (int32_t)(((uint64_t)w[0] * (uint64_t)h->n_edges) >> 32);
+    const int pick = (int)(((uint64_t)w[1] * 5u) >> 32);
+    int n = 0;
+    value = 0;
+    for (int a = 0; a < 6; ++a) {
+        if (vals[a] == J[edge]) continue;
+        if (n == pick) value = vals[a];
+        ++n;
+    }
+    uid = w[2];
+    uacc = w[3];
+}
+
+bool engineer_accept(const pt_rule& rule, int32_t cur, int32_t cand, uint32_t uacc)
+{
+    const int64_t gain = (int64_t)rule.direction * ((int64_t)cand - (int64_t)cur);
+    if (gain > 0) return true;
+    if (rule.beta_rao >= 0.0) {
+        const double dt = std::fabs((double)cand - (double)cur);
+        return uacc < to_u32_threshold(std::exp(-rule.beta_rao * dt));
+    }
+    return false;
+}
+
+int ensure_candidates(pt_handle* h, int k)
+{
+    if (h->cand.n_inst >= k) return PT_OK;
+    free_group(h->cand);
+    int rc = group_alloc(h, h->cand, k);
+    if (rc) return rc;
+    return group_schedule(h, h->cand);
+}
+
+}  // namespace
+
+// ==========================================================================
+// C ABI
+// ==========================================================================
+extern "C" {
+
+const char* pt_last_error(const pt_handle* h)
+{
+    if (h) return h->err.c_str();
+    std::lock_guard<std::mutex> g(g_err_mu);
+    return g_create_err.c_str();
+}
+
+int pt_create(pt_handle** out, int32_t L, const int8_t* J, int32_t n_edges, const double* betas,
+              int32_t n_temps, int32_t n_runs, uint32_t seed, uint32_t uid, void* stream)
+{
+    pt_handle* h = nullptr;
+    if (!out || !J || !betas) return fail(nullptr, PT_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    if (L < 1 || L > MAX_L) return fail(nullptr, PT_ERR_ARG, "chimera_L must be in [1, 16]");
+    if (n_edges != n_edges_of(L)) return fail(nullptr, PT_ERR_ARG, "n_edges != 16 L^2 + 8 L (L-1)");
+    if (n_temps < 1 || n_temps > MAX_TEMPS) return fail(nullptr, PT_ERR_ARG, "n_temps must be in [1, 64]");
+    if (n_runs < 1 || n_runs > 1024) return fail(nullptr, PT_ERR_ARG, "n_runs must be in [1, 1024]");
+    for (int e = 0; e < n_edges; ++e)
+        if (J[e] < -3 || J[e] > 3) return fail(nullptr, PT_ERR_ARG, "coupler outside [-3, 3]");
+    for (int t = 0; t < n_temps; ++t) {
+        if (!(betas[t] > 0.0) || !std::isfinite(betas[t])) return fail(nullptr, PT_ERR_ARG, "beta must be finite and > 0");
+        if (t > 0 && !(betas[t] < betas[t - 1])) return fail(nullptr, PT_ERR_ARG, "betas must be strictly descending");
+    }
+    h = new (std::nothrow) pt_handle();
+    if (!h) return fail(nullptr, PT_ERR_OOM, "host allocation failed");
+    h->L = L; h->NT = n_temps; h->R = n_runs; h->N = 8 * L * L; h->n_edges = n_edges;
+    h->seed = seed; h->uid = uid;
+    h->J.assign(J, J + n_edges);
+    h->betas.assign(betas, betas + n_temps);
+    std::string why = build_tables(n_temps, betas, h->tb);
+    if (!why.empty()) { delete h; return fail(nullptr, PT_ERR_ARG, why); }
+    int rc = PT_OK;
+    auto bail = [&](int code) { std::string m = h->err; pt_destroy(h); return fail(nullptr, code, m); };
+    if (stream) h->stream = (cudaStream_t)stream;
+    else {
+        cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { cuda_fail(h, e, "cudaStreamCreate"); return bail(PT_ERR_CUDA); }
+        h->own_stream = true;
+    }
+#define CKC(call, what)                                                       \
+    do {                                                                      \
+        cudaError_t e_ = (call);                                              \
+        if (e_ != cudaSuccess) { int c_ = cuda_fail(h, e_, what); return bail(c_); } \
+    } while (0)
+    const int64_t xt = (int64_t)h->tb.xthr.size();
+    std::vector<int32_t> xoff32(h->tb.xoff.begin(), h->tb.xoff.end());
+    std::vector<int16_t> nbr((size_t)L * L * 4);
+    build_neighbours(L, nbr.data());
+    CKC(dalloc(&h->d_thr, h->tb.thr.size()), "cudaMalloc thr");
+    CKC(dalloc(&h->d_xoff, xoff32.size()), "cudaMalloc xoff");
+    CKC(dalloc(&h->d_xthr, (size_t)xt), "cudaMalloc xthr");
+    CKC(dalloc(&h->d_xhint, h->tb.xhint.size()), "cudaMalloc xhint");
+    CKC(dalloc(&h->d_nbr, nbr.size()), "cudaMalloc nbr");
+    CKC(cudaMemcpy(h->d_thr, h->tb.thr.data(), 4 * h->tb.thr.size(), cudaMemcpyHostToDevice), "upload thr");
+    CKC(cudaMemcpy(h->d_xoff, xoff32.data(), 4 * xoff32.size(), cudaMemcpyHostToDevice), "upload xoff");
+    if (xt) CKC(cudaMemcpy(h->d_xthr, h->tb.xthr.data(), 4 * (size_t)xt, cudaMemcpyHostToDevice), "upload xthr");
+    CKC(cudaMemcpy(h->d_xhint, h->tb.xhint.data(), 4 * h->tb.xhint.size(), cudaMemcpyHostToDevice), "upload xhint");
+    CKC(cudaMemcpy(h->d_nbr, nbr.data(), 2 * nbr.size(), cudaMemcpyHostToDevice), "upload nbr");
+    default_schedule(L, n_temps, n_runs, h->sp, h->ipc);
+    if ((rc = group_alloc(h, h->main, 1))) return bail(rc);
+    if ((rc = group_schedule(h, h->main))) return bail(rc);
+    if ((rc = upload_couplers(h, h->main, 0, h->J.data()))) return bail(rc);
+    if ((rc = upload_desc(h, h->main))) return bail(rc);
+    if ((rc = group_reset(h, h->main, true))) return bail(rc);
+    CKC(cudaStreamSynchronize(h->stream), "sync after create");
+#undef CKC
+    *out = h;
+    return PT_OK;
+}
+
+void pt_destroy(pt_handle* h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_group(h->main);
+    free_group(h->cand);
+    cudaFree(h->d_thr); cudaFree(h->d_xoff); cudaFree(h->d_xthr); cudaFree(h->d_xhint); cudaFree(h->d_nbr);
+    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    if (h->eb0) cudaEventDestroy(h->eb0);
+    if (h->eb1) cudaEventDestroy(h->eb1);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+int pt_reset(pt_handle* h, uint32_t uid)
+{
+    if (!h) return PT_ERR_ARG;
+    h->uid = uid;
+    h->main.desc[0].uid = uid;
+    int rc;
+    if ((rc = upload_desc(h, h->main))) return rc;
+    if ((rc = group_reset(h, h->main, true))) return rc;
+    CK(cudaStreamSynchronize(h->stream), "sync reset");
+    return PT_OK;
+}
+
+int pt_set_spins(pt_handle* h, const int8_t* spins)
+{
+    if (!h || !spins) return fail(h, PT_ERR_ARG, "NULL argument");
+    const size_t n = (size_t)h->R * h->NT * h->N;
+    for (size_t i = 0; i < n; ++i)
+        if (spins[i] != 1 && spins[i] != -1) return fail(h, PT_ERR_ARG, "spins must be +-1");
+    CK(cudaMemcpyAsync(h->main.spins, spins, n, cudaMemcpyHostToDevice, h->stream), "upload spins");
+    CK(launch_init(h->main.d_desc, h->main.d_items, h->R, false, h->stream), "init kernel");
+    CK(launch_energy(h->main.d_desc, h->main.d_items, h->R, (int32_t)h->main.sweep, h->stream), "energy kernel");
+    h->launches += 2;
+    CK(cudaStreamSynchronize(h->stream), "sync set_spins");
+    return PT_OK;
+}
+
+int pt_sweep(pt_handle* h, int32_t n_sweeps, int32_t exchange_every)
+{
+    if (!h) return PT_ERR_ARG;
+    if (n_sweeps < 0 || n_sweeps > (1 << 24) || exchange_every < 0)
+        return fail(h, PT_ERR_ARG, "n_sweeps must be in [0, 2^24], exchange_every >= 0");
+    if (h->main.sweep + (uint64_t)n_sweeps > 0x7FFFFFFFull) return fail(h, PT_ERR_STATE, "sweep counter would exceed 2^31-1");
+    int rc = group_sweeps(h, h->main, n_sweeps, exchange_every);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(h->stream), "sync sweep");
+    return collect_timing(h);
+}
+
+int pt_exchange(pt_handle* h)
+{
+    if (!h) return PT_ERR_ARG;
+    Group& g = h->main;
+    CK(launch_sweeps(g.d_desc, g.d_bundles, (int)g.bundles.size(), (int)g.bundles.size(), g.block,
+                     g.smem, (uint32_t)g.sweep, 0, 0, 1, nullptr, h->stream), "exchange kernel");
+    ++h->launches;
+    CK(cudaStreamSynchronize(h->stream), "sync exchange");
+    return PT_OK;
+}
+
+int pt_get_state(pt_handle* h, int8_t* spins, int32_t* E, uint8_t* perm, int32_t* best, int32_t* first,
+                 uint64_t* macc, uint64_t* xacc, uint64_t* sweep)
+{
+    if (!h) return PT_ERR_ARG;
+    Group& g = h->main;
+    const size_t reps = (size_t)h->R * h->NT, N = h->N;
+    std::vector<uint8_t> pm(reps);
+    CK(cudaMemcpyAsync(pm.data(), g.perm, reps, cudaMemcpyDeviceToHost, h->stream), "download perm");
+    std::vector<int8_t> sp;
+    if (spins) {
+        sp.resize(reps * N);
+        CK(cudaMemcpyAsync(sp.data(), g.spins, reps * N, cudaMemcpyDeviceToHost, h->stream), "download spins");
+    }
+    if (E) CK(cudaMemcpyAsync(E, g.E, 4 * reps, cudaMemcpyDeviceToHost, h->stream), "download E");
+    if (best) CK(cudaMemcpyAsync(best, g.best, 4 * (size_t)h->R, cudaMemcpyDeviceToHost, h->stream), "download best");
+    if (first) CK(cudaMemcpyAsync(first, g.first, 4 * (size_t)h->R, cudaMemcpyDeviceToHost, h->stream), "download first");
+    if (macc) CK(cudaMemcpyAsync(macc, g.macc, 8 * reps, cudaMemcpyDeviceToHost, h->stream), "download macc");
+    if (xacc && h->NT > 1)
+        CK(cudaMemcpyAsync(xacc, g.xacc, 8 * (size_t)h->R * (h->NT - 1), cudaMemcpyDeviceToHost, h->stream), "download xacc");
+    CK(cudaStreamSynchronize(h->stream), "sync get_state");
+    if (perm) std::memcpy(perm, pm.data(), reps);
+    if (spins)   // slot order: slot t holds buffer perm[t]
+        for (int r = 0; r < h->R; ++r)
+            for (int t = 0; t < h->NT; ++t)
+                std::memcpy(spins + ((size_t)r * h->NT + t) * N,
+                            sp.data() + ((size_t)r * h->NT + pm[(size_t)r * h->NT + t]) * N, N);
+    if (sweep) *sweep = g.sweep;
+    return PT_OK;
+}
+
+int pt_tts(pt_handle* h, int32_t E_target, int32_t horizon, int32_t* tts, int32_t* n_hit, int32_t* target_used)
+{
+    if (!h || !tts) return fail(h, PT_ERR_ARG, "NULL argument");
+    if (horizon < 0 || horizon == INT32_MAX) return fail(h, PT_ERR_ARG, "horizon must be in [0, 2^31-2]");
+    std::vector<int32_t> out;
+    int rc = group_tts(h, h->main, E_target, horizon, out);
+    if (rc) return rc;
+    *tts = out[0];
+    if (n_hit) *n_hit = out[1];
+    if (target_used) *target_used = out[2];
+    return PT_OK;
+}
+
+int pt_tts_eval(pt_handle* h, uint32_t uid, int32_t S, int32_t pass_mult, int32_t xevery,
+                int32_t* tts, int32_t* n_hit, int32_t* target)
+{
+    if (!h || !tts) return fail(h, PT_ERR_ARG, "NULL argument");
+    if (S < 1 || pass_mult < 1 || xevery < 0 || (int64_t)S * pass_mult > (1 << 30))
+        return fail(h, PT_ERR_ARG, "need S >= 1, pass_mult >= 1, S * pass_mult <= 2^30");
+    h->uid = uid;
+    h->main.desc[0].uid = uid;
+    std::vector<int32_t> out;
+    int rc = group_eval(h, h->main, S, pass_mult, xevery, out);
+    if (rc) return rc;
+    *tts = out[0];
+    if (n_hit) *n_hit = out[1];
+    if (target) *target = out[2];
+    return PT_OK;
+}
+
+int pt_set_coupler(pt_handle* h, int32_t edge, int8_t value)
+{
+    if (!h) return PT_ERR_ARG;
+    if (edge < 0 || edge >= h->n_edges || value < -3 || value > 3)
+        return fail(h, PT_ERR_ARG, "edge out of range or |value| > 3");
+    h->J[edge] = value;
+    int rc = upload_couplers(h, h->main, 0, h->J.data());
+    if (rc) return rc;
+    CK(launch_energy(h->main.d_desc, h->main.d_items, h->R, (int32_t)h->main.sweep, h->stream), "energy kernel");
+    ++h->launches;
+    CK(cudaStreamSynchronize(h->stream), "sync set_coupler");
+    return PT_OK;
+}
+
+int pt_get_couplers(pt_handle* h, int8_t* J)
+{
+    if (!h || !J) return fail(h, PT_ERR_ARG, "NULL argument");
+    std::memcpy(J, h->J.data(), h->J.size());
+    return PT_OK;
+}
+
+int pt_get_tables(const pt_handle* h, uint32_t* thr, int64_t* xoff, uint32_t* xthr, int64_t cap, int64_t* len)
+{
+    if (!h) return PT_ERR_ARG;
+    const int64_t n = (int64_t)h->tb.xthr.size();
+    if (len) *len = n;
+    if (thr) std::memcpy(thr, h->tb.thr.data(), 4 * h->tb.thr.size());
+    if (xoff) std::memcpy(xoff, h->tb.xoff.data(), 8 * h->tb.xoff.size());
+    if (xthr) {
+        if (cap < n) return PT_ERR_ARG;
+        std::memcpy(xthr, h->tb.xthr.data(), 4 * (size_t)n);
+    }
+    return PT_OK;
+}
+
+int engineer_begin(pt_handle* h, const pt_rule* rule, uint32_t base_uid, int32_t* tts0)
+{
+    if (!h || !rule) return fail(h, PT_ERR_ARG, "NULL argument");
+    if (rule->S < 1 || rule->pass_mult < 1 || rule->exchange_every < 0 ||
+        (rule->direction != 1 && rule->direction != -1) || (int64_t)rule->S * rule->pass_mult > (1 << 30))
+        return fail(h, PT_ERR_ARG, "invalid pt_rule");
+    h->rule = *rule;
+    h->base_uid = base_uid;
+    int32_t t;
+    int rc = pt_tts_eval(h, base_uid, rule->S, rule->pass_mult, rule->exchange_every, &t, nullptr, nullptr);
+    if (rc) return rc;
+    h->tts_cur = t;
+    h->eng = true;
+    if (tts0) *tts0 = t;
+    return PT_OK;
+}
+
+int engineer_run(pt_handle* h, uint32_t step0, int32_t n_steps, int32_t spec, pt_step_result* out)
+{
+    if (!h) return PT_ERR_ARG;
+    if (!h->eng) return fail(h, PT_ERR_STATE, "engineer_begin not called");
+    if (n_steps < 0 || spec < 1 || spec > 16) return fail(h, PT_ERR_ARG, "need n_steps >= 0, speculation in [1, 16]");
+    int rc = ensure_candidates(h, spec);
+    if (rc) return rc;
+    Group& g = h->cand;
+    std::vector<int8_t> Jc((size_t)spec * h->n_edges);
+    std::vector<int32_t> e(spec), v(spec);
+    std::vector<uint32_t> cu(spec), ua(spec);
+    int32_t done = 0;
+    bool changed = false;
+    while (done < n_steps) {
+        const int k = std::min<int>(spec, n_steps - done);
+        std::vector<uint32_t> jw((size_t)k * h->L * h->L * 16);
+        for (int j = 0; j < k; ++j) {
+            engineer_draw(h, h->J.data(), step0 + (uint32_t)(done + j), 0u, e[j], v[j], cu[j], ua[j]);
+            int8_t* Jj = Jc.data() + (size_t)j * h->n_edges;
+            std::memcpy(Jj, h->J.data(), h->n_edges);
+            Jj[e[j]] = (int8_t)v[j];
+            pack_couplers(h->L, Jj, jw.data() + (size_t)j * h->L * h->L * 16);
+            g.desc[j].uid = cu[j];
+        }
+        CK(cudaMemcpyAsync(g.jw, jw.data(), 4 * jw.size(), cudaMemcpyHostToDevice, h->stream), "upload candidates");
+        // evaluate only the first k candidates: shrink the group view temporarily
+        const int n_full = g.n_inst;
+        std::vector<Bundle> keep = g.bundles;
+        g.n_inst = k;
+        std::vector<Bundle> sub;
+        for (const Bundle& b : keep) if (b.inst < k) sub.push_back(b);
+        g.bundles = sub;
+        std::vector<int32_t> res;
+        rc = group_eval(h, g, h->rule.S, h->rule.pass_mult, h->rule.exchange_every, res);
+        g.n_inst = n_full;
+        g.bundles = keep;
+        if (rc) return rc;
+        int used = k;
+        for (int j = 0; j < k; ++j) {
+            const int32_t tn = res[(size_t)j * 3];
+            const bool acc = engineer_accept(h->rule, h->tts_cur, tn, ua[j]);
+            if (out) {
+                pt_step_result& o = out[done + j];
+                o.edge = e[j]; o.old_value = h->J[e[j]]; o.new_value = v[j];
+                o.tts_old = h->tts_cur; o.tts_new = tn; o.accepted = acc ? 1 : 0; o.cand_uid = cu[j];
+            }
+            if (acc) {
+                h->J[e[j]] = (int8_t)v[j];
+                h->tts_cur = tn;
+                changed = true;
+                used = j + 1;
+                break;
+            }
+        }
+        done += used;
+    }
+    if (changed) {
+        rc = upload_couplers(h, h->main, 0, h->J.data());
+        if (rc) return rc;
+    }
+    return PT_OK;
+}
+
+int engineer_step(pt_handle* h, uint32_t step, pt_step_result* out)
+{
+    return engineer_run(h, step, 1, 1, out);
+}
+
+int engineer_current_tts(const pt_handle* h, int32_t* tts)
+{
+    if (!h || !tts || !h->eng) return PT_ERR_STATE;
+    *tts = h->tts_cur;
+    return PT_OK;
+}
+
+int pt_checkpoint(pt_handle* h, void* buf, size_t* len)
+{
+    if (!h || !len) return fail(h, PT_ERR_ARG, "NULL argument");
+    const size_t reps = (size_t)h->R * h->NT, npair = (size_t)h->R * (h->NT > 1 ? h->NT - 1 : 1);
+    const size_t need = 64 + (size_t)h->n_edges + reps * h->N + 4 * reps + reps + 8 * (size_t)h->R +
+                        8 * reps + 8 * npair;
+    if (!buf) { *len = need; return PT_OK; }
+    if (*len < need) return fail(h, PT_ERR_ARG, "checkpoint buffer too small");
+    Group& g = h->main;
+    uint8_t* p = static_cast<uint8_t*>(buf);
+    int64_t hdr[8] = {0x5054434bLL, h->L, h->NT, h->R, (int64_t)g.sweep, (int64_t)h->uid, (int64_t)h->seed, 0};
+    std::memcpy(p, hdr, 64); p += 64;
+    std::memcpy(p, h->J.data(), h->n_edges); p += h->n_edges;
+    CK(cudaMemcpyAsync(p, g.spins, reps * h->N, cudaMemcpyDeviceToHost, h->stream), "ckpt spins"); p += reps * h->N;
+    CK(cudaMemcpyAsync(p, g.E, 4 * reps, cudaMemcpyDeviceToHost, h->stream), "ckpt E"); p += 4 * reps;
+    CK(cudaMemcpyAsync(p, g.perm, reps, cudaMemcpyDeviceToHost, h->stream), "ckpt perm"); p += reps;
+    CK(cudaMemcpyAsync(p, g.best, 4 * (size_t)h->R, cudaMemcpyDeviceToHost, h->stream), "ckpt best"); p += 4 * (size_t)h->R;
+    CK(cudaMemcpyAsync(p, g.first, 4 * (size_t)h->R, cudaMemcpyDeviceToHost, h->stream), "ckpt first"); p += 4 * (size_t)h->R;
+    CK(cudaMemcpyAsync(p, g.macc, 8 * reps, cudaMemcpyDeviceToHost, h->stream), "ckpt macc"); p += 8 * reps;
+    CK(cudaMemcpyAsync(p, g.xacc, 8 * npair, cudaMemcpyDeviceToHost, h->stream), "ckpt xacc");
+    CK(cudaStreamSynchronize(h->stream), "sync checkpoint");
+    *len = need;
+    return PT_OK;
+}
+
+int pt_restore(pt_handle* h, const void* buf, size_t len)
+{
+    if (!h || !buf) return fail(h, PT_ERR_ARG, "NULL argument");
+    size_t need = 0;
+    pt_checkpoint(h, nullptr, &need);
+    if (len != need) return fail(h, PT_ERR_ARG, "checkpoint size does not match this handle");
+    const uint8_t* p = static_cast<const uint8_t*>(buf);
+    int64_t hdr[8];
+    std::memcpy(hdr, p, 64);
+    if (hdr[0] != 0x5054434bLL || hdr[1] != h->L || hdr[2] != h->NT || hdr[3] != h->R)
+        return fail(h, PT_ERR_ARG, "checkpoint shape does not match this handle");
+    p += 64;
+    for (int e = 0; e < h->n_edges; ++e)
+        if ((int8_t)p[e] < -3 || (int8_t)p[e] > 3) return fail(h, PT_ERR_ARG, "corrupt couplers in checkpoint");
+    Group& g = h->main;
+    const size_t reps = (size_t)h->R * h->NT, npair = (size_t)h->R * (h->NT > 1 ? h->NT - 1 : 1);
+    {
+        // the kernels index tables by local field and buffers by slot map:
+        // spins must be +-1 and every run's map a permutation of the slots
+        const int8_t* sp = reinterpret_cast<const int8_t*>(p + h->n_edges);
+        for (size_t i = 0; i < reps * h->N; ++i)
+            if (sp[i] != 1 && sp[i] != -1) return fail(h, PT_ERR_ARG, "corrupt spins in checkpoint");
+        const uint8_t* pm = p + h->n_edges + reps * h->N + 4 * reps;
+        for (int r = 0; r < h->R; ++r) {
+            uint64_t seen = 0;
+            for (int t = 0; t < h->NT; ++t) {
+                const int b = pm[(size_t)r * h->NT + t];
+                if (b >= h->NT || (seen >> b & 1ull)) return fail(h, PT_ERR_ARG, "corrupt slot map in checkpoint");
+                seen |= 1ull << b;
+            }
+        }
+    }
+    h->J.assign(reinterpret_cast<const int8_t*>(p), reinterpret_cast<const int8_t*>(p) + h->n_edges);
+    p += h->n_edges;
+    int rc = upload_couplers(h, g, 0, h->J.data());
+    if (rc) return rc;
+    g.sweep = (uint64_t)hdr[4];
+    h->uid = (uint32_t)hdr[5];
+    g.desc[0].uid = h->uid;
+    if ((rc = upload_desc(h, g))) return rc;
+    CK(cudaMemcpyAsync(g.spins, p, reps * h->N, cudaMemcpyHostToDevice, h->stream), "restore spins"); p += reps * h->N;
+    CK(cudaMemcpyAsync(g.E, p, 4 * reps, cudaMemcpyHostToDevice, h->stream), "restore E"); p += 4 * reps;
+    CK(cudaMemcpyAsync(g.perm, p, reps, cudaMemcpyHostToDevice, h->stream), "restore perm"); p += reps;
+    CK(cudaMemcpyAsync(g.best, p, 4 * (size_t)h->R, cudaMemcpyHostToDevice, h->stream), "restore best"); p += 4 * (size_t)h->R;
+    CK(cudaMemcpyAsync(g.first, p, 4 * (size_t)h->R, cudaMemcpyHostToDevice, h->stream), "restore first"); p += 4 * (size_t)h->R;
+    CK(cudaMemcpyAsync(g.macc, p, 8 * reps, cudaMemcpyHostToDevice, h->stream), "restore macc"); p += 8 * reps;
+    CK(cudaMemcpyAsync(g.xacc, p, 8 * npair, cudaMemcpyHostToDevice, h->stream), "restore xacc");
+    CK(cudaStreamSynchronize(h->stream), "sync restore");
+    return PT_OK;
+}
+
+int pt_set_schedule(pt_handle* h, int32_t sp, int32_t ipc, int32_t spl)
+{
+    if (!h) return PT_ERR_ARG;
+    const int nsp = sp > 0 ? sp : h->sp, nipc = ipc > 0 ? ipc : h->ipc;
+    if (spl < 0) return fail(h, PT_ERR_ARG, "sweeps_per_launch must be >= 0");
+    int rc = check_schedule(h, h->L, h->NT, nsp, nipc);
+    if (rc) return rc;
+    h->sp = nsp;
+    h->ipc = std::min(nipc, h->R);
+    if (spl > 0) h->spl = spl;
+    if ((rc = group_schedule(h, h->main))) return rc;
+    if (h->cand.n_inst > 0 && (rc = group_schedule(h, h->cand))) return rc;
+    CK(cudaStreamSynchronize(h->stream), "sync schedule");
+    return PT_OK;
+}
+
+int pt_get_schedule(const pt_handle* h, int32_t* sp, int32_t* ipc, int32_t* spl)
+{
+    if (!h) return PT_ERR_ARG;
+    if (sp) *sp = h->sp;
+    if (ipc) *ipc = h->ipc;
+    if (spl) *spl = h->spl;
+    return PT_OK;
+}
+
+uint64_t pt_launch_count(const pt_handle* h) { return h ? h->launches : 0; }
+
+int pt_select_device(int32_t device)
+{
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDeviceCount");
+    if (device < 0 || device >= n) return fail(nullptr, PT_ERR_ARG, "device index out of range");
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaSetDevice");
+    return PT_OK;
+}
+
+int pt_set_timing(pt_handle* h, int on)
+{
+    if (!h) return PT_ERR_ARG;
+    h->timing = on != 0;
+    h->total_ms = 0.0;
+    h->total_launches = 0;
+    return PT_OK;
+}
+
+int pt_sweep_timing_total(const pt_handle* h, double* ms, uint64_t* launches)
+{
+    if (!h) return PT_ERR_ARG;
+    if (ms) *ms = h->total_ms;
+    if (launches) *launches = h->total_launches;
+    return PT_OK;
+}
+
+int pt_eval_stats(pt_handle* h, uint64_t* evals, uint64_t* batches, double* device_ms, int reset)
+{
+    if (!h) return PT_ERR_ARG;
+    if (evals) *evals = h->evals;
+    if (batches) *batches = h->batches;
+    if (device_ms) *device_ms = h->eval_ms;
+    if (reset) {
+        h->evals = h->batches = 0;
+        h->eval_ms = 0.0;
+    }
+    return PT_OK;
+}
+
+int pt_last_sweep_timing(const pt_handle* h, double* ms, int32_t* launches)
+{
+    if (!h) return PT_ERR_ARG;
+    if (ms) *ms = h->last_ms;
+    if (launches) *launches = h->last_launches;
+    return PT_OK;
+}
+
+}  // extern "C"

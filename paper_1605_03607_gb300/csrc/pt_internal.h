@@ -1,0 +1,83 @@
+// pt_internal.h -- device data layout shared by the kernels and the host runtime
+// of the GB300 PT engine (library-private; the public ABI is include/pt.h).
+#pragma once
+#include <cstdint>
+#ifndef __CUDACC__
+#define __host__
+#define __device__
+#endif
+
+namespace ptg {
+
+constexpr int KT = 19;             // Metropolis table entries per slot: k = 0..18
+constexpr int MAX_TEMPS = 64;
+constexpr int MAX_L = 16;
+constexpr int MAX_THREADS = 1024;
+
+// Per instance.  All pointers are device pointers.
+//
+// Couplers are repacked per (cell, colour): the cell's group of 4 spins of
+// that colour (orientation u = (r + c + colour) & 1) needs
+//   jin[k]  bytes k' = 0..3: -J to the 4 opposite-orientation spins of the cell
+//   jud[k]  -J to the inter-cell neighbours of spin k: spin 0/2 in bytes 0,1,
+//           spin 1/3 in bytes 2,3 (minus-side neighbour first)
+// stored as jw[(cell * 2 + colour) * 8 + {0..3 jin, 4..7 jud}].  The negation
+// makes dp4a produce -h_i directly.  nbr[(cell * 2 + colour) * 2 + {0,1}] is the
+// minus/plus neighbour cell of that group (the cell itself where absent; its
+// couplers are 0 there).
+struct InstDesc {
+    int32_t L, NT, R, n_xpairs;
+    uint32_t seed, uid;
+    const uint32_t* jw;
+    const int16_t* nbr;
+    const uint32_t* thr;      // [NT][KT]; entry 0 = 0xFFFFFFFF (unused: k <= 0 always accepts)
+    const int32_t* xoff;      // [NT]  pair p owns xthr[xoff[p] .. xoff[p+1]-1], h = 1..H_p
+    const uint32_t* xthr;
+    const float* xhint;       // [NT-1] ln2 / (2 dbeta_p): start point of the exact table search
+    int8_t* spins;            // [R][NT][N] by configuration buffer, natural spin order
+    int32_t* E;               // [R][NT] by slot
+    uint8_t* perm;            // [R][NT] slot -> buffer
+    int32_t* best;            // [R]
+    int32_t* first;           // [R]
+    unsigned long long* macc; // [R][NT] accepted flips per slot
+    unsigned long long* xacc; // [R][max(NT-1,1)] accepted swaps per pair
+};
+
+// One CTA work unit: `nitems` consecutive runs of one instance, processed by
+// slot_parallel * L^2 threads each.
+struct Bundle {
+    int32_t inst, run0, nitems, sp;
+};
+
+// Shared-memory layout of one bundle: the Metropolis table of the instance,
+// then per item (run): spins [NT][N] (colour-major words per buffer), E by slot,
+// exchange critical h by pair, flip / swap counters, perm, best/first.
+struct ItemLayout {
+    int64_t spins, E, ccrit, macc, xacc, perm, misc, bytes;
+};
+
+__host__ __device__ inline int64_t pad16(int64_t x) { return (x + 15) & ~15LL; }
+
+__host__ __device__ inline ItemLayout item_layout(int L, int NT)
+{
+    ItemLayout o;
+    const int64_t N = 8LL * L * L;
+    o.spins = 0;
+    o.E = pad16((int64_t)NT * N);
+    o.ccrit = o.E + 4LL * NT;
+    o.macc = o.ccrit + 4LL * NT;
+    o.xacc = o.macc + 4LL * NT;
+    o.perm = o.xacc + 4LL * NT;
+    o.misc = pad16(o.perm + NT);
+    o.bytes = o.misc + 16;
+    return o;
+}
+
+__host__ __device__ inline int64_t table_bytes(int NT) { return pad16(4LL * NT * KT); }
+
+inline int64_t bundle_smem_bytes(int L, int NT, int nitems)
+{
+    return table_bytes(NT) + (int64_t)nitems * item_layout(L, NT).bytes;
+}
+
+}  // namespace ptg

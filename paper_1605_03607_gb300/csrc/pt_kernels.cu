@@ -1,0 +1,481 @@
+// pt_kernels.cu -- sm_103a kernels of the parallel-tempering hardness engine.
+//
+// Method (arXiv:1605.03607): Ising cost of Eq. 1 on the Chimera graph
+// (Appendix A), parallel tempering of Sec. II (independent Metropolis updates,
+// neighbour swaps with detailed-balance acceptance), sweeps as in Sec. III.B.
+//
+// Design (GB300):
+//   * One CTA "bundle" = a few PT runs of one instance.  Every replica of those
+//     runs lives in shared memory for the whole launch as int8 spins, one
+//     32-bit word per group of 4 same-colour spins of a cell, colour-major.
+//   * A thread owns one Chimera cell (its couplers, negated and packed for
+//     dp4a, sit in 16 registers) and a strided subset of temperature slots.
+//     Per group update: 4 shared loads, one Philox4x32-10 call for the 4
+//     spins, 8 dp4a for the local fields, 4 table compares, 1 store.
+//   * Energies are kept incrementally: per-lane dE and flip counts are packed
+//     in one int, reduced with redux.sync (a warp spans at most two slots) and
+//     added to the slot energy with one shared atomic.
+//   * Replica exchange is fused: before each sweep one warp turns every pair's
+//     uniform into the largest accepted half energy gap c_p (exact search of
+//     the host-built table, which is non-increasing), so the serial ascending
+//     swap chain is a subtract and compare per pair.
+//   * No tensor cores: this is integer ALU / shared-memory work.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "pt_internal.h"
+#include "pt_kernels.h"
+
+namespace ptg {
+
+namespace {
+
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two
+// 32x32->64 multiplies and a Weyl-sequence key schedule.
+__device__ __forceinline__ uint4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                          uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        c1 = (uint32_t)p1;
+        c3 = (uint32_t)p0;
+        c0 = n0;
+        c2 = n2;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+// Largest h in [0, H_p] with xthr[p][h'] > u for all 1 <= h' <= h: a swap with
+// energy gap d = 2h > 0 is accepted iff h <= c_p.  Exact for any start point
+// because the table is non-increasing in h (checked on the host).
+__device__ __forceinline__ int critical_half_gap(const InstDesc& in, int p, uint32_t u)
+{
+    const int o = in.xoff[p];
+    const int H = in.xoff[p + 1] - o;
+    const uint32_t* tab = in.xthr + o - 1;       // tab[h], h = 1..H
+    int c = H;
+    if (u != 0u) {
+        const float est = (32.0f - __log2f((float)u)) * in.xhint[p];
+        c = est <= 0.0f ? 0 : (est >= (float)H ? H : (int)est);
+    }
+    while (c > 0 && tab[c] <= u) --c;
+    while (c < H && tab[c + 1] > u) ++c;
+    return c;
+}
+
+struct CellRegs {
+    uint32_t jin[4], jud[4];
+    int own, opp, mn, pl;   // word offsets inside one buffer
+    uint32_t gidx;          // natural group index i >> 2 of the group
+};
+
+__device__ __forceinline__ void load_cell(const InstDesc& in, int q, int col, int L2, int L,
+                                          CellRegs& cr)
+{
+    const uint32_t* jw = in.jw + (q * 2 + col) * 8;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        cr.jin[k] = jw[k];
+        cr.jud[k] = jw[4 + k];
+    }
+    const int r = q / L, c = q - r * L;
+    const int u = (r + c + col) & 1;
+    cr.gidx = (uint32_t)(2 * q + u);
+    cr.own = col * L2 + q;
+    cr.opp = (1 - col) * L2 + q;
+    cr.mn = (1 - col) * L2 + in.nbr[(q * 2 + col) * 2 + 0];
+    cr.pl = (1 - col) * L2 + in.nbr[(q * 2 + col) * 2 + 1];
+}
+
+__device__ __forceinline__ void apply_packed(int32_t* Es, uint32_t* macc, int t, int v)
+{
+    const int na = v & 255;
+    const int dk = (v - na) >> 8;
+    if (dk) atomicAdd(&Es[t], 2 * dk);
+    if (na) atomicAdd(&macc[t], (uint32_t)na);
+}
+
+// One Metropolis half-sweep (one colour) over this thread's slots.
+__device__ __forceinline__ void colour_phase(const CellRegs& cr, uint32_t* sw, int NW,
+                                             const uint32_t* thr_sm, int32_t* Es, uint32_t* macc,
+                                             const uint8_t* perm, int NT, int SP, int sp,
+                                             int iters, uint32_t s, uint32_t runbits,
+                                             uint32_t k0, uint32_t k1, bool warp_reduce,
+                                             bool seg_lo, int lane, int lane_hi, int sp_first)
+{
+    for (int i = 0; i < iters; ++i) {
+        const int t = sp + i * SP;
+        int packed = 0;
+        if (t < NT) {
+            uint32_t* bw = sw + perm[t] * NW;
+            const uint32_t own = bw[cr.own];
+            const int opp = (int)bw[cr.opp];
+            const uint32_t mw = bw[cr.mn], pw = bw[cr.pl];
+            const uint4 rn = philox10(s, runbits | (uint32_t)t, cr.gidx, 0u, k0, k1);
+            const uint32_t* th = thr_sm + t * KT;
+            const int x01 = (int)__byte_perm(mw, pw, 0x5140);
+            const int x23 = (int)__byte_perm(mw, pw, 0x7362);
+            // -h_i for the 4 spins (couplers are stored negated)
+            const int h0 = __dp4a((int)cr.jin[0], opp, __dp4a((int)cr.jud[0], x01, 0));
+            const int h1 = __dp4a((int)cr.jin[1], opp, __dp4a((int)cr.jud[1], x01, 0));
+            const int h2 = __dp4a((int)cr.jin[2], opp, __dp4a((int)cr.jud[2], x23, 0));
+            const int h3 = __dp4a((int)cr.jin[3], opp, __dp4a((int)cr.jud[3], x23, 0));
+            // k_i = -s_i h_i, dE = 2 k_i; accept if k_i <= 0 or u < thr[slot][k_i]
+            const int kk0 = (int)(int8_t)(own) * h0;
+            const int kk1 = (int)(int8_t)(own >> 8) * h1;
+            const int kk2 = (int)(int8_t)(own >> 16) * h2;
+            const int kk3 = (int)(int8_t)(own >> 24) * h3;
+            const bool a0 = (kk0 <= 0) | (rn.x < th[max(kk0, 0)]);
+            const bool a1 = (kk1 <= 0) | (rn.y < th[max(kk1, 0)]);
+            const bool a2 = (kk2 <= 0) | (rn.z < th[max(kk2, 0)]);
+            const bool a3 = (kk3 <= 0) | (rn.w < th[max(kk3, 0)]);
+            const uint32_t flip = (a0 ? 0x000000FEu : 0u) | (a1 ? 0x0000FE00u : 0u) |
+                                  (a2 ? 0x00FE0000u : 0u) | (a3 ? 0xFE000000u : 0u);
+            const int dk = (a0 ? kk0 : 0) + (a1 ? kk1 : 0) + (a2 ? kk2 : 0) + (a3 ? kk3 : 0);
+            const int na = (int)a0 + (int)a1 + (int)a2 + (int)a3;
+            if (flip) bw[cr.own] = own ^ flip;
+            packed = dk * 256 + na;
+        }
+        if (warp_reduce) {
+            const int lo = __reduce_add_sync(FULL, seg_lo ? packed : 0);
+            const int hi = __reduce_add_sync(FULL, seg_lo ? 0 : packed);
+            if (lane == 0 && lo) apply_packed(Es, macc, sp_first + i * SP, lo);
+            if (lane == lane_hi && hi) apply_packed(Es, macc, sp_first + 1 + i * SP, hi);
+        } else if (packed) {
+            apply_packed(Es, macc, t, packed);
+        }
+    }
+}
+
+__device__ void process_bundle(const InstDesc* __restrict__ insts, const Bundle bd,
+                               uint32_t sweep0, int nsweeps, int xevery, int mode,
+                               unsigned char* smem)
+{
+    const InstDesc& in = insts[bd.inst];
+    const int L = in.L, NT = in.NT, L2 = L * L, N = 8 * L2, NW = N / 4;
+    const int SP = bd.sp, TPI = SP * L2;
+    const int tid = threadIdx.x;
+    const int item = tid / TPI, j = tid - item * TPI;
+    const bool active = item < bd.nitems;
+    const int q = j % L2, sp = j / L2;
+    const int run = bd.run0 + (active ? item : 0);
+    const ItemLayout lay = item_layout(L, NT);
+
+    uint32_t* thr_sm = reinterpret_cast<uint32_t*>(smem);
+    unsigned char* ib = smem + table_bytes(NT) + (active ? item : 0) * lay.bytes;
+    uint32_t* sw = reinterpret_cast<uint32_t*>(ib + lay.spins);
+    int32_t* Es = reinterpret_cast<int32_t*>(ib + lay.E);
+    int32_t* ccrit = reinterpret_cast<int32_t*>(ib + lay.ccrit);
+    uint32_t* macc = reinterpret_cast<uint32_t*>(ib + lay.macc);
+    uint32_t* xacc = reinterpret_cast<uint32_t*>(ib + lay.xacc);
+    uint8_t* perm = ib + lay.perm;
+    int32_t* misc = reinterpret_cast<int32_t*>(ib + lay.misc);
+
+    // ---- load the instance table and this bundle's runs into shared memory
+    for (int w = tid; w < NT * KT; w += blockDim.x) thr_sm[w] = in.thr[w];
+    const size_t rep0 = (size_t)run * NT;
+    if (active) {
+        const uint32_t* gsp = reinterpret_cast<const uint32_t*>(in.spins + rep0 * N);
+        for (int w = j; w < NT * NW; w += TPI) {
+            const int buf = w / NW, g = w - buf * NW;
+            const int cell = g >> 1, u = g & 1, r = cell / L, c = cell - r * L;
+            sw[buf * NW + ((r + c + u) & 1) * L2 + cell] = gsp[w];
+        }
+        for (int t = j; t < NT; t += TPI) {
+            Es[t] = in.E[rep0 + t];
+            perm[t] = in.perm[rep0 + t];
+            macc[t] = 0u;
+            xacc[t] = 0u;
+        }
+        if (j == 0) {
+            misc[0] = in.best[run];
+            misc[1] = in.first[run];
+        }
+    }
+
+    CellRegs c0r, c1r;
+    if (active) {
+        load_cell(in, q, 0, L2, L, c0r);
+        load_cell(in, q, 1, L2, L, c1r);
+    }
+    const int lane = tid & 31;
+    const int sp_first = __shfl_sync(FULL, sp, 0);
+    const bool seg_lo = (sp == sp_first);
+    const unsigned hi_mask = __ballot_sync(FULL, !seg_lo);
+    const int lane_hi = hi_mask ? __ffs(hi_mask) - 1 : 32;
+    // redux path needs every warp to span at most two slots (checked per shape)
+    const bool warp_reduce = (L2 >= 32) || (L2 == 16);
+    const int iters = (NT + SP - 1) / SP;
+    const uint32_t k0 = in.seed, k1 = in.uid;
+    const uint32_t runbits = (uint32_t)run << 16;
+    __syncthreads();
+
+    const int n_iter = (mode == 0) ? nsweeps : 1;
+    for (int it = 0; it < n_iter; ++it) {
+        const uint32_t s = (mode == 0) ? sweep0 + (uint32_t)it + 1u : sweep0;
+        const bool do_x = (NT > 1) && ((mode == 1) || (xevery > 0 && (s % (uint32_t)xevery) == 0u));
+        if (do_x && active && j < 32) {
+            const int npairs = NT - 1;
+            for (int call = j; call * 4 < npairs; call += 32) {
+                const uint4 w = philox10(s, runbits, (uint32_t)call, 1u, k0, k1);
+                const uint32_t wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int p = call * 4 + e;
+                    if (p < npairs) ccrit[p] = critical_half_gap(in, p, wv[e]);
+                }
+            }
+        }
+        if (mode == 0) {
+            if (active)
+                colour_phase(c0r, sw, NW, thr_sm, Es, macc, perm, NT, SP, sp, iters, s, runbits,
+                             k0, k1, warp_reduce, seg_lo, lane, lane_hi, sp_first);
+            __syncthreads();
+            if (active)
+                colour_phase(c1r, sw, NW, thr_sm, Es, macc, perm, NT, SP, sp, iters, s, runbits,
+                             k0, k1, warp_reduce, seg_lo, lane, lane_hi, sp_first);
+        }
+        __syncthreads();
+        if (active && j == 0) {
+            int m;
+            if (do_x) {
+                int cb = perm[0], ce = Es[0];
+                m = ce;
+                for (int p = 0; p < NT - 1; ++p) {
+                    const int nb = perm[p + 1], ne = Es[p + 1], c2 = 2 * ccrit[p];
+                    m = min(m, ne);
+                    if (ne - ce <= c2) {            // swap: the carried configuration moves up
+                        perm[p] = (uint8_t)nb;
+                        Es[p] = ne;
+                        xacc[p] += 1u;
+                    } else {
+                        perm[p] = (uint8_t)cb;
+                        Es[p] = ce;
+                        cb = nb;
+                        ce = ne;
+                    }
+                }
+                perm[NT - 1] = (uint8_t)cb;
+                Es[NT - 1] = ce;
+            } else {
+                m = Es[0];
+                for (int p = 1; p < NT; ++p) m = min(m, Es[p]);
+            }
+            if (mode == 0 && m < misc[0]) {
+                misc[0] = m;
+                misc[1] = (int32_t)s;
+            }
+        }
+        __syncthreads();
+    }
+
+    // ---- write the state back
+    if (active) {
+        uint32_t* gsp = reinterpret_cast<uint32_t*>(in.spins + rep0 * N);
+        for (int w = j; w < NT * NW; w += TPI) {
+            const int buf = w / NW, g = w - buf * NW;
+            const int cell = g >> 1, u = g & 1, r = cell / L, c = cell - r * L;
+            gsp[w] = sw[buf * NW + ((r + c + u) & 1) * L2 + cell];
+        }
+        for (int t = j; t < NT; t += TPI) {
+            in.E[rep0 + t] = Es[t];
+            in.perm[rep0 + t] = perm[t];
+            in.macc[rep0 + t] += macc[t];
+            if (t < NT - 1) in.xacc[(size_t)run * (NT > 1 ? NT - 1 : 1) + t] += xacc[t];
+        }
+        if (j == 0) {
+            in.best[run] = misc[0];
+            in.first[run] = misc[1];
+        }
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(MAX_THREADS)
+pt_sweep_kernel(const InstDesc* __restrict__ insts, const Bundle* __restrict__ bundles,
+                int nbundles, uint32_t sweep0, int nsweeps, int xevery, int mode,
+                int* __restrict__ queue)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_next;
+    int b = blockIdx.x;
+    if (queue) {
+        if (threadIdx.x == 0) s_next = atomicAdd(queue, 1);
+        __syncthreads();
+        b = s_next;
+    }
+    while (b < nbundles) {
+        process_bundle(insts, bundles[b], sweep0, nsweeps, xevery, mode, smem);
+        if (!queue) break;
+        if (threadIdx.x == 0) s_next = atomicAdd(queue, 1);
+        __syncthreads();
+        b = s_next;
+        __syncthreads();
+    }
+}
+
+// Initial spins from the kind-2 stream (counter (0, run << 16 | slot, group, 2)),
+// identity slot map, zero counters.  One block per (instance, run).
+__global__ void pt_init_kernel(const InstDesc* __restrict__ insts, const int2* __restrict__ items,
+                               int draw)
+{
+    const int2 it = items[blockIdx.x];
+    const InstDesc& in = insts[it.x];
+    const int run = it.y, NT = in.NT, NW = 2 * in.L * in.L;
+    const size_t rep0 = (size_t)run * NT;
+    if (draw) {
+        uint32_t* gsp = reinterpret_cast<uint32_t*>(in.spins + rep0 * 8 * in.L * in.L);
+        for (int w = threadIdx.x; w < NT * NW; w += blockDim.x) {
+            const int slot = w / NW, g = w - slot * NW;
+            const uint4 r = philox10(0u, ((uint32_t)run << 16) | (uint32_t)slot, (uint32_t)g, 2u,
+                                     in.seed, in.uid);
+            gsp[w] = ((r.x >> 31) ? 0x000000FFu : 0x00000001u) |
+                     ((r.y >> 31) ? 0x0000FF00u : 0x00000100u) |
+                     ((r.z >> 31) ? 0x00FF0000u : 0x00010000u) |
+                     ((r.w >> 31) ? 0xFF000000u : 0x01000000u);
+        }
+    }
+    for (int t = threadIdx.x; t < NT; t += blockDim.x) {
+        in.perm[rep0 + t] = (uint8_t)t;
+        in.macc[rep0 + t] = 0ull;
+        if (t < NT - 1) in.xacc[(size_t)run * (NT - 1) + t] = 0ull;
+    }
+}
+
+// Full energies of every slot (Eq. 1 summed over the colour-0 endpoint of each
+// coupler), best = min over slots, first = `first_value`.  One block per
+// (instance, run), one warp per slot.
+__global__ void pt_energy_kernel(const InstDesc* __restrict__ insts, const int2* __restrict__ items,
+                                 int32_t first_value)
+{
+    const int2 it = items[blockIdx.x];
+    const InstDesc& in = insts[it.x];
+    const int run = it.y, NT = in.NT, L = in.L, L2 = L * L;
+    const size_t rep0 = (size_t)run * NT;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    __shared__ int s_min;
+    if (threadIdx.x == 0) s_min = INT32_MAX;
+    __syncthreads();
+    for (int t = warp; t < NT; t += nwarps) {
+        const int buf = in.perm[rep0 + t];
+        const uint32_t* w = reinterpret_cast<const uint32_t*>(in.spins + (rep0 + buf) * 8 * L2);
+        int acc = 0;
+        for (int q = lane; q < L2; q += 32) {
+            const int r = q / L, c = q - r * L, u = (r + c) & 1;      // colour-0 group of cell q
+            const uint32_t* jw = in.jw + (q * 2 + 0) * 8;
+            const uint32_t own = w[2 * q + u];
+            const int opp = (int)w[2 * q + (1 - u)];
+            const uint32_t mw = w[2 * in.nbr[(q * 2) * 2 + 0] + u];
+            const uint32_t pw = w[2 * in.nbr[(q * 2) * 2 + 1] + u];
+            const int x01 = (int)__byte_perm(mw, pw, 0x5140), x23 = (int)__byte_perm(mw, pw, 0x7362);
+            const int h0 = __dp4a((int)jw[0], opp, __dp4a((int)jw[4], x01, 0));
+            const int h1 = __dp4a((int)jw[1], opp, __dp4a((int)jw[5], x01, 0));
+            const int h2 = __dp4a((int)jw[2], opp, __dp4a((int)jw[6], x23, 0));
+            const int h3 = __dp4a((int)jw[3], opp, __dp4a((int)jw[7], x23, 0));
+            acc -= (int)(int8_t)own * h0 + (int)(int8_t)(own >> 8) * h1 +
+                   (int)(int8_t)(own >> 16) * h2 + (int)(int8_t)(own >> 24) * h3;
+        }
+        const int e = __reduce_add_sync(FULL, acc);
+        if (lane == 0) {
+            in.E[rep0 + t] = e;
+            atomicMin(&s_min, e);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        in.best[run] = s_min;
+        in.first[run] = first_value;
+    }
+}
+
+// Time to solution per instance: target = explicit or min best, hit if
+// best <= target and first <= horizon, lower median (rank ceil(R/2)) of hit
+// sweeps with misses as +inf, horizon + 1 when unsolved.  One block per instance.
+__global__ void pt_tts_kernel(const InstDesc* __restrict__ insts, int32_t target, int32_t horizon,
+                              int32_t* __restrict__ out)
+{
+    const InstDesc& in = insts[blockIdx.x];
+    const int R = in.R;
+    __shared__ long long v[1024];
+    __shared__ int s_min, s_hits;
+    __shared__ long long s_med;
+    const long long INF = 0x7FFFFFFFFFFFFFFFll;
+    if (threadIdx.x == 0) {
+        s_min = INT32_MAX;
+        s_hits = 0;
+        s_med = INF;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < R; r += blockDim.x) atomicMin(&s_min, in.best[r]);
+    __syncthreads();
+    const int T = (target == INT32_MAX) ? s_min : target;
+    for (int r = threadIdx.x; r < R; r += blockDim.x) {
+        const bool hit = in.best[r] <= T && in.first[r] <= horizon;
+        v[r] = hit ? (long long)in.first[r] : INF;
+        if (hit) atomicAdd(&s_hits, 1);
+    }
+    __syncthreads();
+    const int m = (R + 1) / 2 - 1;
+    for (int r = threadIdx.x; r < R; r += blockDim.x) {
+        int rank = 0;
+        for (int x = 0; x < R; ++x) rank += (v[x] < v[r]) || (v[x] == v[r] && x < r);
+        if (rank == m) s_med = v[r];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        out[blockIdx.x * 3 + 0] = (s_med == INF) ? horizon + 1 : (int32_t)s_med;
+        out[blockIdx.x * 3 + 1] = s_hits;
+        out[blockIdx.x * 3 + 2] = T;
+    }
+}
+
+}  // namespace
+
+cudaError_t set_sweep_smem_limit(int bytes)
+{
+    return cudaFuncSetAttribute(pt_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+cudaError_t launch_init(const InstDesc* insts, const int2* items, int nitems, bool draw,
+                        cudaStream_t st)
+{
+    if (nitems <= 0) return cudaSuccess;
+    pt_init_kernel<<<nitems, 256, 0, st>>>(insts, items, draw ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_energy(const InstDesc* insts, const int2* items, int nitems, int32_t first_value,
+                          cudaStream_t st)
+{
+    if (nitems <= 0) return cudaSuccess;
+    pt_energy_kernel<<<nitems, 256, 0, st>>>(insts, items, first_value);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweeps(const InstDesc* insts, const Bundle* bundles, int nbundles, int grid,
+                          int block, int smem_bytes, uint32_t sweep0, int nsweeps, int xevery,
+                          int mode, int* queue, cudaStream_t st)
+{
+    if (nbundles <= 0) return cudaSuccess;
+    pt_sweep_kernel<<<grid, block, smem_bytes, st>>>(insts, bundles, nbundles, sweep0, nsweeps,
+                                                     xevery, mode, queue);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tts(const InstDesc* insts, int ninst, int32_t target, int32_t horizon,
+                       int32_t* out, cudaStream_t st)
+{
+    if (ninst <= 0) return cudaSuccess;
+    pt_tts_kernel<<<ninst, 256, 0, st>>>(insts, target, horizon, out);
+    return cudaGetLastError();
+}
+
+}  // namespace ptg

@@ -1,0 +1,21 @@
+// pt_kernels.h -- launchers of the sm_103a kernels (library-private).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "pt_internal.h"
+
+namespace ptg {
+
+cudaError_t set_sweep_smem_limit(int bytes);
+cudaError_t launch_init(const InstDesc* insts, const int2* items, int nitems, bool draw,
+                        cudaStream_t st);
+cudaError_t launch_energy(const InstDesc* insts, const int2* items, int nitems, int32_t first_value,
+                          cudaStream_t st);
+// mode 0: nsweeps sweeps s = sweep0+1..; mode 1: one exchange sweep with counter sweep0.
+cudaError_t launch_sweeps(const InstDesc* insts, const Bundle* bundles, int nbundles, int grid,
+                          int block, int smem_bytes, uint32_t sweep0, int nsweeps, int xevery,
+                          int mode, int* queue, cudaStream_t st);
+cudaError_t launch_tts(const InstDesc* insts, int ninst, int32_t target, int32_t horizon,
+                       int32_t* out, cudaStream_t st);
+
+}  // namespace ptg
