@@ -308,8 +308,37 @@ def run_gpu(args):
     return 0
 
 
+def run_profile_case(args):
+    """A fixed, small sequence of sweep-kernel launches on the bench instance
+    (for ncu captures): fresh runs, then `profile_sweeps` launches of
+    sweeps_per_launch sweeps each, through pt_sweep."""
+    import paper_1605_03607_gb300 as P
+    from paper_1605_03607_gb300 import build as B
+    B.build()
+    cfg = workload()
+    J = W.random_couplers(cfg["L"], cfg["seed"], 0)
+    betas = W.beta_ladder(cfg["n_temps"], cfg["beta_min"], cfg["beta_max"])
+    h = P.PTHandle(cfg["L"], J, betas, cfg["n_runs"] * args.profile_instances, cfg["seed"], 0)
+    if args.schedule:
+        h.set_schedule(*[int(x) for x in args.schedule.split(",")])
+    spl = h.schedule()[2]
+    h.set_timing(True)
+    for _ in range(args.profile_sweeps):
+        h.sweep(spl, cfg["exchange_every"])
+    ms, n = h.sweep_timing_total()
+    att = args.profile_sweeps * spl * h.R * h.NT * h.N
+    print(json.dumps({"profile_case": True, "launches": n, "ms": ms, "attempts_per_s": att / (ms / 1e3),
+                      "runs": h.R, "schedule": list(h.schedule())}))
+    h.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--profile-sweeps", type=int, default=0,
+                    help="profiling case: this many sweep launches on the bench instance, then exit")
+    ap.add_argument("--profile-instances", type=int, default=4,
+                    help="profiling case: runs = 64 x this (as many runs as a speculative batch)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=3)
@@ -323,6 +352,8 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_sweeps > 0:
+        return run_profile_case(args)
     return run_gpu(args)
 
 

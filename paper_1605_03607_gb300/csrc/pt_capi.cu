@@ -340,7 +340,10 @@ int group_schedule(pt_handle* h, Group& g)
     CK(dalloc(&g.d_bundles, g.bundles.size()), "cudaMalloc bundles");
     CK(cudaMemcpyAsync(g.d_bundles, g.bundles.data(), sizeof(Bundle) * g.bundles.size(),
                        cudaMemcpyHostToDevice, h->stream), "upload bundles");
-    CK(set_sweep_smem_limit(227 * 1024), "cudaFuncSetAttribute");
+    int cap = 0;
+    CK(sweep_smem_capacity(&cap), "shared memory capacity");
+    if (g.smem > cap) return fail(h, PT_ERR_ARG, "bundle needs more shared memory than a CTA can have");
+    CK(set_sweep_smem_limit(cap), "cudaFuncSetAttribute");
     return PT_OK;
 }
 

@@ -439,6 +439,20 @@ __global__ void pt_tts_kernel(const InstDesc* __restrict__ insts, int32_t target
 
 }  // namespace
 
+cudaError_t sweep_smem_capacity(int* bytes)
+{
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, pt_sweep_kernel);
+    if (e != cudaSuccess) return e;
+    *bytes = optin - (int)fa.sharedSizeBytes;
+    return cudaSuccess;
+}
+
 cudaError_t set_sweep_smem_limit(int bytes)
 {
     return cudaFuncSetAttribute(pt_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);

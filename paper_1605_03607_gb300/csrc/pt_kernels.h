@@ -6,6 +6,8 @@
 
 namespace ptg {
 
+// Largest dynamic shared memory a sweep-kernel CTA may request on the current device.
+cudaError_t sweep_smem_capacity(int* bytes);
 cudaError_t set_sweep_smem_limit(int bytes);
 cudaError_t launch_init(const InstDesc* insts, const int2* items, int nitems, bool draw,
                         cudaStream_t st);

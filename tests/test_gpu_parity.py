@@ -94,7 +94,7 @@ def test_sweeps_bit_exact(P, L, NT, R, n, x, sched):
 
 def test_schedule_and_split_invariance(P):
     outs = []
-    for sched in ((0, 0, 4096), (2, 1, 1), (8, 4, 13), (16, 8, 64)):
+    for sched in ((0, 0, 4096), (2, 1, 1), (8, 4, 13), (16, 4, 64)):
         h, _, _, _ = _pair(P, 4, 16, 8, seed=5, uid=9)
         h.set_schedule(*sched)
         h.sweep(97, 1)
