@@ -51,7 +51,7 @@ struct Bundle {
 
 // Shared-memory layout of one bundle: the Metropolis table of the instance,
 // then per item (run): spins [NT][N] (colour-major words per buffer), E by slot,
-// exchange critical h by pair, flip / swap counters, perm, best/first.
+// exchange critical h by pair (two sweeps), flip / swap counters, perm, best/first.
 struct ItemLayout {
     int64_t spins, E, ccrit, macc, xacc, perm, misc, bytes;
 };
@@ -65,7 +65,7 @@ __host__ __device__ inline ItemLayout item_layout(int L, int NT)
     o.spins = 0;
     o.E = pad16((int64_t)NT * N);
     o.ccrit = o.E + 4LL * NT;
-    o.macc = o.ccrit + 4LL * NT;
+    o.macc = o.ccrit + 8LL * NT;
     o.xacc = o.macc + 4LL * NT;
     o.perm = o.xacc + 4LL * NT;
     o.misc = pad16(o.perm + NT);

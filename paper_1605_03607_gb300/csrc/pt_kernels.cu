@@ -25,6 +25,7 @@
 
 #include "pt_internal.h"
 #include "pt_kernels.h"
+#include "pt_philox.cuh"
 
 namespace ptg {
 
@@ -32,30 +33,11 @@ namespace {
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
-// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two
-// 32x32->64 multiplies and a Weyl-sequence key schedule.
-__device__ __forceinline__ uint4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                          uint32_t k0, uint32_t k1)
-{
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
-        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
-        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
-        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
-        c1 = (uint32_t)p1;
-        c3 = (uint32_t)p0;
-        c0 = n0;
-        c2 = n2;
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-    return make_uint4(c0, c1, c2, c3);
-}
-
 // Largest h in [0, H_p] with xthr[p][h'] > u for all 1 <= h' <= h: a swap with
 // energy gap d = 2h > 0 is accepted iff h <= c_p.  Exact for any start point
-// because the table is non-increasing in h (checked on the host).
+// because the table is non-increasing in h (checked on the host); the float
+// estimate only picks where the exact search starts, and both neighbours of
+// the estimate are loaded at once.
 __device__ __forceinline__ int critical_half_gap(const InstDesc& in, int p, uint32_t u)
 {
     const int o = in.xoff[p];
@@ -66,8 +48,15 @@ __device__ __forceinline__ int critical_half_gap(const InstDesc& in, int p, uint
         const float est = (32.0f - __log2f((float)u)) * in.xhint[p];
         c = est <= 0.0f ? 0 : (est >= (float)H ? H : (int)est);
     }
-    while (c > 0 && tab[c] <= u) --c;
-    while (c < H && tab[c + 1] > u) ++c;
+    const uint32_t at = c > 0 ? tab[c] : 0xFFFFFFFFu;
+    const uint32_t above = c < H ? tab[c + 1] : 0u;
+    if (c > 0 && at <= u) {
+        --c;
+        while (c > 0 && tab[c] <= u) --c;
+    } else if (c < H && above > u) {
+        ++c;
+        while (c < H && tab[c + 1] > u) ++c;
+    }
     return c;
 }
 
@@ -95,22 +84,32 @@ __device__ __forceinline__ void load_cell(const InstDesc& in, int q, int col, in
     cr.pl = (1 - col) * L2 + in.nbr[(q * 2 + col) * 2 + 1];
 }
 
+// Per-lane result of one group update, packed for one warp reduction:
+// (sum of accepted k) * 1024 + popcount of the flip mask (7 bits per flip).
 __device__ __forceinline__ void apply_packed(int32_t* Es, uint32_t* macc, int t, int v)
 {
-    const int na = v & 255;
-    const int dk = (v - na) >> 8;
+    const int pc = v & 1023;
+    const int dk = (v - pc) >> 10;
     if (dk) atomicAdd(&Es[t], 2 * dk);
-    if (na) atomicAdd(&macc[t], (uint32_t)na);
+    if (pc) atomicAdd(&macc[t], (uint32_t)(pc / 7));
 }
+
+struct WarpSeg {
+    bool two;        // the warp's lanes cover two slots
+    bool lo;         // this lane belongs to the first of them
+    int lane_hi;     // first lane of the second slot
+    int sp_first;    // slot phase of lane 0
+    bool redux;      // warp reduction usable (at most two slots per warp)
+};
 
 // One Metropolis half-sweep (one colour) over this thread's slots.
 __device__ __forceinline__ void colour_phase(const CellRegs& cr, uint32_t* sw, int NW,
                                              const uint32_t* thr_sm, int32_t* Es, uint32_t* macc,
                                              const uint8_t* perm, int NT, int SP, int sp,
                                              int iters, uint32_t s, uint32_t runbits,
-                                             uint32_t k0, uint32_t k1, bool warp_reduce,
-                                             bool seg_lo, int lane, int lane_hi, int sp_first)
+                                             uint32_t k0, uint32_t k1, const WarpSeg& ws, int lane)
 {
+    const PhiloxPre pre = philox_pre(s, cr.gidx, k0, k1);
     for (int i = 0; i < iters; ++i) {
         const int t = sp + i * SP;
         int packed = 0;
@@ -119,7 +118,7 @@ __device__ __forceinline__ void colour_phase(const CellRegs& cr, uint32_t* sw, i
             const uint32_t own = bw[cr.own];
             const int opp = (int)bw[cr.opp];
             const uint32_t mw = bw[cr.mn], pw = bw[cr.pl];
-            const uint4 rn = philox10(s, runbits | (uint32_t)t, cr.gidx, 0u, k0, k1);
+            const uint4 rn = philox_slot(pre, runbits | (uint32_t)t, k0, k1);
             const uint32_t* th = thr_sm + t * KT;
             const int x01 = (int)__byte_perm(mw, pw, 0x5140);
             const int x23 = (int)__byte_perm(mw, pw, 0x7362);
@@ -137,22 +136,108 @@ __device__ __forceinline__ void colour_phase(const CellRegs& cr, uint32_t* sw, i
             const bool a1 = (kk1 <= 0) | (rn.y < th[max(kk1, 0)]);
             const bool a2 = (kk2 <= 0) | (rn.z < th[max(kk2, 0)]);
             const bool a3 = (kk3 <= 0) | (rn.w < th[max(kk3, 0)]);
-            const uint32_t flip = (a0 ? 0x000000FEu : 0u) | (a1 ? 0x0000FE00u : 0u) |
-                                  (a2 ? 0x00FE0000u : 0u) | (a3 ? 0xFE000000u : 0u);
-            const int dk = (a0 ? kk0 : 0) + (a1 ? kk1 : 0) + (a2 ? kk2 : 0) + (a3 ? kk3 : 0);
-            const int na = (int)a0 + (int)a1 + (int)a2 + (int)a3;
+            uint32_t flip = 0u;
+            int dk = 0;
+            if (a0) { flip |= 0x000000FEu; dk += kk0; }
+            if (a1) { flip |= 0x0000FE00u; dk += kk1; }
+            if (a2) { flip |= 0x00FE0000u; dk += kk2; }
+            if (a3) { flip |= 0xFE000000u; dk += kk3; }
             if (flip) bw[cr.own] = own ^ flip;
-            packed = dk * 256 + na;
+            packed = dk * 1024 + __popc(flip);
         }
-        if (warp_reduce) {
-            const int lo = __reduce_add_sync(FULL, seg_lo ? packed : 0);
-            const int hi = __reduce_add_sync(FULL, seg_lo ? 0 : packed);
-            if (lane == 0 && lo) apply_packed(Es, macc, sp_first + i * SP, lo);
-            if (lane == lane_hi && hi) apply_packed(Es, macc, sp_first + 1 + i * SP, hi);
+        if (ws.redux) {
+            if (ws.two) {
+                const int lo = __reduce_add_sync(FULL, ws.lo ? packed : 0);
+                const int hi = __reduce_add_sync(FULL, ws.lo ? 0 : packed);
+                if (lane == 0 && lo) apply_packed(Es, macc, ws.sp_first + i * SP, lo);
+                if (lane == ws.lane_hi && hi) apply_packed(Es, macc, ws.sp_first + 1 + i * SP, hi);
+            } else {
+                const int v = __reduce_add_sync(FULL, packed);
+                if (lane == 0 && v) apply_packed(Es, macc, ws.sp_first + i * SP, v);
+            }
         } else if (packed) {
             apply_packed(Es, macc, t, packed);
         }
     }
+}
+
+// Exchange critical gaps of every pair of this run for sweep counter s
+// (called by one warp; lane l handles pairs 4l..4l+3 from one Philox call).
+__device__ __forceinline__ void exchange_prepare(const InstDesc& in, int lane, uint32_t s,
+                                                 uint32_t runbits, uint32_t k0, uint32_t k1,
+                                                 int NT, int32_t* cc)
+{
+    const int npairs = NT - 1;
+    for (int call = lane; call * 4 < npairs; call += 32) {
+        const uint4 w = philox10(s, runbits, (uint32_t)call, 1u, k0, k1);
+        const uint32_t wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int p = call * 4 + e;
+            if (p < npairs) cc[p] = critical_half_gap(in, p, wv[e]);
+        }
+    }
+}
+
+// The ascending exchange sweep of one run (one thread): a configuration that
+// wins pair p is carried on to pair p+1.  Slot energies, slot map and
+// acceptance criteria are read in blocks of 4 ahead of the carried chain.
+__device__ __forceinline__ int exchange_chain(int32_t* Es, uint8_t* perm, uint32_t* xacc,
+                                              const int32_t* cc, int NT)
+{
+    constexpr int B = 4;
+    const int np = NT - 1;
+    int ce = Es[0], cb = perm[0], m = ce;
+    int nxe[B], nxb[B], nxt[B];
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+        const bool v = i < np;
+        nxe[i] = v ? Es[i + 1] : 0;
+        nxb[i] = v ? perm[i + 1] : 0;
+        nxt[i] = v ? nxe[i] - 2 * cc[i] : 0;
+    }
+    for (int p0 = 0; p0 < np; p0 += B) {
+        int ne[B], nb[B], tt[B];
+#pragma unroll
+        for (int i = 0; i < B; ++i) {
+            ne[i] = nxe[i];
+            nb[i] = nxb[i];
+            tt[i] = nxt[i];
+        }
+#pragma unroll
+        for (int i = 0; i < B; ++i) {            // prefetch: indices > p0+B, never stored below
+            const int q = p0 + B + i;
+            const bool v = q < np;
+            nxe[i] = v ? Es[q + 1] : 0;
+            nxb[i] = v ? perm[q + 1] : 0;
+            nxt[i] = v ? nxe[i] - 2 * cc[q] : 0;
+        }
+        int oe[B], ob[B];
+        unsigned bits = 0u;
+#pragma unroll
+        for (int i = 0; i < B; ++i) {
+            if (p0 + i < np) {
+                m = min(m, ne[i]);
+                const bool a = tt[i] <= ce;          // E_{p+1} - E_p <= 2 c_p
+                oe[i] = a ? ne[i] : ce;
+                ob[i] = a ? nb[i] : cb;
+                ce = a ? ce : ne[i];
+                cb = a ? cb : nb[i];
+                bits |= (unsigned)a << i;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < B; ++i) {
+            if (p0 + i < np) {
+                Es[p0 + i] = oe[i];
+                perm[p0 + i] = (uint8_t)ob[i];
+                xacc[p0 + i] += (bits >> i) & 1u;
+            }
+        }
+    }
+    Es[np] = ce;
+    perm[np] = (uint8_t)cb;
+    return m;
 }
 
 __device__ void process_bundle(const InstDesc* __restrict__ insts, const Bundle bd,
@@ -173,7 +258,7 @@ __device__ void process_bundle(const InstDesc* __restrict__ insts, const Bundle 
     unsigned char* ib = smem + table_bytes(NT) + (active ? item : 0) * lay.bytes;
     uint32_t* sw = reinterpret_cast<uint32_t*>(ib + lay.spins);
     int32_t* Es = reinterpret_cast<int32_t*>(ib + lay.E);
-    int32_t* ccrit = reinterpret_cast<int32_t*>(ib + lay.ccrit);
+    int32_t* ccrit = reinterpret_cast<int32_t*>(ib + lay.ccrit);     // 2 x NT, by sweep parity
     uint32_t* macc = reinterpret_cast<uint32_t*>(ib + lay.macc);
     uint32_t* xacc = reinterpret_cast<uint32_t*>(ib + lay.xacc);
     uint8_t* perm = ib + lay.perm;
@@ -201,70 +286,52 @@ __device__ void process_bundle(const InstDesc* __restrict__ insts, const Bundle 
         }
     }
 
-    CellRegs c0r, c1r;
-    if (active) {
-        load_cell(in, q, 0, L2, L, c0r);
-        load_cell(in, q, 1, L2, L, c1r);
-    }
+    // couplers of the colour about to be updated; the other colour's are
+    // loaded right after each phase so the load latency hides behind the barrier
+    CellRegs cr;
+    if (active) load_cell(in, q, 0, L2, L, cr);
     const int lane = tid & 31;
-    const int sp_first = __shfl_sync(FULL, sp, 0);
-    const bool seg_lo = (sp == sp_first);
-    const unsigned hi_mask = __ballot_sync(FULL, !seg_lo);
-    const int lane_hi = hi_mask ? __ffs(hi_mask) - 1 : 32;
-    // redux path needs every warp to span at most two slots (checked per shape)
-    const bool warp_reduce = (L2 >= 32) || (L2 == 16);
+    WarpSeg ws;
+    ws.sp_first = __shfl_sync(FULL, sp, 0);
+    ws.lo = (sp == ws.sp_first);
+    const unsigned hi_mask = __ballot_sync(FULL, !ws.lo);
+    ws.two = hi_mask != 0u;
+    ws.lane_hi = ws.two ? __ffs(hi_mask) - 1 : 32;
+    ws.redux = (L2 >= 32) || (L2 == 16);       // then no warp spans more than two slots
     const int iters = (NT + SP - 1) / SP;
     const uint32_t k0 = in.seed, k1 = in.uid;
     const uint32_t runbits = (uint32_t)run << 16;
+    const int prep_warp_j0 = TPI - 32;          // last warp of the run prepares exchanges
+    auto exch = [&](uint32_t sw_) {
+        return (NT > 1) && ((mode == 1) || (xevery > 0 && (sw_ % (uint32_t)xevery) == 0u));
+    };
+    const int n_iter = (mode == 0) ? nsweeps : 1;
+    const uint32_t s_first = (mode == 0) ? sweep0 + 1u : sweep0;
+    if (n_iter > 0 && exch(s_first) && active && j >= prep_warp_j0)
+        exchange_prepare(in, j - prep_warp_j0, s_first, runbits, k0, k1, NT, ccrit + (s_first & 1u) * NT);
     __syncthreads();
 
-    const int n_iter = (mode == 0) ? nsweeps : 1;
     for (int it = 0; it < n_iter; ++it) {
-        const uint32_t s = (mode == 0) ? sweep0 + (uint32_t)it + 1u : sweep0;
-        const bool do_x = (NT > 1) && ((mode == 1) || (xevery > 0 && (s % (uint32_t)xevery) == 0u));
-        if (do_x && active && j < 32) {
-            const int npairs = NT - 1;
-            for (int call = j; call * 4 < npairs; call += 32) {
-                const uint4 w = philox10(s, runbits, (uint32_t)call, 1u, k0, k1);
-                const uint32_t wv[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int p = call * 4 + e;
-                    if (p < npairs) ccrit[p] = critical_half_gap(in, p, wv[e]);
-                }
-            }
-        }
+        const uint32_t s = s_first + (uint32_t)it;
+        const bool do_x = exch(s);
         if (mode == 0) {
-            if (active)
-                colour_phase(c0r, sw, NW, thr_sm, Es, macc, perm, NT, SP, sp, iters, s, runbits,
-                             k0, k1, warp_reduce, seg_lo, lane, lane_hi, sp_first);
+            if (active) {
+                colour_phase(cr, sw, NW, thr_sm, Es, macc, perm, NT, SP, sp, iters, s, runbits,
+                             k0, k1, ws, lane);
+                load_cell(in, q, 1, L2, L, cr);
+            }
             __syncthreads();
-            if (active)
-                colour_phase(c1r, sw, NW, thr_sm, Es, macc, perm, NT, SP, sp, iters, s, runbits,
-                             k0, k1, warp_reduce, seg_lo, lane, lane_hi, sp_first);
+            if (active) {
+                colour_phase(cr, sw, NW, thr_sm, Es, macc, perm, NT, SP, sp, iters, s, runbits,
+                             k0, k1, ws, lane);
+                load_cell(in, q, 0, L2, L, cr);
+            }
         }
         __syncthreads();
         if (active && j == 0) {
             int m;
             if (do_x) {
-                int cb = perm[0], ce = Es[0];
-                m = ce;
-                for (int p = 0; p < NT - 1; ++p) {
-                    const int nb = perm[p + 1], ne = Es[p + 1], c2 = 2 * ccrit[p];
-                    m = min(m, ne);
-                    if (ne - ce <= c2) {            // swap: the carried configuration moves up
-                        perm[p] = (uint8_t)nb;
-                        Es[p] = ne;
-                        xacc[p] += 1u;
-                    } else {
-                        perm[p] = (uint8_t)cb;
-                        Es[p] = ce;
-                        cb = nb;
-                        ce = ne;
-                    }
-                }
-                perm[NT - 1] = (uint8_t)cb;
-                Es[NT - 1] = ce;
+                m = exchange_chain(Es, perm, xacc, ccrit + (s & 1u) * NT, NT);
             } else {
                 m = Es[0];
                 for (int p = 1; p < NT; ++p) m = min(m, Es[p]);
@@ -274,6 +341,9 @@ __device__ void process_bundle(const InstDesc* __restrict__ insts, const Bundle 
                 misc[1] = (int32_t)s;
             }
         }
+        // meanwhile the last warp prepares the next sweep's exchange criteria
+        if (it + 1 < n_iter && exch(s + 1u) && active && j >= prep_warp_j0)
+            exchange_prepare(in, j - prep_warp_j0, s + 1u, runbits, k0, k1, NT, ccrit + ((s + 1u) & 1u) * NT);
         __syncthreads();
     }
 
