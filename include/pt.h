@@ -144,6 +144,28 @@ int pt_get_couplers(pt_handle *h, int8_t *J);
 int pt_get_tables(const pt_handle *h, uint32_t *thr, int64_t *xoff, uint32_t *xthr,
                   int64_t xthr_cap, int64_t *xthr_len);
 
+/* The paper has no counterpart to this entry point: it is pt_tts_eval for
+ * callers that cannot allocate device memory at call time, for instance code
+ * running inside another framework whose allocator or memory pool already
+ * owns the GPU's memory (a new cudaMalloc would fail or fragment it), or
+ * latency-critical loops that cannot take the device-wide synchronisation
+ * cudaMalloc/cudaFree may cause.  It creates no handle and allocates nothing:
+ * its device scratch is one static 4 MiB array that every GPU loading this
+ * library holds until the process exits, and its host staging is static.
+ * Same arguments and results as pt_create + pt_tts_eval (J, betas: host
+ * arrays as in pt_create; tts, n_hit, target: host outputs, n_hit and target
+ * may be NULL); the call synchronises `stream` (NULL: the legacy default
+ * stream).  Limits: n_runs * n_temps * 8 L^2 <= 2^21, n_runs * n_temps <=
+ * 16384, n_runs <= 1024, exchange tables <= 2^17 entries; larger problems
+ * return PT_ERR_ARG and pt_last_error(NULL) says which limit was exceeded.
+ * All calls share the scratch (each call re-initialises it); calls that
+ * overlap on the GPU race.  The first call on a device resolves the
+ * scratch's device address; make that first call before any stream capture. */
+int pt_tts_eval_noalloc(int32_t chimera_L, const int8_t *J, int32_t n_edges, const double *betas,
+                        int32_t n_temps, int32_t n_runs, uint32_t seed, uint32_t uid, int32_t S,
+                        int32_t pass_mult, int32_t exchange_every, void *stream, int32_t *tts,
+                        int32_t *n_hit, int32_t *target);
+
 /* Random adaptive optimisation (Algorithm 1). */
 typedef struct {
     int32_t S;               /* TTS horizon in sweeps */

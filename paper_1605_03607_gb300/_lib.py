@@ -71,6 +71,9 @@ SIGNATURES = [
     ("pt_sweep_timing_total", C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_uint64)]),
     ("pt_eval_stats", C.c_int, [_VP, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64),
                                 C.POINTER(C.c_double), C.c_int]),
+    ("pt_tts_eval_noalloc", C.c_int, [C.c_int32, _VP, C.c_int32, _VP, C.c_int32, C.c_int32,
+                                      C.c_uint32, C.c_uint32, C.c_int32, C.c_int32, C.c_int32, _VP,
+                                      _I32P, _I32P, _I32P]),
 ]
 
 _lib = None

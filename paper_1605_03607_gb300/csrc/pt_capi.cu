@@ -508,6 +508,12 @@ int ensure_candidates(pt_handle* h, int k)
 
 }  // namespace
 
+void ptg::set_global_error(const char* msg)
+{
+    std::lock_guard<std::mutex> g(g_err_mu);
+    g_create_err = msg;
+}
+
 // ==========================================================================
 // C ABI
 // ==========================================================================

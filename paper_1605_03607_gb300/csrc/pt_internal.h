@@ -75,6 +75,9 @@ __host__ __device__ inline ItemLayout item_layout(int L, int NT)
 
 __host__ __device__ inline int64_t table_bytes(int NT) { return pad16(4LL * NT * KT); }
 
+// Sets the message pt_last_error(NULL) returns (defined with the C ABI).
+void set_global_error(const char* msg);
+
 inline int64_t bundle_smem_bytes(int L, int NT, int nitems)
 {
     return table_bytes(NT) + (int64_t)nitems * item_layout(L, NT).bytes;
