@@ -308,6 +308,61 @@ def run_gpu(args):
     return 0
 
 
+def run_batched(args):
+    """Batched workload: 256 instances mixed over C_4/8/12/16 with 24..48
+    temperatures, 32 runs each; a step is fresh runs + `batch_sweeps` sweeps of
+    every run (one graph replay of the persistent launch) + per-instance TTS."""
+    import torch
+    import paper_1605_03607_gb300 as P
+    from paper_1605_03607_gb300 import build as B
+    B.build()
+    cfg = W.CONFIGS["batched_256"]
+    inst = W.batched_instances(cfg)
+    sweeps = args.batch_sweeps
+    attempts = sum(cfg["n_runs"] * len(x["betas"]) * 8 * x["L"] ** 2 for x in inst) * sweeps
+    stream = torch.cuda.current_stream()
+    b = P.PTBatch(inst, cfg["n_runs"], cfg["seed"], stream=stream.cuda_stream)
+    if not args.no_autotune:
+        b.autotune(trial_sweeps=16)
+    for _ in range(args.warmup):
+        b.reset()
+        b.run(sweeps, cfg["exchange_every"])
+    sampler = ClockSampler(0)
+    torch.cuda.synchronize()
+    sampler.start()
+    kern_ms, wall = 0.0, 0.0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        b.reset()
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        e0.record(stream)
+        b.run(sweeps, cfg["exchange_every"])
+        b.tts(sweeps)
+        e1.record(stream)
+        e1.synchronize()
+        wall += time.perf_counter() - w0
+        kern_ms += b.info()["last_run_ms"]
+    clocks = sampler.stop()
+    peaks, peak_kind = load_peaks()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak_ops = sms * INT_LANES_PER_SM_CLK * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    achieved = attempts * args.steps * OPS_PER_ATTEMPT / (kern_ms / 1e3)
+    sched = {L: b.schedule(L) for L in (4, 8, 12, 16)}
+    print(json.dumps({
+        "workload": "batched_256", "metric": METRIC, "value": attempts * args.steps / (wall),
+        "unit": UNIT, "steps": args.steps, "warmup": args.warmup, "sweeps_per_step": sweeps,
+        "kernel_attempts_per_s": attempts * args.steps / (kern_ms / 1e3),
+        "pt_tts_evals_per_s": 256 * args.steps / wall,
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                     "unit": "Tops/s (int32 issue)", "frac": achieved / peak_ops,
+                     "kernel": "pt_sweep_kernel (persistent)", "ops_per_attempt": OPS_PER_ATTEMPT},
+        "schedule": {str(k): v for k, v in sched.items()}, "info": b.info(), "clocks": clocks,
+        "peak_source": peak_kind}))
+    b.close()
+    return 0
+
+
 def run_profile_case(args):
     """A fixed, small sequence of sweep-kernel launches on the bench instance
     (for ncu captures): fresh runs, then `profile_sweeps` launches of
@@ -335,6 +390,9 @@ def run_profile_case(args):
 
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="c8_single", choices=["c8_single", "batched_256"])
+    ap.add_argument("--batch-sweeps", type=int, default=1 << 14)
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--profile-sweeps", type=int, default=0,
                     help="profiling case: this many sweep launches on the bench instance, then exit")
     ap.add_argument("--profile-instances", type=int, default=4,
@@ -354,6 +412,8 @@ def main():
         return run_reference(args)
     if args.profile_sweeps > 0:
         return run_profile_case(args)
+    if args.workload == "batched_256":
+        return run_batched(args)
     return run_gpu(args)
 
 

@@ -250,6 +250,66 @@ int pt_eval_stats(pt_handle *h, uint64_t *evals, uint64_t *batches, double *devi
  * call, summed (ms, CUDA events on the handle's stream), and their count. */
 int pt_last_sweep_timing(const pt_handle *h, double *ms, int32_t *launches);
 
+/* ---------------------------------------------------------------------
+ * Batched PT: many instances of uneven size and temperature count, each
+ * with n_runs independent runs (Sec. II), in one persistent kernel launch.
+ * Instance i keeps its own key (seed, uid_i): its trajectory is identical to
+ * a pt_create handle with the same (J, betas, n_runs, seed, uid).
+ * --------------------------------------------------------------------- */
+typedef struct {
+    int32_t chimera_L;       /* 1..16 */
+    int32_t n_temps;         /* 1..64 */
+    const int8_t *J;         /* 16 L^2 + 8 L (L-1) couplers in [-3, 3], read during the call */
+    const double *betas;     /* n_temps, strictly descending, > 0 */
+    uint32_t uid;            /* second key word of this instance's random streams */
+} pt_instance_desc;
+
+typedef struct pt_batch pt_batch;
+
+/* Message for the last failure on b (NULL: last failed pt_batch_create). */
+const char *pt_batch_last_error(const pt_batch *b);
+
+/* Copies the instances, builds their FP64 tables, allocates device state and
+ * starts fresh runs (as pt_reset).  Errors: PT_ERR_ARG, PT_ERR_OOM, PT_ERR_CUDA. */
+int pt_batch_create(pt_batch **b, int32_t n_inst, const pt_instance_desc *d, int32_t n_runs,
+                    uint32_t seed, void *stream);
+void pt_batch_destroy(pt_batch *b);
+
+/* Fresh runs of every instance (spins from the kind-2 streams, sweep 0). */
+int pt_batch_reset(pt_batch *b);
+
+/* n_sweeps sweeps of every run of every instance (same sweep/exchange rule
+ * as pt_sweep) as one replay of a CUDA graph holding the work-queue reset
+ * and one persistent launch: CTAs pull bundles of runs, longest first, from
+ * an atomic counter until none is left. */
+int pt_batch_run(pt_batch *b, int32_t n_sweeps, int32_t exchange_every);
+
+/* Per-instance TTS (rule of pt_tts with target = best found, horizon given):
+ * tts, n_hit, target: host arrays of n_inst (n_hit, target may be NULL). */
+int pt_batch_tts(pt_batch *b, int32_t horizon, int32_t *tts, int32_t *n_hit, int32_t *target);
+
+/* State of instance `inst` in the layout of pt_get_state (any pointer may be NULL). */
+int pt_batch_get_state(pt_batch *b, int32_t inst, int8_t *spins, int32_t *E, int32_t *best,
+                       int32_t *first, uint64_t *macc, uint64_t *xacc);
+
+/* Schedule: CTA size `block` (multiple of 32, <= 1024; 0 keeps it) and, for
+ * the instances of size chimera_L (0: none), slot_parallel * L^2 threads per
+ * run and runs_per_cta runs per CTA.  Results never depend on the schedule. */
+int pt_batch_set_schedule(pt_batch *b, int32_t block, int32_t chimera_L, int32_t slot_parallel,
+                          int32_t runs_per_cta);
+int pt_batch_get_schedule(const pt_batch *b, int32_t chimera_L, int32_t *block,
+                          int32_t *slot_parallel, int32_t *runs_per_cta);
+
+/* Autotuner: times every feasible (slot_parallel, runs_per_cta) of every
+ * size for block sizes 256 and 512 over `trial_sweeps` sweeps of that size's
+ * instances, keeps the fastest, then resets the runs. */
+int pt_batch_autotune(pt_batch *b, int32_t trial_sweeps, int32_t *block);
+
+/* Device time of the last pt_batch_run (CUDA events), persistent grid size,
+ * block size, bundle count, kernels launched so far. */
+int pt_batch_info(const pt_batch *b, double *last_run_ms, int32_t *grid, int32_t *block,
+                  int32_t *n_bundles, uint64_t *launches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -74,7 +74,23 @@ SIGNATURES = [
     ("pt_tts_eval_noalloc", C.c_int, [C.c_int32, _VP, C.c_int32, _VP, C.c_int32, C.c_int32,
                                       C.c_uint32, C.c_uint32, C.c_int32, C.c_int32, C.c_int32, _VP,
                                       _I32P, _I32P, _I32P]),
+    ("pt_batch_last_error", C.c_char_p, [_VP]),
+    ("pt_batch_create", C.c_int, [C.POINTER(_VP), C.c_int32, _VP, C.c_int32, C.c_uint32, _VP]),
+    ("pt_batch_destroy", None, [_VP]),
+    ("pt_batch_reset", C.c_int, [_VP]),
+    ("pt_batch_run", C.c_int, [_VP, C.c_int32, C.c_int32]),
+    ("pt_batch_tts", C.c_int, [_VP, C.c_int32, _VP, _VP, _VP]),
+    ("pt_batch_get_state", C.c_int, [_VP, C.c_int32] + [_VP] * 6),
+    ("pt_batch_set_schedule", C.c_int, [_VP, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
+    ("pt_batch_get_schedule", C.c_int, [_VP, C.c_int32, _I32P, _I32P, _I32P]),
+    ("pt_batch_autotune", C.c_int, [_VP, C.c_int32, _I32P]),
+    ("pt_batch_info", C.c_int, [_VP, C.POINTER(C.c_double), _I32P, _I32P, _I32P, C.POINTER(C.c_uint64)]),
 ]
+
+
+class pt_instance_desc(C.Structure):
+    _fields_ = [("chimera_L", C.c_int32), ("n_temps", C.c_int32), ("J", C.c_void_p),
+                ("betas", C.c_void_p), ("uid", C.c_uint32)]
 
 _lib = None
 
@@ -264,3 +280,94 @@ class PTHandle:
         ms, n = C.c_double(), C.c_int32()
         _check(load().pt_last_sweep_timing(self.h, C.byref(ms), C.byref(n)), self.h)
         return ms.value, n.value
+
+
+def _check_batch(rc, b=None):
+    if rc != PT_OK:
+        msg = load().pt_batch_last_error(b)
+        raise PTError(rc, msg.decode() if msg else "")
+
+
+class PTBatch:
+    """Many instances (list of dicts with L, J, betas, uid) x n_runs PT runs in one persistent launch."""
+
+    def __init__(self, instances, n_runs, seed, stream=None):
+        lib = load()
+        self.inst = [dict(L=int(x["L"]), J=np.ascontiguousarray(x["J"], np.int8),
+                          betas=np.ascontiguousarray(x["betas"], np.float64), uid=int(x["uid"]))
+                     for x in instances]
+        self.R = int(n_runs)
+        descs = (pt_instance_desc * len(self.inst))()
+        for d, x in zip(descs, self.inst):
+            d.chimera_L = x["L"]
+            d.n_temps = len(x["betas"])
+            d.J = x["J"].ctypes.data
+            d.betas = x["betas"].ctypes.data
+            d.uid = x["uid"] & 0xFFFFFFFF
+        b = C.c_void_p()
+        rc = lib.pt_batch_create(C.byref(b), len(self.inst), descs, self.R, int(seed) & 0xFFFFFFFF,
+                                 None if stream is None else C.c_void_p(stream))
+        _check_batch(rc, None)
+        self.b = b
+
+    def close(self):
+        if getattr(self, "b", None):
+            load().pt_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def reset(self):
+        _check_batch(load().pt_batch_reset(self.b), self.b)
+
+    def run(self, n_sweeps, exchange_every=1):
+        _check_batch(load().pt_batch_run(self.b, int(n_sweeps), int(exchange_every)), self.b)
+
+    def tts(self, horizon):
+        n = len(self.inst)
+        t, h, tg = (np.zeros(n, np.int32) for _ in range(3))
+        _check_batch(load().pt_batch_tts(self.b, int(horizon), _ptr(t), _ptr(h), _ptr(tg)), self.b)
+        return t, h, tg
+
+    def state(self, i):
+        x = self.inst[i]
+        NT, N = len(x["betas"]), 8 * x["L"] ** 2
+        spins = np.zeros((self.R, NT, N), np.int8)
+        E = np.zeros((self.R, NT), np.int32)
+        best = np.zeros(self.R, np.int32)
+        first = np.zeros(self.R, np.int32)
+        macc = np.zeros((self.R, NT), np.uint64)
+        xacc = np.zeros((self.R, max(NT - 1, 1)), np.uint64)
+        _check_batch(load().pt_batch_get_state(self.b, int(i), _ptr(spins), _ptr(E), _ptr(best), _ptr(first),
+                                               _ptr(macc), _ptr(xacc)), self.b)
+        return dict(spins=spins, E=E, best=best, first=first, macc=macc, xacc=xacc)
+
+    def set_schedule(self, block=0, L=0, slot_parallel=0, runs_per_cta=0):
+        _check_batch(load().pt_batch_set_schedule(self.b, int(block), int(L), int(slot_parallel),
+                                                  int(runs_per_cta)), self.b)
+
+    def schedule(self, L):
+        a, b_, c = C.c_int32(), C.c_int32(), C.c_int32()
+        _check_batch(load().pt_batch_get_schedule(self.b, int(L), C.byref(a), C.byref(b_), C.byref(c)), self.b)
+        return a.value, b_.value, c.value
+
+    def autotune(self, trial_sweeps=32):
+        blk = C.c_int32()
+        _check_batch(load().pt_batch_autotune(self.b, int(trial_sweeps), C.byref(blk)), self.b)
+        return blk.value
+
+    def info(self):
+        ms, g, bl, nb, la = C.c_double(), C.c_int32(), C.c_int32(), C.c_int32(), C.c_uint64()
+        _check_batch(load().pt_batch_info(self.b, C.byref(ms), C.byref(g), C.byref(bl), C.byref(nb),
+                                          C.byref(la)), self.b)
+        return dict(last_run_ms=ms.value, grid=g.value, block=bl.value, bundles=nb.value, launches=int(la.value))

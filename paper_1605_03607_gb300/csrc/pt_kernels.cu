@@ -297,7 +297,12 @@ __device__ void process_bundle(const InstDesc* __restrict__ insts, const Bundle 
     const unsigned hi_mask = __ballot_sync(FULL, !ws.lo);
     ws.two = hi_mask != 0u;
     ws.lane_hi = ws.two ? __ffs(hi_mask) - 1 : 32;
-    ws.redux = (L2 >= 32) || (L2 == 16);       // then no warp spans more than two slots
+    // warp reductions need a full warp of one run spanning at most two slots
+    // (true for L^2 >= 32 or L^2 == 16 with whole warps per run); otherwise
+    // every lane adds its own result atomically
+    const unsigned act_mask = __ballot_sync(FULL, active);
+    const bool one_item = __shfl_sync(FULL, item, 0) == __shfl_sync(FULL, item, 31);
+    ws.redux = ((L2 >= 32) || (L2 == 16 && TPI % 32 == 0)) && act_mask == FULL && one_item;
     const int iters = (NT + SP - 1) / SP;
     const uint32_t k0 = in.seed, k1 = in.uid;
     const uint32_t runbits = (uint32_t)run << 16;
@@ -521,6 +526,11 @@ cudaError_t sweep_smem_capacity(int* bytes)
     if (e != cudaSuccess) return e;
     *bytes = optin - (int)fa.sharedSizeBytes;
     return cudaSuccess;
+}
+
+cudaError_t sweep_occupancy(int block, int smem_bytes, int* blocks_per_sm)
+{
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, pt_sweep_kernel, block, smem_bytes);
 }
 
 cudaError_t set_sweep_smem_limit(int bytes)

@@ -9,6 +9,8 @@ namespace ptg {
 // Largest dynamic shared memory a sweep-kernel CTA may request on the current device.
 cudaError_t sweep_smem_capacity(int* bytes);
 cudaError_t set_sweep_smem_limit(int bytes);
+// Resident sweep-kernel CTAs per SM for a block size and dynamic shared memory.
+cudaError_t sweep_occupancy(int block, int smem_bytes, int* blocks_per_sm);
 cudaError_t launch_init(const InstDesc* insts, const int2* items, int nitems, bool draw,
                         cudaStream_t st);
 cudaError_t launch_energy(const InstDesc* insts, const int2* items, int nitems, int32_t first_value,
