@@ -83,6 +83,36 @@ CONFIGS = {
 }
 
 
+def surrogate_param_sizes(H=64, layers=4):
+    """Sizes of the surrogate's flat parameter vector, in order: embeddings
+    X[2,H], Jt[6,H]; per layer Wm[H,2H], bm[H], Wu[H,2H], bu[H], We[H,2H], be[H];
+    readout W1[H,H], b1[H], w2[H], b2[1]."""
+    sizes = [("X", 2 * H, 2), ("Jt", 6 * H, 6)]
+    for l in range(layers):
+        for n in ("m", "u", "e"):
+            sizes += [(f"W{n}{l}", 2 * H * H, 2 * H), (f"b{n}{l}", H, 0)]
+    sizes += [("W1", H * H, H), ("b1", H, 0), ("w2", H, H), ("b2", 1, 0)]
+    return sizes
+
+
+def surrogate_init_params(seed, H=64, layers=4):
+    """Initial surrogate parameters: weights uniform in +-1/sqrt(fan_in),
+    embeddings uniform in +-1, biases 0 except the output bias (3, a typical
+    log10 TTS)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for name, n, fan_in in surrogate_param_sizes(H, layers):
+        if name in ("X", "Jt"):
+            out.append(rng.uniform(-1, 1, n))
+        elif fan_in > 0:
+            out.append(rng.uniform(-1, 1, n) / np.sqrt(fan_in))
+        elif name == "b2":
+            out.append(np.array([3.0]))
+        else:
+            out.append(np.zeros(n))
+    return np.concatenate(out)
+
+
 def batched_instances(cfg=None):
     """Instance list of the batched workload: (L, n_temps, J, betas, uid)."""
     cfg = cfg or CONFIGS["batched_256"]
