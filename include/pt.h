@@ -310,6 +310,53 @@ int pt_batch_autotune(pt_batch *b, int32_t trial_sweeps, int32_t *block);
 int pt_batch_info(const pt_batch *b, double *last_run_ms, int32_t *grid, int32_t *block,
                   int32_t *n_bundles, uint64_t *launches);
 
+/* ---------------------------------------------------------------------
+ * Surrogate hardness model.  The paper has no surrogate: it is this
+ * library's way to rank RAO proposals (Algorithm 1) so that only the most
+ * promising ones get a PT-TTS evaluation (Sec. II TTS); PT stays the judge
+ * of every kept move.  Message-passing network over the Chimera coupler
+ * graph predicting log10 TTS:
+ *   h0_i = X[u_i] (orientation), e0_e = Jt[idx(J_e)], idx: -3..-1,1..3 -> 0..5
+ *   per layer: m_i = sum_{j in N(i)} relu(Wm [h_j, e_ij] + bm)
+ *              h_i += relu(Wu [h_i, m_i] + bu); e_ij += relu(We [e_ij, h_i + h_j] + be)
+ *   y = w2 . relu(W1 mean_i h_i + b1) + b2
+ * Hidden width 64.  Parameters are one FP32 vector in the order X[2,64],
+ * Jt[6,64], per layer Wm[64,128], bm, Wu[64,128], bu, We[64,128], be, then
+ * W1[64,64], b1, w2, b2 (matrices row-major, rows = outputs).  Forward and
+ * backward use BF16 weights/activations with FP32 accumulation (tensor
+ * cores); master weights, gradients and Adam moments are FP32.
+ * --------------------------------------------------------------------- */
+typedef struct sg_model sg_model;
+
+const char *sg_last_error(const sg_model *m);
+
+/* hidden must be 64, 1 <= layers <= 8.  Parameters start at zero. */
+int sg_create(sg_model **m, int32_t hidden, int32_t layers, void *stream);
+void sg_destroy(sg_model *m);
+int64_t sg_num_params(const sg_model *m);
+
+/* Copies FP32 parameters in (resetting Adam) / out (host arrays of sg_num_params). */
+int sg_set_params(sg_model *m, const float *theta);
+int sg_get_params(sg_model *m, float *theta);
+
+/* Predictions for B instances of C_L: J host [B][16 L^2 + 8 L (L-1)] with
+ * values in {+-1, +-2, +-3}; y host [B]. */
+int sg_forward(sg_model *m, int32_t L, int32_t B, const int8_t *J, float *y);
+
+/* Mean squared error against targets t [B] and its gradient (host array of
+ * sg_num_params, may be NULL). */
+int sg_grad(sg_model *m, int32_t L, int32_t B, const int8_t *J, const float *t, float *loss, float *grad);
+
+/* One Adam update (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) with
+ * the gradient of the last sg_grad. */
+int sg_adam(sg_model *m, float lr);
+
+/* sg_grad followed by sg_adam. */
+int sg_train_step(sg_model *m, int32_t L, int32_t B, const int8_t *J, const float *t, float lr, float *loss);
+
+/* Kernels launched by this model so far. */
+uint64_t sg_launch_count(const sg_model *m);
+
 #ifdef __cplusplus
 }
 #endif

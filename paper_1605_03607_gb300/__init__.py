@@ -7,4 +7,4 @@ hand-written sm_103a kernels behind the C ABI of include/pt.h; this package is
 the Python binding of that ABI.
 """
 from ._lib import (PT_KMAX, PT_TARGET_BEST, PTError, PTHandle, load, pt_rule,  # noqa: F401
-                   pt_step_result, SIGNATURES, LIB_PATH, select_device, PTBatch)
+                   pt_step_result, SIGNATURES, LIB_PATH, select_device, PTBatch, Surrogate)

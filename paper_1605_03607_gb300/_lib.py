@@ -85,6 +85,17 @@ SIGNATURES = [
     ("pt_batch_get_schedule", C.c_int, [_VP, C.c_int32, _I32P, _I32P, _I32P]),
     ("pt_batch_autotune", C.c_int, [_VP, C.c_int32, _I32P]),
     ("pt_batch_info", C.c_int, [_VP, C.POINTER(C.c_double), _I32P, _I32P, _I32P, C.POINTER(C.c_uint64)]),
+    ("sg_last_error", C.c_char_p, [_VP]),
+    ("sg_create", C.c_int, [C.POINTER(_VP), C.c_int32, C.c_int32, _VP]),
+    ("sg_destroy", None, [_VP]),
+    ("sg_num_params", C.c_int64, [_VP]),
+    ("sg_set_params", C.c_int, [_VP, _VP]),
+    ("sg_get_params", C.c_int, [_VP, _VP]),
+    ("sg_forward", C.c_int, [_VP, C.c_int32, C.c_int32, _VP, _VP]),
+    ("sg_grad", C.c_int, [_VP, C.c_int32, C.c_int32, _VP, _VP, C.POINTER(C.c_float), _VP]),
+    ("sg_adam", C.c_int, [_VP, C.c_float]),
+    ("sg_train_step", C.c_int, [_VP, C.c_int32, C.c_int32, _VP, _VP, C.c_float, C.POINTER(C.c_float)]),
+    ("sg_launch_count", C.c_uint64, [_VP]),
 ]
 
 
@@ -371,3 +382,75 @@ class PTBatch:
         _check_batch(load().pt_batch_info(self.b, C.byref(ms), C.byref(g), C.byref(bl), C.byref(nb),
                                           C.byref(la)), self.b)
         return dict(last_run_ms=ms.value, grid=g.value, block=bl.value, bundles=nb.value, launches=int(la.value))
+
+
+def _check_sg(rc, m=None):
+    if rc != PT_OK:
+        msg = load().sg_last_error(m)
+        raise PTError(rc, msg.decode() if msg else "")
+
+
+class Surrogate:
+    """The surrogate hardness model (log10 TTS from couplers) on the GPU."""
+
+    def __init__(self, hidden=64, layers=4, stream=None):
+        m = C.c_void_p()
+        _check_sg(load().sg_create(C.byref(m), int(hidden), int(layers),
+                                   None if stream is None else C.c_void_p(stream)), None)
+        self.m = m
+        self.n = int(load().sg_num_params(m))
+
+    def close(self):
+        if getattr(self, "m", None):
+            load().sg_destroy(self.m)
+            self.m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_params(self, theta):
+        th = np.ascontiguousarray(theta, np.float32)
+        assert th.size == self.n
+        _check_sg(load().sg_set_params(self.m, _ptr(th)), self.m)
+
+    def params(self):
+        th = np.zeros(self.n, np.float32)
+        _check_sg(load().sg_get_params(self.m, _ptr(th)), self.m)
+        return th
+
+    def forward(self, L, J):
+        J = np.ascontiguousarray(np.atleast_2d(J), np.int8)
+        y = np.zeros(J.shape[0], np.float32)
+        _check_sg(load().sg_forward(self.m, int(L), J.shape[0], _ptr(J), _ptr(y)), self.m)
+        return y
+
+    def grad(self, L, J, t):
+        J = np.ascontiguousarray(np.atleast_2d(J), np.int8)
+        t = np.ascontiguousarray(t, np.float32)
+        g = np.zeros(self.n, np.float32)
+        loss = C.c_float()
+        _check_sg(load().sg_grad(self.m, int(L), J.shape[0], _ptr(J), _ptr(t), C.byref(loss), _ptr(g)), self.m)
+        return loss.value, g
+
+    def adam(self, lr=1e-3):
+        _check_sg(load().sg_adam(self.m, float(lr)), self.m)
+
+    def train_step(self, L, J, t, lr=1e-3):
+        J = np.ascontiguousarray(np.atleast_2d(J), np.int8)
+        t = np.ascontiguousarray(t, np.float32)
+        loss = C.c_float()
+        _check_sg(load().sg_train_step(self.m, int(L), J.shape[0], _ptr(J), _ptr(t), float(lr), C.byref(loss)),
+                  self.m)
+        return loss.value
+
+    def launch_count(self):
+        return int(load().sg_launch_count(self.m))

@@ -73,7 +73,9 @@ __host__ __device__ inline ItemLayout item_layout(int L, int NT)
     return o;
 }
 
-__host__ __device__ inline int64_t table_bytes(int NT) { return pad16(4LL * NT * KT); }
+// Instance tables staged per bundle: thr [NT][KT], then exchange offsets [NT]
+// and search hints [NT].
+__host__ __device__ inline int64_t table_bytes(int NT) { return pad16(4LL * NT * KT + 8LL * NT); }
 
 // Sets the message pt_last_error(NULL) returns (defined with the C ABI).
 void set_global_error(const char* msg);

@@ -38,14 +38,15 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 // because the table is non-increasing in h (checked on the host); the float
 // estimate only picks where the exact search starts, and both neighbours of
 // the estimate are loaded at once.
-__device__ __forceinline__ int critical_half_gap(const InstDesc& in, int p, uint32_t u)
+__device__ __forceinline__ int critical_half_gap(const InstDesc& in, const int32_t* xoff_sm,
+                                                 const float* xhint_sm, int p, uint32_t u)
 {
-    const int o = in.xoff[p];
-    const int H = in.xoff[p + 1] - o;
+    const int o = xoff_sm[p];
+    const int H = xoff_sm[p + 1] - o;
     const uint32_t* tab = in.xthr + o - 1;       // tab[h], h = 1..H
     int c = H;
     if (u != 0u) {
-        const float est = (32.0f - __log2f((float)u)) * in.xhint[p];
+        const float est = (32.0f - __log2f((float)u)) * xhint_sm[p];
         c = est <= 0.0f ? 0 : (est >= (float)H ? H : (int)est);
     }
     const uint32_t at = c > 0 ? tab[c] : 0xFFFFFFFFu;
@@ -162,11 +163,15 @@ __device__ __forceinline__ void colour_phase(const CellRegs& cr, uint32_t* sw, i
 }
 
 // Exchange critical gaps of every pair of this run for sweep counter s
-// (called by one warp; lane l handles pairs 4l..4l+3 from one Philox call).
-__device__ __forceinline__ void exchange_prepare(const InstDesc& in, int lane, uint32_t s,
-                                                 uint32_t runbits, uint32_t k0, uint32_t k1,
+// (called by one group of 32 threads; lane l handles pairs 4l..4l+3 from one
+// Philox call).  Table offsets and search hints come from shared memory.
+__device__ __forceinline__ void exchange_prepare(const InstDesc& in, const uint32_t* thr_sm, int lane,
+                                                 uint32_t s, uint32_t runbits, uint32_t k0, uint32_t k1,
                                                  int NT, int32_t* cc)
 {
+    // bundle tables: thr [NT][KT], then exchange offsets [NT] and search hints [NT]
+    const int32_t* xoff_sm = reinterpret_cast<const int32_t*>(thr_sm + NT * KT);
+    const float* xhint_sm = reinterpret_cast<const float*>(thr_sm + NT * KT + NT);
     const int npairs = NT - 1;
     for (int call = lane; call * 4 < npairs; call += 32) {
         const uint4 w = philox10(s, runbits, (uint32_t)call, 1u, k0, k1);
@@ -174,7 +179,7 @@ __device__ __forceinline__ void exchange_prepare(const InstDesc& in, int lane, u
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int p = call * 4 + e;
-            if (p < npairs) cc[p] = critical_half_gap(in, p, wv[e]);
+            if (p < npairs) cc[p] = critical_half_gap(in, xoff_sm, xhint_sm, p, wv[e]);
         }
     }
 }
@@ -254,6 +259,7 @@ __device__ void process_bundle(const InstDesc* __restrict__ insts, const Bundle 
     const int run = bd.run0 + (active ? item : 0);
     const ItemLayout lay = item_layout(L, NT);
 
+    // bundle tables: thr [NT][KT], then exchange offsets [NT] and search hints [NT]
     uint32_t* thr_sm = reinterpret_cast<uint32_t*>(smem);
     unsigned char* ib = smem + table_bytes(NT) + (active ? item : 0) * lay.bytes;
     uint32_t* sw = reinterpret_cast<uint32_t*>(ib + lay.spins);
@@ -266,6 +272,10 @@ __device__ void process_bundle(const InstDesc* __restrict__ insts, const Bundle 
 
     // ---- load the instance table and this bundle's runs into shared memory
     for (int w = tid; w < NT * KT; w += blockDim.x) thr_sm[w] = in.thr[w];
+    for (int p = tid; p < NT; p += blockDim.x) {
+        reinterpret_cast<int32_t*>(thr_sm + NT * KT)[p] = in.xoff[p];
+        reinterpret_cast<float*>(thr_sm + NT * KT + NT)[p] = p < NT - 1 ? in.xhint[p] : 0.0f;
+    }
     const size_t rep0 = (size_t)run * NT;
     if (active) {
         const uint32_t* gsp = reinterpret_cast<const uint32_t*>(in.spins + rep0 * N);
@@ -313,7 +323,7 @@ __device__ void process_bundle(const InstDesc* __restrict__ insts, const Bundle 
     const int n_iter = (mode == 0) ? nsweeps : 1;
     const uint32_t s_first = (mode == 0) ? sweep0 + 1u : sweep0;
     if (n_iter > 0 && exch(s_first) && active && j >= prep_warp_j0)
-        exchange_prepare(in, j - prep_warp_j0, s_first, runbits, k0, k1, NT, ccrit + (s_first & 1u) * NT);
+        exchange_prepare(in, thr_sm, j - prep_warp_j0, s_first, runbits, k0, k1, NT, ccrit + (s_first & 1u) * NT);
     __syncthreads();
 
     for (int it = 0; it < n_iter; ++it) {
@@ -348,7 +358,7 @@ __device__ void process_bundle(const InstDesc* __restrict__ insts, const Bundle 
         }
         // meanwhile the last warp prepares the next sweep's exchange criteria
         if (it + 1 < n_iter && exch(s + 1u) && active && j >= prep_warp_j0)
-            exchange_prepare(in, j - prep_warp_j0, s + 1u, runbits, k0, k1, NT, ccrit + ((s + 1u) & 1u) * NT);
+            exchange_prepare(in, thr_sm, j - prep_warp_j0, s + 1u, runbits, k0, k1, NT, ccrit + ((s + 1u) & 1u) * NT);
         __syncthreads();
     }
 
