@@ -363,6 +363,75 @@ def run_batched(args):
     return 0
 
 
+def run_guided_experiment(args):
+    """Surrogate-guided vs plain engineering at equal GPU time.
+
+    1. Training pairs: the plain RAO loop (speculative batches of 16) on
+       `--guided-train-instances` C_8 seed instances, every evaluated candidate
+       kept as (couplers, log10 TTS).
+    2. Training: the GPU surrogate, minibatch 256, Adam lr 1e-3, 20 epochs.
+    3. From one fresh C_8 instance: plain loop, guided loop (64 proposals,
+       top 16 PT-evaluated) with the trained network, and the same guided loop
+       with an untrained network, each for `--guided-seconds` of GPU time.
+    """
+    import paper_1605_03607_gb300 as P
+    from paper_1605_03607_gb300 import build as B
+    from paper_1605_03607_gb300 import guided as G
+    B.build()
+    cfg = W.CONFIGS["c8_single"]
+    L, NT, R, seed = cfg["L"], cfg["n_temps"], cfg["n_runs"], cfg["seed"]
+    S, pm = args.guided_S, 4
+    betas = W.beta_ladder(NT, cfg["beta_min"], cfg["beta_max"])
+    t0 = time.perf_counter()
+    uids = list(range(100, 100 + args.guided_train_instances))
+    J0s = [W.random_couplers(L, seed, u) for u in uids]
+    J, y, tts = G.collect_pairs(L, J0s, betas, R, seed, uids, S, pm, args.guided_train_steps, 16)
+    t_data = time.perf_counter() - t0
+    rng = np.random.default_rng(0)
+    perm = rng.permutation(len(y))
+    nval = max(len(y) // 10, 1)
+    val, tr = perm[:nval], perm[nval:]
+    model = P.Surrogate()
+    model.set_params(W.surrogate_init_params(1))
+    t1 = time.perf_counter()
+    hist = G.train(model, L, J[tr], y[tr], epochs=20, batch=256, lr=1e-3)
+    t_train = time.perf_counter() - t1
+    pv = model.forward(L, J[val])
+
+    def spearman(a, b):
+        ra, rb = np.argsort(np.argsort(a)), np.argsort(np.argsort(b))
+        return float(np.corrcoef(ra, rb)[0, 1])
+
+    untrained = P.Surrogate()
+    untrained.set_params(W.surrogate_init_params(1))
+    test_uid = 999
+    Jt = W.random_couplers(L, seed, test_uid)
+    out = {}
+    for name in ("plain", "guided", "guided_untrained"):
+        with P.PTHandle(L, Jt, betas, R, seed, test_uid) as h:
+            h.engineer_begin(S=S, pass_mult=pm, exchange_every=1, base_uid=test_uid)
+            if name == "plain":
+                tr_ = G.run_plain(h, args.guided_seconds, speculation=16)
+            else:
+                tr_ = G.run_guided(h, model if name == "guided" else untrained, args.guided_seconds,
+                                   n_prop=64, top=16)
+            out[name] = {"gain_log10_tts_per_gpu_s": G.gain_per_second(tr_), "tts_initial": int(tr_[0][1]),
+                         "tts_final": int(tr_[-1][1]), "gpu_s": tr_[-1][0], "steps": tr_[-1][2]}
+    print(json.dumps({
+        "workload": "guided_vs_plain", "metric": "log-TTS gain per GPU-s, surrogate vs plain",
+        "config": {"instance": "C_8, 32 temps beta [0.1,4], 64 runs", "S": S, "pass_mult": pm,
+                   "proposals": 64, "top": 16, "plain_speculation": 16, "gpu_seconds_each": args.guided_seconds},
+        "training": {"pairs": int(len(y)), "instances": len(uids), "epochs": 20, "batch": 256, "lr": 1e-3,
+                     "loss_first": hist[0], "loss_last": hist[-1], "val_spearman": spearman(pv, y[val]),
+                     "data_s": t_data, "train_s": t_train,
+                     "unsolved_fraction": float(np.mean(tts > S))},
+        "loops": out,
+        "surrogate_over_plain": out["guided"]["gain_log10_tts_per_gpu_s"] - out["plain"]["gain_log10_tts_per_gpu_s"],
+        "trained_over_untrained": out["guided"]["gain_log10_tts_per_gpu_s"] -
+                                  out["guided_untrained"]["gain_log10_tts_per_gpu_s"]}))
+    return 0
+
+
 def run_profile_case(args):
     """A fixed, small sequence of sweep-kernel launches on the bench instance
     (for ncu captures): fresh runs, then `profile_sweeps` launches of
@@ -390,7 +459,11 @@ def run_profile_case(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="c8_single", choices=["c8_single", "batched_256"])
+    ap.add_argument("--workload", default="c8_single", choices=["c8_single", "batched_256", "guided"])
+    ap.add_argument("--guided-S", type=int, default=1 << 14)
+    ap.add_argument("--guided-train-instances", type=int, default=24)
+    ap.add_argument("--guided-train-steps", type=int, default=48)
+    ap.add_argument("--guided-seconds", type=float, default=60.0)
     ap.add_argument("--batch-sweeps", type=int, default=1 << 14)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--profile-sweeps", type=int, default=0,
@@ -414,6 +487,8 @@ def main():
         return run_profile_case(args)
     if args.workload == "batched_256":
         return run_batched(args)
+    if args.workload == "guided":
+        return run_guided_experiment(args)
     return run_gpu(args)
 
 

@@ -357,6 +357,19 @@ int sg_train_step(sg_model *m, int32_t L, int32_t B, const int8_t *J, const floa
 /* Kernels launched by this model so far. */
 uint64_t sg_launch_count(const sg_model *m);
 
+/* Surrogate-guided RAO step t (Algorithm 1 with a learned proposal filter):
+ * draws n_prop proposals j = 0..n_prop-1 against the current couplers (the
+ * draw of engineer_step with counter (t, j, 0, 3)), predicts their log10 TTS
+ * with the surrogate m, PT-evaluates the `top` best-ranked ones (ties: lower
+ * j first) in one batched launch, and keeps the one with the largest TTS
+ * (ties: better rank) under the rule of engineer_step.  PT alone decides.
+ * out: `top` results in rank order (accepted = 1 on the kept one, if any);
+ * pred (may be NULL): the n_prop predictions; ranked (may be NULL): the
+ * proposal indices of out.  1 <= top <= min(n_prop, 16), n_prop <= 1024.
+ * Requires engineer_begin and couplers in {+-1, +-2, +-3}. */
+int engineer_guided_step(pt_handle *h, sg_model *m, uint32_t step, int32_t n_prop, int32_t top,
+                         pt_step_result *out, float *pred, int32_t *ranked);
+
 #ifdef __cplusplus
 }
 #endif

@@ -80,18 +80,38 @@ def relu(x):
     return np.maximum(x, 0.0)
 
 
-def forward(theta, L, J, H=64, layers=4, keep=False):
+def bf16_round(x):
+    """Round to the nearest bfloat16 (ties to even) and return float64."""
+    a = np.ascontiguousarray(x, np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _identity(x):
+    return x
+
+
+# bf16=True models a BF16-storage implementation: the per-layer weight
+# matrices, the embedded inputs, every stored activation (m, updated h, s,
+# updated e) and every backward pre-activation gradient dZ are rounded to
+# bfloat16, while all sums stay in float64.  It is a precision model used to
+# separate rounding from mistakes on graphs too small for the 2e-2 bar; the
+# default (bf16=False) is the exact float64 network.
+def forward(theta, L, J, H=64, layers=4, keep=False, bf16=False):
     """J: [B, E] couplers.  Returns y [B] (and the saved activations if keep)."""
+    q = bf16_round if bf16 else _identity
     p = unpack(theta, H, layers)
     ei, ej, u = chimera_graph(L)
     J = np.atleast_2d(np.asarray(J))
     B, N = J.shape[0], 8 * L * L
     jidx = np.vectorize(J_INDEX.__getitem__)(J)
-    h = np.repeat(p["X"][u][None], B, axis=0)                      # [B, N, H]
-    e = p["Jt"][jidx]                                              # [B, E, H]
+    h = q(np.repeat(p["X"][u][None], B, axis=0))                   # [B, N, H]
+    e = q(p["Jt"][jidx])                                           # [B, E, H]
     saved = []
     for l in range(layers):
         Wm, bm, Wu, bu, We, be = (p[f"{n}{l}"] for n in ("Wm", "bm", "Wu", "bu", "We", "be"))
+        Wm, Wu, We = q(Wm), q(Wu), q(We)
         # messages in both directions of every edge
         zf = np.concatenate([h[:, ej], e], -1) @ Wm.T + bm          # j -> i  (to ei)
         zb = np.concatenate([h[:, ei], e], -1) @ Wm.T + bm          # i -> j  (to ej)
@@ -99,11 +119,12 @@ def forward(theta, L, J, H=64, layers=4, keep=False):
         for b in range(B):
             np.add.at(m[b], ei, relu(zf[b]))
             np.add.at(m[b], ej, relu(zb[b]))
+        m = q(m)
         zu = np.concatenate([h, m], -1) @ Wu.T + bu
-        h2 = h + relu(zu)
-        s = h2[:, ei] + h2[:, ej]
+        h2 = q(h + relu(zu))
+        s = q(h2[:, ei] + h2[:, ej])
         ze = np.concatenate([e, s], -1) @ We.T + be
-        e2 = e + relu(ze)
+        e2 = q(e + relu(ze))
         saved.append((h, e, zf, zb, m, zu, h2, s, ze))
         h, e = h2, e2
     g = h.mean(axis=1)                                             # [B, H]
@@ -115,10 +136,11 @@ def forward(theta, L, J, H=64, layers=4, keep=False):
     return y
 
 
-def loss_and_grad(theta, L, J, t, H=64, layers=4):
+def loss_and_grad(theta, L, J, t, H=64, layers=4, bf16=False):
     """MSE loss mean_b (y_b - t_b)^2 and its gradient with respect to theta."""
+    q = bf16_round if bf16 else _identity
     p = unpack(theta, H, layers)
-    y, c = forward(theta, L, J, H, layers, keep=True)
+    y, c = forward(theta, L, J, H, layers, keep=True, bf16=bf16)
     t = np.asarray(t, np.float64)
     B = y.shape[0]
     N = 8 * L * L
@@ -137,9 +159,9 @@ def loss_and_grad(theta, L, J, t, H=64, layers=4):
     de = np.zeros_like(c["e"])                                     # grad wrt final e (unused by readout)
     for l in reversed(range(layers)):
         h, e, zf, zb, m, zu, h2, s, ze = c["saved"][l]
-        Wm, Wu, We = p[f"Wm{l}"], p[f"Wu{l}"], p[f"We{l}"]
+        Wm, Wu, We = q(p[f"Wm{l}"]), q(p[f"Wu{l}"]), q(p[f"We{l}"])
         # edge update e2 = e + relu(ze), ze = We [e, s] + be, s = h2_i + h2_j
-        dze = de * (ze > 0)
+        dze = q(de * (ze > 0))
         g[f"We{l}"] = np.einsum("beo,bei->oi", dze, np.concatenate([e, s], -1))
         g[f"be{l}"] = dze.sum((0, 1))
         dx = dze @ We                                              # [B, E, 2H]
@@ -150,15 +172,15 @@ def loss_and_grad(theta, L, J, t, H=64, layers=4):
             np.add.at(dh2[b], ei, ds[b])
             np.add.at(dh2[b], ej, ds[b])
         # node update h2 = h + relu(zu), zu = Wu [h, m] + bu
-        dzu = dh2 * (zu > 0)
+        dzu = q(dh2 * (zu > 0))
         g[f"Wu{l}"] = np.einsum("bno,bni->oi", dzu, np.concatenate([h, m], -1))
         g[f"bu{l}"] = dzu.sum((0, 1))
         dxu = dzu @ Wu
         dh_in = dh2 + dxu[..., :H]
         dm = dxu[..., H:]
         # messages m_i = sum relu(zf) (to ei) + relu(zb) (to ej)
-        dzf = dm[:, ei] * (zf > 0)
-        dzb = dm[:, ej] * (zb > 0)
+        dzf = q(dm[:, ei] * (zf > 0))
+        dzb = q(dm[:, ej] * (zb > 0))
         g[f"Wm{l}"] = (np.einsum("beo,bei->oi", dzf, np.concatenate([h[:, ej], e], -1)) +
                        np.einsum("beo,bei->oi", dzb, np.concatenate([h[:, ei], e], -1)))
         g[f"bm{l}"] = dzf.sum((0, 1)) + dzb.sum((0, 1))

@@ -96,6 +96,8 @@ SIGNATURES = [
     ("sg_adam", C.c_int, [_VP, C.c_float]),
     ("sg_train_step", C.c_int, [_VP, C.c_int32, C.c_int32, _VP, _VP, C.c_float, C.POINTER(C.c_float)]),
     ("sg_launch_count", C.c_uint64, [_VP]),
+    ("engineer_guided_step", C.c_int, [_VP, _VP, C.c_uint32, C.c_int32, C.c_int32,
+                                       C.POINTER(pt_step_result), _VP, _VP]),
 ]
 
 
@@ -245,6 +247,17 @@ class PTHandle:
 
     def engineer_step(self, step):
         return self.engineer_run(step, 1, 1)
+
+    def engineer_guided_step(self, model, step, n_prop=64, top=4):
+        """One surrogate-guided step; returns (results in rank order, predictions, ranked indices)."""
+        out = (pt_step_result * top)()
+        pred = np.zeros(n_prop, np.float32)
+        ranked = np.zeros(top, np.int32)
+        _check(load().engineer_guided_step(self.h, model.m, int(step) & 0xFFFFFFFF, int(n_prop), int(top), out,
+                                           _ptr(pred), _ptr(ranked)), self.h)
+        keys = ("edge", "old_value", "new_value", "tts_old", "tts_new", "accepted", "cand_uid")
+        res = {k: np.array([getattr(out[i], k) for i in range(top)], np.int64) for k in keys}
+        return res, pred, ranked
 
     def engineer_tts(self):
         t = C.c_int32()

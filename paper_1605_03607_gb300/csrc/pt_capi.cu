@@ -364,6 +364,34 @@ bool engineer_accept(const pt_rule& rule, int32_t cur, int32_t cand, uint32_t ua
     return false;
 }
 
+int ensure_candidates(pt_handle* h, int k);
+
+// PT-TTS evaluation of k candidate coupler vectors (host [k][n_edges]) with
+// PT keys uids[0..k-1], as one batched launch sequence; res = k x {tts, hits, target}.
+int eval_candidates(pt_handle* h, int k, const int8_t* Jc, const uint32_t* uids, std::vector<int32_t>& res)
+{
+    int rc = ensure_candidates(h, k);
+    if (rc) return rc;
+    Group& g = h->cand;
+    std::vector<uint32_t> jw((size_t)k * h->L * h->L * 16);
+    for (int j = 0; j < k; ++j) {
+        pack_couplers(h->L, Jc + (size_t)j * h->n_edges, jw.data() + (size_t)j * h->L * h->L * 16);
+        g.desc[j].uid = uids[j];
+    }
+    CK(cudaMemcpyAsync(g.jw, jw.data(), 4 * jw.size(), cudaMemcpyHostToDevice, h->stream), "upload candidates");
+    // evaluate only the first k candidates: shrink the group view temporarily
+    const int n_full = g.n_inst;
+    std::vector<Bundle> keep = g.bundles;
+    g.n_inst = k;
+    std::vector<Bundle> sub;
+    for (const Bundle& b : keep) if (b.inst < k) sub.push_back(b);
+    g.bundles = sub;
+    rc = group_eval(h, g, h->rule.S, h->rule.pass_mult, h->rule.exchange_every, res);
+    g.n_inst = n_full;
+    g.bundles = keep;
+    return rc;
+}
+
 int ensure_candidates(pt_handle* h, int k)
 {
     if (h->cand.n_inst >= k) return PT_OK;
@@ -638,7 +666,6 @@ int engineer_run(pt_handle* h, uint32_t step0, int32_t n_steps, int32_t spec, pt
     if (n_steps < 0 || spec < 1 || spec > 16) return fail(h, PT_ERR_ARG, "need n_steps >= 0, speculation in [1, 16]");
     int rc = ensure_candidates(h, spec);
     if (rc) return rc;
-    Group& g = h->cand;
     std::vector<int8_t> Jc((size_t)spec * h->n_edges);
     std::vector<int32_t> e(spec), v(spec);
     std::vector<uint32_t> cu(spec), ua(spec);
@@ -646,27 +673,14 @@ int engineer_run(pt_handle* h, uint32_t step0, int32_t n_steps, int32_t spec, pt
     bool changed = false;
     while (done < n_steps) {
         const int k = std::min<int>(spec, n_steps - done);
-        std::vector<uint32_t> jw((size_t)k * h->L * h->L * 16);
         for (int j = 0; j < k; ++j) {
             engineer_draw(h, h->J.data(), step0 + (uint32_t)(done + j), 0u, e[j], v[j], cu[j], ua[j]);
             int8_t* Jj = Jc.data() + (size_t)j * h->n_edges;
             std::memcpy(Jj, h->J.data(), h->n_edges);
             Jj[e[j]] = (int8_t)v[j];
-            pack_couplers(h->L, Jj, jw.data() + (size_t)j * h->L * h->L * 16);
-            g.desc[j].uid = cu[j];
         }
-        CK(cudaMemcpyAsync(g.jw, jw.data(), 4 * jw.size(), cudaMemcpyHostToDevice, h->stream), "upload candidates");
-        // evaluate only the first k candidates: shrink the group view temporarily
-        const int n_full = g.n_inst;
-        std::vector<Bundle> keep = g.bundles;
-        g.n_inst = k;
-        std::vector<Bundle> sub;
-        for (const Bundle& b : keep) if (b.inst < k) sub.push_back(b);
-        g.bundles = sub;
         std::vector<int32_t> res;
-        rc = group_eval(h, g, h->rule.S, h->rule.pass_mult, h->rule.exchange_every, res);
-        g.n_inst = n_full;
-        g.bundles = keep;
+        rc = eval_candidates(h, k, Jc.data(), cu.data(), res);
         if (rc) return rc;
         int used = k;
         for (int j = 0; j < k; ++j) {
@@ -697,6 +711,64 @@ int engineer_run(pt_handle* h, uint32_t step0, int32_t n_steps, int32_t spec, pt
 int engineer_step(pt_handle* h, uint32_t step, pt_step_result* out)
 {
     return engineer_run(h, step, 1, 1, out);
+}
+
+int engineer_guided_step(pt_handle* h, sg_model* m, uint32_t step, int32_t n_prop, int32_t top,
+                         pt_step_result* out, float* pred, int32_t* ranked)
+{
+    if (!h || !m) return fail(h, PT_ERR_ARG, "NULL argument");
+    if (!h->eng) return fail(h, PT_ERR_STATE, "engineer_begin not called");
+    if (n_prop < 1 || n_prop > 1024 || top < 1 || top > 16 || top > n_prop)
+        return fail(h, PT_ERR_ARG, "need 1 <= top <= min(n_prop, 16), n_prop <= 1024");
+    for (int e = 0; e < h->n_edges; ++e)
+        if (h->J[e] == 0) return fail(h, PT_ERR_STATE, "the surrogate needs couplers in {+-1, +-2, +-3}");
+    std::vector<int8_t> Jp((size_t)n_prop * h->n_edges);
+    std::vector<int32_t> e(n_prop), v(n_prop);
+    std::vector<uint32_t> cu(n_prop), ua(n_prop);
+    for (int j = 0; j < n_prop; ++j) {
+        engineer_draw(h, h->J.data(), step, (uint32_t)j, e[j], v[j], cu[j], ua[j]);
+        int8_t* Jj = Jp.data() + (size_t)j * h->n_edges;
+        std::memcpy(Jj, h->J.data(), h->n_edges);
+        Jj[e[j]] = (int8_t)v[j];
+    }
+    std::vector<float> y(n_prop);
+    if (sg_forward(m, h->L, n_prop, Jp.data(), y.data()) != PT_OK)
+        return fail(h, PT_ERR_CUDA, std::string("surrogate forward: ") + sg_last_error(m));
+    std::vector<int> order(n_prop);
+    for (int j = 0; j < n_prop; ++j) order[j] = j;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return y[a] > y[b]; });
+    std::vector<int8_t> Jc((size_t)top * h->n_edges);
+    std::vector<uint32_t> uid(top);
+    for (int r = 0; r < top; ++r) {
+        std::memcpy(Jc.data() + (size_t)r * h->n_edges, Jp.data() + (size_t)order[r] * h->n_edges, h->n_edges);
+        uid[r] = cu[order[r]];
+    }
+    std::vector<int32_t> res;
+    int rc = eval_candidates(h, top, Jc.data(), uid.data(), res);
+    if (rc) return rc;
+    int best = 0;   // largest TTS in the direction of the rule; ties keep the better-ranked one
+    for (int r = 1; r < top; ++r)
+        if ((int64_t)h->rule.direction * ((int64_t)res[(size_t)r * 3] - res[(size_t)best * 3]) > 0) best = r;
+    const int jb = order[best];
+    const bool acc = engineer_accept(h->rule, h->tts_cur, res[(size_t)best * 3], ua[jb]);
+    for (int r = 0; r < top; ++r) {
+        const int j = order[r];
+        if (out) {
+            pt_step_result& o = out[r];
+            o.edge = e[j]; o.old_value = h->J[e[j]]; o.new_value = v[j];
+            o.tts_old = h->tts_cur; o.tts_new = res[(size_t)r * 3];
+            o.accepted = (acc && r == best) ? 1 : 0; o.cand_uid = cu[j];
+        }
+        if (ranked) ranked[r] = j;
+    }
+    if (pred) std::memcpy(pred, y.data(), sizeof(float) * n_prop);
+    if (acc) {
+        h->J[e[jb]] = (int8_t)v[jb];
+        h->tts_cur = res[(size_t)best * 3];
+        rc = upload_couplers(h, h->main, 0, h->J.data());
+        if (rc) return rc;
+    }
+    return PT_OK;
 }
 
 int engineer_current_tts(const pt_handle* h, int32_t* tts)

@@ -119,6 +119,24 @@ def test_chimera_automorphisms_leave_prediction_unchanged():
     assert not np.allclose(S.forward(theta, L, J3[None], H, layers), y0)
 
 
+def test_bf16_rounding_matches_library():
+    torch = pytest.importorskip("torch")
+    x = np.concatenate([np.random.default_rng(0).standard_normal(10000) * 10.0 ** np.arange(-5, 5).repeat(1000),
+                        [1.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -9, -0.0, 3.0e38]])
+    want = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(S.bf16_round(x), want)
+    assert S.bf16_round(np.array([1.0 + 2.0 ** -8]))[0] == 1.0          # tie goes to even
+
+
+def test_bf16_model_close_to_fp64_on_workload_sizes():
+    theta = W.surrogate_init_params(2)
+    J = _rand_J(4, 2, 5)
+    t = np.array([2.0, 3.0])
+    _, g = S.loss_and_grad(theta, 4, J, t)
+    _, gq = S.loss_and_grad(theta, 4, J, t, bf16=True)
+    assert np.linalg.norm(gq - g) / np.linalg.norm(g) < 2e-2
+
+
 def test_adam_first_step_closed_form():
     theta = np.array([1.0, -2.0, 0.5])
     g = np.array([0.3, -4.0, 1e-3])
