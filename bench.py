@@ -218,6 +218,8 @@ def run_gpu(args):
     h = P.PTHandle(L, J, betas, R, cfg["seed"], uid, stream=stream.cuda_stream)
     if args.schedule:
         h.set_schedule(*[int(x) for x in args.schedule.split(",")])
+    elif not args.no_autotune:
+        h.autotune(n_inst=spec, trial_sweeps=64)
     h.set_timing(True)
     h.engineer_begin(S=S, pass_mult=pm, exchange_every=cfg["exchange_every"], base_uid=uid)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")   # > 129 MB L2
@@ -474,7 +476,7 @@ def main():
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--speculation", type=int, default=8)
+    ap.add_argument("--speculation", type=int, default=16)
     ap.add_argument("--schedule", default="", help="slot_parallel,runs_per_cta,sweeps_per_launch")
     ap.add_argument("--cpu-sweeps", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true")

@@ -223,6 +223,12 @@ int pt_set_schedule(pt_handle *h, int32_t slot_parallel, int32_t runs_per_cta,
 int pt_get_schedule(const pt_handle *h, int32_t *slot_parallel, int32_t *runs_per_cta,
                     int32_t *sweeps_per_launch);
 
+/* Autotuner: times every feasible (slot_parallel, runs_per_cta in {1,2,4})
+ * for `trial_sweeps` sweeps of a batch of n_inst (1..16) copies of this
+ * instance, the shape of engineer_run's speculative batches, and keeps the
+ * fastest.  The main runs are untouched; results never depend on the choice. */
+int pt_autotune(pt_handle *h, int32_t n_inst, int32_t trial_sweeps);
+
 /* Makes `device` the current device of the calling host thread for the
  * library's CUDA runtime (handles created afterwards live there).  Errors:
  * PT_ERR_ARG (index out of range), PT_ERR_CUDA; failures are reported by

@@ -64,6 +64,7 @@ SIGNATURES = [
     ("pt_restore", C.c_int, [_VP, _VP, C.c_size_t]),
     ("pt_set_schedule", C.c_int, [_VP, C.c_int32, C.c_int32, C.c_int32]),
     ("pt_get_schedule", C.c_int, [_VP, _I32P, _I32P, _I32P]),
+    ("pt_autotune", C.c_int, [_VP, C.c_int32, C.c_int32]),
     ("pt_launch_count", C.c_uint64, [_VP]),
     ("pt_select_device", C.c_int, [C.c_int32]),
     ("pt_set_timing", C.c_int, [_VP, C.c_int]),
@@ -278,6 +279,10 @@ class PTHandle:
 
     def set_schedule(self, slot_parallel=0, runs_per_cta=0, sweeps_per_launch=0):
         _check(load().pt_set_schedule(self.h, int(slot_parallel), int(runs_per_cta), int(sweeps_per_launch)), self.h)
+
+    def autotune(self, n_inst=16, trial_sweeps=64):
+        _check(load().pt_autotune(self.h, int(n_inst), int(trial_sweeps)), self.h)
+        return self.schedule()
 
     def schedule(self):
         a, b, c = C.c_int32(), C.c_int32(), C.c_int32()

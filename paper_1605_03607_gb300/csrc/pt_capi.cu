@@ -870,6 +870,59 @@ int pt_set_schedule(pt_handle* h, int32_t sp, int32_t ipc, int32_t spl)
     return PT_OK;
 }
 
+// Times candidate schedules on a batch of `n_inst` copies of this instance
+// (the speculative engineering batch) and keeps the fastest.  Candidates: every
+// slot_parallel with slot_parallel * L^2 a multiple of 32 and at most 1024
+// threads, with runs per CTA 1, 2 or 4 (shared memory permitting).  The
+// candidate batch is left in an unspecified state; the main runs are untouched.
+int pt_autotune(pt_handle* h, int32_t n_inst, int32_t trial_sweeps)
+{
+    if (!h || n_inst < 1 || n_inst > 16 || trial_sweeps < 1) return fail(h, PT_ERR_ARG, "need 1 <= n_inst <= 16, trial_sweeps >= 1");
+    int rc = ensure_candidates(h, n_inst);
+    if (rc) return rc;
+    Group& g = h->cand;
+    for (int j = 0; j < g.n_inst; ++j) {
+        int r2 = upload_couplers(h, g, j, h->J.data());
+        if (r2) return r2;
+        g.desc[j].uid = 0x7A11u + (uint32_t)j;
+    }
+    if ((rc = upload_desc(h, g))) return rc;
+    if ((rc = group_reset(h, g, true))) return rc;
+    const int L2 = h->L * h->L;
+    const int old_sp = h->sp, old_ipc = h->ipc;
+    const bool old_timing = h->timing;
+    h->timing = true;
+    double best_rate = 0.0;
+    int best_sp = old_sp, best_ipc = old_ipc;
+    for (int sp = 1; sp <= h->NT && sp * L2 <= MAX_THREADS; ++sp) {
+        if ((sp * L2) % 32 != 0) continue;
+        for (int ipc : {1, 2, 4}) {
+            if (sp * L2 * ipc > MAX_THREADS || ipc > h->R) break;
+            if (bundle_smem_bytes(h->L, h->NT, ipc) > 200 * 1024) break;
+            h->sp = sp;
+            h->ipc = ipc;
+            if ((rc = group_schedule(h, g))) { h->timing = old_timing; return rc; }
+            if ((rc = group_sweeps(h, g, trial_sweeps, 1))) { h->timing = old_timing; return rc; }
+            CK(cudaStreamSynchronize(h->stream), "sync autotune");
+            double ms = 0.0;
+            for (int i = 0; i < h->ev_used; ++i) {
+                float t = 0.f;
+                CK(cudaEventElapsedTime(&t, h->ev[2 * i], h->ev[2 * i + 1]), "event time");
+                ms += t;
+            }
+            const double rate = (double)g.n_inst * h->R * h->NT * h->N * trial_sweeps / (ms * 1e-3);
+            if (rate > best_rate) { best_rate = rate; best_sp = sp; best_ipc = ipc; }
+        }
+    }
+    h->timing = old_timing;
+    h->sp = best_sp;
+    h->ipc = best_ipc;
+    if ((rc = group_schedule(h, h->main))) return rc;
+    if ((rc = group_schedule(h, g))) return rc;
+    CK(cudaStreamSynchronize(h->stream), "sync autotune");
+    return PT_OK;
+}
+
 int pt_get_schedule(const pt_handle* h, int32_t* sp, int32_t* ipc, int32_t* spl)
 {
     if (!h) return PT_ERR_ARG;
