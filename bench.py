@@ -389,10 +389,12 @@ def run_guided_experiment(args):
     J0s = [W.random_couplers(L, seed, u) for u in uids]
     J, y, tts = G.collect_pairs(L, J0s, betas, R, seed, uids, S, pm, args.guided_train_steps, 16)
     t_data = time.perf_counter() - t0
-    rng = np.random.default_rng(0)
-    perm = rng.permutation(len(y))
-    nval = max(len(y) // 10, 1)
-    val, tr = perm[:nval], perm[nval:]
+    # hold out whole seed instances (their loops) for validation
+    per = 1 + args.guided_train_steps
+    n_inst = len(uids)
+    n_val_inst = max(1, n_inst // 8)
+    val = np.arange((n_inst - n_val_inst) * per, n_inst * per)
+    tr = np.arange(0, (n_inst - n_val_inst) * per)
     model = P.Surrogate()
     model.set_params(W.surrogate_init_params(1))
     t1 = time.perf_counter()
@@ -409,20 +411,25 @@ def run_guided_experiment(args):
     test_uid = 999
     Jt = W.random_couplers(L, seed, test_uid)
     out = {}
+    Sc = args.guided_cmp_S
     for name in ("plain", "guided", "guided_untrained"):
         with P.PTHandle(L, Jt, betas, R, seed, test_uid) as h:
-            h.engineer_begin(S=S, pass_mult=pm, exchange_every=1, base_uid=test_uid)
+            h.engineer_begin(S=Sc, pass_mult=pm, exchange_every=1, base_uid=test_uid)
             if name == "plain":
                 tr_ = G.run_plain(h, args.guided_seconds, speculation=16)
             else:
                 tr_ = G.run_guided(h, model if name == "guided" else untrained, args.guided_seconds,
                                    n_prop=64, top=16)
-            out[name] = {"gain_log10_tts_per_gpu_s": G.gain_per_second(tr_), "tts_initial": int(tr_[0][1]),
-                         "tts_final": int(tr_[-1][1]), "gpu_s": tr_[-1][0], "steps": tr_[-1][2]}
+            out[name] = {"gain_log10_tts_per_gpu_s": G.gain_per_second(tr_, cap=Sc + 1),
+                         "tts_initial": int(tr_[0][1]), "tts_final": int(tr_[-1][1]), "gpu_s": tr_[-1][0],
+                         "steps": tr_[-1][2],
+                         "trace": [(round(t, 2), int(v)) for t, v, _ in tr_[:: max(1, len(tr_) // 12)]]}
     print(json.dumps({
         "workload": "guided_vs_plain", "metric": "log-TTS gain per GPU-s, surrogate vs plain",
-        "config": {"instance": "C_8, 32 temps beta [0.1,4], 64 runs", "S": S, "pass_mult": pm,
-                   "proposals": 64, "top": 16, "plain_speculation": 16, "gpu_seconds_each": args.guided_seconds},
+        "config": {"instance": "C_8, 32 temps beta [0.1,4], 64 runs", "S_train": S, "S_compare": Sc,
+                   "pass_mult": pm, "proposals": 64, "top": 16, "plain_speculation": 16,
+                   "gpu_seconds_each": args.guided_seconds,
+                   "gain": "until the TTS first reaches the unsolved cap S_compare + 1, or the budget ends"},
         "training": {"pairs": int(len(y)), "instances": len(uids), "epochs": 20, "batch": 256, "lr": 1e-3,
                      "loss_first": hist[0], "loss_last": hist[-1], "val_spearman": spearman(pv, y[val]),
                      "data_s": t_data, "train_s": t_train,
@@ -466,6 +473,7 @@ def main():
     ap.add_argument("--guided-train-instances", type=int, default=24)
     ap.add_argument("--guided-train-steps", type=int, default=48)
     ap.add_argument("--guided-seconds", type=float, default=60.0)
+    ap.add_argument("--guided-cmp-S", type=int, default=1 << 15)
     ap.add_argument("--batch-sweeps", type=int, default=1 << 14)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--profile-sweeps", type=int, default=0,

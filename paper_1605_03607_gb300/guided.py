@@ -24,25 +24,35 @@ def log10_tts(tts):
     return np.log10(np.maximum(np.asarray(tts, np.float64), 1.0))
 
 
-def collect_pairs(L, J0s, betas, n_runs, seed, uids, S, pass_mult, steps, speculation=16, on_step=None):
-    """Plain RAO from each seed instance; returns (J [n, E] int8, y [n] log10 TTS, tts [n])."""
+def _one_loop(L, J0, betas, n_runs, seed, uid, S, pass_mult, steps, speculation):
     Js, ys = [], []
-    for J0, uid in zip(J0s, uids):
-        with PTHandle(L, J0, betas, n_runs, seed, uid) as h:
-            t0 = h.engineer_begin(S=S, pass_mult=pass_mult, exchange_every=1, base_uid=uid)
-            J = np.asarray(J0, np.int8).copy()
-            Js.append(J.copy())
-            ys.append(t0)
-            res = h.engineer_run(0, steps, speculation)
-            for k in range(steps):
-                Jc = J.copy()
-                Jc[res["edge"][k]] = res["new_value"][k]
-                Js.append(Jc)
-                ys.append(int(res["tts_new"][k]))
-                if res["accepted"][k]:
-                    J = Jc
-            if on_step:
-                on_step(uid)
+    with PTHandle(L, J0, betas, n_runs, seed, uid) as h:
+        t0 = h.engineer_begin(S=S, pass_mult=pass_mult, exchange_every=1, base_uid=uid)
+        J = np.asarray(J0, np.int8).copy()
+        Js.append(J.copy())
+        ys.append(t0)
+        res = h.engineer_run(0, steps, speculation)
+        for k in range(steps):
+            Jc = J.copy()
+            Jc[res["edge"][k]] = res["new_value"][k]
+            Js.append(Jc)
+            ys.append(int(res["tts_new"][k]))
+            if res["accepted"][k]:
+                J = Jc
+    return Js, ys
+
+
+def collect_pairs(L, J0s, betas, n_runs, seed, uids, S, pass_mult, steps, speculation=16, workers=4):
+    """Plain RAO from each seed instance; returns (J [n, E] int8, y [n] log10 TTS, tts [n]).
+
+    `workers` loops run at once from host threads, each on its own handle and
+    stream (the library calls release the interpreter), to keep the GPU full."""
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=max(1, workers)) as ex:
+        parts = list(ex.map(lambda a: _one_loop(L, a[0], betas, n_runs, seed, a[1], S, pass_mult, steps,
+                                                speculation), zip(J0s, uids)))
+    Js = [j for p in parts for j in p[0]]
+    ys = [y for p in parts for y in p[1]]
     tts = np.array(ys, np.int64)
     return np.array(Js, np.int8), log10_tts(tts), tts
 
@@ -95,7 +105,15 @@ def run_guided(h, model, seconds, step0=0, n_prop=64, top=4, max_steps=10**9, pa
     return trace
 
 
-def gain_per_second(trace):
-    """(log10 TTS_final - log10 TTS_initial) / GPU-seconds of a loop trace."""
-    t_end, tts_end, _ = trace[-1]
+def gain_per_second(trace, cap=None):
+    """(log10 TTS - log10 TTS_initial) / GPU-seconds, up to the first point where
+    the TTS reaches `cap` (the unsolved value S + 1, beyond which no move can
+    count as harder) or to the end of the trace."""
+    end = len(trace) - 1
+    if cap is not None:
+        for i, (_, tts, _) in enumerate(trace):
+            if tts >= cap:
+                end = i
+                break
+    t_end, tts_end, _ = trace[end]
     return (log10_tts(tts_end) - log10_tts(trace[0][1])) / max(t_end, 1e-9)
