@@ -223,8 +223,18 @@ int pt_set_schedule(pt_handle *h, int32_t slot_parallel, int32_t runs_per_cta,
 int pt_get_schedule(const pt_handle *h, int32_t *slot_parallel, int32_t *runs_per_cta,
                     int32_t *sweeps_per_launch);
 
+/* Thread mapping of the sweep kernel.  team == 0: cell-major (a thread owns
+ * one Chimera cell and every slot_parallel-th temperature slot).  team > 0
+ * (a power of two <= 32): slot-major, slot_parallel teams of `team` lanes per
+ * run; a team owns every slot_parallel-th slot and its lanes split the cells,
+ * so the two colours of a slot are separated by a team sync instead of a CTA
+ * barrier.  0 keeps slot_parallel / runs_per_cta.  Results never depend on it. */
+int pt_set_mapping(pt_handle *h, int32_t team, int32_t slot_parallel, int32_t runs_per_cta);
+int pt_get_mapping(const pt_handle *h, int32_t *team);
+
 /* Autotuner: times every feasible (slot_parallel, runs_per_cta in {1,2,4})
- * for `trial_sweeps` sweeps of a batch of n_inst (1..16) copies of this
+ * of both mappings (slot-major teams of 2..32 lanes, 1/8 .. all slots per
+ * team) for `trial_sweeps` sweeps of a batch of n_inst (1..16) copies of this
  * instance, the shape of engineer_run's speculative batches, and keeps the
  * fastest.  The main runs are untouched; results never depend on the choice. */
 int pt_autotune(pt_handle *h, int32_t n_inst, int32_t trial_sweeps);

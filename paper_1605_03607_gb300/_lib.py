@@ -65,6 +65,8 @@ SIGNATURES = [
     ("pt_set_schedule", C.c_int, [_VP, C.c_int32, C.c_int32, C.c_int32]),
     ("pt_get_schedule", C.c_int, [_VP, _I32P, _I32P, _I32P]),
     ("pt_autotune", C.c_int, [_VP, C.c_int32, C.c_int32]),
+    ("pt_set_mapping", C.c_int, [_VP, C.c_int32, C.c_int32, C.c_int32]),
+    ("pt_get_mapping", C.c_int, [_VP, _I32P]),
     ("pt_launch_count", C.c_uint64, [_VP]),
     ("pt_select_device", C.c_int, [C.c_int32]),
     ("pt_set_timing", C.c_int, [_VP, C.c_int]),
@@ -283,6 +285,14 @@ class PTHandle:
     def autotune(self, n_inst=16, trial_sweeps=64):
         _check(load().pt_autotune(self.h, int(n_inst), int(trial_sweeps)), self.h)
         return self.schedule()
+
+    def set_mapping(self, team, slot_parallel=0, runs_per_cta=0):
+        _check(load().pt_set_mapping(self.h, int(team), int(slot_parallel), int(runs_per_cta)), self.h)
+
+    def mapping(self):
+        t = C.c_int32()
+        _check(load().pt_get_mapping(self.h, C.byref(t)), self.h)
+        return t.value
 
     def schedule(self):
         a, b, c = C.c_int32(), C.c_int32(), C.c_int32()

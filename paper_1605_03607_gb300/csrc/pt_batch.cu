@@ -130,7 +130,7 @@ int build_bundles(pt_batch* b, const std::vector<int>* only_L = nullptr, int max
         const ShapeSched& s = b->sched[L];
         for (int r = 0; r < b->R; r += s.ipc) {
             Bundle bd;
-            bd.inst = i; bd.run0 = r; bd.nitems = std::min(s.ipc, b->R - r); bd.sp = s.sp;
+            bd.inst = i; bd.run0 = r; bd.nitems = std::min(s.ipc, b->R - r); bd.sp = s.sp; bd.team = 0;
             b->bundles.push_back(bd);
         }
         smem = std::max<int>(smem, (int)bundle_smem_bytes(L, b->NT[i], s.ipc));

@@ -67,6 +67,7 @@ struct pt_handle {
     int16_t* d_nbr = nullptr;
     Group main, cand;
     int sp = 0, ipc = 0, spl = 4096;
+    int team = 0;              // 0: cell-major mapping; > 0: slot-major with teams of this size
     uint64_t launches = 0;
     // timing of sweep launches
     bool timing = false;
@@ -139,13 +140,19 @@ void default_schedule(int L, int NT, int R, int& sp, int& ipc)
     while (ipc > 1 && bundle_smem_bytes(L, NT, ipc) > 110 * 1024) --ipc;
 }
 
-int check_schedule(pt_handle* h, int L, int NT, int sp, int ipc)
+int check_schedule(pt_handle* h, int L, int NT, int sp, int ipc, int team)
 {
     const int L2 = L * L;
     if (sp < 1 || ipc < 1) return fail(h, PT_ERR_ARG, "schedule values must be >= 1");
-    if ((sp * L2) % 32 != 0) return fail(h, PT_ERR_ARG, "slot_parallel * L^2 must be a multiple of 32");
-    if (sp * L2 * ipc > MAX_THREADS) return fail(h, PT_ERR_ARG, "more than 1024 threads per CTA");
-    if (bundle_smem_bytes(L, NT, ipc) > 227 * 1024) return fail(h, PT_ERR_ARG, "shared memory above 227 KB");
+    if (team > 0) {
+        if (team > 32 || (team & (team - 1)) != 0) return fail(h, PT_ERR_ARG, "team must be a power of two <= 32");
+        if (sp * team < 32) return fail(h, PT_ERR_ARG, "teams * team must be >= 32");
+        if (sp * team * ipc > MAX_THREADS) return fail(h, PT_ERR_ARG, "more than 1024 threads per CTA");
+    } else {
+        if ((sp * L2) % 32 != 0) return fail(h, PT_ERR_ARG, "slot_parallel * L^2 must be a multiple of 32");
+        if (sp * L2 * ipc > MAX_THREADS) return fail(h, PT_ERR_ARG, "more than 1024 threads per CTA");
+    }
+    if (bundle_smem_bytes(L, NT, ipc, team) > 227 * 1024) return fail(h, PT_ERR_ARG, "shared memory above 227 KB");
     return PT_OK;
 }
 
@@ -197,11 +204,11 @@ int group_schedule(pt_handle* h, Group& g)
     for (int i = 0; i < g.n_inst; ++i)
         for (int r = 0; r < g.R; r += h->ipc) {
             Bundle b;
-            b.inst = i; b.run0 = r; b.nitems = std::min(h->ipc, g.R - r); b.sp = h->sp;
+            b.inst = i; b.run0 = r; b.nitems = std::min(h->ipc, g.R - r); b.sp = h->sp; b.team = h->team;
             g.bundles.push_back(b);
         }
-    g.block = h->sp * L2 * h->ipc;
-    g.smem = (int)bundle_smem_bytes(g.L, g.NT, h->ipc);
+    g.block = (h->team > 0 ? h->sp * h->team : h->sp * L2) * h->ipc;
+    g.smem = (int)bundle_smem_bytes(g.L, g.NT, h->ipc, h->team);
     cudaFree(g.d_bundles);
     g.d_bundles = nullptr;
     CK(dalloc(&g.d_bundles, g.bundles.size()), "cudaMalloc bundles");
@@ -264,7 +271,7 @@ int group_sweeps(pt_handle* h, Group& g, int64_t n, int xevery)
         const int chunk = (int)std::min<int64_t>(h->spl, n - done);
         if (h->timing) CK(cudaEventRecord(h->ev[2 * li], h->stream), "event");
         CK(launch_sweeps(g.d_desc, g.d_bundles, (int)g.bundles.size(), (int)g.bundles.size(), g.block,
-                         g.smem, (uint32_t)g.sweep, chunk, xevery, 0, nullptr, h->stream),
+                         g.smem, (uint32_t)g.sweep, chunk, xevery, 0, nullptr, h->stream, h->team > 0),
            "sweep kernel");
         if (h->timing) CK(cudaEventRecord(h->ev[2 * li + 1], h->stream), "event");
         ++h->launches;
@@ -541,7 +548,7 @@ int pt_exchange(pt_handle* h)
     if (!h) return PT_ERR_ARG;
     Group& g = h->main;
     CK(launch_sweeps(g.d_desc, g.d_bundles, (int)g.bundles.size(), (int)g.bundles.size(), g.block,
-                     g.smem, (uint32_t)g.sweep, 0, 0, 1, nullptr, h->stream), "exchange kernel");
+                     g.smem, (uint32_t)g.sweep, 0, 0, 1, nullptr, h->stream, h->team > 0), "exchange kernel");
     ++h->launches;
     CK(cudaStreamSynchronize(h->stream), "sync exchange");
     return PT_OK;
@@ -859,7 +866,7 @@ int pt_set_schedule(pt_handle* h, int32_t sp, int32_t ipc, int32_t spl)
     if (!h) return PT_ERR_ARG;
     const int nsp = sp > 0 ? sp : h->sp, nipc = ipc > 0 ? ipc : h->ipc;
     if (spl < 0) return fail(h, PT_ERR_ARG, "sweeps_per_launch must be >= 0");
-    int rc = check_schedule(h, h->L, h->NT, nsp, nipc);
+    int rc = check_schedule(h, h->L, h->NT, nsp, nipc, h->team);
     if (rc) return rc;
     h->sp = nsp;
     h->ipc = std::min(nipc, h->R);
@@ -867,6 +874,28 @@ int pt_set_schedule(pt_handle* h, int32_t sp, int32_t ipc, int32_t spl)
     if ((rc = group_schedule(h, h->main))) return rc;
     if (h->cand.n_inst > 0 && (rc = group_schedule(h, h->cand))) return rc;
     CK(cudaStreamSynchronize(h->stream), "sync schedule");
+    return PT_OK;
+}
+
+int pt_set_mapping(pt_handle* h, int32_t team, int32_t slot_parallel, int32_t runs_per_cta)
+{
+    if (!h || team < 0) return fail(h, PT_ERR_ARG, "team must be >= 0");
+    const int nsp = slot_parallel > 0 ? slot_parallel : h->sp, nipc = runs_per_cta > 0 ? runs_per_cta : h->ipc;
+    int rc = check_schedule(h, h->L, h->NT, nsp, nipc, team);
+    if (rc) return rc;
+    h->team = team;
+    h->sp = nsp;
+    h->ipc = std::min(nipc, h->R);
+    if ((rc = group_schedule(h, h->main))) return rc;
+    if (h->cand.n_inst > 0 && (rc = group_schedule(h, h->cand))) return rc;
+    CK(cudaStreamSynchronize(h->stream), "sync mapping");
+    return PT_OK;
+}
+
+int pt_get_mapping(const pt_handle* h, int32_t* team)
+{
+    if (!h || !team) return PT_ERR_ARG;
+    *team = h->team;
     return PT_OK;
 }
 
@@ -889,16 +918,27 @@ int pt_autotune(pt_handle* h, int32_t n_inst, int32_t trial_sweeps)
     if ((rc = upload_desc(h, g))) return rc;
     if ((rc = group_reset(h, g, true))) return rc;
     const int L2 = h->L * h->L;
-    const int old_sp = h->sp, old_ipc = h->ipc;
+    const int old_sp = h->sp, old_ipc = h->ipc, old_team = h->team;
     const bool old_timing = h->timing;
     h->timing = true;
     double best_rate = 0.0;
-    int best_sp = old_sp, best_ipc = old_ipc;
-    for (int sp = 1; sp <= h->NT && sp * L2 <= MAX_THREADS; ++sp) {
-        if ((sp * L2) % 32 != 0) continue;
+    int best_sp = old_sp, best_ipc = old_ipc, best_team = old_team;
+    // candidate (team, slot_parallel) pairs: cell-major (team 0) and slot-major
+    std::vector<std::pair<int, int>> cands;
+    for (int sp = 1; sp <= h->NT && sp * L2 <= MAX_THREADS; ++sp)
+        if ((sp * L2) % 32 == 0) cands.push_back({0, sp});
+    for (int team : {2, 4, 8, 16, 32}) {
+        if (team > L2) break;
+        for (int nt : {h->NT, (h->NT + 1) / 2, (h->NT + 3) / 4, (h->NT + 7) / 8})
+            if (nt >= 1 && nt * team >= 32 && nt * team <= MAX_THREADS) cands.push_back({team, nt});
+    }
+    for (const auto& c : cands) {
+        const int team = c.first, sp = c.second;
+        const int tpr = team > 0 ? sp * team : sp * L2;
         for (int ipc : {1, 2, 4}) {
-            if (sp * L2 * ipc > MAX_THREADS || ipc > h->R) break;
-            if (bundle_smem_bytes(h->L, h->NT, ipc) > 200 * 1024) break;
+            if (tpr * ipc > MAX_THREADS || ipc > h->R) break;
+            if (bundle_smem_bytes(h->L, h->NT, ipc, team) > 200 * 1024) break;
+            h->team = team;
             h->sp = sp;
             h->ipc = ipc;
             if ((rc = group_schedule(h, g))) { h->timing = old_timing; return rc; }
@@ -911,10 +951,11 @@ int pt_autotune(pt_handle* h, int32_t n_inst, int32_t trial_sweeps)
                 ms += t;
             }
             const double rate = (double)g.n_inst * h->R * h->NT * h->N * trial_sweeps / (ms * 1e-3);
-            if (rate > best_rate) { best_rate = rate; best_sp = sp; best_ipc = ipc; }
+            if (rate > best_rate) { best_rate = rate; best_sp = sp; best_ipc = ipc; best_team = team; }
         }
     }
     h->timing = old_timing;
+    h->team = best_team;
     h->sp = best_sp;
     h->ipc = best_ipc;
     if ((rc = group_schedule(h, h->main))) return rc;

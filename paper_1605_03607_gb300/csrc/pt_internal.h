@@ -43,27 +43,36 @@ struct InstDesc {
     unsigned long long* xacc; // [R][max(NT-1,1)] accepted swaps per pair
 };
 
-// One CTA work unit: `nitems` consecutive runs of one instance, processed by
-// slot_parallel * L^2 threads each.
+// One CTA work unit: `nitems` consecutive runs of one instance.
+//   team == 0 (cell-major): sp * L^2 threads per run; a thread owns one cell
+//              and every sp-th temperature slot.
+//   team  > 0 (slot-major): sp teams of `team` lanes (a power of two <= 32)
+//              per run; a team owns every sp-th slot, its lanes split the cells.
 struct Bundle {
-    int32_t inst, run0, nitems, sp;
+    int32_t inst, run0, nitems, sp, team;
 };
 
+__host__ __device__ inline int threads_per_run(int L, const Bundle& b)
+{
+    return b.team > 0 ? b.sp * b.team : b.sp * L * L;
+}
+
 // Shared-memory layout of one bundle: the Metropolis table of the instance,
-// then per item (run): spins [NT][N] (colour-major words per buffer), E by slot,
-// exchange critical h by pair (two sweeps), flip / swap counters, perm, best/first.
+// then per item (run): spins [NT][N] (colour-major words per buffer, plus
+// `pad` words per buffer in the slot-major mapping), E by slot, exchange
+// critical h by pair (two sweeps), flip / swap counters, perm, best/first.
 struct ItemLayout {
     int64_t spins, E, ccrit, macc, xacc, perm, misc, bytes;
 };
 
 __host__ __device__ inline int64_t pad16(int64_t x) { return (x + 15) & ~15LL; }
 
-__host__ __device__ inline ItemLayout item_layout(int L, int NT)
+__host__ __device__ inline ItemLayout item_layout(int L, int NT, int pad = 0)
 {
     ItemLayout o;
     const int64_t N = 8LL * L * L;
     o.spins = 0;
-    o.E = pad16((int64_t)NT * N);
+    o.E = pad16((int64_t)NT * (N + 4LL * pad));
     o.ccrit = o.E + 4LL * NT;
     o.macc = o.ccrit + 8LL * NT;
     o.xacc = o.macc + 4LL * NT;
@@ -80,8 +89,13 @@ __host__ __device__ inline int64_t table_bytes(int NT) { return pad16(4LL * NT *
 // Sets the message pt_last_error(NULL) returns (defined with the C ABI).
 void set_global_error(const char* msg);
 
-inline int64_t bundle_smem_bytes(int L, int NT, int nitems)
+// Slot-major mapping only: couplers [L^2][2][8] words and per (cell, colour)
+// one packed word: group index | minus-neighbour word << 10 | plus-neighbour word << 20.
+__host__ __device__ inline int64_t cell_table_bytes(int L) { return pad16(4LL * L * L * 16 + 4LL * L * L * 2); }
+
+inline int64_t bundle_smem_bytes(int L, int NT, int nitems, int team = 0)
 {
+    if (team > 0) return table_bytes(NT) + cell_table_bytes(L) + (int64_t)nitems * item_layout(L, NT, 1).bytes;
     return table_bytes(NT) + (int64_t)nitems * item_layout(L, NT).bytes;
 }
 

@@ -384,6 +384,187 @@ __device__ void process_bundle(const InstDesc* __restrict__ insts, const Bundle 
     __syncthreads();
 }
 
+// Slot-major mapping: a team of G lanes (a power of two, inside one warp)
+// owns every sp-th temperature slot of a run; its lanes split the cells.  For
+// each owned slot the team updates colour 0, syncs the team, updates colour 1,
+// and reduces its energy change and flip count once.  Teams of different
+// slots never wait for each other inside a sweep; the run's threads meet only
+// around the exchange.  Couplers and per-group offsets come from shared
+// memory; buffers are padded by one word so teams on different slots hit
+// different banks.
+__device__ void process_bundle_sm(const InstDesc* __restrict__ insts, const Bundle bd,
+                                  uint32_t sweep0, int nsweeps, int xevery, int mode,
+                                  unsigned char* smem)
+{
+    const InstDesc& in = insts[bd.inst];
+    const int L = in.L, NT = in.NT, L2 = L * L, N = 8 * L2, NW = N / 4, NWP = NW + 1;
+    const int G = bd.team, NTEAM = bd.sp, TPI = G * NTEAM;
+    const int tid = threadIdx.x;
+    const int item = tid / TPI, j = tid - item * TPI;
+    const bool active = item < bd.nitems;
+    const int team = j / G, tl = j - team * G;
+    const int run = bd.run0 + (active ? item : 0);
+    const ItemLayout lay = item_layout(L, NT, 1);
+
+    uint32_t* thr_sm = reinterpret_cast<uint32_t*>(smem);
+    uint32_t* jw_sm = reinterpret_cast<uint32_t*>(smem + table_bytes(NT));
+    uint32_t* meta_sm = jw_sm + L2 * 16;
+    unsigned char* ib = smem + table_bytes(NT) + cell_table_bytes(L) + (active ? item : 0) * lay.bytes;
+    uint32_t* sw = reinterpret_cast<uint32_t*>(ib + lay.spins);
+    int32_t* Es = reinterpret_cast<int32_t*>(ib + lay.E);
+    int32_t* ccrit = reinterpret_cast<int32_t*>(ib + lay.ccrit);
+    uint32_t* macc = reinterpret_cast<uint32_t*>(ib + lay.macc);
+    uint32_t* xacc = reinterpret_cast<uint32_t*>(ib + lay.xacc);
+    uint8_t* perm = ib + lay.perm;
+    int32_t* misc = reinterpret_cast<int32_t*>(ib + lay.misc);
+
+    // ---- tables, couplers, per-group offsets and this bundle's runs
+    for (int w = tid; w < NT * KT; w += blockDim.x) thr_sm[w] = in.thr[w];
+    for (int p = tid; p < NT; p += blockDim.x) {
+        reinterpret_cast<int32_t*>(thr_sm + NT * KT)[p] = in.xoff[p];
+        reinterpret_cast<float*>(thr_sm + NT * KT + NT)[p] = p < NT - 1 ? in.xhint[p] : 0.0f;
+    }
+    for (int w = tid; w < L2 * 16; w += blockDim.x) jw_sm[w] = in.jw[w];
+    for (int w = tid; w < L2 * 2; w += blockDim.x) {
+        const int q = w >> 1, col = w & 1, r = q / L, c = q - r * L;
+        const uint32_t gidx = (uint32_t)(2 * q + ((r + c + col) & 1));
+        const uint32_t mn = (uint32_t)((1 - col) * L2 + in.nbr[w * 2 + 0]);
+        const uint32_t pl = (uint32_t)((1 - col) * L2 + in.nbr[w * 2 + 1]);
+        meta_sm[w] = gidx | (mn << 10) | (pl << 20);
+    }
+    const size_t rep0 = (size_t)run * NT;
+    if (active) {
+        const uint32_t* gsp = reinterpret_cast<const uint32_t*>(in.spins + rep0 * N);
+        for (int w = j; w < NT * NW; w += TPI) {
+            const int buf = w / NW, g = w - buf * NW;
+            const int cell = g >> 1, u = g & 1, r = cell / L, c = cell - r * L;
+            sw[buf * NWP + ((r + c + u) & 1) * L2 + cell] = gsp[w];
+        }
+        for (int t = j; t < NT; t += TPI) {
+            Es[t] = in.E[rep0 + t];
+            perm[t] = in.perm[rep0 + t];
+            macc[t] = 0u;
+            xacc[t] = 0u;
+        }
+        if (j == 0) {
+            misc[0] = in.best[run];
+            misc[1] = in.first[run];
+        }
+    }
+    const int lane = tid & 31;
+    const unsigned tmask = G >= 32 ? FULL : (((1u << G) - 1u) << (lane & ~(G - 1)));
+    const uint32_t k0 = in.seed, k1 = in.uid;
+    const uint32_t runbits = (uint32_t)run << 16;
+    const int prep_warp_j0 = TPI >= 32 ? TPI - 32 : 0;
+    auto exch = [&](uint32_t sw_) {
+        return (NT > 1) && ((mode == 1) || (xevery > 0 && (sw_ % (uint32_t)xevery) == 0u));
+    };
+    const int n_iter = (mode == 0) ? nsweeps : 1;
+    const uint32_t s_first = (mode == 0) ? sweep0 + 1u : sweep0;
+    if (n_iter > 0 && exch(s_first) && active && j >= prep_warp_j0)
+        exchange_prepare(in, thr_sm, j - prep_warp_j0, s_first, runbits, k0, k1, NT, ccrit + (s_first & 1u) * NT);
+    __syncthreads();
+
+    for (int it = 0; it < n_iter; ++it) {
+        const uint32_t s = s_first + (uint32_t)it;
+        const bool do_x = exch(s);
+        if (mode == 0 && active) {
+            const PhiloxSweep ps = philox_sweep_pre(s, k0, k1);
+            for (int t = team; t < NT; t += NTEAM) {
+                uint32_t* bw = sw + perm[t] * NWP;
+                const uint32_t* th = thr_sm + t * KT;
+                const uint32_t c1 = runbits | (uint32_t)t;
+                int dk = 0, pc = 0;
+#pragma unroll
+                for (int col = 0; col < 2; ++col) {
+                    for (int q = tl; q < L2; q += G) {
+                        const uint4 jin = *reinterpret_cast<const uint4*>(jw_sm + (q * 2 + col) * 8);
+                        const uint4 jud = *reinterpret_cast<const uint4*>(jw_sm + (q * 2 + col) * 8 + 4);
+                        const uint32_t meta = meta_sm[q * 2 + col];
+                        const int ow = col * L2 + q;
+                        const uint32_t own = bw[ow];
+                        const int opp = (int)bw[(1 - col) * L2 + q];
+                        const uint32_t mw = bw[(meta >> 10) & 1023u], pw = bw[meta >> 20];
+                        const uint4 rn = philox_group(ps, c1, meta & 1023u, k0, k1);
+                        const int x01 = (int)__byte_perm(mw, pw, 0x5140);
+                        const int x23 = (int)__byte_perm(mw, pw, 0x7362);
+                        const int h0 = __dp4a((int)jin.x, opp, __dp4a((int)jud.x, x01, 0));
+                        const int h1 = __dp4a((int)jin.y, opp, __dp4a((int)jud.y, x01, 0));
+                        const int h2 = __dp4a((int)jin.z, opp, __dp4a((int)jud.z, x23, 0));
+                        const int h3 = __dp4a((int)jin.w, opp, __dp4a((int)jud.w, x23, 0));
+                        const int kk0 = (int)(int8_t)(own) * h0;
+                        const int kk1 = (int)(int8_t)(own >> 8) * h1;
+                        const int kk2 = (int)(int8_t)(own >> 16) * h2;
+                        const int kk3 = (int)(int8_t)(own >> 24) * h3;
+                        const bool a0 = (kk0 <= 0) | (rn.x < th[max(kk0, 0)]);
+                        const bool a1 = (kk1 <= 0) | (rn.y < th[max(kk1, 0)]);
+                        const bool a2 = (kk2 <= 0) | (rn.z < th[max(kk2, 0)]);
+                        const bool a3 = (kk3 <= 0) | (rn.w < th[max(kk3, 0)]);
+                        uint32_t flip = 0u;
+                        if (a0) { flip |= 0x000000FEu; dk += kk0; }
+                        if (a1) { flip |= 0x0000FE00u; dk += kk1; }
+                        if (a2) { flip |= 0x00FE0000u; dk += kk2; }
+                        if (a3) { flip |= 0xFE000000u; dk += kk3; }
+                        if (flip) bw[ow] = own ^ flip;
+                        pc += __popc(flip);
+                    }
+                    __syncwarp(tmask);                  // colour 0 of this slot done by the whole team
+                }
+                for (int o = G >> 1; o > 0; o >>= 1) {
+                    dk += __shfl_xor_sync(tmask, dk, o);
+                    pc += __shfl_xor_sync(tmask, pc, o);
+                }
+                if (tl == 0) {
+                    Es[t] += 2 * dk;
+                    macc[t] += (uint32_t)(pc / 7);
+                }
+            }
+        }
+        __syncthreads();
+        if (active && j == 0) {
+            int m;
+            if (do_x) {
+                m = exchange_chain(Es, perm, xacc, ccrit + (s & 1u) * NT, NT);
+            } else {
+                m = Es[0];
+                for (int p = 1; p < NT; ++p) m = min(m, Es[p]);
+            }
+            if (mode == 0 && m < misc[0]) {
+                misc[0] = m;
+                misc[1] = (int32_t)s;
+            }
+        }
+        if (it + 1 < n_iter && exch(s + 1u) && active && j >= prep_warp_j0)
+            exchange_prepare(in, thr_sm, j - prep_warp_j0, s + 1u, runbits, k0, k1, NT,
+                             ccrit + ((s + 1u) & 1u) * NT);
+        __syncthreads();
+    }
+
+    // ---- write the state back
+    if (active) {
+        uint32_t* gsp = reinterpret_cast<uint32_t*>(in.spins + rep0 * N);
+        for (int w = j; w < NT * NW; w += TPI) {
+            const int buf = w / NW, g = w - buf * NW;
+            const int cell = g >> 1, u = g & 1, r = cell / L, c = cell - r * L;
+            gsp[w] = sw[buf * NWP + ((r + c + u) & 1) * L2 + cell];
+        }
+        for (int t = j; t < NT; t += TPI) {
+            in.E[rep0 + t] = Es[t];
+            in.perm[rep0 + t] = perm[t];
+            in.macc[rep0 + t] += macc[t];
+            if (t < NT - 1) in.xacc[(size_t)run * (NT > 1 ? NT - 1 : 1) + t] += xacc[t];
+        }
+        if (j == 0) {
+            in.best[run] = misc[0];
+            in.first[run] = misc[1];
+        }
+    }
+    __syncthreads();
+}
+
+// SLOT_MAJOR selects the mapping of every bundle of the launch (the two are
+// separate instantiations so each keeps its own register allocation).
+template <bool SLOT_MAJOR>
 __global__ void __launch_bounds__(MAX_THREADS)
 pt_sweep_kernel(const InstDesc* __restrict__ insts, const Bundle* __restrict__ bundles,
                 int nbundles, uint32_t sweep0, int nsweeps, int xevery, int mode,
@@ -398,7 +579,11 @@ pt_sweep_kernel(const InstDesc* __restrict__ insts, const Bundle* __restrict__ b
         b = s_next;
     }
     while (b < nbundles) {
-        process_bundle(insts, bundles[b], sweep0, nsweeps, xevery, mode, smem);
+        const Bundle bd = bundles[b];
+        if (SLOT_MAJOR)
+            process_bundle_sm(insts, bd, sweep0, nsweeps, xevery, mode, smem);
+        else
+            process_bundle(insts, bd, sweep0, nsweeps, xevery, mode, smem);
         if (!queue) break;
         if (threadIdx.x == 0) s_next = atomicAdd(queue, 1);
         __syncthreads();
@@ -531,21 +716,27 @@ cudaError_t sweep_smem_capacity(int* bytes)
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    cudaFuncAttributes fa;
-    e = cudaFuncGetAttributes(&fa, pt_sweep_kernel);
+    cudaFuncAttributes fa, fb;
+    e = cudaFuncGetAttributes(&fa, pt_sweep_kernel<false>);
     if (e != cudaSuccess) return e;
-    *bytes = optin - (int)fa.sharedSizeBytes;
+    e = cudaFuncGetAttributes(&fb, pt_sweep_kernel<true>);
+    if (e != cudaSuccess) return e;
+    *bytes = optin - (int)(fa.sharedSizeBytes > fb.sharedSizeBytes ? fa.sharedSizeBytes : fb.sharedSizeBytes);
     return cudaSuccess;
 }
 
-cudaError_t sweep_occupancy(int block, int smem_bytes, int* blocks_per_sm)
+cudaError_t sweep_occupancy(int block, int smem_bytes, int* blocks_per_sm, bool slot_major)
 {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, pt_sweep_kernel, block, smem_bytes);
+    if (slot_major)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, pt_sweep_kernel<true>, block, smem_bytes);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, pt_sweep_kernel<false>, block, smem_bytes);
 }
 
 cudaError_t set_sweep_smem_limit(int bytes)
 {
-    return cudaFuncSetAttribute(pt_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e = cudaFuncSetAttribute(pt_sweep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(pt_sweep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 cudaError_t launch_init(const InstDesc* insts, const int2* items, int nitems, bool draw,
@@ -566,11 +757,15 @@ cudaError_t launch_energy(const InstDesc* insts, const int2* items, int nitems, 
 
 cudaError_t launch_sweeps(const InstDesc* insts, const Bundle* bundles, int nbundles, int grid,
                           int block, int smem_bytes, uint32_t sweep0, int nsweeps, int xevery,
-                          int mode, int* queue, cudaStream_t st)
+                          int mode, int* queue, cudaStream_t st, bool slot_major)
 {
     if (nbundles <= 0) return cudaSuccess;
-    pt_sweep_kernel<<<grid, block, smem_bytes, st>>>(insts, bundles, nbundles, sweep0, nsweeps,
-                                                     xevery, mode, queue);
+    if (slot_major)
+        pt_sweep_kernel<true><<<grid, block, smem_bytes, st>>>(insts, bundles, nbundles, sweep0, nsweeps,
+                                                               xevery, mode, queue);
+    else
+        pt_sweep_kernel<false><<<grid, block, smem_bytes, st>>>(insts, bundles, nbundles, sweep0, nsweeps,
+                                                                xevery, mode, queue);
     return cudaGetLastError();
 }
 

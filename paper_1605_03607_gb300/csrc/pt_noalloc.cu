@@ -218,6 +218,7 @@ extern "C" int pt_tts_eval_noalloc(int32_t L, const int8_t* J, int32_t n_edges, 
     for (int r = 0; r < n_runs; ++r) {
         h_items[r] = make_int2(0, r);
         h_bundles[r].inst = 0; h_bundles[r].run0 = r; h_bundles[r].nitems = 1; h_bundles[r].sp = sp;
+        h_bundles[r].team = 0;
     }
 
     // carve the scratch

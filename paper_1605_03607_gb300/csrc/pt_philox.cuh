@@ -100,4 +100,54 @@ __host__ __device__ __forceinline__ uint4 philox_slot(const PhiloxPre& p, uint32
     return make_uint4(a0, a1, a2, a3);
 }
 
+// The same counter (s, c1, g, 0) when a thread keeps the slot word c1 and
+// walks over groups g: only the products of round 0 word 0 and round 1 word 2
+// are independent of g; they are formed once per sweep.
+struct PhiloxSweep {
+    uint32_t y0k;   // round-1 high product of word 2, xor round-1 key word 0
+    uint32_t y1;    // round-1 low product of word 2
+    uint32_t x3k;   // round-0 low product of word 0, xor round-1 key word 1
+};
+
+__host__ __device__ __forceinline__ PhiloxSweep philox_sweep_pre(uint32_t s, uint32_t k0, uint32_t k1)
+{
+    const uint64_t A = (uint64_t)PHILOX_M0 * s;            // round 0, word 0
+    const uint32_t x2 = (uint32_t)(A >> 32) ^ k1;          // counter word 3 is 0
+    const uint64_t D = (uint64_t)PHILOX_M1 * x2;           // round 1, word 2
+    PhiloxSweep p;
+    p.y0k = (uint32_t)(D >> 32) ^ (k0 + PHILOX_W0);
+    p.y1 = (uint32_t)D;
+    p.x3k = (uint32_t)A ^ (k1 + PHILOX_W1);
+    return p;
+}
+
+// Output of philox10(s, c1, g, 0, k0, k1) given philox_sweep_pre(s, k0, k1).
+__host__ __device__ __forceinline__ uint4 philox_group(const PhiloxSweep& p, uint32_t c1, uint32_t g, uint32_t k0,
+                                                       uint32_t k1)
+{
+    const uint64_t B = (uint64_t)PHILOX_M1 * g;            // round 0, word 2
+    const uint32_t x0 = (uint32_t)(B >> 32) ^ c1 ^ k0;
+    const uint64_t C = (uint64_t)PHILOX_M0 * x0;           // round 1, word 0
+    uint32_t a0 = p.y0k ^ (uint32_t)B;
+    uint32_t a1 = p.y1;
+    uint32_t a2 = (uint32_t)(C >> 32) ^ p.x3k;
+    uint32_t a3 = (uint32_t)C;
+    k0 += 2u * PHILOX_W0;
+    k1 += 2u * PHILOX_W1;
+#pragma unroll
+    for (int r = 2; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)PHILOX_M0 * a0;
+        const uint64_t p1 = (uint64_t)PHILOX_M1 * a2;
+        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ a1 ^ k0;
+        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ a3 ^ k1;
+        a1 = (uint32_t)p1;
+        a3 = (uint32_t)p0;
+        a0 = n0;
+        a2 = n2;
+        k0 += PHILOX_W0;
+        k1 += PHILOX_W1;
+    }
+    return make_uint4(a0, a1, a2, a3);
+}
+
 }  // namespace ptg

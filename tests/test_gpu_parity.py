@@ -92,6 +92,46 @@ def test_sweeps_bit_exact(P, L, NT, R, n, x, sched):
     h.close()
 
 
+SLOT_MAJOR = [
+    # L, NT, R, sweeps, exchange_every, (team, slot_parallel teams, runs_per_cta)
+    (4, 16, 8, 150, 1, (4, 16, 1)),
+    (4, 16, 5, 120, 2, (2, 16, 2)),             # ragged runs per CTA
+    (8, 32, 4, 60, 1, (4, 32, 1)),
+    (8, 32, 3, 60, 1, (16, 8, 2)),              # a team owns 4 slots
+    (8, 32, 3, 40, 3, (32, 4, 1)),
+    (12, 24, 2, 20, 1, (8, 24, 1)),
+    (16, 48, 2, 8, 1, (16, 24, 1)),
+    (1, 4, 3, 300, 1, (8, 4, 1)),               # more lanes than cells
+    (5, 8, 2, 100, 1, (4, 8, 1)),
+    (4, 1, 4, 150, 1, (32, 1, 1)),              # one temperature
+    (4, 64, 2, 40, 1, (2, 64, 2)),              # maximum slots
+]
+
+
+@pytest.mark.parametrize("L,NT,R,n,x,mapping", SLOT_MAJOR)
+def test_slot_major_bit_exact(P, L, NT, R, n, x, mapping):
+    h, ref, _, _ = _pair(P, L, NT, R, seed=19 + L, uid=NT + 1)
+    h.set_mapping(*mapping)
+    assert h.mapping() == mapping[0]
+    h.sweep(n // 3, x)
+    h.sweep(n - n // 3, x)
+    ref.sweeps(n // 3, x)
+    ref.sweeps(n - n // 3, x)
+    _assert_state_equal(h.state(), ref, f"slot-major L={L} NT={NT} {mapping}")
+    h.exchange()
+    ref.exchange()
+    _assert_state_equal(h.state(), ref, "slot-major standalone exchange")
+    h.close()
+
+
+def test_autotune_keeps_results(P):
+    h, ref, _, _ = _pair(P, 8, 32, 4, seed=3, uid=3)
+    h.autotune(n_inst=4, trial_sweeps=8)
+    h.sweep(50, 1)
+    ref.sweeps(50, 1)
+    _assert_state_equal(h.state(), ref, f"autotuned {h.schedule()} team {h.mapping()}")
+
+
 def test_schedule_and_split_invariance(P):
     outs = []
     for sched in ((0, 0, 4096), (2, 1, 1), (8, 4, 13), (16, 4, 64)):
