@@ -350,7 +350,7 @@ def run_batched(args):
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     peak_ops = sms * INT_LANES_PER_SM_CLK * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     achieved = attempts * args.steps * OPS_PER_ATTEMPT / (kern_ms / 1e3)
-    sched = {L: b.schedule(L) for L in (4, 8, 12, 16)}
+    sched = {L: b.schedule(L) + (b.mapping(L),) for L in (4, 8, 12, 16)}
     print(json.dumps({
         "workload": "batched_256", "metric": METRIC, "value": attempts * args.steps / (wall),
         "unit": UNIT, "steps": args.steps, "warmup": args.warmup, "sweeps_per_step": sweeps,

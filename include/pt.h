@@ -309,16 +309,31 @@ int pt_batch_get_state(pt_batch *b, int32_t inst, int8_t *spins, int32_t *E, int
                        int32_t *first, uint64_t *macc, uint64_t *xacc);
 
 /* Schedule: CTA size `block` (multiple of 32, <= 1024; 0 keeps it) and, for
- * the instances of size chimera_L (0: none), slot_parallel * L^2 threads per
- * run and runs_per_cta runs per CTA.  Results never depend on the schedule. */
+ * the instances of size chimera_L (0: none), slot_parallel slots (cell-major:
+ * slot_parallel * L^2 threads, a multiple of 32) or teams (slot-major:
+ * slot_parallel * team threads, >= 32) per run and runs_per_cta runs per CTA.
+ * A size whose threads no longer fit the block gets the default schedule of
+ * the batch's mapping.  Results never depend on the schedule. */
 int pt_batch_set_schedule(pt_batch *b, int32_t block, int32_t chimera_L, int32_t slot_parallel,
                           int32_t runs_per_cta);
 int pt_batch_get_schedule(const pt_batch *b, int32_t chimera_L, int32_t *block,
                           int32_t *slot_parallel, int32_t *runs_per_cta);
 
-/* Autotuner: times every feasible (slot_parallel, runs_per_cta) of every
- * size for block sizes 256 and 512 over `trial_sweeps` sweeps of that size's
- * instances, keeps the fastest, then resets the runs. */
+/* Mapping of the batch (the rule of pt_set_mapping): team 0 is cell-major,
+ * team > 0 (a power of two <= 32) slot-major with slot_parallel teams of
+ * `team` lanes per run.  Every size of a batch shares one mapping, since one
+ * persistent launch runs one kernel: switching it gives every other size the
+ * mapping's default schedule.  chimera_L 0 switches the mapping only;
+ * slot_parallel / runs_per_cta 0 keep the current values.  PT_ERR_ARG when the
+ * result does not fit the block or 227 KB of shared memory. */
+int pt_batch_set_mapping(pt_batch *b, int32_t chimera_L, int32_t team, int32_t slot_parallel,
+                         int32_t runs_per_cta);
+int pt_batch_get_mapping(const pt_batch *b, int32_t chimera_L, int32_t *team);
+
+/* Autotuner: for block sizes 256 and 512 and both mappings, times every
+ * feasible schedule of every size over `trial_sweeps` sweeps of that size's
+ * instances, keeps the (block, mapping, schedules) with the shortest predicted
+ * batch time, then resets the runs. */
 int pt_batch_autotune(pt_batch *b, int32_t trial_sweeps, int32_t *block);
 
 /* Device time of the last pt_batch_run (CUDA events), persistent grid size,

@@ -86,6 +86,8 @@ SIGNATURES = [
     ("pt_batch_get_state", C.c_int, [_VP, C.c_int32] + [_VP] * 6),
     ("pt_batch_set_schedule", C.c_int, [_VP, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
     ("pt_batch_get_schedule", C.c_int, [_VP, C.c_int32, _I32P, _I32P, _I32P]),
+    ("pt_batch_set_mapping", C.c_int, [_VP, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
+    ("pt_batch_get_mapping", C.c_int, [_VP, C.c_int32, _I32P]),
     ("pt_batch_autotune", C.c_int, [_VP, C.c_int32, _I32P]),
     ("pt_batch_info", C.c_int, [_VP, C.POINTER(C.c_double), _I32P, _I32P, _I32P, C.POINTER(C.c_uint64)]),
     ("sg_last_error", C.c_char_p, [_VP]),
@@ -399,6 +401,15 @@ class PTBatch:
         a, b_, c = C.c_int32(), C.c_int32(), C.c_int32()
         _check_batch(load().pt_batch_get_schedule(self.b, int(L), C.byref(a), C.byref(b_), C.byref(c)), self.b)
         return a.value, b_.value, c.value
+
+    def set_mapping(self, team, L=0, slot_parallel=0, runs_per_cta=0):
+        _check_batch(load().pt_batch_set_mapping(self.b, int(L), int(team), int(slot_parallel),
+                                                 int(runs_per_cta)), self.b)
+
+    def mapping(self, L):
+        t = C.c_int32()
+        _check_batch(load().pt_batch_get_mapping(self.b, int(L), C.byref(t)), self.b)
+        return t.value
 
     def autotune(self, trial_sweeps=32):
         blk = C.c_int32()

@@ -27,9 +27,18 @@ using namespace ptg;
 
 namespace {
 
+// Per Chimera size: runs per CTA and, per run, either slot_parallel slots of
+// L^2 threads (cell-major, team 0) or slot_parallel teams of `team` lanes
+// (slot-major).  All sizes of a batch share one mapping: one launch runs one
+// kernel instantiation.
 struct ShapeSched {
-    int sp = 0, ipc = 0;
+    int sp = 0, ipc = 0, team = 0;
 };
+
+int sched_threads(int L, const ShapeSched& s)
+{
+    return s.team > 0 ? s.sp * s.team : s.sp * L * L;
+}
 
 }  // namespace
 
@@ -63,6 +72,7 @@ struct pt_batch {
     std::vector<size_t> rep_off;      // first replica of each instance
     std::map<int, ShapeSched> sched;  // per L
     int block = 512;
+    bool slot_major = false;
     std::vector<Bundle> bundles;
     int smem = 0, grid = 0;
     uint64_t sweep = 0;
@@ -98,15 +108,36 @@ int bcuda(pt_batch* b, cudaError_t e, const char* what)
         if (e_ != cudaSuccess) return bcuda(b, e_, what);   \
     } while (0)
 
+int max_temps_of(const pt_batch* b, int L)
+{
+    int nt = 1;
+    for (int i = 0; i < b->n_inst; ++i)
+        if (b->L[i] == L) nt = std::max(nt, b->NT[i]);
+    return nt;
+}
+
 template <class T>
 cudaError_t balloc(T** p, size_t n)
 {
     return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (n ? n : 1));
 }
 
-void default_shape_sched(int L, int NT, int R, int block, ShapeSched& s)
+void default_shape_sched(int L, int NT, int R, int block, bool slot_major, ShapeSched& s)
 {
     const int L2 = L * L;
+    if (slot_major) {
+        // one team of 4 lanes per slot (2 for the single-cell lattice), widened
+        // until a run has at least a warp
+        int team = L2 >= 4 ? 4 : 2, sp = std::max(1, NT);
+        while (sp * team < 32 && team < 32) team *= 2;
+        while (sp * team > block && sp > 1) sp = (sp + 1) / 2;
+        int ipc = std::max(1, std::min(block / (sp * team), R));
+        while (ipc > 1 && bundle_smem_bytes(L, NT, ipc, team) > 110 * 1024) --ipc;
+        s.team = team;
+        s.sp = sp;
+        s.ipc = ipc;
+        return;
+    }
     // about block/2 .. block threads per CTA, >= 32 threads per run
     int sp = std::max(1, std::min(NT, block / L2));
     while (sp * L2 < 32) ++sp;
@@ -114,13 +145,17 @@ void default_shape_sched(int L, int NT, int R, int block, ShapeSched& s)
     int ipc = std::max(1, block / (sp * L2));
     ipc = std::min(ipc, R);
     while (ipc > 1 && bundle_smem_bytes(L, NT, ipc) > 110 * 1024) --ipc;
+    s.team = 0;
     s.sp = sp;
     s.ipc = ipc;
 }
 
+// Builds the bundle list of the current schedules (optionally only the sizes
+// in only_L) and uploads it; on any error the previous list, grid and graph
+// stay as they were.
 int build_bundles(pt_batch* b, const std::vector<int>* only_L = nullptr, int max_inst_per_L = 0)
 {
-    b->bundles.clear();
+    std::vector<Bundle> bundles;
     std::map<int, int> taken;
     int smem = 0;
     for (int i = 0; i < b->n_inst; ++i) {
@@ -130,13 +165,16 @@ int build_bundles(pt_batch* b, const std::vector<int>* only_L = nullptr, int max
         const ShapeSched& s = b->sched[L];
         for (int r = 0; r < b->R; r += s.ipc) {
             Bundle bd;
-            bd.inst = i; bd.run0 = r; bd.nitems = std::min(s.ipc, b->R - r); bd.sp = s.sp; bd.team = 0;
-            b->bundles.push_back(bd);
+            bd.inst = i; bd.run0 = r; bd.nitems = std::min(s.ipc, b->R - r); bd.sp = s.sp;
+            bd.team = b->slot_major ? s.team : 0;
+            bundles.push_back(bd);
         }
-        smem = std::max<int>(smem, (int)bundle_smem_bytes(L, b->NT[i], s.ipc));
+        if (sched_threads(L, s) * s.ipc > b->block || (b->slot_major != (s.team > 0)))
+            return bfail(b, PT_ERR_ARG, "schedule of L=" + std::to_string(L) + " does not fit the block or mapping");
+        smem = std::max<int>(smem, (int)bundle_smem_bytes(L, b->NT[i], s.ipc, b->slot_major ? s.team : 0));
     }
     // longest bundles first (work per sweep = runs x slots x spins)
-    std::stable_sort(b->bundles.begin(), b->bundles.end(), [&](const Bundle& x, const Bundle& y) {
+    std::stable_sort(bundles.begin(), bundles.end(), [&](const Bundle& x, const Bundle& y) {
         const int64_t cx = (int64_t)x.nitems * b->NT[x.inst] * b->N[x.inst];
         const int64_t cy = (int64_t)y.nitems * b->NT[y.inst] * b->N[y.inst];
         return cx > cy;
@@ -145,17 +183,21 @@ int build_bundles(pt_batch* b, const std::vector<int>* only_L = nullptr, int max
     BK(sweep_smem_capacity(&cap), "shared memory capacity");
     if (smem > cap) return bfail(b, PT_ERR_ARG, "a bundle needs more shared memory than a CTA can have");
     BK(set_sweep_smem_limit(cap), "cudaFuncSetAttribute");
-    b->smem = smem;
     int dev = 0, sms = 0, per_sm = 0;
     BK(cudaGetDevice(&dev), "cudaGetDevice");
     BK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device attribute");
-    BK(sweep_occupancy(b->block, smem, &per_sm), "occupancy");
-    b->grid = std::max(1, std::min<int>((int)b->bundles.size(), sms * std::max(1, per_sm)));
+    BK(sweep_occupancy(b->block, smem, &per_sm, b->slot_major), "occupancy");
+    Bundle* d = nullptr;
+    BK(balloc(&d, bundles.size()), "cudaMalloc bundles");
+    cudaError_t e = cudaMemcpyAsync(d, bundles.data(), sizeof(Bundle) * bundles.size(), cudaMemcpyHostToDevice,
+                                    b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) { cudaFree(d); return bcuda(b, e, "upload bundles"); }
     cudaFree(b->d_bundles);
-    b->d_bundles = nullptr;
-    BK(balloc(&b->d_bundles, b->bundles.size()), "cudaMalloc bundles");
-    BK(cudaMemcpyAsync(b->d_bundles, b->bundles.data(), sizeof(Bundle) * b->bundles.size(),
-                       cudaMemcpyHostToDevice, b->stream), "upload bundles");
+    b->d_bundles = d;
+    b->bundles.swap(bundles);
+    b->smem = smem;
+    b->grid = std::max(1, std::min<int>((int)b->bundles.size(), sms * std::max(1, per_sm)));
     // the captured graph holds the old bundle list
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
     if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
@@ -174,7 +216,7 @@ int run_graph(pt_batch* b, int nsweeps, int xevery)
         if (e == cudaSuccess) e = cudaMemsetAsync(b->d_queue, 0, sizeof(int), cs);
         if (e == cudaSuccess)
             e = launch_sweeps(b->d_desc, b->d_bundles, (int)b->bundles.size(), b->grid, b->block, b->smem,
-                              (uint32_t)b->sweep, nsweeps, xevery, 0, b->d_queue, cs);
+                              (uint32_t)b->sweep, nsweeps, xevery, 0, b->d_queue, cs, b->slot_major);
         cudaGraph_t g = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(cs, &g);
         cudaStreamDestroy(cs);
@@ -342,8 +384,10 @@ int pt_batch_create(pt_batch** out, int32_t n_inst, const pt_instance_desc* d, i
         o_nt += (size_t)NT;
         o_pair += (size_t)n_runs * std::max(NT - 1, 1);
         for (int r = 0; r < n_runs; ++r) items.push_back(make_int2(i, r));
-        if (!b->sched.count(L)) default_shape_sched(L, NT, n_runs, b->block, b->sched[L]);
     }
+    for (auto& kv : b->sched) kv.second = ShapeSched();
+    for (int i = 0; i < n_inst; ++i) b->sched[b->L[i]];
+    for (auto& kv : b->sched) default_shape_sched(kv.first, max_temps_of(b, kv.first), n_runs, b->block, false, kv.second);
     BKC(cudaMemcpy(b->d_desc, b->desc.data(), sizeof(InstDesc) * b->desc.size(), cudaMemcpyHostToDevice), "upload desc");
     BKC(cudaMemcpy(b->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice), "upload items");
     // per-L smem check against the largest temperature count of that L
@@ -450,30 +494,75 @@ int pt_batch_get_state(pt_batch* b, int32_t inst, int8_t* spins, int32_t* E, int
 int pt_batch_set_schedule(pt_batch* b, int32_t block, int32_t chimera_L, int32_t slot_parallel, int32_t runs_per_cta)
 {
     if (!b) return PT_ERR_ARG;
-    if (block > 0) {
-        if (block % 32 != 0 || block > MAX_THREADS) return bfail(b, PT_ERR_ARG, "block must be a multiple of 32, <= 1024");
-        b->block = block;
-    }
+    if (block > 0 && (block % 32 != 0 || block > MAX_THREADS))
+        return bfail(b, PT_ERR_ARG, "block must be a multiple of 32, <= 1024");
+    if (chimera_L > 0 && !b->sched.count(chimera_L)) return bfail(b, PT_ERR_ARG, "no instance of that size");
+    // validate on copies; the batch changes only when everything fits
+    const int nblock = block > 0 ? block : b->block;
+    std::map<int, ShapeSched> sched = b->sched;
     if (chimera_L > 0) {
-        if (!b->sched.count(chimera_L)) return bfail(b, PT_ERR_ARG, "no instance of that size");
-        const int L2 = chimera_L * chimera_L;
-        if (slot_parallel < 1 || runs_per_cta < 1 || slot_parallel * L2 < 32 ||
-            slot_parallel * L2 * runs_per_cta > b->block)
-            return bfail(b, PT_ERR_ARG, "need slot_parallel * L^2 >= 32 and slot_parallel * L^2 * runs_per_cta <= block");
-        b->sched[chimera_L].sp = slot_parallel;
-        b->sched[chimera_L].ipc = std::min(runs_per_cta, b->R);
+        ShapeSched s = sched[chimera_L];
+        s.sp = slot_parallel;
+        s.ipc = std::min<int>(runs_per_cta, b->R);
+        const int tpr = sched_threads(chimera_L, s);
+        if (slot_parallel < 1 || runs_per_cta < 1 || tpr < 32 || tpr * s.ipc > nblock)
+            return bfail(b, PT_ERR_ARG, "need threads per run >= 32 and threads per run * runs_per_cta <= block");
+        if (s.team == 0 && tpr % 32 != 0)
+            return bfail(b, PT_ERR_ARG, "cell-major: slot_parallel * L^2 must be a multiple of 32");
+        sched[chimera_L] = s;
     }
-    for (auto& kv : b->sched) {       // keep every size inside the block
-        const int L2 = kv.first * kv.first;
-        if (kv.second.sp * L2 * kv.second.ipc > b->block) {
-            int nt = 1;
-            for (int i = 0; i < b->n_inst; ++i) if (b->L[i] == kv.first) nt = std::max(nt, b->NT[i]);
-            default_shape_sched(kv.first, nt, b->R, b->block, kv.second);
-        }
-    }
+    for (auto& kv : sched)           // keep every size inside the block
+        if (sched_threads(kv.first, kv.second) * kv.second.ipc > nblock)
+            default_shape_sched(kv.first, max_temps_of(b, kv.first), b->R, nblock, b->slot_major, kv.second);
+    const std::map<int, ShapeSched> old_sched = b->sched;
+    const int old_block = b->block;
+    b->sched = sched;
+    b->block = nblock;
     int rc = build_bundles(b);
-    if (rc) return rc;
+    if (rc) {
+        b->sched = old_sched;
+        b->block = old_block;
+        return rc;
+    }
     BK(cudaStreamSynchronize(b->stream), "sync schedule");
+    return PT_OK;
+}
+
+int pt_batch_set_mapping(pt_batch* b, int32_t chimera_L, int32_t team, int32_t slot_parallel, int32_t runs_per_cta)
+{
+    if (!b || team < 0) return bfail(b, PT_ERR_ARG, "team must be >= 0");
+    if (team > 0 && (team > 32 || (team & (team - 1)) != 0))
+        return bfail(b, PT_ERR_ARG, "team must be a power of two <= 32");
+    if (chimera_L > 0 && !b->sched.count(chimera_L)) return bfail(b, PT_ERR_ARG, "no instance of that size");
+    // validate on copies; the batch changes only when everything fits
+    const bool sm = team > 0;
+    std::map<int, ShapeSched> sched = b->sched;
+    if (sm != b->slot_major)        // the other sizes follow to the new mapping
+        for (auto& kv : sched)
+            default_shape_sched(kv.first, max_temps_of(b, kv.first), b->R, b->block, sm, kv.second);
+    if (chimera_L > 0) {
+        ShapeSched s = sched[chimera_L];
+        s.team = team;
+        if (slot_parallel > 0) s.sp = slot_parallel;
+        if (runs_per_cta > 0) s.ipc = std::min<int>(runs_per_cta, b->R);
+        const int tpr = sched_threads(chimera_L, s);
+        if (tpr < 32 || tpr * s.ipc > b->block || (!sm && tpr % 32 != 0))
+            return bfail(b, PT_ERR_ARG, "mapping does not fit the block (threads per run >= 32, x runs_per_cta <= block)");
+        if (bundle_smem_bytes(chimera_L, max_temps_of(b, chimera_L), s.ipc, team) > 227 * 1024)
+            return bfail(b, PT_ERR_ARG, "shared memory above 227 KB");
+        sched[chimera_L] = s;
+    }
+    const std::map<int, ShapeSched> old_sched = b->sched;
+    const bool old_sm = b->slot_major;
+    b->sched = sched;
+    b->slot_major = sm;
+    int rc = build_bundles(b);
+    if (rc) {
+        b->sched = old_sched;
+        b->slot_major = old_sm;
+        return rc;
+    }
+    BK(cudaStreamSynchronize(b->stream), "sync mapping");
     return PT_OK;
 }
 
@@ -489,11 +578,20 @@ int pt_batch_get_schedule(const pt_batch* b, int32_t chimera_L, int32_t* block, 
     return PT_OK;
 }
 
+int pt_batch_get_mapping(const pt_batch* b, int32_t chimera_L, int32_t* team)
+{
+    if (!b) return PT_ERR_ARG;
+    auto it = b->sched.find(chimera_L);
+    if (it == b->sched.end()) return PT_ERR_ARG;
+    if (team) *team = b->slot_major ? it->second.team : 0;
+    return PT_OK;
+}
+
 // Times candidate schedules and keeps the fastest.  For each block size in
-// {256, 512} and each Chimera size, every (threads per run, runs per CTA)
-// that fits is timed on all instances of that size for `trial_sweeps`
-// sweeps; the block size whose best per-size schedules give the shortest
-// predicted batch time wins.  The state is reset afterwards.
+// {256, 512}, each mapping (cell-major, slot-major) and each Chimera size,
+// every schedule that fits is timed on all instances of that size for
+// `trial_sweeps` sweeps; the (block, mapping) whose best per-size schedules
+// give the shortest predicted batch time wins.  The state is reset afterwards.
 int pt_batch_autotune(pt_batch* b, int32_t trial_sweeps, int32_t* block_out)
 {
     if (!b || trial_sweeps < 1) return bfail(b, PT_ERR_ARG, "need trial_sweeps >= 1");
@@ -503,54 +601,90 @@ int pt_batch_autotune(pt_batch* b, int32_t trial_sweeps, int32_t* block_out)
         work[b->L[i]] += (int64_t)b->R * b->NT[i] * b->N[i];
         maxnt[b->L[i]] = std::max(maxnt[b->L[i]], b->NT[i]);
     }
+    const int old_block = b->block;
+    const bool old_sm = b->slot_major;
+    const std::map<int, ShapeSched> old_sched = b->sched;
+    auto restore = [&]() {
+        b->block = old_block;
+        b->slot_major = old_sm;
+        b->sched = old_sched;
+        build_bundles(b);
+    };
     double best_total = 1e300;
     int best_block = b->block;
-    std::map<int, ShapeSched> best_sched;
+    bool best_sm = b->slot_major;
+    std::map<int, ShapeSched> best_sched = b->sched;
     for (int block : {256, 512}) {
-        b->block = block;
-        std::map<int, ShapeSched> chosen;
-        double total = 0.0;
-        for (auto& kv : work) {
-            const int L = kv.first, L2 = L * L;
-            double best_rate = 0.0;
-            ShapeSched bs;
-            for (int sp : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64}) {
-                if (sp > maxnt[L] || sp * L2 > block) break;
-                if (sp * L2 < 32) continue;
-                const int ipc_max = std::min(block / (sp * L2), b->R);
-                for (int ipc : {1, 2, 4, 8, 16}) {
-                    if (ipc > ipc_max) break;
-                    if (bundle_smem_bytes(L, maxnt[L], ipc) > 200 * 1024) break;
-                    b->sched[L].sp = sp;
-                    b->sched[L].ipc = ipc;
-                    std::vector<int> only{L};
-                    int rc = build_bundles(b, &only, 0);
-                    if (rc) continue;
-                    int64_t att = 0;
-                    for (const Bundle& x : b->bundles) att += (int64_t)x.nitems * b->NT[x.inst] * b->N[x.inst];
-                    att *= trial_sweeps;
-                    BK(cudaEventRecord(b->e0, b->stream), "event");
-                    BK(cudaMemsetAsync(b->d_queue, 0, sizeof(int), b->stream), "queue reset");
-                    BK(launch_sweeps(b->d_desc, b->d_bundles, (int)b->bundles.size(), b->grid, b->block, b->smem,
-                                     0u, trial_sweeps, 1, 0, b->d_queue, b->stream), "trial launch");
-                    BK(cudaEventRecord(b->e1, b->stream), "event");
-                    BK(cudaEventSynchronize(b->e1), "sync trial");
-                    float ms = 0.f;
-                    BK(cudaEventElapsedTime(&ms, b->e0, b->e1), "event time");
-                    const double rate = att / (ms * 1e-3);
-                    if (rate > best_rate) { best_rate = rate; bs.sp = sp; bs.ipc = ipc; }
+        for (bool sm : {false, true}) {
+            b->block = block;
+            b->slot_major = sm;
+            std::map<int, ShapeSched> chosen;
+            double total = 0.0;
+            for (auto& kv : work) {
+                const int L = kv.first, L2 = L * L, NT = maxnt[L];
+                // (team, slot_parallel) candidates of this mapping
+                std::vector<std::pair<int, int>> cands;
+                if (!sm) {
+                    for (int sp : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64})
+                        if (sp <= NT && sp * L2 <= block && (sp * L2) % 32 == 0) cands.push_back({0, sp});
+                } else {
+                    for (int team : {2, 4, 8, 16, 32}) {
+                        if (team > 2 * L2 && !cands.empty()) break;
+                        int prev = 0;
+                        for (int nt : {NT, (NT + 1) / 2, (NT + 3) / 4, (NT + 7) / 8})
+                            if (nt != prev && nt * team >= 32 && nt * team <= block) {
+                                cands.push_back({team, nt});
+                                prev = nt;
+                            }
+                    }
                 }
+                double best_rate = 0.0;
+                ShapeSched bs;
+                for (const auto& c : cands) {
+                    const int tpr = c.first > 0 ? c.second * c.first : c.second * L2;
+                    for (int ipc : {1, 2, 4, 8, 16}) {
+                        if (tpr * ipc > block || ipc > b->R) break;
+                        if (bundle_smem_bytes(L, NT, ipc, c.first) > 200 * 1024) break;
+                        ShapeSched& s = b->sched[L];
+                        s.team = c.first;
+                        s.sp = c.second;
+                        s.ipc = ipc;
+                        std::vector<int> only{L};
+                        int rc = build_bundles(b, &only, 0);
+                        if (rc) continue;
+                        int64_t att = 0;
+                        for (const Bundle& x : b->bundles) att += (int64_t)x.nitems * b->NT[x.inst] * b->N[x.inst];
+                        att *= trial_sweeps;
+                        cudaError_t e = cudaEventRecord(b->e0, b->stream);
+                        if (e == cudaSuccess) e = cudaMemsetAsync(b->d_queue, 0, sizeof(int), b->stream);
+                        if (e == cudaSuccess)
+                            e = launch_sweeps(b->d_desc, b->d_bundles, (int)b->bundles.size(), b->grid, b->block,
+                                              b->smem, 0u, trial_sweeps, 1, 0, b->d_queue, b->stream, sm);
+                        if (e == cudaSuccess) e = cudaEventRecord(b->e1, b->stream);
+                        if (e == cudaSuccess) e = cudaEventSynchronize(b->e1);
+                        float ms = 0.f;
+                        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, b->e0, b->e1);
+                        if (e != cudaSuccess) {
+                            const int code = bcuda(b, e, "trial launch");
+                            restore();
+                            return code;
+                        }
+                        const double rate = att / (ms * 1e-3);
+                        if (rate > best_rate) { best_rate = rate; bs = s; }
+                    }
+                }
+                if (best_rate <= 0.0) { total = 1e300; break; }
+                chosen[L] = bs;
+                total += (double)kv.second / best_rate;
             }
-            if (best_rate <= 0.0) { total = 1e300; break; }
-            chosen[L] = bs;
-            total += (double)kv.second / best_rate;
+            if (total < best_total) { best_total = total; best_block = block; best_sm = sm; best_sched = chosen; }
         }
-        if (total < best_total) { best_total = total; best_block = block; best_sched = chosen; }
     }
     b->block = best_block;
+    b->slot_major = best_sm;
     for (auto& kv : best_sched) b->sched[kv.first] = kv.second;
     int rc = build_bundles(b);
-    if (rc) return rc;
+    if (rc) { restore(); return rc; }
     rc = pt_batch_reset(b);
     if (rc) return rc;
     if (block_out) *block_out = b->block;

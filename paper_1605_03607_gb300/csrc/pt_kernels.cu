@@ -322,6 +322,7 @@ __device__ void process_bundle(const InstDesc* __restrict__ insts, const Bundle 
     };
     const int n_iter = (mode == 0) ? nsweeps : 1;
     const uint32_t s_first = (mode == 0) ? sweep0 + 1u : sweep0;
+    __syncthreads();                            // tables staged before the first exchange preparation
     if (n_iter > 0 && exch(s_first) && active && j >= prep_warp_j0)
         exchange_prepare(in, thr_sm, j - prep_warp_j0, s_first, runbits, k0, k1, NT, ccrit + (s_first & 1u) * NT);
     __syncthreads();
@@ -461,6 +462,7 @@ __device__ void process_bundle_sm(const InstDesc* __restrict__ insts, const Bund
     };
     const int n_iter = (mode == 0) ? nsweeps : 1;
     const uint32_t s_first = (mode == 0) ? sweep0 + 1u : sweep0;
+    __syncthreads();                            // tables staged before the first exchange preparation
     if (n_iter > 0 && exch(s_first) && active && j >= prep_warp_j0)
         exchange_prepare(in, thr_sm, j - prep_warp_j0, s_first, runbits, k0, k1, NT, ccrit + (s_first & 1u) * NT);
     __syncthreads();

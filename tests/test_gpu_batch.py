@@ -89,6 +89,54 @@ def test_batch_schedule_and_autotune_invariance(P):
                 assert np.array_equal(st[i][k], states[0][i][k]), (i, k)
 
 
+def test_slot_major_batch_bit_exact(P):
+    """The whole batch on the slot-major mapping (one kernel instantiation per
+    launch), default schedules and several per-size team layouts, against the
+    oracle and against the cell-major batch."""
+    seed, R = 94, 3
+    inst = _mixed(seed)
+    with P.PTBatch(inst, R, seed) as b:
+        b.run(30, 1)
+        cell = [b.state(i) for i in range(len(inst))]
+        b.set_mapping(4)                                 # switch only: defaults for every size
+        assert all(b.mapping(x["L"]) > 0 for x in inst)
+        b.reset()
+        b.run(18, 1)
+        b.run(12, 1)
+        for i, x in enumerate(inst):
+            _check_instance(b.state(i), x, R, seed, 30, f"slot-major instance {i} L={x['L']}")
+        layouts = ((4, 2, 16, 2), (8, 8, 4, 1), (16, 16, 2, 1), (12, 32, 2, 2), (1, 8, 4, 1),
+                   (4, 32, 1, 3))
+        for L, team, sp, ipc in layouts:
+            b.set_mapping(team, L, sp, ipc)
+            assert b.mapping(L) == team and b.schedule(L)[1:] == (sp, min(ipc, R))
+            b.reset()
+            b.run(30, 1)
+            for i in range(len(inst)):
+                st = b.state(i)
+                for k in ("spins", "E", "best", "first", "macc", "xacc"):
+                    assert np.array_equal(st[k], cell[i][k]), (L, team, sp, ipc, i, k)
+        b.set_mapping(0)                                 # back to cell-major
+        assert b.mapping(4) == 0
+        b.reset()
+        b.run(30, 1)
+        for i in range(len(inst)):
+            assert np.array_equal(b.state(i)["spins"], cell[i]["spins"]), i
+
+
+def test_batch_mapping_rejects_misfits(P):
+    inst = _mixed(5)[:3]                                 # sizes 4, 8, 12
+    with P.PTBatch(inst, 2, 5) as b:
+        with pytest.raises(P.PTError, match="power of two"):
+            b.set_mapping(6, 4, 8, 1)
+        with pytest.raises(P.PTError, match="fit"):
+            b.set_mapping(4, 8, 4, 1)                    # 16 threads per run
+        with pytest.raises(P.PTError, match="fit"):
+            b.set_mapping(32, 8, 32, 1)                  # 1024 threads > block 512
+        with pytest.raises(P.PTError, match="no instance"):
+            b.set_mapping(4, 7, 8, 1)
+
+
 def test_batched_config_shape_sampled(P):
     """The batched configuration (256 instances, C_4/8/12/16, 24..48 temperatures,
     32 runs): a short run compared with the oracle on one instance of each size,
