@@ -216,9 +216,11 @@ def run_gpu(args):
     betas = W.beta_ladder(NT, cfg["beta_min"], cfg["beta_max"])
     stream = torch.cuda.current_stream()
     h = P.PTHandle(L, J, betas, R, cfg["seed"], uid, stream=stream.cuda_stream)
+    if args.mapping:
+        h.set_mapping(*[int(x) for x in args.mapping.split(",")])
     if args.schedule:
         h.set_schedule(*[int(x) for x in args.schedule.split(",")])
-    elif not args.no_autotune:
+    elif not args.no_autotune and not args.mapping:
         h.autotune(n_inst=spec, trial_sweeps=64)
     h.set_timing(True)
     h.engineer_begin(S=S, pass_mult=pm, exchange_every=cfg["exchange_every"], base_uid=uid)
@@ -287,7 +289,8 @@ def run_gpu(args):
                                "beta geometric [0.1,4], 64 PT runs, S=2^16, target from 4x pass, "
                                "exchange every sweep",
                    "step": f"engineer_run: {spec} RAO steps, candidates evaluated in batches of {spec}",
-                   "speculation": spec, "schedule": list(h.schedule()), "l2": "flushed between steps",
+                   "speculation": spec, "schedule": list(h.schedule()), "team": h.mapping(),
+                   "l2": "flushed between steps",
                    "parallelism": f"{ws} independent instance(s), one per GPU"},
         "pt_tts_evals_per_s": tot_evals / t_dev,
         "rao_steps_per_s": tot_steps / t_dev,
@@ -324,7 +327,13 @@ def run_batched(args):
     attempts = sum(cfg["n_runs"] * len(x["betas"]) * 8 * x["L"] ** 2 for x in inst) * sweeps
     stream = torch.cuda.current_stream()
     b = P.PTBatch(inst, cfg["n_runs"], cfg["seed"], stream=stream.cuda_stream)
-    if not args.no_autotune:
+    if args.batch_mapping:
+        # "L:team,slot_parallel,runs_per_cta;..." (team 0: cell-major)
+        for item in args.batch_mapping.split(";"):
+            Ls, rest = item.split(":")
+            team, sp, ipc = (int(x) for x in rest.split(","))
+            b.set_mapping(team, int(Ls), sp, ipc)
+    elif not args.no_autotune:
         b.autotune(trial_sweeps=16)
     for _ in range(args.warmup):
         b.reset()
@@ -452,6 +461,8 @@ def run_profile_case(args):
     J = W.random_couplers(cfg["L"], cfg["seed"], 0)
     betas = W.beta_ladder(cfg["n_temps"], cfg["beta_min"], cfg["beta_max"])
     h = P.PTHandle(cfg["L"], J, betas, cfg["n_runs"] * args.profile_instances, cfg["seed"], 0)
+    if args.mapping:
+        h.set_mapping(*[int(x) for x in args.mapping.split(",")])
     if args.schedule:
         h.set_schedule(*[int(x) for x in args.schedule.split(",")])
     spl = h.schedule()[2]
@@ -461,7 +472,7 @@ def run_profile_case(args):
     ms, n = h.sweep_timing_total()
     att = args.profile_sweeps * spl * h.R * h.NT * h.N
     print(json.dumps({"profile_case": True, "launches": n, "ms": ms, "attempts_per_s": att / (ms / 1e3),
-                      "runs": h.R, "schedule": list(h.schedule())}))
+                      "runs": h.R, "schedule": list(h.schedule()), "team": h.mapping()}))
     h.close()
     return 0
 
@@ -475,6 +486,8 @@ def main():
     ap.add_argument("--guided-seconds", type=float, default=60.0)
     ap.add_argument("--guided-cmp-S", type=int, default=1 << 15)
     ap.add_argument("--batch-sweeps", type=int, default=1 << 14)
+    ap.add_argument("--batch-mapping", default="",
+                    help="batched workload: 'L:team,slot_parallel,runs_per_cta;...' instead of the autotuner")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--profile-sweeps", type=int, default=0,
                     help="profiling case: this many sweep launches on the bench instance, then exit")
@@ -486,6 +499,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--speculation", type=int, default=16)
     ap.add_argument("--schedule", default="", help="slot_parallel,runs_per_cta,sweeps_per_launch")
+    ap.add_argument("--mapping", default="", help="team,slot_parallel,runs_per_cta (team 0: cell-major); "
+                    "skips the autotuner")
     ap.add_argument("--cpu-sweeps", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()

@@ -226,9 +226,11 @@ int pt_get_schedule(const pt_handle *h, int32_t *slot_parallel, int32_t *runs_pe
 /* Thread mapping of the sweep kernel.  team == 0: cell-major (a thread owns
  * one Chimera cell and every slot_parallel-th temperature slot).  team > 0
  * (a power of two <= 32): slot-major, slot_parallel teams of `team` lanes per
- * run; a team owns every slot_parallel-th slot and its lanes split the cells,
- * so the two colours of a slot are separated by a team sync instead of a CTA
- * barrier.  0 keeps slot_parallel / runs_per_cta.  Results never depend on it. */
+ * run (>= 32 threads per run, <= 768 threads per CTA); a team owns every
+ * slot_parallel-th spin buffer, updates it at the temperature of the slot
+ * holding it, and its lanes split the cells, so the two colours are separated
+ * by a team sync instead of a CTA barrier.  0 keeps slot_parallel /
+ * runs_per_cta.  Results never depend on it. */
 int pt_set_mapping(pt_handle *h, int32_t team, int32_t slot_parallel, int32_t runs_per_cta);
 int pt_get_mapping(const pt_handle *h, int32_t *team);
 
@@ -268,7 +270,10 @@ int pt_last_sweep_timing(const pt_handle *h, double *ms, int32_t *launches);
 
 /* ---------------------------------------------------------------------
  * Batched PT: many instances of uneven size and temperature count, each
- * with n_runs independent runs (Sec. II), in one persistent kernel launch.
+ * with n_runs independent runs (Sec. II), in one graph replay.  Instances
+ * are grouped by Chimera size; each size has its own thread mapping,
+ * schedule, CTA size and persistent grid, and the sizes run as concurrent
+ * graph branches (largest work first by stream priority).
  * Instance i keeps its own key (seed, uid_i): its trajectory is identical to
  * a pt_create handle with the same (J, betas, n_runs, seed, uid).
  * --------------------------------------------------------------------- */
@@ -295,9 +300,9 @@ void pt_batch_destroy(pt_batch *b);
 int pt_batch_reset(pt_batch *b);
 
 /* n_sweeps sweeps of every run of every instance (same sweep/exchange rule
- * as pt_sweep) as one replay of a CUDA graph holding the work-queue reset
- * and one persistent launch: CTAs pull bundles of runs, longest first, from
- * an atomic counter until none is left. */
+ * as pt_sweep) as one replay of a CUDA graph holding the work-counter reset
+ * and one persistent launch per size: a size's CTAs pull bundles of its runs,
+ * longest first, from that size's atomic counter until none is left. */
 int pt_batch_run(pt_batch *b, int32_t n_sweeps, int32_t exchange_every);
 
 /* Per-instance TTS (rule of pt_tts with target = best found, horizon given):
@@ -308,36 +313,41 @@ int pt_batch_tts(pt_batch *b, int32_t horizon, int32_t *tts, int32_t *n_hit, int
 int pt_batch_get_state(pt_batch *b, int32_t inst, int8_t *spins, int32_t *E, int32_t *best,
                        int32_t *first, uint64_t *macc, uint64_t *xacc);
 
-/* Schedule: CTA size `block` (multiple of 32, <= 1024; 0 keeps it) and, for
- * the instances of size chimera_L (0: none), slot_parallel slots (cell-major:
- * slot_parallel * L^2 threads, a multiple of 32) or teams (slot-major:
- * slot_parallel * team threads, >= 32) per run and runs_per_cta runs per CTA.
- * A size whose threads no longer fit the block gets the default schedule of
- * the batch's mapping.  Results never depend on the schedule. */
+/* Schedule of the instances of size chimera_L: slot_parallel slots
+ * (cell-major: slot_parallel * L^2 threads per run) or teams (slot-major:
+ * slot_parallel * team threads per run, at the size's largest temperature
+ * count; an instance with fewer temperatures gets proportionally fewer
+ * teams) per run, >= 32 threads per run, runs_per_cta runs per CTA, and the
+ * CTA size `block` (a multiple of 32, <= 1024, <= 768 slot-major; 0: the
+ * bundle's thread count rounded up to a warp).  chimera_L 0 sets `block` for
+ * every size.  PT_ERR_ARG (nothing changed) when a size does not fit its
+ * block or 227 KB of shared memory.  Results never depend on the schedule. */
 int pt_batch_set_schedule(pt_batch *b, int32_t block, int32_t chimera_L, int32_t slot_parallel,
                           int32_t runs_per_cta);
 int pt_batch_get_schedule(const pt_batch *b, int32_t chimera_L, int32_t *block,
                           int32_t *slot_parallel, int32_t *runs_per_cta);
 
-/* Mapping of the batch (the rule of pt_set_mapping): team 0 is cell-major,
- * team > 0 (a power of two <= 32) slot-major with slot_parallel teams of
- * `team` lanes per run.  Every size of a batch shares one mapping, since one
- * persistent launch runs one kernel: switching it gives every other size the
- * mapping's default schedule.  chimera_L 0 switches the mapping only;
- * slot_parallel / runs_per_cta 0 keep the current values.  PT_ERR_ARG when the
- * result does not fit the block or 227 KB of shared memory. */
+/* Thread mapping of size chimera_L (the rule of pt_set_mapping): team 0 is
+ * cell-major, team > 0 (a power of two <= 32) slot-major with slot_parallel
+ * teams of `team` lanes per run.  Switching mapping starts from that mapping's
+ * default schedule; slot_parallel / runs_per_cta 0 keep it; the CTA size
+ * becomes the bundle's thread count.  chimera_L 0 gives every size the
+ * mapping's default schedule.  PT_ERR_ARG (nothing changed) when the result
+ * does not fit (>= 32 threads per run, <= 768 threads per CTA slot-major,
+ * 227 KB of shared memory). */
 int pt_batch_set_mapping(pt_batch *b, int32_t chimera_L, int32_t team, int32_t slot_parallel,
                          int32_t runs_per_cta);
 int pt_batch_get_mapping(const pt_batch *b, int32_t chimera_L, int32_t *team);
 
-/* Autotuner: for block sizes 256 and 512 and both mappings, times every
- * feasible schedule of every size over `trial_sweeps` sweeps of that size's
- * instances, keeps the (block, mapping, schedules) with the shortest predicted
- * batch time, then resets the runs. */
+/* Autotuner: size by size, times every feasible cell-major (slot_parallel,
+ * runs_per_cta) and slot-major (team, slot_parallel, runs_per_cta) on all
+ * instances of that size over `trial_sweeps` sweeps, with the CTA size the
+ * bundle needs, keeps the fastest, then resets the runs.  *block (may be
+ * NULL): the CTA size of the size with the most work. */
 int pt_batch_autotune(pt_batch *b, int32_t trial_sweeps, int32_t *block);
 
-/* Device time of the last pt_batch_run (CUDA events), persistent grid size,
- * block size, bundle count, kernels launched so far. */
+/* Device time of the last pt_batch_run (CUDA events), persistent CTAs over
+ * all sizes, largest CTA size, bundle count, kernels launched so far. */
 int pt_batch_info(const pt_batch *b, double *last_run_ms, int32_t *grid, int32_t *block,
                   int32_t *n_bundles, uint64_t *launches);
 

@@ -1,13 +1,16 @@
 // pt_batch.cu -- batched PT of many instances of uneven size and temperature
-// count in one persistent, graph-captured launch (C ABI: pt_batch_* in pt.h).
+// count in one graph replay (C ABI: pt_batch_* in pt.h).
 //
-// Every (instance, run) pair is an independent PT run (Sec. II); the host packs
-// them into CTA bundles (a few runs of one instance), orders the bundles by
-// cost (longest first), and one persistent kernel grid pulls bundles from an
-// atomic counter until none is left.  The queue reset and the launch are
-// captured once in a CUDA graph; each pt_batch_run replays it with the sweep
-// counter patched into the kernel node.  Schedules per Chimera size (threads
-// per run, runs per CTA) come from pt_batch_autotune and never change results.
+// Every (instance, run) pair is an independent PT run (Sec. II).  Instances
+// are grouped by Chimera size, and each size group has its own thread mapping,
+// schedule, CTA size and persistent grid.  The host packs a group's runs into
+// CTA bundles (a few runs of one instance), orders them by cost (longest
+// first), and the group's persistent kernel pulls bundles from its own atomic
+// counter until none is left.  The counter reset and one persistent launch per
+// group, as concurrent graph branches (largest work at the highest priority, so
+// the smaller groups fill its tail), are captured once in a CUDA graph; each
+// pt_batch_run replays it with the sweep counter patched into the kernel
+// nodes.  Schedules come from pt_batch_autotune and never change results.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
@@ -27,18 +30,25 @@ using namespace ptg;
 
 namespace {
 
-// Per Chimera size: runs per CTA and, per run, either slot_parallel slots of
-// L^2 threads (cell-major, team 0) or slot_parallel teams of `team` lanes
-// (slot-major).  All sizes of a batch share one mapping: one launch runs one
-// kernel instantiation.
+// Schedule of one size: runs per CTA and, per run, either slot_parallel slots
+// of L^2 threads (cell-major, team 0) or slot_parallel teams of `team` lanes
+// (slot-major, at the size's largest temperature count).  block 0: the CTA
+// size is the bundle's thread count rounded up to a warp.
 struct ShapeSched {
-    int sp = 0, ipc = 0, team = 0;
+    int sp = 0, ipc = 0, team = 0, block = 0;
 };
 
-int sched_threads(int L, const ShapeSched& s)
-{
-    return s.team > 0 ? s.sp * s.team : s.sp * L * L;
-}
+struct SizeGroup {
+    int L = 0, ntmax = 0, prio = 0;
+    int64_t work = 0;                 // attempts per sweep
+    ShapeSched s;
+    std::vector<Bundle> bundles;
+    Bundle* d_bundles = nullptr;
+    int block = 0, smem = 0, grid = 0;
+    cudaStream_t st = nullptr;        // capture branch
+    cudaEvent_t ev = nullptr;
+    cudaGraphNode_t knode = nullptr;
+};
 
 }  // namespace
 
@@ -65,22 +75,17 @@ struct pt_batch {
     int16_t* nbr = nullptr;
     InstDesc* d_desc = nullptr;
     int2* d_items = nullptr;
-    Bundle* d_bundles = nullptr;
-    int* d_queue = nullptr;
+    int* d_queue = nullptr;            // one work counter per group
     int32_t* d_tts = nullptr;
     std::vector<InstDesc> desc;
     std::vector<size_t> rep_off;      // first replica of each instance
-    std::map<int, ShapeSched> sched;  // per L
-    int block = 512;
-    bool slot_major = false;
-    std::vector<Bundle> bundles;
-    int smem = 0, grid = 0;
+    std::vector<SizeGroup> groups;    // largest work first
     uint64_t sweep = 0;
     uint64_t launches = 0;
-    // graph of {queue reset, persistent sweep kernel}
+    // graph of {counter reset, one persistent sweep kernel per group}
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    cudaGraphNode_t knode = nullptr;
+    cudaEvent_t ev_fork = nullptr;
     int g_nsweeps = -1, g_xevery = -1;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     double last_ms = 0.0;
@@ -116,63 +121,111 @@ int max_temps_of(const pt_batch* b, int L)
     return nt;
 }
 
+int group_of(const pt_batch* b, int L)
+{
+    for (size_t k = 0; k < b->groups.size(); ++k)
+        if (b->groups[k].L == L) return (int)k;
+    return -1;
+}
+
 template <class T>
 cudaError_t balloc(T** p, size_t n)
 {
     return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (n ? n : 1));
 }
 
-void default_shape_sched(int L, int NT, int R, int block, bool slot_major, ShapeSched& s)
+void default_shape_sched(int L, int NT, int R, bool slot_major, ShapeSched& s)
 {
     const int L2 = L * L;
+    s.block = 0;
     if (slot_major) {
-        // one team of 4 lanes per slot (2 for the single-cell lattice), widened
-        // until a run has at least a warp
-        int team = L2 >= 4 ? 4 : 2, sp = std::max(1, NT);
+        // teams of about L^2/16 lanes (2..32), one buffer each, widened until a
+        // run has at least a warp; up to about 384 threads per CTA
+        int team = 2;
+        while (team < 32 && team * 16 < L2) team *= 2;
+        int sp = std::max(1, NT);
         while (sp * team < 32 && team < 32) team *= 2;
-        while (sp * team > block && sp > 1) sp = (sp + 1) / 2;
-        int ipc = std::max(1, std::min(block / (sp * team), R));
+        while (sp * team > 384 && sp > 1) sp = (sp + 1) / 2;
+        int ipc = std::max(1, std::min(384 / (sp * team), R));
         while (ipc > 1 && bundle_smem_bytes(L, NT, ipc, team) > 110 * 1024) --ipc;
         s.team = team;
         s.sp = sp;
         s.ipc = ipc;
         return;
     }
-    // about block/2 .. block threads per CTA, >= 32 threads per run
-    int sp = std::max(1, std::min(NT, block / L2));
+    // cell-major: about 256..512 threads per CTA, >= 32 per run
+    int sp = std::max(1, std::min(NT, 512 / L2));
     while (sp * L2 < 32) ++sp;
-    if (sp * L2 > block) sp = std::max(1, block / L2);
-    int ipc = std::max(1, block / (sp * L2));
-    ipc = std::min(ipc, R);
+    int ipc = std::max(1, std::min(512 / (sp * L2), R));
     while (ipc > 1 && bundle_smem_bytes(L, NT, ipc) > 110 * 1024) --ipc;
     s.team = 0;
     s.sp = sp;
     s.ipc = ipc;
 }
 
-// Builds the bundle list of the current schedules (optionally only the sizes
-// in only_L) and uploads it; on any error the previous list, grid and graph
-// stay as they were.
-int build_bundles(pt_batch* b, const std::vector<int>* only_L = nullptr, int max_inst_per_L = 0)
+// Bundle shape of one instance of group g: slot-major groups scale the team
+// count to the instance's temperature count (the buffers per team of the
+// group's largest count) and take more runs per CTA where that frees
+// threads, within the group's shared memory at its largest count.
+void instance_shape(const pt_batch* b, const SizeGroup& g, int NT, int* sp, int* ipc)
 {
+    const ShapeSched& s = g.s;
+    if (s.team == 0) {
+        *sp = s.sp;
+        *ipc = std::min(s.ipc, b->R);
+        return;
+    }
+    const int per = (g.ntmax + s.sp - 1) / s.sp;
+    const int spi = std::max((NT + per - 1) / per, (32 + s.team - 1) / s.team);
+    const int threads = s.sp * s.team * s.ipc;
+    const int64_t smem_cap = bundle_smem_bytes(g.L, g.ntmax, s.ipc, s.team);
+    int ipci = std::min(s.ipc, b->R);
+    while (ipci < b->R && spi * s.team * (ipci + 1) <= threads &&
+           bundle_smem_bytes(g.L, NT, ipci + 1, s.team) <= smem_cap)
+        ++ipci;
+    *sp = spi;
+    *ipc = ipci;
+}
+
+// Builds group k's bundle list from its schedule and uploads it; on any
+// error the group keeps its previous list, grid and CTA size.
+int build_group(pt_batch* b, int k)
+{
+    SizeGroup& g = b->groups[k];
+    const ShapeSched& s = g.s;
+    const bool sm = s.team > 0;
+    if (s.sp < 1 || s.ipc < 1 || (sm && (s.team > 32 || (s.team & (s.team - 1)) != 0)))
+        return bfail(b, PT_ERR_ARG, "bad schedule values");
+    if ((sm ? s.sp * s.team : s.sp * g.L * g.L) < 32)
+        return bfail(b, PT_ERR_ARG, "schedule of L=" + std::to_string(g.L) + " does not fit (threads per run >= 32)");
     std::vector<Bundle> bundles;
-    std::map<int, int> taken;
-    int smem = 0;
+    int threads = 0;
+    int64_t smem = 0;
     for (int i = 0; i < b->n_inst; ++i) {
-        const int L = b->L[i];
-        if (only_L && std::find(only_L->begin(), only_L->end(), L) == only_L->end()) continue;
-        if (max_inst_per_L > 0 && taken[L]++ >= max_inst_per_L) continue;
-        const ShapeSched& s = b->sched[L];
-        for (int r = 0; r < b->R; r += s.ipc) {
+        if (b->L[i] != g.L) continue;
+        int spi = 0, ipci = 0;
+        instance_shape(b, g, b->NT[i], &spi, &ipci);
+        const int tpr = sm ? spi * s.team : spi * g.L * g.L;
+        if (tpr < 32)
+            return bfail(b, PT_ERR_ARG, "schedule of L=" + std::to_string(g.L) + " does not fit (threads per run >= 32)");
+        for (int r = 0; r < b->R; r += ipci) {
             Bundle bd;
-            bd.inst = i; bd.run0 = r; bd.nitems = std::min(s.ipc, b->R - r); bd.sp = s.sp;
-            bd.team = b->slot_major ? s.team : 0;
+            bd.inst = i; bd.run0 = r; bd.nitems = std::min(ipci, b->R - r); bd.sp = spi; bd.team = s.team;
             bundles.push_back(bd);
         }
-        if (sched_threads(L, s) * s.ipc > b->block || (b->slot_major != (s.team > 0)))
-            return bfail(b, PT_ERR_ARG, "schedule of L=" + std::to_string(L) + " does not fit the block or mapping");
-        smem = std::max<int>(smem, (int)bundle_smem_bytes(L, b->NT[i], s.ipc, b->slot_major ? s.team : 0));
+        threads = std::max(threads, tpr * ipci);
+        smem = std::max<int64_t>(smem, bundle_smem_bytes(g.L, b->NT[i], ipci, s.team));
     }
+    int block = (threads + 31) / 32 * 32;
+    if (s.block > 0) {
+        if (s.block < block || s.block % 32 != 0)
+            return bfail(b, PT_ERR_ARG, "schedule of L=" + std::to_string(g.L) + " does not fit the block");
+        block = s.block;
+    }
+    if (block > (sm ? MAX_THREADS_SM : MAX_THREADS))
+        return bfail(b, PT_ERR_ARG, "schedule of L=" + std::to_string(g.L) + " does not fit: " +
+                                        std::to_string(block) + " threads per CTA (limit " +
+                                        std::to_string(sm ? MAX_THREADS_SM : MAX_THREADS) + ")");
     // longest bundles first (work per sweep = runs x slots x spins)
     std::stable_sort(bundles.begin(), bundles.end(), [&](const Bundle& x, const Bundle& y) {
         const int64_t cx = (int64_t)x.nitems * b->NT[x.inst] * b->N[x.inst];
@@ -186,69 +239,102 @@ int build_bundles(pt_batch* b, const std::vector<int>* only_L = nullptr, int max
     int dev = 0, sms = 0, per_sm = 0;
     BK(cudaGetDevice(&dev), "cudaGetDevice");
     BK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device attribute");
-    BK(sweep_occupancy(b->block, smem, &per_sm, b->slot_major), "occupancy");
+    BK(sweep_occupancy(block, (int)smem, &per_sm, sm), "occupancy");
+    if (per_sm < 1) return bfail(b, PT_ERR_ARG, "schedule of L=" + std::to_string(g.L) + " fits no CTA on an SM");
     Bundle* d = nullptr;
     BK(balloc(&d, bundles.size()), "cudaMalloc bundles");
     cudaError_t e = cudaMemcpyAsync(d, bundles.data(), sizeof(Bundle) * bundles.size(), cudaMemcpyHostToDevice,
                                     b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) { cudaFree(d); return bcuda(b, e, "upload bundles"); }
-    cudaFree(b->d_bundles);
-    b->d_bundles = d;
-    b->bundles.swap(bundles);
-    b->smem = smem;
-    b->grid = std::max(1, std::min<int>((int)b->bundles.size(), sms * std::max(1, per_sm)));
-    // the captured graph holds the old bundle list
+    cudaFree(g.d_bundles);
+    g.d_bundles = d;
+    g.bundles.swap(bundles);
+    g.block = block;
+    g.smem = (int)smem;
+    g.grid = std::max(1, std::min<int>((int)g.bundles.size(), sms * per_sm));
+    // the captured graph holds the old bundle lists
     if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
     if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
     b->g_nsweeps = b->g_xevery = -1;
     return PT_OK;
 }
 
+// Sets group k's schedule and rebuilds it, keeping the old one on failure.
+int set_group(pt_batch* b, int k, const ShapeSched& s)
+{
+    const ShapeSched old = b->groups[k].s;
+    b->groups[k].s = s;
+    const int rc = build_group(b, k);
+    if (rc) b->groups[k].s = old;
+    return rc;
+}
+
 int run_graph(pt_batch* b, int nsweeps, int xevery)
 {
+    const int ng = (int)b->groups.size();
     if (!b->exec || b->g_nsweeps != nsweeps || b->g_xevery != xevery) {
         if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
         if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
         cudaStream_t cs;
         BK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) e = cudaMemsetAsync(b->d_queue, 0, sizeof(int), cs);
-        if (e == cudaSuccess)
-            e = launch_sweeps(b->d_desc, b->d_bundles, (int)b->bundles.size(), b->grid, b->block, b->smem,
-                              (uint32_t)b->sweep, nsweeps, xevery, 0, b->d_queue, cs, b->slot_major);
-        cudaGraph_t g = nullptr;
-        cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->d_queue, 0, sizeof(int) * ng, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(b->ev_fork, cs);
+        for (int k = 0; k < ng && e == cudaSuccess; ++k) {
+            SizeGroup& g = b->groups[k];
+            e = cudaStreamWaitEvent(g.st, b->ev_fork, 0);
+            if (e == cudaSuccess)
+                e = launch_sweeps(b->d_desc, g.d_bundles, (int)g.bundles.size(), g.grid, g.block, g.smem,
+                                  (uint32_t)b->sweep, nsweeps, xevery, 0, b->d_queue + k, g.st, g.s.team > 0);
+            if (e == cudaSuccess) e = cudaEventRecord(g.ev, g.st);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, g.ev, 0);
+        }
+        cudaGraph_t gr = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(cs, &gr);
         cudaStreamDestroy(cs);
-        if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return bcuda(b, e, "graph capture"); }
+        if (e != cudaSuccess) { if (gr) cudaGraphDestroy(gr); return bcuda(b, e, "graph capture"); }
         if (e2 != cudaSuccess) return bcuda(b, e2, "end capture");
-        b->graph = g;
+        b->graph = gr;
         size_t n = 0;
-        BK(cudaGraphGetNodes(g, nullptr, &n), "graph nodes");
+        BK(cudaGraphGetNodes(gr, nullptr, &n), "graph nodes");
         std::vector<cudaGraphNode_t> nodes(n);
-        BK(cudaGraphGetNodes(g, nodes.data(), &n), "graph nodes");
-        b->knode = nullptr;
-        for (auto nd : nodes) {
+        BK(cudaGraphGetNodes(gr, nodes.data(), &n), "graph nodes");
+        for (auto& g : b->groups) g.knode = nullptr;
+        for (auto nd : nodes) {                  // a kernel node is known by its work counter
             cudaGraphNodeType t;
             BK(cudaGraphNodeGetType(nd, &t), "node type");
-            if (t == cudaGraphNodeTypeKernel) b->knode = nd;
+            if (t != cudaGraphNodeTypeKernel) continue;
+            cudaKernelNodeParams kp;
+            BK(cudaGraphKernelNodeGetParams(nd, &kp), "kernel node params");
+            const int* q = *reinterpret_cast<int* const*>(kp.kernelParams[7]);
+            const long k = (long)(q - b->d_queue);
+            if (k >= 0 && k < ng) b->groups[k].knode = nd;
         }
-        if (!b->knode) return bfail(b, PT_ERR_CUDA, "captured graph has no kernel node");
-        BK(cudaGraphInstantiate(&b->exec, g, 0), "graph instantiate");
+        for (auto& g : b->groups) {
+            if (!g.knode) return bfail(b, PT_ERR_CUDA, "captured graph lacks a group's kernel node");
+            cudaKernelNodeAttrValue v;
+            std::memset(&v, 0, sizeof(v));
+            v.priority = g.prio;
+            BK(cudaGraphKernelNodeSetAttribute(g.knode, cudaKernelNodeAttributePriority, &v), "node priority");
+        }
+        BK(cudaGraphInstantiate(&b->exec, gr, 0), "graph instantiate");
         b->g_nsweeps = nsweeps;
         b->g_xevery = xevery;
     }
     // patch the sweep counter (argument 3 of pt_sweep_kernel) and replay
-    cudaKernelNodeParams kp;
-    BK(cudaGraphKernelNodeGetParams(b->knode, &kp), "kernel node params");
     uint32_t sweep0 = (uint32_t)b->sweep;
-    void* args[8];
-    for (int i = 0; i < 8; ++i) args[i] = kp.kernelParams[i];
-    args[3] = &sweep0;
-    kp.kernelParams = args;
-    BK(cudaGraphExecKernelNodeSetParams(b->exec, b->knode, &kp), "patch kernel node");
+    for (auto& g : b->groups) {
+        cudaKernelNodeParams kp;
+        BK(cudaGraphKernelNodeGetParams(g.knode, &kp), "kernel node params");
+        void* args[8];
+        for (int i = 0; i < 8; ++i) args[i] = kp.kernelParams[i];
+        args[3] = &sweep0;
+        kp.kernelParams = args;
+        BK(cudaGraphExecKernelNodeSetParams(b->exec, g.knode, &kp), "patch kernel node");
+    }
     BK(cudaGraphLaunch(b->exec, b->stream), "graph launch");
-    b->launches += 1;
+    b->launches += (uint64_t)b->groups.size();
     return PT_OK;
 }
 
@@ -335,7 +421,9 @@ int pt_batch_create(pt_batch** out, int32_t n_inst, const pt_instance_desc* d, i
     BKC(balloc(&b->nbr, (size_t)(MAX_L + 1) * MAX_L * MAX_L * 4), "cudaMalloc nbr");
     BKC(balloc(&b->d_desc, (size_t)n_inst), "cudaMalloc desc");
     BKC(balloc(&b->d_items, runs), "cudaMalloc items");
-    BKC(balloc(&b->d_queue, 1), "cudaMalloc queue");
+    std::map<int, int> sizes;                                    // L -> instances
+    for (int i = 0; i < n_inst; ++i) sizes[b->L[i]] += 1;
+    BKC(balloc(&b->d_queue, sizes.size()), "cudaMalloc queues");
     BKC(balloc(&b->d_tts, (size_t)n_inst * 3), "cudaMalloc tts");
     BKC(cudaEventCreate(&b->e0), "event");
     BKC(cudaEventCreate(&b->e1), "event");
@@ -385,14 +473,35 @@ int pt_batch_create(pt_batch** out, int32_t n_inst, const pt_instance_desc* d, i
         o_pair += (size_t)n_runs * std::max(NT - 1, 1);
         for (int r = 0; r < n_runs; ++r) items.push_back(make_int2(i, r));
     }
-    for (auto& kv : b->sched) kv.second = ShapeSched();
-    for (int i = 0; i < n_inst; ++i) b->sched[b->L[i]];
-    for (auto& kv : b->sched) default_shape_sched(kv.first, max_temps_of(b, kv.first), n_runs, b->block, false, kv.second);
+    // one group per size, largest work first (that order is also the
+    // branches' stream priority order)
+    for (auto& kv : sizes) {
+        SizeGroup g;
+        g.L = kv.first;
+        g.ntmax = max_temps_of(b, g.L);
+        for (int i = 0; i < n_inst; ++i)
+            if (b->L[i] == g.L) g.work += (int64_t)n_runs * b->NT[i] * b->N[i];
+        default_shape_sched(g.L, g.ntmax, n_runs, false, g.s);
+        b->groups.push_back(g);
+    }
+    std::stable_sort(b->groups.begin(), b->groups.end(),
+                     [](const SizeGroup& x, const SizeGroup& y) { return x.work > y.work; });
+    int prio_least = 0, prio_greatest = 0;
+    BKC(cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest), "stream priorities");
+    for (size_t k = 0; k < b->groups.size(); ++k) {
+        SizeGroup& g = b->groups[k];
+        g.prio = std::min(prio_least, prio_greatest + (int)k);
+        BKC(cudaStreamCreateWithPriority(&g.st, cudaStreamNonBlocking, g.prio), "group stream");
+        BKC(cudaEventCreateWithFlags(&g.ev, cudaEventDisableTiming), "group event");
+    }
+    BKC(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming), "fork event");
     BKC(cudaMemcpy(b->d_desc, b->desc.data(), sizeof(InstDesc) * b->desc.size(), cudaMemcpyHostToDevice), "upload desc");
     BKC(cudaMemcpy(b->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice), "upload items");
-    // per-L smem check against the largest temperature count of that L
-    int rc = build_bundles(b);
-    if (rc) return bail(rc);
+    for (size_t k = 0; k < b->groups.size(); ++k) {
+        int rc = build_group(b, (int)k);
+        if (rc) return bail(rc);
+    }
+    int rc = PT_OK;
     rc = pt_batch_reset(b);
     if (rc) return bail(rc);
 #undef BKC
@@ -406,10 +515,16 @@ void pt_batch_destroy(pt_batch* b)
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
+    for (auto& g : b->groups) {
+        cudaFree(g.d_bundles);
+        if (g.st) cudaStreamDestroy(g.st);
+        if (g.ev) cudaEventDestroy(g.ev);
+    }
     cudaFree(b->spins); cudaFree(b->E); cudaFree(b->perm); cudaFree(b->best); cudaFree(b->first);
     cudaFree(b->macc); cudaFree(b->xacc); cudaFree(b->jw); cudaFree(b->thr); cudaFree(b->xoff);
     cudaFree(b->xthr); cudaFree(b->xhint); cudaFree(b->nbr); cudaFree(b->d_desc); cudaFree(b->d_items);
-    cudaFree(b->d_bundles); cudaFree(b->d_queue); cudaFree(b->d_tts);
+    cudaFree(b->d_queue); cudaFree(b->d_tts);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
     if (b->e0) cudaEventDestroy(b->e0);
     if (b->e1) cudaEventDestroy(b->e1);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
@@ -494,35 +609,30 @@ int pt_batch_get_state(pt_batch* b, int32_t inst, int8_t* spins, int32_t* E, int
 int pt_batch_set_schedule(pt_batch* b, int32_t block, int32_t chimera_L, int32_t slot_parallel, int32_t runs_per_cta)
 {
     if (!b) return PT_ERR_ARG;
-    if (block > 0 && (block % 32 != 0 || block > MAX_THREADS))
-        return bfail(b, PT_ERR_ARG, "block must be a multiple of 32, <= 1024");
-    if (chimera_L > 0 && !b->sched.count(chimera_L)) return bfail(b, PT_ERR_ARG, "no instance of that size");
-    // validate on copies; the batch changes only when everything fits
-    const int nblock = block > 0 ? block : b->block;
-    std::map<int, ShapeSched> sched = b->sched;
-    if (chimera_L > 0) {
-        ShapeSched s = sched[chimera_L];
+    if (block < 0 || block % 32 != 0 || block > MAX_THREADS)
+        return bfail(b, PT_ERR_ARG, "block must be 0 or a multiple of 32, <= 1024");
+    if (chimera_L <= 0) {                  // CTA size of every size (validated group by group)
+        std::vector<ShapeSched> old;
+        for (auto& g : b->groups) old.push_back(g.s);
+        for (size_t k = 0; k < b->groups.size(); ++k) {
+            ShapeSched s = b->groups[k].s;
+            s.block = block;
+            const int rc = set_group(b, (int)k, s);
+            if (rc) {
+                for (size_t m = 0; m < k; ++m) set_group(b, (int)m, old[m]);
+                return rc;
+            }
+        }
+    } else {
+        const int k = group_of(b, chimera_L);
+        if (k < 0) return bfail(b, PT_ERR_ARG, "no instance of that size");
+        if (slot_parallel < 1 || runs_per_cta < 1) return bfail(b, PT_ERR_ARG, "slot_parallel, runs_per_cta must be >= 1");
+        ShapeSched s = b->groups[k].s;
         s.sp = slot_parallel;
         s.ipc = std::min<int>(runs_per_cta, b->R);
-        const int tpr = sched_threads(chimera_L, s);
-        if (slot_parallel < 1 || runs_per_cta < 1 || tpr < 32 || tpr * s.ipc > nblock)
-            return bfail(b, PT_ERR_ARG, "need threads per run >= 32 and threads per run * runs_per_cta <= block");
-        if (s.team == 0 && tpr % 32 != 0)
-            return bfail(b, PT_ERR_ARG, "cell-major: slot_parallel * L^2 must be a multiple of 32");
-        sched[chimera_L] = s;
-    }
-    for (auto& kv : sched)           // keep every size inside the block
-        if (sched_threads(kv.first, kv.second) * kv.second.ipc > nblock)
-            default_shape_sched(kv.first, max_temps_of(b, kv.first), b->R, nblock, b->slot_major, kv.second);
-    const std::map<int, ShapeSched> old_sched = b->sched;
-    const int old_block = b->block;
-    b->sched = sched;
-    b->block = nblock;
-    int rc = build_bundles(b);
-    if (rc) {
-        b->sched = old_sched;
-        b->block = old_block;
-        return rc;
+        s.block = block;
+        const int rc = set_group(b, k, s);
+        if (rc) return rc;
     }
     BK(cudaStreamSynchronize(b->stream), "sync schedule");
     return PT_OK;
@@ -533,34 +643,31 @@ int pt_batch_set_mapping(pt_batch* b, int32_t chimera_L, int32_t team, int32_t s
     if (!b || team < 0) return bfail(b, PT_ERR_ARG, "team must be >= 0");
     if (team > 0 && (team > 32 || (team & (team - 1)) != 0))
         return bfail(b, PT_ERR_ARG, "team must be a power of two <= 32");
-    if (chimera_L > 0 && !b->sched.count(chimera_L)) return bfail(b, PT_ERR_ARG, "no instance of that size");
-    // validate on copies; the batch changes only when everything fits
-    const bool sm = team > 0;
-    std::map<int, ShapeSched> sched = b->sched;
-    if (sm != b->slot_major)        // the other sizes follow to the new mapping
-        for (auto& kv : sched)
-            default_shape_sched(kv.first, max_temps_of(b, kv.first), b->R, b->block, sm, kv.second);
-    if (chimera_L > 0) {
-        ShapeSched s = sched[chimera_L];
-        s.team = team;
+    if (chimera_L <= 0) {                  // every size: the mapping's default schedule
+        std::vector<ShapeSched> old;
+        for (auto& g : b->groups) old.push_back(g.s);
+        for (size_t k = 0; k < b->groups.size(); ++k) {
+            SizeGroup& g = b->groups[k];
+            ShapeSched s;
+            default_shape_sched(g.L, g.ntmax, b->R, team > 0, s);
+            const int rc = set_group(b, (int)k, s);
+            if (rc) {
+                for (size_t m = 0; m < k; ++m) set_group(b, (int)m, old[m]);
+                return rc;
+            }
+        }
+    } else {
+        const int k = group_of(b, chimera_L);
+        if (k < 0) return bfail(b, PT_ERR_ARG, "no instance of that size");
+        SizeGroup& g = b->groups[k];
+        ShapeSched s = g.s;
+        if ((s.team > 0) != (team > 0)) default_shape_sched(g.L, g.ntmax, b->R, team > 0, s);
+        if (team > 0) s.team = team;
         if (slot_parallel > 0) s.sp = slot_parallel;
         if (runs_per_cta > 0) s.ipc = std::min<int>(runs_per_cta, b->R);
-        const int tpr = sched_threads(chimera_L, s);
-        if (tpr < 32 || tpr * s.ipc > b->block || (!sm && tpr % 32 != 0))
-            return bfail(b, PT_ERR_ARG, "mapping does not fit the block (threads per run >= 32, x runs_per_cta <= block)");
-        if (bundle_smem_bytes(chimera_L, max_temps_of(b, chimera_L), s.ipc, team) > 227 * 1024)
-            return bfail(b, PT_ERR_ARG, "shared memory above 227 KB");
-        sched[chimera_L] = s;
-    }
-    const std::map<int, ShapeSched> old_sched = b->sched;
-    const bool old_sm = b->slot_major;
-    b->sched = sched;
-    b->slot_major = sm;
-    int rc = build_bundles(b);
-    if (rc) {
-        b->sched = old_sched;
-        b->slot_major = old_sm;
-        return rc;
+        s.block = 0;
+        const int rc = set_group(b, k, s);
+        if (rc) return rc;
     }
     BK(cudaStreamSynchronize(b->stream), "sync mapping");
     return PT_OK;
@@ -570,124 +677,90 @@ int pt_batch_get_schedule(const pt_batch* b, int32_t chimera_L, int32_t* block, 
                           int32_t* runs_per_cta)
 {
     if (!b) return PT_ERR_ARG;
-    if (block) *block = b->block;
-    auto it = b->sched.find(chimera_L);
-    if (it == b->sched.end()) return PT_ERR_ARG;
-    if (slot_parallel) *slot_parallel = it->second.sp;
-    if (runs_per_cta) *runs_per_cta = it->second.ipc;
+    const int k = group_of(b, chimera_L);
+    if (k < 0) return PT_ERR_ARG;
+    const SizeGroup& g = b->groups[k];
+    if (block) *block = g.block;
+    if (slot_parallel) *slot_parallel = g.s.sp;
+    if (runs_per_cta) *runs_per_cta = g.s.ipc;
     return PT_OK;
 }
 
 int pt_batch_get_mapping(const pt_batch* b, int32_t chimera_L, int32_t* team)
 {
     if (!b) return PT_ERR_ARG;
-    auto it = b->sched.find(chimera_L);
-    if (it == b->sched.end()) return PT_ERR_ARG;
-    if (team) *team = b->slot_major ? it->second.team : 0;
+    const int k = group_of(b, chimera_L);
+    if (k < 0) return PT_ERR_ARG;
+    if (team) *team = b->groups[k].s.team;
     return PT_OK;
 }
 
-// Times candidate schedules and keeps the fastest.  For each block size in
-// {256, 512}, each mapping (cell-major, slot-major) and each Chimera size,
-// every schedule that fits is timed on all instances of that size for
-// `trial_sweeps` sweeps; the (block, mapping) whose best per-size schedules
-// give the shortest predicted batch time wins.  The state is reset afterwards.
+// Times candidate schedules and keeps the fastest, size by size: every
+// cell-major (slot_parallel, runs_per_cta) and slot-major (team,
+// slot_parallel, runs_per_cta) that fits runs all instances of that size
+// alone for `trial_sweeps` sweeps, with the CTA size the bundle needs.  The
+// state is reset afterwards.
 int pt_batch_autotune(pt_batch* b, int32_t trial_sweeps, int32_t* block_out)
 {
     if (!b || trial_sweeps < 1) return bfail(b, PT_ERR_ARG, "need trial_sweeps >= 1");
-    std::map<int, int64_t> work;          // attempts per sweep per size
-    std::map<int, int> maxnt;
-    for (int i = 0; i < b->n_inst; ++i) {
-        work[b->L[i]] += (int64_t)b->R * b->NT[i] * b->N[i];
-        maxnt[b->L[i]] = std::max(maxnt[b->L[i]], b->NT[i]);
-    }
-    const int old_block = b->block;
-    const bool old_sm = b->slot_major;
-    const std::map<int, ShapeSched> old_sched = b->sched;
-    auto restore = [&]() {
-        b->block = old_block;
-        b->slot_major = old_sm;
-        b->sched = old_sched;
-        build_bundles(b);
-    };
-    double best_total = 1e300;
-    int best_block = b->block;
-    bool best_sm = b->slot_major;
-    std::map<int, ShapeSched> best_sched = b->sched;
-    for (int block : {256, 512}) {
-        for (bool sm : {false, true}) {
-            b->block = block;
-            b->slot_major = sm;
-            std::map<int, ShapeSched> chosen;
-            double total = 0.0;
-            for (auto& kv : work) {
-                const int L = kv.first, L2 = L * L, NT = maxnt[L];
-                // (team, slot_parallel) candidates of this mapping
-                std::vector<std::pair<int, int>> cands;
-                if (!sm) {
-                    for (int sp : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64})
-                        if (sp <= NT && sp * L2 <= block && (sp * L2) % 32 == 0) cands.push_back({0, sp});
-                } else {
-                    for (int team : {2, 4, 8, 16, 32}) {
-                        if (team > 2 * L2 && !cands.empty()) break;
-                        int prev = 0;
-                        for (int nt : {NT, (NT + 1) / 2, (NT + 3) / 4, (NT + 7) / 8})
-                            if (nt != prev && nt * team >= 32 && nt * team <= block) {
-                                cands.push_back({team, nt});
-                                prev = nt;
-                            }
-                    }
-                }
-                double best_rate = 0.0;
-                ShapeSched bs;
-                for (const auto& c : cands) {
-                    const int tpr = c.first > 0 ? c.second * c.first : c.second * L2;
-                    for (int ipc : {1, 2, 4, 8, 16}) {
-                        if (tpr * ipc > block || ipc > b->R) break;
-                        if (bundle_smem_bytes(L, NT, ipc, c.first) > 200 * 1024) break;
-                        ShapeSched& s = b->sched[L];
-                        s.team = c.first;
-                        s.sp = c.second;
-                        s.ipc = ipc;
-                        std::vector<int> only{L};
-                        int rc = build_bundles(b, &only, 0);
-                        if (rc) continue;
-                        int64_t att = 0;
-                        for (const Bundle& x : b->bundles) att += (int64_t)x.nitems * b->NT[x.inst] * b->N[x.inst];
-                        att *= trial_sweeps;
-                        cudaError_t e = cudaEventRecord(b->e0, b->stream);
-                        if (e == cudaSuccess) e = cudaMemsetAsync(b->d_queue, 0, sizeof(int), b->stream);
-                        if (e == cudaSuccess)
-                            e = launch_sweeps(b->d_desc, b->d_bundles, (int)b->bundles.size(), b->grid, b->block,
-                                              b->smem, 0u, trial_sweeps, 1, 0, b->d_queue, b->stream, sm);
-                        if (e == cudaSuccess) e = cudaEventRecord(b->e1, b->stream);
-                        if (e == cudaSuccess) e = cudaEventSynchronize(b->e1);
-                        float ms = 0.f;
-                        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, b->e0, b->e1);
-                        if (e != cudaSuccess) {
-                            const int code = bcuda(b, e, "trial launch");
-                            restore();
-                            return code;
-                        }
-                        const double rate = att / (ms * 1e-3);
-                        if (rate > best_rate) { best_rate = rate; bs = s; }
-                    }
-                }
-                if (best_rate <= 0.0) { total = 1e300; break; }
-                chosen[L] = bs;
-                total += (double)kv.second / best_rate;
+    for (size_t k = 0; k < b->groups.size(); ++k) {
+        SizeGroup& g = b->groups[k];
+        const int L2 = g.L * g.L, NT = g.ntmax;
+        std::vector<ShapeSched> cands;
+        for (int sp : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64}) {
+            const int tpr = sp * L2;
+            if (sp > NT || tpr > MAX_THREADS) break;
+            if (tpr < 32) continue;
+            for (int ipc : {1, 2, 4, 8, 16}) {
+                if (tpr * ipc > MAX_THREADS || ipc > b->R || bundle_smem_bytes(g.L, NT, ipc) > 200 * 1024) break;
+                ShapeSched s; s.sp = sp; s.ipc = ipc; s.team = 0;
+                cands.push_back(s);
             }
-            if (total < best_total) { best_total = total; best_block = block; best_sm = sm; best_sched = chosen; }
         }
+        for (int team : {2, 4, 8, 16, 32}) {
+            if (team > 2 * L2) break;
+            int prev = 0;
+            for (int nt : {NT, (NT + 1) / 2, (NT + 3) / 4, (NT + 7) / 8}) {
+                if (nt == prev || nt * team < 32 || nt * team > MAX_THREADS_SM) continue;
+                prev = nt;
+                for (int ipc : {1, 2, 4, 8}) {
+                    if (nt * team * ipc > MAX_THREADS_SM || ipc > b->R ||
+                        bundle_smem_bytes(g.L, NT, ipc, team) > 200 * 1024)
+                        break;
+                    ShapeSched s; s.sp = nt; s.ipc = ipc; s.team = team;
+                    cands.push_back(s);
+                }
+            }
+        }
+        const ShapeSched old = g.s;
+        double best_rate = 0.0;
+        ShapeSched best = old;
+        for (const ShapeSched& c : cands) {
+            if (set_group(b, (int)k, c) != PT_OK) continue;
+            const double att = (double)g.work * trial_sweeps;
+            cudaError_t e = cudaEventRecord(b->e0, b->stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(b->d_queue + k, 0, sizeof(int), b->stream);
+            if (e == cudaSuccess)
+                e = launch_sweeps(b->d_desc, g.d_bundles, (int)g.bundles.size(), g.grid, g.block, g.smem, 0u,
+                                  trial_sweeps, 1, 0, b->d_queue + k, b->stream, g.s.team > 0);
+            if (e == cudaSuccess) e = cudaEventRecord(b->e1, b->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(b->e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, b->e0, b->e1);
+            if (e != cudaSuccess) {
+                const int code = bcuda(b, e, "trial launch");
+                set_group(b, (int)k, old);
+                return code;
+            }
+            const double rate = att / (ms * 1e-3);
+            if (rate > best_rate) { best_rate = rate; best = c; }
+        }
+        const int rc = set_group(b, (int)k, best);
+        if (rc) { set_group(b, (int)k, old); return rc; }
     }
-    b->block = best_block;
-    b->slot_major = best_sm;
-    for (auto& kv : best_sched) b->sched[kv.first] = kv.second;
-    int rc = build_bundles(b);
-    if (rc) { restore(); return rc; }
-    rc = pt_batch_reset(b);
+    const int rc = pt_batch_reset(b);
     if (rc) return rc;
-    if (block_out) *block_out = b->block;
+    if (block_out) *block_out = b->groups.empty() ? 0 : b->groups[0].block;
     return PT_OK;
 }
 
@@ -695,10 +768,16 @@ int pt_batch_info(const pt_batch* b, double* last_run_ms, int32_t* grid, int32_t
                   uint64_t* launches)
 {
     if (!b) return PT_ERR_ARG;
+    int gsum = 0, bmax = 0, nb = 0;
+    for (const auto& g : b->groups) {
+        gsum += g.grid;
+        bmax = std::max(bmax, g.block);
+        nb += (int)g.bundles.size();
+    }
     if (last_run_ms) *last_run_ms = b->last_ms;
-    if (grid) *grid = b->grid;
-    if (block) *block = b->block;
-    if (n_bundles) *n_bundles = (int32_t)b->bundles.size();
+    if (grid) *grid = gsum;
+    if (block) *block = bmax;
+    if (n_bundles) *n_bundles = nb;
     if (launches) *launches = b->launches;
     return PT_OK;
 }

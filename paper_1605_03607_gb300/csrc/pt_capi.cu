@@ -147,7 +147,8 @@ int check_schedule(pt_handle* h, int L, int NT, int sp, int ipc, int team)
     if (team > 0) {
         if (team > 32 || (team & (team - 1)) != 0) return fail(h, PT_ERR_ARG, "team must be a power of two <= 32");
         if (sp * team < 32) return fail(h, PT_ERR_ARG, "teams * team must be >= 32");
-        if (sp * team * ipc > MAX_THREADS) return fail(h, PT_ERR_ARG, "more than 1024 threads per CTA");
+        if (sp * team * ipc > MAX_THREADS_SM)
+            return fail(h, PT_ERR_ARG, "more than 768 threads per CTA (slot-major mapping)");
     } else {
         if ((sp * L2) % 32 != 0) return fail(h, PT_ERR_ARG, "slot_parallel * L^2 must be a multiple of 32");
         if (sp * L2 * ipc > MAX_THREADS) return fail(h, PT_ERR_ARG, "more than 1024 threads per CTA");
@@ -930,13 +931,13 @@ int pt_autotune(pt_handle* h, int32_t n_inst, int32_t trial_sweeps)
     for (int team : {2, 4, 8, 16, 32}) {
         if (team > L2) break;
         for (int nt : {h->NT, (h->NT + 1) / 2, (h->NT + 3) / 4, (h->NT + 7) / 8})
-            if (nt >= 1 && nt * team >= 32 && nt * team <= MAX_THREADS) cands.push_back({team, nt});
+            if (nt >= 1 && nt * team >= 32 && nt * team <= MAX_THREADS_SM) cands.push_back({team, nt});
     }
     for (const auto& c : cands) {
         const int team = c.first, sp = c.second;
         const int tpr = team > 0 ? sp * team : sp * L2;
         for (int ipc : {1, 2, 4}) {
-            if (tpr * ipc > MAX_THREADS || ipc > h->R) break;
+            if (tpr * ipc > (team > 0 ? MAX_THREADS_SM : MAX_THREADS) || ipc > h->R) break;
             if (bundle_smem_bytes(h->L, h->NT, ipc, team) > 200 * 1024) break;
             h->team = team;
             h->sp = sp;

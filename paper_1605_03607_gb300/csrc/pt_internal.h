@@ -13,6 +13,9 @@ constexpr int KT = 19;             // Metropolis table entries per slot: k = 0..
 constexpr int MAX_TEMPS = 64;
 constexpr int MAX_L = 16;
 constexpr int MAX_THREADS = 1024;
+// CTA size limit of the slot-major sweep kernel: its register budget (up to
+// 80 per thread) fits 768 threads per CTA.
+constexpr int MAX_THREADS_SM = 768;
 
 // Per instance.  All pointers are device pointers.
 //
@@ -60,9 +63,10 @@ __host__ __device__ inline int threads_per_run(int L, const Bundle& b)
 // Shared-memory layout of one bundle: the Metropolis table of the instance,
 // then per item (run): spins [NT][N] (colour-major words per buffer, plus
 // `pad` words per buffer in the slot-major mapping), E by slot, exchange
-// critical h by pair (two sweeps), flip / swap counters, perm, best/first.
+// critical h by pair (two sweeps), flip / swap counters, perm (slot ->
+// buffer), its inverse (buffer -> slot, slot-major mapping), best/first.
 struct ItemLayout {
-    int64_t spins, E, ccrit, macc, xacc, perm, misc, bytes;
+    int64_t spins, E, ccrit, macc, xacc, perm, inv, misc, bytes;
 };
 
 __host__ __device__ inline int64_t pad16(int64_t x) { return (x + 15) & ~15LL; }
@@ -77,9 +81,20 @@ __host__ __device__ inline ItemLayout item_layout(int L, int NT, int pad = 0)
     o.macc = o.ccrit + 8LL * NT;
     o.xacc = o.macc + 4LL * NT;
     o.perm = o.xacc + 4LL * NT;
-    o.misc = pad16(o.perm + NT);
+    o.inv = o.perm + NT;
+    o.misc = pad16(o.inv + NT);
     o.bytes = o.misc + 16;
     return o;
+}
+
+// Slot-major mapping: padding words per spin buffer so that the buffer
+// stride is congruent to the team width modulo the 32 shared-memory banks.
+// Teams of one warp own consecutive buffers and their lanes read consecutive
+// words, so the spin words a warp reads at once fall into distinct banks.
+__host__ __device__ inline int sm_pad(int L, int team)
+{
+    const int NW = 2 * L * L;
+    return ((team & 31) - (NW & 31) + 64) & 31;
 }
 
 // Instance tables staged per bundle: thr [NT][KT], then exchange offsets [NT]
@@ -89,13 +104,18 @@ __host__ __device__ inline int64_t table_bytes(int NT) { return pad16(4LL * NT *
 // Sets the message pt_last_error(NULL) returns (defined with the C ABI).
 void set_global_error(const char* msg);
 
-// Slot-major mapping only: couplers [L^2][2][8] words and per (cell, colour)
-// one packed word: group index | minus-neighbour word << 10 | plus-neighbour word << 20.
-__host__ __device__ inline int64_t cell_table_bytes(int L) { return pad16(4LL * L * L * 16 + 4LL * L * L * 2); }
+// Slot-major mapping only: one 12-word record per (colour, cell), colour-major:
+// in-cell couplers (4 words), inter-cell couplers (4 words), one packed word
+// (group index | minus-neighbour word << 10 | plus-neighbour word << 20) and 3
+// unused words.  The 48-byte stride puts the records a team reads at once
+// into distinct banks.
+constexpr int CELL_REC = 12;
+__host__ __device__ inline int64_t cell_table_bytes(int L) { return 4LL * CELL_REC * 2 * L * L; }
 
 inline int64_t bundle_smem_bytes(int L, int NT, int nitems, int team = 0)
 {
-    if (team > 0) return table_bytes(NT) + cell_table_bytes(L) + (int64_t)nitems * item_layout(L, NT, 1).bytes;
+    if (team > 0)
+        return table_bytes(NT) + cell_table_bytes(L) + (int64_t)nitems * item_layout(L, NT, sm_pad(L, team)).bytes;
     return table_bytes(NT) + (int64_t)nitems * item_layout(L, NT).bytes;
 }
 

@@ -187,7 +187,9 @@ __device__ __forceinline__ void exchange_prepare(const InstDesc& in, const uint3
 // The ascending exchange sweep of one run (one thread): a configuration that
 // wins pair p is carried on to pair p+1.  Slot energies, slot map and
 // acceptance criteria are read in blocks of 4 ahead of the carried chain.
-__device__ __forceinline__ int exchange_chain(int32_t* Es, uint8_t* perm, uint32_t* xacc,
+// With INV the inverse map (buffer -> slot) is rewritten along the way.
+template <bool INV>
+__device__ __forceinline__ int exchange_chain(int32_t* Es, uint8_t* perm, uint8_t* inv, uint32_t* xacc,
                                               const int32_t* cc, int NT)
 {
     constexpr int B = 4;
@@ -236,12 +238,14 @@ __device__ __forceinline__ int exchange_chain(int32_t* Es, uint8_t* perm, uint32
             if (p0 + i < np) {
                 Es[p0 + i] = oe[i];
                 perm[p0 + i] = (uint8_t)ob[i];
+                if (INV) inv[ob[i]] = (uint8_t)(p0 + i);
                 xacc[p0 + i] += (bits >> i) & 1u;
             }
         }
     }
     Es[np] = ce;
     perm[np] = (uint8_t)cb;
+    if (INV) inv[cb] = (uint8_t)np;
     return m;
 }
 
@@ -347,7 +351,7 @@ __device__ void process_bundle(const InstDesc* __restrict__ insts, const Bundle 
         if (active && j == 0) {
             int m;
             if (do_x) {
-                m = exchange_chain(Es, perm, xacc, ccrit + (s & 1u) * NT, NT);
+                m = exchange_chain<false>(Es, perm, nullptr, xacc, ccrit + (s & 1u) * NT, NT);
             } else {
                 m = Es[0];
                 for (int p = 1; p < NT; ++p) m = min(m, Es[p]);
@@ -385,31 +389,70 @@ __device__ void process_bundle(const InstDesc* __restrict__ insts, const Bundle 
     __syncthreads();
 }
 
+// One colour-`col` word (4 spins, cell q) of the slot-major update at the
+// temperature of the slot whose threshold row is `th`: local fields from the
+// cell record (dp4a over int8 couplers and spins), Metropolis test of each
+// spin against its uniform in `rn`, flips written back, energy change and
+// flip bits accumulated.
+__device__ __forceinline__ void sm_word(const uint32_t* rec, uint32_t meta, uint32_t* bw, int col, int L2, int q,
+                                        const uint4 rn, const uint32_t* th, int& dk, int& pc)
+{
+    const uint4 jin = *reinterpret_cast<const uint4*>(rec);
+    const uint4 jud = *reinterpret_cast<const uint4*>(rec + 4);
+    const int ow = col * L2 + q;
+    const uint32_t own = bw[ow];
+    const int opp = (int)bw[(1 - col) * L2 + q];
+    const uint32_t mw = bw[(meta >> 10) & 1023u], pw = bw[meta >> 20];
+    const int x01 = (int)__byte_perm(mw, pw, 0x5140);
+    const int x23 = (int)__byte_perm(mw, pw, 0x7362);
+    const int h0 = __dp4a((int)jin.x, opp, __dp4a((int)jud.x, x01, 0));
+    const int h1 = __dp4a((int)jin.y, opp, __dp4a((int)jud.y, x01, 0));
+    const int h2 = __dp4a((int)jin.z, opp, __dp4a((int)jud.z, x23, 0));
+    const int h3 = __dp4a((int)jin.w, opp, __dp4a((int)jud.w, x23, 0));
+    const int kk0 = (int)(int8_t)(own) * h0;
+    const int kk1 = (int)(int8_t)(own >> 8) * h1;
+    const int kk2 = (int)(int8_t)(own >> 16) * h2;
+    const int kk3 = (int)(int8_t)(own >> 24) * h3;
+    const bool a0 = (kk0 <= 0) | (rn.x < th[max(kk0, 0)]);
+    const bool a1 = (kk1 <= 0) | (rn.y < th[max(kk1, 0)]);
+    const bool a2 = (kk2 <= 0) | (rn.z < th[max(kk2, 0)]);
+    const bool a3 = (kk3 <= 0) | (rn.w < th[max(kk3, 0)]);
+    uint32_t flip = 0u;
+    if (a0) { flip |= 0x000000FEu; dk += kk0; }
+    if (a1) { flip |= 0x0000FE00u; dk += kk1; }
+    if (a2) { flip |= 0x00FE0000u; dk += kk2; }
+    if (a3) { flip |= 0xFE000000u; dk += kk3; }
+    if (flip) bw[ow] = own ^ flip;
+    pc += __popc(flip);
+}
+
 // Slot-major mapping: a team of G lanes (a power of two, inside one warp)
-// owns every sp-th temperature slot of a run; its lanes split the cells.  For
-// each owned slot the team updates colour 0, syncs the team, updates colour 1,
-// and reduces its energy change and flip count once.  Teams of different
-// slots never wait for each other inside a sweep; the run's threads meet only
-// around the exchange.  Couplers and per-group offsets come from shared
-// memory; buffers are padded by one word so teams on different slots hit
-// different banks.
+// owns every sp-th spin buffer of a run and updates it at the temperature of
+// the slot that buffer currently sits in (inverse slot map); its lanes split
+// the cells.  For each owned buffer the team updates colour 0, syncs the
+// team, updates colour 1, and reduces its energy change and flip count once.
+// Teams never wait for each other inside a sweep; the run's threads meet only
+// around the exchange.  The random numbers stay indexed by (sweep, run, slot,
+// group), so which team does the work does not change any result.
+// Bank layout: buffer strides are congruent to G modulo 32 and the cell
+// records are colour-major with a 48-byte stride, so a warp's own/opposite
+// spin words and coupler records come without bank conflicts.
 __device__ void process_bundle_sm(const InstDesc* __restrict__ insts, const Bundle bd,
                                   uint32_t sweep0, int nsweeps, int xevery, int mode,
                                   unsigned char* smem)
 {
     const InstDesc& in = insts[bd.inst];
-    const int L = in.L, NT = in.NT, L2 = L * L, N = 8 * L2, NW = N / 4, NWP = NW + 1;
     const int G = bd.team, NTEAM = bd.sp, TPI = G * NTEAM;
+    const int L = in.L, NT = in.NT, L2 = L * L, N = 8 * L2, NW = N / 4, NWP = NW + sm_pad(L, G);
     const int tid = threadIdx.x;
     const int item = tid / TPI, j = tid - item * TPI;
     const bool active = item < bd.nitems;
     const int team = j / G, tl = j - team * G;
     const int run = bd.run0 + (active ? item : 0);
-    const ItemLayout lay = item_layout(L, NT, 1);
+    const ItemLayout lay = item_layout(L, NT, sm_pad(L, G));
 
     uint32_t* thr_sm = reinterpret_cast<uint32_t*>(smem);
-    uint32_t* jw_sm = reinterpret_cast<uint32_t*>(smem + table_bytes(NT));
-    uint32_t* meta_sm = jw_sm + L2 * 16;
+    uint32_t* rec_sm = reinterpret_cast<uint32_t*>(smem + table_bytes(NT));   // [2][L2][CELL_REC]
     unsigned char* ib = smem + table_bytes(NT) + cell_table_bytes(L) + (active ? item : 0) * lay.bytes;
     uint32_t* sw = reinterpret_cast<uint32_t*>(ib + lay.spins);
     int32_t* Es = reinterpret_cast<int32_t*>(ib + lay.E);
@@ -417,6 +460,7 @@ __device__ void process_bundle_sm(const InstDesc* __restrict__ insts, const Bund
     uint32_t* macc = reinterpret_cast<uint32_t*>(ib + lay.macc);
     uint32_t* xacc = reinterpret_cast<uint32_t*>(ib + lay.xacc);
     uint8_t* perm = ib + lay.perm;
+    uint8_t* inv = ib + lay.inv;
     int32_t* misc = reinterpret_cast<int32_t*>(ib + lay.misc);
 
     // ---- tables, couplers, per-group offsets and this bundle's runs
@@ -425,13 +469,17 @@ __device__ void process_bundle_sm(const InstDesc* __restrict__ insts, const Bund
         reinterpret_cast<int32_t*>(thr_sm + NT * KT)[p] = in.xoff[p];
         reinterpret_cast<float*>(thr_sm + NT * KT + NT)[p] = p < NT - 1 ? in.xhint[p] : 0.0f;
     }
-    for (int w = tid; w < L2 * 16; w += blockDim.x) jw_sm[w] = in.jw[w];
+    for (int w = tid; w < L2 * 4; w += blockDim.x) {  // global: [cell][colour][in 4 | inter 4]
+        const int qc = w >> 1, half = w & 1, q = qc >> 1, col = qc & 1;
+        const uint4 v = reinterpret_cast<const uint4*>(in.jw)[w];
+        *reinterpret_cast<uint4*>(rec_sm + (col * L2 + q) * CELL_REC + 4 * half) = v;
+    }
     for (int w = tid; w < L2 * 2; w += blockDim.x) {
         const int q = w >> 1, col = w & 1, r = q / L, c = q - r * L;
         const uint32_t gidx = (uint32_t)(2 * q + ((r + c + col) & 1));
         const uint32_t mn = (uint32_t)((1 - col) * L2 + in.nbr[w * 2 + 0]);
         const uint32_t pl = (uint32_t)((1 - col) * L2 + in.nbr[w * 2 + 1]);
-        meta_sm[w] = gidx | (mn << 10) | (pl << 20);
+        rec_sm[(col * L2 + q) * CELL_REC + 8] = gidx | (mn << 10) | (pl << 20);
     }
     const size_t rep0 = (size_t)run * NT;
     if (active) {
@@ -442,8 +490,10 @@ __device__ void process_bundle_sm(const InstDesc* __restrict__ insts, const Bund
             sw[buf * NWP + ((r + c + u) & 1) * L2 + cell] = gsp[w];
         }
         for (int t = j; t < NT; t += TPI) {
+            const uint8_t b = in.perm[rep0 + t];
             Es[t] = in.E[rep0 + t];
-            perm[t] = in.perm[rep0 + t];
+            perm[t] = b;
+            inv[b] = (uint8_t)t;
             macc[t] = 0u;
             xacc[t] = 0u;
         }
@@ -472,45 +522,21 @@ __device__ void process_bundle_sm(const InstDesc* __restrict__ insts, const Bund
         const bool do_x = exch(s);
         if (mode == 0 && active) {
             const PhiloxSweep ps = philox_sweep_pre(s, k0, k1);
-            for (int t = team; t < NT; t += NTEAM) {
-                uint32_t* bw = sw + perm[t] * NWP;
+            for (int b = team; b < NT; b += NTEAM) {
+                const int t = inv[b];
+                uint32_t* bw = sw + b * NWP;
                 const uint32_t* th = thr_sm + t * KT;
                 const uint32_t c1 = runbits | (uint32_t)t;
                 int dk = 0, pc = 0;
 #pragma unroll
                 for (int col = 0; col < 2; ++col) {
                     for (int q = tl; q < L2; q += G) {
-                        const uint4 jin = *reinterpret_cast<const uint4*>(jw_sm + (q * 2 + col) * 8);
-                        const uint4 jud = *reinterpret_cast<const uint4*>(jw_sm + (q * 2 + col) * 8 + 4);
-                        const uint32_t meta = meta_sm[q * 2 + col];
-                        const int ow = col * L2 + q;
-                        const uint32_t own = bw[ow];
-                        const int opp = (int)bw[(1 - col) * L2 + q];
-                        const uint32_t mw = bw[(meta >> 10) & 1023u], pw = bw[meta >> 20];
+                        const uint32_t* rec = rec_sm + (col * L2 + q) * CELL_REC;
+                        const uint32_t meta = rec[8];
                         const uint4 rn = philox_group(ps, c1, meta & 1023u, k0, k1);
-                        const int x01 = (int)__byte_perm(mw, pw, 0x5140);
-                        const int x23 = (int)__byte_perm(mw, pw, 0x7362);
-                        const int h0 = __dp4a((int)jin.x, opp, __dp4a((int)jud.x, x01, 0));
-                        const int h1 = __dp4a((int)jin.y, opp, __dp4a((int)jud.y, x01, 0));
-                        const int h2 = __dp4a((int)jin.z, opp, __dp4a((int)jud.z, x23, 0));
-                        const int h3 = __dp4a((int)jin.w, opp, __dp4a((int)jud.w, x23, 0));
-                        const int kk0 = (int)(int8_t)(own) * h0;
-                        const int kk1 = (int)(int8_t)(own >> 8) * h1;
-                        const int kk2 = (int)(int8_t)(own >> 16) * h2;
-                        const int kk3 = (int)(int8_t)(own >> 24) * h3;
-                        const bool a0 = (kk0 <= 0) | (rn.x < th[max(kk0, 0)]);
-                        const bool a1 = (kk1 <= 0) | (rn.y < th[max(kk1, 0)]);
-                        const bool a2 = (kk2 <= 0) | (rn.z < th[max(kk2, 0)]);
-                        const bool a3 = (kk3 <= 0) | (rn.w < th[max(kk3, 0)]);
-                        uint32_t flip = 0u;
-                        if (a0) { flip |= 0x000000FEu; dk += kk0; }
-                        if (a1) { flip |= 0x0000FE00u; dk += kk1; }
-                        if (a2) { flip |= 0x00FE0000u; dk += kk2; }
-                        if (a3) { flip |= 0xFE000000u; dk += kk3; }
-                        if (flip) bw[ow] = own ^ flip;
-                        pc += __popc(flip);
+                        sm_word(rec, meta, bw, col, L2, q, rn, th, dk, pc);
                     }
-                    __syncwarp(tmask);                  // colour 0 of this slot done by the whole team
+                    __syncwarp(tmask);                  // colour 0 of this buffer done by the whole team
                 }
                 for (int o = G >> 1; o > 0; o >>= 1) {
                     dk += __shfl_xor_sync(tmask, dk, o);
@@ -526,7 +552,7 @@ __device__ void process_bundle_sm(const InstDesc* __restrict__ insts, const Bund
         if (active && j == 0) {
             int m;
             if (do_x) {
-                m = exchange_chain(Es, perm, xacc, ccrit + (s & 1u) * NT, NT);
+                m = exchange_chain<true>(Es, perm, inv, xacc, ccrit + (s & 1u) * NT, NT);
             } else {
                 m = Es[0];
                 for (int p = 1; p < NT; ++p) m = min(m, Es[p]);
@@ -567,7 +593,7 @@ __device__ void process_bundle_sm(const InstDesc* __restrict__ insts, const Bund
 // SLOT_MAJOR selects the mapping of every bundle of the launch (the two are
 // separate instantiations so each keeps its own register allocation).
 template <bool SLOT_MAJOR>
-__global__ void __launch_bounds__(MAX_THREADS)
+__global__ void __launch_bounds__(SLOT_MAJOR ? MAX_THREADS_SM : MAX_THREADS)
 pt_sweep_kernel(const InstDesc* __restrict__ insts, const Bundle* __restrict__ bundles,
                 int nbundles, uint32_t sweep0, int nsweeps, int xevery, int mode,
                 int* __restrict__ queue)

@@ -124,6 +124,22 @@ def test_slot_major_batch_bit_exact(P):
             assert np.array_equal(b.state(i)["spins"], cell[i]["spins"]), i
 
 
+def test_slot_major_uneven_temperatures(P):
+    """One size whose instances have 8..32 temperatures: on the slot-major
+    mapping each instance gets teams in proportion to its slots and more runs
+    per CTA where that frees threads; every instance matches the oracle."""
+    seed, R = 95, 5
+    inst = [dict(L=4, J=W.random_couplers(4, seed, i), betas=W.beta_ladder(nt, 0.1, 3.0), uid=2000 + i)
+            for i, nt in enumerate((8, 13, 32, 20))]
+    with P.PTBatch(inst, R, seed) as b:
+        for team, sp, ipc in ((8, 16, 1), (4, 16, 2), (2, 32, 1)):
+            b.set_mapping(team, 4, sp, ipc)
+            b.reset()
+            b.run(40, 1)
+            for i, x in enumerate(inst):
+                _check_instance(b.state(i), x, R, seed, 40, f"team {team} sp {sp} ipc {ipc} instance {i}")
+
+
 def test_batch_mapping_rejects_misfits(P):
     inst = _mixed(5)[:3]                                 # sizes 4, 8, 12
     with P.PTBatch(inst, 2, 5) as b:
@@ -132,7 +148,11 @@ def test_batch_mapping_rejects_misfits(P):
         with pytest.raises(P.PTError, match="fit"):
             b.set_mapping(4, 8, 4, 1)                    # 16 threads per run
         with pytest.raises(P.PTError, match="fit"):
-            b.set_mapping(32, 8, 32, 1)                  # 1024 threads > block 512
+            b.set_schedule(0, 12, 4, 2)                  # cell-major: 2 runs x 576 threads > 1024
+        b.set_mapping(4, 8, 8, 1)
+        with pytest.raises(P.PTError, match="fit"):
+            b.set_schedule(1024, 8, 8, 1)                # slot-major CTAs hold <= 768 threads
+        assert b.mapping(8) == 4 and b.schedule(8)[1:] == (8, 1)   # failures change nothing
         with pytest.raises(P.PTError, match="no instance"):
             b.set_mapping(4, 7, 8, 1)
 
