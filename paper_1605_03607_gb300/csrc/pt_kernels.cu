@@ -318,7 +318,9 @@ __device__ void process_bundle(const InstDesc* __restrict__ insts, const Bundle 
     const bool one_item = __shfl_sync(FULL, item, 0) == __shfl_sync(FULL, item, 31);
     ws.redux = ((L2 >= 32) || (L2 == 16 && TPI % 32 == 0)) && act_mask == FULL && one_item;
     const int iters = (NT + SP - 1) / SP;
-    const uint32_t k0 = in.seed, k1 = in.uid;
+    // read through a warp reduction: the keys (and every Philox round key and
+    // per-sweep product derived from them) are then warp-uniform values
+    const uint32_t k0 = __reduce_or_sync(FULL, in.seed), k1 = __reduce_or_sync(FULL, in.uid);
     const uint32_t runbits = (uint32_t)run << 16;
     const int prep_warp_j0 = TPI - 32;          // last warp of the run prepares exchanges
     auto exch = [&](uint32_t sw_) {
@@ -504,7 +506,9 @@ __device__ void process_bundle_sm(const InstDesc* __restrict__ insts, const Bund
     }
     const int lane = tid & 31;
     const unsigned tmask = G >= 32 ? FULL : (((1u << G) - 1u) << (lane & ~(G - 1)));
-    const uint32_t k0 = in.seed, k1 = in.uid;
+    // read through a warp reduction: the keys (and every Philox round key and
+    // per-sweep product derived from them) are then warp-uniform values
+    const uint32_t k0 = __reduce_or_sync(FULL, in.seed), k1 = __reduce_or_sync(FULL, in.uid);
     const uint32_t runbits = (uint32_t)run << 16;
     const int prep_warp_j0 = TPI >= 32 ? TPI - 32 : 0;
     auto exch = [&](uint32_t sw_) {
