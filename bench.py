@@ -334,7 +334,7 @@ def run_batched(args):
             team, sp, ipc = (int(x) for x in rest.split(","))
             b.set_mapping(team, int(Ls), sp, ipc)
     elif not args.no_autotune:
-        b.autotune(trial_sweeps=16)
+        b.autotune(trial_sweeps=32)
     for _ in range(args.warmup):
         b.reset()
         b.run(sweeps, cfg["exchange_every"])
@@ -451,16 +451,24 @@ def run_guided_experiment(args):
 
 
 def run_profile_case(args):
-    """A fixed, small sequence of sweep-kernel launches on the bench instance
-    (for ncu captures): fresh runs, then `profile_sweeps` launches of
-    sweeps_per_launch sweeps each, through pt_sweep."""
+    """A fixed, small sequence of sweep-kernel launches (for ncu captures):
+    fresh runs, then `profile_sweeps` launches of sweeps_per_launch sweeps each,
+    through pt_sweep.  Default shape: the bench instance with 64 x
+    profile_instances runs; --profile-shape L,NT,R picks a seeded C_L instance
+    with NT temperatures (beta geometric in [0.1, 4]) and R runs."""
     import paper_1605_03607_gb300 as P
     from paper_1605_03607_gb300 import build as B
     B.build()
     cfg = workload()
-    J = W.random_couplers(cfg["L"], cfg["seed"], 0)
-    betas = W.beta_ladder(cfg["n_temps"], cfg["beta_min"], cfg["beta_max"])
-    h = P.PTHandle(cfg["L"], J, betas, cfg["n_runs"] * args.profile_instances, cfg["seed"], 0)
+    if args.profile_shape:
+        L, NT, R = (int(x) for x in args.profile_shape.split(","))
+        J = W.random_couplers(L, cfg["seed"], 0)
+        betas = W.beta_ladder(NT, cfg["beta_min"], cfg["beta_max"])
+    else:
+        L, R = cfg["L"], cfg["n_runs"] * args.profile_instances
+        J = W.random_couplers(L, cfg["seed"], 0)
+        betas = W.beta_ladder(cfg["n_temps"], cfg["beta_min"], cfg["beta_max"])
+    h = P.PTHandle(L, J, betas, R, cfg["seed"], 0)
     if args.mapping:
         h.set_mapping(*[int(x) for x in args.mapping.split(",")])
     if args.schedule:
@@ -471,8 +479,9 @@ def run_profile_case(args):
         h.sweep(spl, cfg["exchange_every"])
     ms, n = h.sweep_timing_total()
     att = args.profile_sweeps * spl * h.R * h.NT * h.N
-    print(json.dumps({"profile_case": True, "launches": n, "ms": ms, "attempts_per_s": att / (ms / 1e3),
-                      "runs": h.R, "schedule": list(h.schedule()), "team": h.mapping()}))
+    print(json.dumps({"profile_case": True, "L": L, "n_temps": h.NT, "launches": n, "ms": ms,
+                      "attempts_per_s": att / (ms / 1e3), "runs": h.R, "schedule": list(h.schedule()),
+                      "team": h.mapping()}))
     h.close()
     return 0
 
@@ -491,6 +500,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--profile-sweeps", type=int, default=0,
                     help="profiling case: this many sweep launches on the bench instance, then exit")
+    ap.add_argument("--profile-shape", default="", help="profiling case: L,n_temps,runs of a seeded C_L instance")
     ap.add_argument("--profile-instances", type=int, default=4,
                     help="profiling case: runs = 64 x this (as many runs as a speculative batch)")
     ap.add_argument("--gpus", type=int, default=1)

@@ -698,8 +698,8 @@ int pt_batch_get_mapping(const pt_batch* b, int32_t chimera_L, int32_t* team)
 // Times candidate schedules and keeps the fastest, size by size: every
 // cell-major (slot_parallel, runs_per_cta) and slot-major (team,
 // slot_parallel, runs_per_cta) that fits runs all instances of that size
-// alone for `trial_sweeps` sweeps, with the CTA size the bundle needs.  The
-// state is reset afterwards.
+// alone for `trial_sweeps` sweeps (the faster of two launches), with the CTA
+// size the bundle needs.  The state is reset afterwards.
 int pt_batch_autotune(pt_batch* b, int32_t trial_sweeps, int32_t* block_out)
 {
     if (!b || trial_sweeps < 1) return bfail(b, PT_ERR_ARG, "need trial_sweeps >= 1");
@@ -738,19 +738,23 @@ int pt_batch_autotune(pt_batch* b, int32_t trial_sweeps, int32_t* block_out)
         for (const ShapeSched& c : cands) {
             if (set_group(b, (int)k, c) != PT_OK) continue;
             const double att = (double)g.work * trial_sweeps;
-            cudaError_t e = cudaEventRecord(b->e0, b->stream);
-            if (e == cudaSuccess) e = cudaMemsetAsync(b->d_queue + k, 0, sizeof(int), b->stream);
-            if (e == cudaSuccess)
-                e = launch_sweeps(b->d_desc, g.d_bundles, (int)g.bundles.size(), g.grid, g.block, g.smem, 0u,
-                                  trial_sweeps, 1, 0, b->d_queue + k, b->stream, g.s.team > 0);
-            if (e == cudaSuccess) e = cudaEventRecord(b->e1, b->stream);
-            if (e == cudaSuccess) e = cudaEventSynchronize(b->e1);
-            float ms = 0.f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, b->e0, b->e1);
-            if (e != cudaSuccess) {
-                const int code = bcuda(b, e, "trial launch");
-                set_group(b, (int)k, old);
-                return code;
+            float ms = 1e30f;
+            for (int rep = 0; rep < 2; ++rep) {      // the faster of two launches
+                cudaError_t e = cudaEventRecord(b->e0, b->stream);
+                if (e == cudaSuccess) e = cudaMemsetAsync(b->d_queue + k, 0, sizeof(int), b->stream);
+                if (e == cudaSuccess)
+                    e = launch_sweeps(b->d_desc, g.d_bundles, (int)g.bundles.size(), g.grid, g.block, g.smem, 0u,
+                                      trial_sweeps, 1, 0, b->d_queue + k, b->stream, g.s.team > 0);
+                if (e == cudaSuccess) e = cudaEventRecord(b->e1, b->stream);
+                if (e == cudaSuccess) e = cudaEventSynchronize(b->e1);
+                float t = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&t, b->e0, b->e1);
+                if (e != cudaSuccess) {
+                    const int code = bcuda(b, e, "trial launch");
+                    set_group(b, (int)k, old);
+                    return code;
+                }
+                ms = std::min(ms, t);
             }
             const double rate = att / (ms * 1e-3);
             if (rate > best_rate) { best_rate = rate; best = c; }
