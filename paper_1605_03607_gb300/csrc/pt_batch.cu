@@ -703,6 +703,8 @@ int pt_batch_get_mapping(const pt_batch* b, int32_t chimera_L, int32_t* team)
 int pt_batch_autotune(pt_batch* b, int32_t trial_sweeps, int32_t* block_out)
 {
     if (!b || trial_sweeps < 1) return bfail(b, PT_ERR_ARG, "need trial_sweeps >= 1");
+    int cap = 0;
+    BK(sweep_smem_capacity(&cap), "shared memory capacity");
     for (size_t k = 0; k < b->groups.size(); ++k) {
         SizeGroup& g = b->groups[k];
         const int L2 = g.L * g.L, NT = g.ntmax;
@@ -712,7 +714,7 @@ int pt_batch_autotune(pt_batch* b, int32_t trial_sweeps, int32_t* block_out)
             if (sp > NT || tpr > MAX_THREADS) break;
             if (tpr < 32) continue;
             for (int ipc : {1, 2, 4, 8, 16}) {
-                if (tpr * ipc > MAX_THREADS || ipc > b->R || bundle_smem_bytes(g.L, NT, ipc) > 200 * 1024) break;
+                if (tpr * ipc > MAX_THREADS || ipc > b->R || bundle_smem_bytes(g.L, NT, ipc) > cap) break;
                 ShapeSched s; s.sp = sp; s.ipc = ipc; s.team = 0;
                 cands.push_back(s);
             }
@@ -725,7 +727,7 @@ int pt_batch_autotune(pt_batch* b, int32_t trial_sweeps, int32_t* block_out)
                 prev = nt;
                 for (int ipc : {1, 2, 4, 8}) {
                     if (nt * team * ipc > MAX_THREADS_SM || ipc > b->R ||
-                        bundle_smem_bytes(g.L, NT, ipc, team) > 200 * 1024)
+                        bundle_smem_bytes(g.L, NT, ipc, team) > cap)
                         break;
                     ShapeSched s; s.sp = nt; s.ipc = ipc; s.team = team;
                     cands.push_back(s);

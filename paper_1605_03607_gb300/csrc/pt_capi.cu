@@ -919,6 +919,8 @@ int pt_autotune(pt_handle* h, int32_t n_inst, int32_t trial_sweeps)
     if ((rc = upload_desc(h, g))) return rc;
     if ((rc = group_reset(h, g, true))) return rc;
     const int L2 = h->L * h->L;
+    int cap = 0;
+    CK(sweep_smem_capacity(&cap), "shared memory capacity");
     const int old_sp = h->sp, old_ipc = h->ipc, old_team = h->team;
     const bool old_timing = h->timing;
     h->timing = true;
@@ -938,7 +940,7 @@ int pt_autotune(pt_handle* h, int32_t n_inst, int32_t trial_sweeps)
         const int tpr = team > 0 ? sp * team : sp * L2;
         for (int ipc : {1, 2, 4}) {
             if (tpr * ipc > (team > 0 ? MAX_THREADS_SM : MAX_THREADS) || ipc > h->R) break;
-            if (bundle_smem_bytes(h->L, h->NT, ipc, team) > 200 * 1024) break;
+            if (bundle_smem_bytes(h->L, h->NT, ipc, team) > cap) break;
             h->team = team;
             h->sp = sp;
             h->ipc = ipc;
