@@ -49,6 +49,12 @@ UNIT = "spin-flip attempts/s"
 OPS_PER_ATTEMPT = 31.25
 # Integer issue peak per SM and clock: 4 sub-partitions x 32 lanes.
 INT_LANES_PER_SM_CLK = 128
+# DRAM bytes (read + write) of one sweep-kernel launch, from the ncu capture
+# summarised in profiles/pt_sweep_kernel_c8_1024runs.md, keyed by (team,
+# slot_parallel, runs_per_cta, runs).  A launch reads the runs' state once and
+# its write-back stays in L2, so the figure does not depend on the sweeps per
+# launch.  Any other schedule reports null.
+PROFILED_TRAFFIC = {(4, 32, 1, 1024): 17554944}
 
 
 def load_peaks():
@@ -300,7 +306,8 @@ def run_gpu(args):
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
                      "unit": "Tops/s (int32 issue)", "frac": achieved_ops / peak_ops if peak_ops else None,
-                     "traffic": None, "kernel": "pt_sweep_kernel",
+                     "traffic": PROFILED_TRAFFIC.get((h.mapping(), *h.schedule()[:2], R * spec)),
+                     "kernel": "pt_sweep_kernel",
                      "ops_per_attempt": OPS_PER_ATTEMPT,
                      "avg_launch_ms": sweep_ms / max(sweep_launches, 1), "launches": sweep_launches,
                      "peak_source": f"{sms} SMs x {INT_LANES_PER_SM_CLK} lanes x "
