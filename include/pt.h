@@ -234,6 +234,28 @@ int pt_get_schedule(const pt_handle *h, int32_t *slot_parallel, int32_t *runs_pe
 int pt_set_mapping(pt_handle *h, int32_t team, int32_t slot_parallel, int32_t runs_per_cta);
 int pt_get_mapping(const pt_handle *h, int32_t *team);
 
+/* Temperature random walk of every system copy (Sec. III.B).  A copy is one
+ * configuration buffer (the slot map of pt_get_state points slots at
+ * buffers); after pt_create, pt_reset, pt_tts_eval or pt_set_spins copy c is
+ * the configuration that started in slot c.  After every exchange pass each
+ * copy in the hot half (the
+ * n_temps/2 highest temperatures, slots n_temps - n_temps/2 .. n_temps-1)
+ * gets one more pass there; this is the statistic of the paper's first
+ * mixing criterion (the copy spending the least time in the hot half spends
+ * at least 20 % of the run there, time counted in exchange passes, i.e. in
+ * elementary Monte Carlo steps of `exchange_every` sweeps + one exchange).
+ * A copy completes a round trip when it is back in the coldest slot after
+ * reaching the hottest slot since its previous visit to the coldest one.
+ * pt_set_walk_stats(h, 1) allocates and zeroes the counters of this handle's
+ * runs (PT_ERR_ARG if the current schedule has no shared memory left for
+ * them), 0 frees them.  Counters restart on pt_reset, pt_tts_eval,
+ * pt_set_spins and pt_restore.  Results of the runs never depend on it.
+ * pt_get_walk_stats: hot and trips are host arrays of n_runs x n_temps
+ * (run-major, by copy; either may be NULL), n_passes the exchange passes
+ * counted since the counters restarted.  PT_ERR_STATE when not tracked. */
+int pt_set_walk_stats(pt_handle *h, int32_t on);
+int pt_get_walk_stats(pt_handle *h, uint64_t *hot, uint64_t *trips, uint64_t *n_passes);
+
 /* Autotuner: times every feasible (slot_parallel, runs_per_cta in {1,2,4})
  * of both mappings (slot-major teams of 2..32 lanes, 1/8 .. all slots per
  * team) for `trial_sweeps` sweeps of a batch of n_inst (1..16) copies of this

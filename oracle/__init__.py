@@ -67,6 +67,10 @@ def _declare(L):
     L.or_pt_exchange.argtypes = [c.c_int, _p(np.int8), c.c_int, _p(np.float64), c.c_int,
                                  c.c_uint32, c.c_uint32, _p(np.int8), _p(np.int32),
                                  _p(np.uint64), c.c_uint32]
+    L.or_pt_sweeps_walk.argtypes = L.or_pt_sweeps.argtypes + [_p(np.int32), _p(np.uint64), _p(np.uint64),
+                                                             _p(np.uint8)]
+    L.or_pt_exchange_walk.argtypes = L.or_pt_exchange.argtypes + [_p(np.int32), _p(np.uint64), _p(np.uint64),
+                                                                 _p(np.uint8)]
     L.or_tts.argtypes = [c.c_int, _p(np.int32), _p(np.int32), c.c_int32, c.c_int32,
                          c.POINTER(c.c_int32), c.POINTER(c.c_int32), c.POINTER(c.c_int32)]
     L.or_tts_eval.argtypes = [c.c_int, _p(np.int8), c.c_int, _p(np.float64), c.c_int,
@@ -132,7 +136,7 @@ def exchange_thresholds(betas):
 class PTState:
     """Oracle PT state for one instance: R runs x N_T slots, configurations in slot order."""
 
-    def __init__(self, L, J, betas, n_runs, seed, uid, spins=None):
+    def __init__(self, L, J, betas, n_runs, seed, uid, spins=None, walk=False):
         self.L = L
         self.N = 8 * L * L
         self.J = np.ascontiguousarray(J, np.int8).copy()
@@ -153,18 +157,37 @@ class PTState:
         self.xacc = np.zeros((self.R, max(self.NT - 1, 1)), np.uint64)
         self.sweep = 0
         lib().or_pt_start(L, self.J, self.NT, self.R, self.spins, self.E, self.best, self.first)
+        # temperature random walk (Sec. III.B): copy[r, t] = copy whose configuration
+        # is in slot t (copies are named by their starting slot); hot / trips by copy
+        self.walk = bool(walk)
+        if self.walk:
+            self.copy = np.tile(np.arange(self.NT, dtype=np.int32), (self.R, 1))
+            self.hot = np.zeros((self.R, self.NT), np.uint64)
+            self.trips = np.zeros((self.R, self.NT), np.uint64)
+            self.wstate = np.zeros((self.R, self.NT), np.uint8)
+            self.n_passes = 0
 
     def sweeps(self, n, exchange_every=1):
-        rc = lib().or_pt_sweeps(self.L, self.J, self.NT, self.betas, self.R, self.seed, self.uid,
-                                self.spins, self.E, self.best, self.first, self.macc, self.xacc,
-                                self.sweep, int(n), int(exchange_every))
+        args = (self.L, self.J, self.NT, self.betas, self.R, self.seed, self.uid, self.spins, self.E,
+                self.best, self.first, self.macc, self.xacc, self.sweep, int(n), int(exchange_every))
+        if self.walk:
+            rc = lib().or_pt_sweeps_walk(*args, self.copy, self.hot, self.trips, self.wstate)
+            if exchange_every > 0 and self.NT > 1:
+                self.n_passes += (self.sweep + int(n)) // exchange_every - self.sweep // exchange_every
+        else:
+            rc = lib().or_pt_sweeps(*args)
         if rc:
             raise ValueError("oracle sweep failed (bad ladder)")
         self.sweep += int(n)
 
     def exchange(self):
-        rc = lib().or_pt_exchange(self.L, self.J, self.NT, self.betas, self.R, self.seed,
-                                  self.uid, self.spins, self.E, self.xacc, self.sweep)
+        args = (self.L, self.J, self.NT, self.betas, self.R, self.seed, self.uid, self.spins, self.E,
+                self.xacc, self.sweep)
+        if self.walk:
+            rc = lib().or_pt_exchange_walk(*args, self.copy, self.hot, self.trips, self.wstate)
+            self.n_passes += 1 if self.NT > 1 else 0
+        else:
+            rc = lib().or_pt_exchange(*args)
         if rc:
             raise ValueError("oracle exchange failed (bad ladder)")
 

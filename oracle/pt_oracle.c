@@ -37,6 +37,9 @@
  *     by even numbers, d = E_{p+1} - E_p = 2h: accept if h <= 0, else if
  *     h <= H_p and u < xthr[p][h] = floor(exp(-2 h (beta_p - beta_{p+1})) 2^32);
  *     configurations are swapped whole (this oracle keeps no permutation);
+ *   - temperature random walk: a system copy is identified by the slot its
+ *     configuration started in; its hot-half time is counted in exchange
+ *     passes, the hot half being the N_T/2 highest temperatures;
  *   - random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11),
  *     key = (seed, uid), counter (sweep, run<<16 | slot, group, kind) with
  *     kind 0 Metropolis (group = i>>2, word i&3), 1 exchange (group = p>>2,
@@ -295,9 +298,35 @@ static void metropolis_sweep(const pt_ctx *cx, int run, int slot, uint32_t sweep
         }
 }
 
+/* Temperature random walk of the copies of one run (Sec. III.B), kept when
+ * `copy` is not NULL: copy[t] is the id of the copy (the slot it started in)
+ * whose configuration sits in slot t.  After an exchange pass, each copy in
+ * the hot half -- the NT/2 highest temperatures, slots NT - NT/2 .. NT-1 --
+ * counts one more pass there (the paper's first mixing criterion is the
+ * least of these over copies), and the copy in the coldest slot completes a
+ * round trip if it reached the hottest slot since it last sat in the coldest
+ * one (state 0: neither end seen yet, 1: coldest seen, 2: hottest seen
+ * after it). */
+typedef struct {
+    int32_t *copy;      /* [NT] slot -> copy */
+    uint64_t *hot;      /* [NT] by copy */
+    uint64_t *trips;    /* [NT] by copy */
+    uint8_t *state;     /* [NT] by copy */
+} walk_run;
+
+static void walk_after_pass(int NT, const walk_run *w)
+{
+    for (int t = NT - NT / 2; t < NT; ++t) w->hot[w->copy[t]] += 1;
+    int c = w->copy[0];
+    if (w->state[c] == 2) w->trips[c] += 1;
+    w->state[c] = 1;
+    int h = w->copy[NT - 1];
+    if (w->state[h] == 1) w->state[h] = 2;
+}
+
 /* One exchange sweep of one run: pairs p = 0..NT-2 in ascending order. */
 static void exchange_pass(const pt_ctx *cx, int run, uint32_t sweep, int8_t *spins_run,
-                          int32_t *E_run, uint64_t *xacc_run)
+                          int32_t *E_run, uint64_t *xacc_run, const walk_run *w)
 {
     int N = cx->N;
     int8_t *tmp = malloc((size_t)N);
@@ -318,18 +347,31 @@ static void exchange_pass(const pt_ctx *cx, int run, uint32_t sweep, int8_t *spi
             memcpy(spins_run + (size_t)(p + 1) * N, tmp, (size_t)N);
             int32_t e = E_run[p]; E_run[p] = E_run[p + 1]; E_run[p + 1] = e;
             xacc_run[p] += 1;
+            if (w) { int32_t c = w->copy[p]; w->copy[p] = w->copy[p + 1]; w->copy[p + 1] = c; }
         }
     }
     free(tmp);
+    if (w && cx->NT > 1) walk_after_pass(cx->NT, w);
+}
+
+static walk_run walk_of_run(int n_temps, int run, int32_t *copy, uint64_t *hot, uint64_t *trips,
+                            uint8_t *state)
+{
+    walk_run w;
+    size_t o = (size_t)run * n_temps;
+    w.copy = copy + o; w.hot = hot + o; w.trips = trips + o; w.state = state + o;
+    return w;
 }
 
 /* Runs sweeps sweep0+1 .. sweep0+n_sweeps in place.  After each sweep s the
  * per-run best energy / first sweep are updated, then, if exchange_every > 0
- * and s % exchange_every == 0, one exchange sweep with counter sweep = s. */
-int or_pt_sweeps(int L, const int8_t *J, int n_temps, const double *betas, int n_runs,
-                 uint32_t seed, uint32_t uid, int8_t *spins, int32_t *E, int32_t *best,
-                 int32_t *first, uint64_t *macc, uint64_t *xacc, uint32_t sweep0,
-                 int n_sweeps, int exchange_every)
+ * and s % exchange_every == 0, one exchange sweep with counter sweep = s.
+ * The walk arrays ([n_runs][n_temps] each) are all NULL or all given. */
+int or_pt_sweeps_walk(int L, const int8_t *J, int n_temps, const double *betas, int n_runs,
+                      uint32_t seed, uint32_t uid, int8_t *spins, int32_t *E, int32_t *best,
+                      int32_t *first, uint64_t *macc, uint64_t *xacc, uint32_t sweep0,
+                      int n_sweeps, int exchange_every, int32_t *copy, uint64_t *hot,
+                      uint64_t *trips, uint8_t *state)
 {
     pt_ctx cx;
     if (ctx_open(&cx, L, J, n_temps, betas, n_runs, seed, uid) != 0) { ctx_close(&cx); return -1; }
@@ -337,6 +379,8 @@ int or_pt_sweeps(int L, const int8_t *J, int n_temps, const double *betas, int n
     for (int run = 0; run < n_runs; ++run) {
         int8_t *sr = spins + (size_t)run * n_temps * N;
         int32_t *Er = E + (size_t)run * n_temps;
+        walk_run w;
+        if (copy) w = walk_of_run(n_temps, run, copy, hot, trips, state);
         for (int step = 1; step <= n_sweeps; ++step) {
             uint32_t s = sweep0 + (uint32_t)step;
             for (int t = 0; t < n_temps; ++t)
@@ -346,25 +390,47 @@ int or_pt_sweeps(int L, const int8_t *J, int n_temps, const double *betas, int n
             for (int t = 0; t < n_temps; ++t) if (Er[t] < m) m = Er[t];
             if (m < best[run]) { best[run] = m; first[run] = (int32_t)s; }
             if (exchange_every > 0 && s % (uint32_t)exchange_every == 0)
-                exchange_pass(&cx, run, s, sr, Er, xacc + (size_t)run * (n_temps > 1 ? n_temps - 1 : 0));
+                exchange_pass(&cx, run, s, sr, Er, xacc + (size_t)run * (n_temps > 1 ? n_temps - 1 : 0),
+                              copy ? &w : NULL);
         }
     }
     ctx_close(&cx);
     return 0;
 }
 
+int or_pt_sweeps(int L, const int8_t *J, int n_temps, const double *betas, int n_runs,
+                 uint32_t seed, uint32_t uid, int8_t *spins, int32_t *E, int32_t *best,
+                 int32_t *first, uint64_t *macc, uint64_t *xacc, uint32_t sweep0,
+                 int n_sweeps, int exchange_every)
+{
+    return or_pt_sweeps_walk(L, J, n_temps, betas, n_runs, seed, uid, spins, E, best, first, macc, xacc,
+                             sweep0, n_sweeps, exchange_every, NULL, NULL, NULL, NULL);
+}
+
 /* One standalone exchange sweep of every run with counter sweep = `sweep`. */
+int or_pt_exchange_walk(int L, const int8_t *J, int n_temps, const double *betas, int n_runs,
+                        uint32_t seed, uint32_t uid, int8_t *spins, int32_t *E, uint64_t *xacc,
+                        uint32_t sweep, int32_t *copy, uint64_t *hot, uint64_t *trips, uint8_t *state)
+{
+    pt_ctx cx;
+    if (ctx_open(&cx, L, J, n_temps, betas, n_runs, seed, uid) != 0) { ctx_close(&cx); return -1; }
+    for (int run = 0; run < n_runs; ++run) {
+        walk_run w;
+        if (copy) w = walk_of_run(n_temps, run, copy, hot, trips, state);
+        exchange_pass(&cx, run, sweep, spins + (size_t)run * n_temps * cx.N,
+                      E + (size_t)run * n_temps, xacc + (size_t)run * (n_temps > 1 ? n_temps - 1 : 0),
+                      copy ? &w : NULL);
+    }
+    ctx_close(&cx);
+    return 0;
+}
+
 int or_pt_exchange(int L, const int8_t *J, int n_temps, const double *betas, int n_runs,
                    uint32_t seed, uint32_t uid, int8_t *spins, int32_t *E, uint64_t *xacc,
                    uint32_t sweep)
 {
-    pt_ctx cx;
-    if (ctx_open(&cx, L, J, n_temps, betas, n_runs, seed, uid) != 0) { ctx_close(&cx); return -1; }
-    for (int run = 0; run < n_runs; ++run)
-        exchange_pass(&cx, run, sweep, spins + (size_t)run * n_temps * cx.N,
-                      E + (size_t)run * n_temps, xacc + (size_t)run * (n_temps > 1 ? n_temps - 1 : 0));
-    ctx_close(&cx);
-    return 0;
+    return or_pt_exchange_walk(L, J, n_temps, betas, n_runs, seed, uid, spins, E, xacc, sweep,
+                               NULL, NULL, NULL, NULL);
 }
 
 /* ------------------------------------------------------------------ */

@@ -67,6 +67,8 @@ SIGNATURES = [
     ("pt_autotune", C.c_int, [_VP, C.c_int32, C.c_int32]),
     ("pt_set_mapping", C.c_int, [_VP, C.c_int32, C.c_int32, C.c_int32]),
     ("pt_get_mapping", C.c_int, [_VP, _I32P]),
+    ("pt_set_walk_stats", C.c_int, [_VP, C.c_int32]),
+    ("pt_get_walk_stats", C.c_int, [_VP, _VP, _VP, C.POINTER(C.c_uint64)]),
     ("pt_launch_count", C.c_uint64, [_VP]),
     ("pt_select_device", C.c_int, [C.c_int32]),
     ("pt_set_timing", C.c_int, [_VP, C.c_int]),
@@ -295,6 +297,18 @@ class PTHandle:
         t = C.c_int32()
         _check(load().pt_get_mapping(self.h, C.byref(t)), self.h)
         return t.value
+
+    def set_walk_stats(self, on=True):
+        _check(load().pt_set_walk_stats(self.h, 1 if on else 0), self.h)
+
+    def walk_stats(self):
+        """(hot, trips, n_passes): per run and copy, exchange passes spent in the
+        hot half and completed cold -> hot -> cold round trips."""
+        hot = np.zeros((self.R, self.NT), np.uint64)
+        trips = np.zeros((self.R, self.NT), np.uint64)
+        n = C.c_uint64()
+        _check(load().pt_get_walk_stats(self.h, _ptr(hot), _ptr(trips), C.byref(n)), self.h)
+        return hot, trips, int(n.value)
 
     def schedule(self):
         a, b, c = C.c_int32(), C.c_int32(), C.c_int32()

@@ -47,6 +47,11 @@ struct Group {
     std::vector<Bundle> bundles;
     int block = 0, smem = 0;
     uint64_t sweep = 0;
+    // temperature random walk (main group only, when tracked)
+    bool walk = false;
+    unsigned long long *whot = nullptr, *wtrips = nullptr;
+    uint8_t* wstate = nullptr;
+    uint64_t walk_passes = 0;        // exchange passes since the counters were cleared
 };
 
 }  // namespace
@@ -124,6 +129,7 @@ void free_group(Group& g)
     cudaFree(g.spins); cudaFree(g.E); cudaFree(g.perm); cudaFree(g.best); cudaFree(g.first);
     cudaFree(g.macc); cudaFree(g.xacc); cudaFree(g.jw); cudaFree(g.d_desc); cudaFree(g.d_items);
     cudaFree(g.d_bundles); cudaFree(g.d_tts); cudaFree(g.d_queue);
+    cudaFree(g.whot); cudaFree(g.wtrips); cudaFree(g.wstate);
     g = Group();
 }
 
@@ -153,7 +159,8 @@ int check_schedule(pt_handle* h, int L, int NT, int sp, int ipc, int team)
         if ((sp * L2) % 32 != 0) return fail(h, PT_ERR_ARG, "slot_parallel * L^2 must be a multiple of 32");
         if (sp * L2 * ipc > MAX_THREADS) return fail(h, PT_ERR_ARG, "more than 1024 threads per CTA");
     }
-    if (bundle_smem_bytes(L, NT, ipc, team) > 227 * 1024) return fail(h, PT_ERR_ARG, "shared memory above 227 KB");
+    if (bundle_smem_bytes(L, NT, ipc, team, h->main.walk) > 227 * 1024)
+        return fail(h, PT_ERR_ARG, "shared memory above 227 KB");
     return PT_OK;
 }
 
@@ -209,7 +216,7 @@ int group_schedule(pt_handle* h, Group& g)
             g.bundles.push_back(b);
         }
     g.block = (h->team > 0 ? h->sp * h->team : h->sp * L2) * h->ipc;
-    g.smem = (int)bundle_smem_bytes(g.L, g.NT, h->ipc, h->team);
+    g.smem = (int)bundle_smem_bytes(g.L, g.NT, h->ipc, h->team, g.walk);
     cudaFree(g.d_bundles);
     g.d_bundles = nullptr;
     CK(dalloc(&g.d_bundles, g.bundles.size()), "cudaMalloc bundles");
@@ -240,8 +247,22 @@ int upload_couplers(pt_handle* h, Group& g, int inst, const int8_t* J)
     return PT_OK;
 }
 
+// Zeroes the walk counters and states of a tracked group.
+int walk_clear(pt_handle* h, Group& g)
+{
+    if (!g.walk) return PT_OK;
+    const size_t reps = (size_t)g.n_inst * g.R * g.NT;
+    CK(cudaMemsetAsync(g.whot, 0, 8 * reps, h->stream), "clear walk");
+    CK(cudaMemsetAsync(g.wtrips, 0, 8 * reps, h->stream), "clear walk");
+    CK(cudaMemsetAsync(g.wstate, 0, reps, h->stream), "clear walk");
+    g.walk_passes = 0;
+    return PT_OK;
+}
+
 int group_reset(pt_handle* h, Group& g, bool draw)
 {
+    int rc = walk_clear(h, g);
+    if (rc) return rc;
     CK(launch_init(g.d_desc, g.d_items, g.n_inst * g.R, draw, h->stream), "init kernel");
     CK(launch_energy(g.d_desc, g.d_items, g.n_inst * g.R, 0, h->stream), "energy kernel");
     h->launches += 2;
@@ -272,8 +293,10 @@ int group_sweeps(pt_handle* h, Group& g, int64_t n, int xevery)
         const int chunk = (int)std::min<int64_t>(h->spl, n - done);
         if (h->timing) CK(cudaEventRecord(h->ev[2 * li], h->stream), "event");
         CK(launch_sweeps(g.d_desc, g.d_bundles, (int)g.bundles.size(), (int)g.bundles.size(), g.block,
-                         g.smem, (uint32_t)g.sweep, chunk, xevery, 0, nullptr, h->stream, h->team > 0),
+                         g.smem, (uint32_t)g.sweep, chunk, xevery, 0, nullptr, h->stream, h->team > 0, g.walk),
            "sweep kernel");
+        if (g.walk && g.NT > 1 && xevery > 0)
+            g.walk_passes += (g.sweep + chunk) / (uint64_t)xevery - g.sweep / (uint64_t)xevery;
         if (h->timing) CK(cudaEventRecord(h->ev[2 * li + 1], h->stream), "event");
         ++h->launches;
         ++li;
@@ -528,6 +551,8 @@ int pt_set_spins(pt_handle* h, const int8_t* spins)
     CK(launch_init(h->main.d_desc, h->main.d_items, h->R, false, h->stream), "init kernel");
     CK(launch_energy(h->main.d_desc, h->main.d_items, h->R, (int32_t)h->main.sweep, h->stream), "energy kernel");
     h->launches += 2;
+    int rc = walk_clear(h, h->main);
+    if (rc) return rc;
     CK(cudaStreamSynchronize(h->stream), "sync set_spins");
     return PT_OK;
 }
@@ -549,8 +574,10 @@ int pt_exchange(pt_handle* h)
     if (!h) return PT_ERR_ARG;
     Group& g = h->main;
     CK(launch_sweeps(g.d_desc, g.d_bundles, (int)g.bundles.size(), (int)g.bundles.size(), g.block,
-                     g.smem, (uint32_t)g.sweep, 0, 0, 1, nullptr, h->stream, h->team > 0), "exchange kernel");
+                     g.smem, (uint32_t)g.sweep, 0, 0, 1, nullptr, h->stream, h->team > 0, g.walk),
+       "exchange kernel");
     ++h->launches;
+    if (g.walk && g.NT > 1) g.walk_passes += 1;
     CK(cudaStreamSynchronize(h->stream), "sync exchange");
     return PT_OK;
 }
@@ -858,6 +885,7 @@ int pt_restore(pt_handle* h, const void* buf, size_t len)
     CK(cudaMemcpyAsync(g.first, p, 4 * (size_t)h->R, cudaMemcpyHostToDevice, h->stream), "restore first"); p += 4 * (size_t)h->R;
     CK(cudaMemcpyAsync(g.macc, p, 8 * reps, cudaMemcpyHostToDevice, h->stream), "restore macc"); p += 8 * reps;
     CK(cudaMemcpyAsync(g.xacc, p, 8 * npair, cudaMemcpyHostToDevice, h->stream), "restore xacc");
+    if ((rc = walk_clear(h, g))) return rc;  // the restored buffers start a new walk
     CK(cudaStreamSynchronize(h->stream), "sync restore");
     return PT_OK;
 }
@@ -897,6 +925,56 @@ int pt_get_mapping(const pt_handle* h, int32_t* team)
 {
     if (!h || !team) return PT_ERR_ARG;
     *team = h->team;
+    return PT_OK;
+}
+
+int pt_set_walk_stats(pt_handle* h, int32_t on)
+{
+    if (!h) return PT_ERR_ARG;
+    Group& g = h->main;
+    const size_t reps = (size_t)g.n_inst * g.R * g.NT;
+    if (on && !g.walk) {
+        // the walk arrays enlarge each run's shared-memory block: check first
+        int cap = 0;
+        CK(sweep_smem_capacity(&cap), "shared memory capacity");
+        if (bundle_smem_bytes(g.L, g.NT, h->ipc, h->team, true) > cap)
+            return fail(h, PT_ERR_ARG, "the current schedule leaves no shared memory for the walk counters");
+        CK(dalloc(&g.whot, reps), "cudaMalloc walk");
+        CK(dalloc(&g.wtrips, reps), "cudaMalloc walk");
+        CK(dalloc(&g.wstate, reps), "cudaMalloc walk");
+        g.walk = true;
+        for (int i = 0; i < g.n_inst; ++i) {
+            const size_t r0 = (size_t)i * g.R * g.NT;
+            g.desc[i].whot = g.whot + r0;
+            g.desc[i].wtrips = g.wtrips + r0;
+            g.desc[i].wstate = g.wstate + r0;
+        }
+    } else if (!on && g.walk) {
+        CK(cudaStreamSynchronize(h->stream), "sync walk");
+        cudaFree(g.whot); cudaFree(g.wtrips); cudaFree(g.wstate);
+        g.whot = g.wtrips = nullptr;
+        g.wstate = nullptr;
+        g.walk = false;
+        for (auto& d : g.desc) d.whot = d.wtrips = nullptr, d.wstate = nullptr;
+    }
+    int rc = upload_desc(h, g);
+    if (!rc) rc = group_schedule(h, g);
+    if (!rc) rc = walk_clear(h, g);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(h->stream), "sync walk");
+    return PT_OK;
+}
+
+int pt_get_walk_stats(pt_handle* h, uint64_t* hot, uint64_t* trips, uint64_t* n_passes)
+{
+    if (!h) return PT_ERR_ARG;
+    Group& g = h->main;
+    if (!g.walk) return fail(h, PT_ERR_STATE, "the walk is not tracked (pt_set_walk_stats)");
+    const size_t reps = (size_t)g.R * g.NT;
+    if (hot) CK(cudaMemcpyAsync(hot, g.whot, 8 * reps, cudaMemcpyDeviceToHost, h->stream), "download walk");
+    if (trips) CK(cudaMemcpyAsync(trips, g.wtrips, 8 * reps, cudaMemcpyDeviceToHost, h->stream), "download walk");
+    CK(cudaStreamSynchronize(h->stream), "sync walk");
+    if (n_passes) *n_passes = g.walk_passes;
     return PT_OK;
 }
 

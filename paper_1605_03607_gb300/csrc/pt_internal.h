@@ -44,6 +44,11 @@ struct InstDesc {
     int32_t* first;           // [R]
     unsigned long long* macc; // [R][NT] accepted flips per slot
     unsigned long long* xacc; // [R][max(NT-1,1)] accepted swaps per pair
+    // temperature random walk of each system copy (= configuration buffer);
+    // all three NULL when the walk is not tracked
+    unsigned long long* whot = nullptr;   // [R][NT] exchange passes spent in the hot half
+    unsigned long long* wtrips = nullptr; // [R][NT] completed cold -> hot -> cold round trips
+    uint8_t* wstate = nullptr;            // [R][NT] 0 none, 1 coldest slot seen, 2 then hottest
 };
 
 // One CTA work unit: `nitems` consecutive runs of one instance.
@@ -66,12 +71,12 @@ __host__ __device__ inline int threads_per_run(int L, const Bundle& b)
 // critical h by pair (two sweeps), flip / swap counters, perm (slot ->
 // buffer), its inverse (buffer -> slot, slot-major mapping), best/first.
 struct ItemLayout {
-    int64_t spins, E, ccrit, macc, xacc, perm, inv, misc, bytes;
+    int64_t spins, E, ccrit, macc, xacc, perm, inv, whot, wtrips, wstate, misc, bytes;
 };
 
 __host__ __device__ inline int64_t pad16(int64_t x) { return (x + 15) & ~15LL; }
 
-__host__ __device__ inline ItemLayout item_layout(int L, int NT, int pad = 0)
+__host__ __device__ inline ItemLayout item_layout(int L, int NT, int pad = 0, bool walk = false)
 {
     ItemLayout o;
     const int64_t N = 8LL * L * L;
@@ -82,7 +87,16 @@ __host__ __device__ inline ItemLayout item_layout(int L, int NT, int pad = 0)
     o.xacc = o.macc + 4LL * NT;
     o.perm = o.xacc + 4LL * NT;
     o.inv = o.perm + NT;
-    o.misc = pad16(o.inv + NT);
+    int64_t end = o.inv + NT;
+    if (walk) {                       // per-copy walk counters for this launch, and walk states
+        o.whot = (end + 3) & ~3LL;
+        o.wtrips = o.whot + 4LL * NT;
+        o.wstate = o.wtrips + 4LL * NT;
+        end = o.wstate + NT;
+    } else {
+        o.whot = o.wtrips = o.wstate = end;
+    }
+    o.misc = pad16(end);
     o.bytes = o.misc + 16;
     return o;
 }
@@ -112,11 +126,12 @@ void set_global_error(const char* msg);
 constexpr int CELL_REC = 12;
 __host__ __device__ inline int64_t cell_table_bytes(int L) { return 4LL * CELL_REC * 2 * L * L; }
 
-inline int64_t bundle_smem_bytes(int L, int NT, int nitems, int team = 0)
+inline int64_t bundle_smem_bytes(int L, int NT, int nitems, int team = 0, bool walk = false)
 {
     if (team > 0)
-        return table_bytes(NT) + cell_table_bytes(L) + (int64_t)nitems * item_layout(L, NT, sm_pad(L, team)).bytes;
-    return table_bytes(NT) + (int64_t)nitems * item_layout(L, NT).bytes;
+        return table_bytes(NT) + cell_table_bytes(L) +
+               (int64_t)nitems * item_layout(L, NT, sm_pad(L, team), walk).bytes;
+    return table_bytes(NT) + (int64_t)nitems * item_layout(L, NT, 0, walk).bytes;
 }
 
 }  // namespace ptg

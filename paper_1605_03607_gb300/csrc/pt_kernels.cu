@@ -184,6 +184,23 @@ __device__ __forceinline__ void exchange_prepare(const InstDesc& in, const uint3
     }
 }
 
+// Temperature random walk, after one exchange pass of a run (one thread).
+// Copies are the configuration buffers.  Every copy in the hot half (the
+// NT/2 highest temperatures: slots NT - NT/2 .. NT-1) gets one more pass
+// there.  A copy at the coldest slot completes a round trip if it reached the
+// hottest slot since it last sat at the coldest one; states: 0 neither end
+// seen yet, 1 coldest slot seen, 2 hottest slot seen after it.
+__device__ __forceinline__ void walk_update(const uint8_t* perm, uint32_t* whot, uint32_t* wtr, uint8_t* wst,
+                                            int NT)
+{
+    for (int t = NT - NT / 2; t < NT; ++t) whot[perm[t]] += 1u;
+    const int c = perm[0];
+    if (wst[c] == 2) wtr[c] += 1u;
+    wst[c] = 1;
+    const int h = perm[NT - 1];
+    if (wst[h] == 1) wst[h] = 2;
+}
+
 // The ascending exchange sweep of one run (one thread): a configuration that
 // wins pair p is carried on to pair p+1.  Slot energies, slot map and
 // acceptance criteria are read in blocks of 4 ahead of the carried chain.
@@ -249,6 +266,7 @@ __device__ __forceinline__ int exchange_chain(int32_t* Es, uint8_t* perm, uint8_
     return m;
 }
 
+template <bool WALK>
 __device__ void process_bundle(const InstDesc* __restrict__ insts, const Bundle bd,
                                uint32_t sweep0, int nsweeps, int xevery, int mode,
                                unsigned char* smem)
@@ -261,7 +279,8 @@ __device__ void process_bundle(const InstDesc* __restrict__ insts, const Bundle 
     const bool active = item < bd.nitems;
     const int q = j % L2, sp = j / L2;
     const int run = bd.run0 + (active ? item : 0);
-    const ItemLayout lay = item_layout(L, NT);
+    constexpr bool walk = WALK;
+    const ItemLayout lay = item_layout(L, NT, 0, walk);
 
     // bundle tables: thr [NT][KT], then exchange offsets [NT] and search hints [NT]
     uint32_t* thr_sm = reinterpret_cast<uint32_t*>(smem);
@@ -293,6 +312,11 @@ __device__ void process_bundle(const InstDesc* __restrict__ insts, const Bundle 
             perm[t] = in.perm[rep0 + t];
             macc[t] = 0u;
             xacc[t] = 0u;
+            if (walk) {
+                reinterpret_cast<uint32_t*>(ib + lay.whot)[t] = 0u;
+                reinterpret_cast<uint32_t*>(ib + lay.wtrips)[t] = 0u;
+                (ib + lay.wstate)[t] = in.wstate[rep0 + t];
+            }
         }
         if (j == 0) {
             misc[0] = in.best[run];
@@ -354,6 +378,9 @@ __device__ void process_bundle(const InstDesc* __restrict__ insts, const Bundle 
             int m;
             if (do_x) {
                 m = exchange_chain<false>(Es, perm, nullptr, xacc, ccrit + (s & 1u) * NT, NT);
+                if (WALK)
+                    walk_update(perm, reinterpret_cast<uint32_t*>(ib + lay.whot),
+                                reinterpret_cast<uint32_t*>(ib + lay.wtrips), ib + lay.wstate, NT);
             } else {
                 m = Es[0];
                 for (int p = 1; p < NT; ++p) m = min(m, Es[p]);
@@ -382,6 +409,11 @@ __device__ void process_bundle(const InstDesc* __restrict__ insts, const Bundle 
             in.perm[rep0 + t] = perm[t];
             in.macc[rep0 + t] += macc[t];
             if (t < NT - 1) in.xacc[(size_t)run * (NT > 1 ? NT - 1 : 1) + t] += xacc[t];
+            if (walk) {
+                in.whot[rep0 + t] += reinterpret_cast<const uint32_t*>(ib + lay.whot)[t];
+                in.wtrips[rep0 + t] += reinterpret_cast<const uint32_t*>(ib + lay.wtrips)[t];
+                in.wstate[rep0 + t] = (ib + lay.wstate)[t];
+            }
         }
         if (j == 0) {
             in.best[run] = misc[0];
@@ -439,6 +471,7 @@ __device__ __forceinline__ void sm_word(const uint32_t* rec, uint32_t meta, uint
 // Bank layout: buffer strides are congruent to G modulo 32 and the cell
 // records are colour-major with a 48-byte stride, so a warp's own/opposite
 // spin words and coupler records come without bank conflicts.
+template <bool WALK>
 __device__ void process_bundle_sm(const InstDesc* __restrict__ insts, const Bundle bd,
                                   uint32_t sweep0, int nsweeps, int xevery, int mode,
                                   unsigned char* smem)
@@ -451,7 +484,8 @@ __device__ void process_bundle_sm(const InstDesc* __restrict__ insts, const Bund
     const bool active = item < bd.nitems;
     const int team = j / G, tl = j - team * G;
     const int run = bd.run0 + (active ? item : 0);
-    const ItemLayout lay = item_layout(L, NT, sm_pad(L, G));
+    constexpr bool walk = WALK;
+    const ItemLayout lay = item_layout(L, NT, sm_pad(L, G), walk);
 
     uint32_t* thr_sm = reinterpret_cast<uint32_t*>(smem);
     uint32_t* rec_sm = reinterpret_cast<uint32_t*>(smem + table_bytes(NT));   // [2][L2][CELL_REC]
@@ -498,6 +532,11 @@ __device__ void process_bundle_sm(const InstDesc* __restrict__ insts, const Bund
             inv[b] = (uint8_t)t;
             macc[t] = 0u;
             xacc[t] = 0u;
+            if (walk) {
+                reinterpret_cast<uint32_t*>(ib + lay.whot)[t] = 0u;
+                reinterpret_cast<uint32_t*>(ib + lay.wtrips)[t] = 0u;
+                (ib + lay.wstate)[t] = in.wstate[rep0 + t];
+            }
         }
         if (j == 0) {
             misc[0] = in.best[run];
@@ -557,6 +596,9 @@ __device__ void process_bundle_sm(const InstDesc* __restrict__ insts, const Bund
             int m;
             if (do_x) {
                 m = exchange_chain<true>(Es, perm, inv, xacc, ccrit + (s & 1u) * NT, NT);
+                if (WALK)
+                    walk_update(perm, reinterpret_cast<uint32_t*>(ib + lay.whot),
+                                reinterpret_cast<uint32_t*>(ib + lay.wtrips), ib + lay.wstate, NT);
             } else {
                 m = Es[0];
                 for (int p = 1; p < NT; ++p) m = min(m, Es[p]);
@@ -585,6 +627,11 @@ __device__ void process_bundle_sm(const InstDesc* __restrict__ insts, const Bund
             in.perm[rep0 + t] = perm[t];
             in.macc[rep0 + t] += macc[t];
             if (t < NT - 1) in.xacc[(size_t)run * (NT > 1 ? NT - 1 : 1) + t] += xacc[t];
+            if (walk) {
+                in.whot[rep0 + t] += reinterpret_cast<const uint32_t*>(ib + lay.whot)[t];
+                in.wtrips[rep0 + t] += reinterpret_cast<const uint32_t*>(ib + lay.wtrips)[t];
+                in.wstate[rep0 + t] = (ib + lay.wstate)[t];
+            }
         }
         if (j == 0) {
             in.best[run] = misc[0];
@@ -594,9 +641,11 @@ __device__ void process_bundle_sm(const InstDesc* __restrict__ insts, const Bund
     __syncthreads();
 }
 
-// SLOT_MAJOR selects the mapping of every bundle of the launch (the two are
-// separate instantiations so each keeps its own register allocation).
-template <bool SLOT_MAJOR>
+// SLOT_MAJOR selects the mapping of every bundle of the launch, WALK whether
+// the launch tracks the temperature random walk of every copy (separate
+// instantiations, so each keeps its own register allocation and the untracked
+// kernels carry no walk code).
+template <bool SLOT_MAJOR, bool WALK>
 __global__ void __launch_bounds__(SLOT_MAJOR ? MAX_THREADS_SM : MAX_THREADS)
 pt_sweep_kernel(const InstDesc* __restrict__ insts, const Bundle* __restrict__ bundles,
                 int nbundles, uint32_t sweep0, int nsweeps, int xevery, int mode,
@@ -613,9 +662,9 @@ pt_sweep_kernel(const InstDesc* __restrict__ insts, const Bundle* __restrict__ b
     while (b < nbundles) {
         const Bundle bd = bundles[b];
         if (SLOT_MAJOR)
-            process_bundle_sm(insts, bd, sweep0, nsweeps, xevery, mode, smem);
+            process_bundle_sm<WALK>(insts, bd, sweep0, nsweeps, xevery, mode, smem);
         else
-            process_bundle(insts, bd, sweep0, nsweeps, xevery, mode, smem);
+            process_bundle<WALK>(insts, bd, sweep0, nsweeps, xevery, mode, smem);
         if (!queue) break;
         if (threadIdx.x == 0) s_next = atomicAdd(queue, 1);
         __syncthreads();
@@ -748,27 +797,35 @@ cudaError_t sweep_smem_capacity(int* bytes)
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    cudaFuncAttributes fa, fb;
-    e = cudaFuncGetAttributes(&fa, pt_sweep_kernel<false>);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncGetAttributes(&fb, pt_sweep_kernel<true>);
-    if (e != cudaSuccess) return e;
-    *bytes = optin - (int)(fa.sharedSizeBytes > fb.sharedSizeBytes ? fa.sharedSizeBytes : fb.sharedSizeBytes);
+    size_t stat = 0;
+    const void* ks[4] = {(const void*)pt_sweep_kernel<false, false>, (const void*)pt_sweep_kernel<true, false>,
+                         (const void*)pt_sweep_kernel<false, true>, (const void*)pt_sweep_kernel<true, true>};
+    for (const void* k : ks) {
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, k);
+        if (e != cudaSuccess) return e;
+        stat = fa.sharedSizeBytes > stat ? fa.sharedSizeBytes : stat;
+    }
+    *bytes = optin - (int)stat;
     return cudaSuccess;
 }
 
-cudaError_t sweep_occupancy(int block, int smem_bytes, int* blocks_per_sm, bool slot_major)
+cudaError_t sweep_occupancy(int block, int smem_bytes, int* blocks_per_sm, bool slot_major, bool walk)
 {
-    if (slot_major)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, pt_sweep_kernel<true>, block, smem_bytes);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, pt_sweep_kernel<false>, block, smem_bytes);
+    const void* k = slot_major ? (walk ? (const void*)pt_sweep_kernel<true, true> : (const void*)pt_sweep_kernel<true, false>)
+                               : (walk ? (const void*)pt_sweep_kernel<false, true> : (const void*)pt_sweep_kernel<false, false>);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, block, smem_bytes);
 }
 
 cudaError_t set_sweep_smem_limit(int bytes)
 {
-    cudaError_t e = cudaFuncSetAttribute(pt_sweep_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(pt_sweep_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    const void* ks[4] = {(const void*)pt_sweep_kernel<false, false>, (const void*)pt_sweep_kernel<true, false>,
+                         (const void*)pt_sweep_kernel<false, true>, (const void*)pt_sweep_kernel<true, true>};
+    for (const void* k : ks) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_init(const InstDesc* insts, const int2* items, int nitems, bool draw,
@@ -789,15 +846,21 @@ cudaError_t launch_energy(const InstDesc* insts, const int2* items, int nitems, 
 
 cudaError_t launch_sweeps(const InstDesc* insts, const Bundle* bundles, int nbundles, int grid,
                           int block, int smem_bytes, uint32_t sweep0, int nsweeps, int xevery,
-                          int mode, int* queue, cudaStream_t st, bool slot_major)
+                          int mode, int* queue, cudaStream_t st, bool slot_major, bool walk)
 {
     if (nbundles <= 0) return cudaSuccess;
-    if (slot_major)
-        pt_sweep_kernel<true><<<grid, block, smem_bytes, st>>>(insts, bundles, nbundles, sweep0, nsweeps,
-                                                               xevery, mode, queue);
+    if (slot_major && walk)
+        pt_sweep_kernel<true, true><<<grid, block, smem_bytes, st>>>(insts, bundles, nbundles, sweep0, nsweeps,
+                                                                     xevery, mode, queue);
+    else if (slot_major)
+        pt_sweep_kernel<true, false><<<grid, block, smem_bytes, st>>>(insts, bundles, nbundles, sweep0, nsweeps,
+                                                                      xevery, mode, queue);
+    else if (walk)
+        pt_sweep_kernel<false, true><<<grid, block, smem_bytes, st>>>(insts, bundles, nbundles, sweep0, nsweeps,
+                                                                      xevery, mode, queue);
     else
-        pt_sweep_kernel<false><<<grid, block, smem_bytes, st>>>(insts, bundles, nbundles, sweep0, nsweeps,
-                                                                xevery, mode, queue);
+        pt_sweep_kernel<false, false><<<grid, block, smem_bytes, st>>>(insts, bundles, nbundles, sweep0, nsweeps,
+                                                                       xevery, mode, queue);
     return cudaGetLastError();
 }
 

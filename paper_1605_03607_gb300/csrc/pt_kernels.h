@@ -10,17 +10,20 @@ namespace ptg {
 cudaError_t sweep_smem_capacity(int* bytes);
 cudaError_t set_sweep_smem_limit(int bytes);
 // Resident sweep-kernel CTAs per SM for a block size and dynamic shared memory.
-cudaError_t sweep_occupancy(int block, int smem_bytes, int* blocks_per_sm, bool slot_major = false);
+cudaError_t sweep_occupancy(int block, int smem_bytes, int* blocks_per_sm, bool slot_major = false,
+                            bool walk = false);
 cudaError_t launch_init(const InstDesc* insts, const int2* items, int nitems, bool draw,
                         cudaStream_t st);
 cudaError_t launch_energy(const InstDesc* insts, const int2* items, int nitems, int32_t first_value,
                           cudaStream_t st);
 // mode 0: nsweeps sweeps s = sweep0+1..; mode 1: one exchange sweep with counter sweep0.
 // slot_major: every bundle uses the slot-major mapping (Bundle::team > 0),
-// otherwise the cell-major one (Bundle::team == 0).
+// otherwise the cell-major one (Bundle::team == 0).  walk: the instances carry
+// walk arrays (InstDesc::whot, wtrips, wstate) and the launch updates them.
 cudaError_t launch_sweeps(const InstDesc* insts, const Bundle* bundles, int nbundles, int grid,
                           int block, int smem_bytes, uint32_t sweep0, int nsweeps, int xevery,
-                          int mode, int* queue, cudaStream_t st, bool slot_major = false);
+                          int mode, int* queue, cudaStream_t st, bool slot_major = false,
+                          bool walk = false);
 cudaError_t launch_tts(const InstDesc* insts, int ninst, int32_t target, int32_t horizon,
                        int32_t* out, cudaStream_t st);
 
