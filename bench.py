@@ -381,6 +381,61 @@ def run_batched(args):
     return 0
 
 
+def run_mixing(args):
+    """Temperature random walk (Sec. III.B): EMCS = 10 Metropolis sweeps + one
+    exchange pass, on the C_8 bench instance with 30 temperatures (beta
+    geometric in [0.1, 4]) and `mixing_runs` independent chains.  Reports the
+    sweep rate with the walk tracked and untracked, the paper's first mixing
+    criterion (the copy with the least hot-half time spends >= 20 % of the run
+    there) and round trips per copy; the round-trip time (sweeps per completed
+    cold -> hot -> cold trip) stands in for the mixing time in the second
+    criterion (run >= 20 tau)."""
+    import torch
+    import paper_1605_03607_gb300 as P
+    from paper_1605_03607_gb300 import build as B
+    B.build()
+    cfg = workload()
+    L, NT, R, X = cfg["L"], 30, args.mixing_runs, 10
+    n_sweeps = X * args.mixing_emcs
+    J = W.random_couplers(L, cfg["seed"], 0)
+    betas = W.beta_ladder(NT, cfg["beta_min"], cfg["beta_max"])
+    h = P.PTHandle(L, J, betas, R, cfg["seed"], 0)
+    if not args.no_autotune:
+        h.autotune(n_inst=1, trial_sweeps=64)
+    att = float(R) * NT * 8 * L * L * n_sweeps
+    rates = {}
+    sampler = ClockSampler(0)
+    sampler.start()
+    for walk in (False, True):
+        h.set_walk_stats(walk)
+        h.reset(0)
+        h.sweep(X * 64, X)                       # warm-up launches
+        h.reset(0)
+        h.set_timing(True)
+        h.sweep(n_sweeps, X)
+        ms, n = h.sweep_timing_total()
+        rates[walk] = att / (ms / 1e3)
+    clocks = sampler.stop()
+    hot, trips, passes = h.walk_stats()
+    frac = hot.astype(np.float64) / max(passes, 1)
+    mean_trips = float(trips.mean())
+    tau_rt = n_sweeps / mean_trips if mean_trips > 0 else None
+    print(json.dumps({
+        "workload": "mixing: C_8 N=512, 30 temps beta geometric [0.1,4], EMCS = 10 sweeps + 1 exchange",
+        "metric": "spin-flip attempts/s (walk tracked)", "value": rates[True], "unit": UNIT,
+        "untracked_attempts_per_s": rates[False], "tracking_cost": 1.0 - rates[True] / rates[False],
+        "chains": R, "emcs": args.mixing_emcs, "sweeps": n_sweeps, "exchange_passes": passes,
+        "schedule": list(h.schedule()), "team": h.mapping(),
+        "walk": {"min_hot_fraction": float(frac.min()), "median_hot_fraction": float(np.median(frac)),
+                 "criterion_hot_half": bool(frac.min() >= 0.2),
+                 "round_trips_per_copy_mean": mean_trips, "round_trips_min": int(trips.min()),
+                 "sweeps_per_round_trip": tau_rt,
+                 "criterion_20_tau": bool(tau_rt is not None and n_sweeps >= 20 * tau_rt)},
+        "clocks": clocks, "data": "synthetic"}))
+    h.close()
+    return 0
+
+
 def run_guided_experiment(args):
     """Surrogate-guided vs plain engineering at equal GPU time.
 
@@ -495,7 +550,9 @@ def run_profile_case(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="c8_single", choices=["c8_single", "batched_256", "guided"])
+    ap.add_argument("--workload", default="c8_single", choices=["c8_single", "batched_256", "guided", "mixing"])
+    ap.add_argument("--mixing-runs", type=int, default=1024, help="mixing workload: independent PT chains")
+    ap.add_argument("--mixing-emcs", type=int, default=1 << 14, help="mixing workload: EMCS per run")
     ap.add_argument("--guided-S", type=int, default=1 << 14)
     ap.add_argument("--guided-train-instances", type=int, default=24)
     ap.add_argument("--guided-train-steps", type=int, default=48)
@@ -529,6 +586,8 @@ def main():
         return run_profile_case(args)
     if args.workload == "batched_256":
         return run_batched(args)
+    if args.workload == "mixing":
+        return run_mixing(args)
     if args.workload == "guided":
         return run_guided_experiment(args)
     return run_gpu(args)

@@ -644,9 +644,12 @@ __device__ void process_bundle_sm(const InstDesc* __restrict__ insts, const Bund
 // SLOT_MAJOR selects the mapping of every bundle of the launch, WALK whether
 // the launch tracks the temperature random walk of every copy (separate
 // instantiations, so each keeps its own register allocation and the untracked
-// kernels carry no walk code).
+// kernels carry no walk code).  The slot-major walk kernel is bounded to the
+// untracked kernel's register count (896 threads: <= 72 registers), so
+// tracking keeps the same CTAs per SM; the host still caps slot-major CTAs
+// at 768 threads.
 template <bool SLOT_MAJOR, bool WALK>
-__global__ void __launch_bounds__(SLOT_MAJOR ? MAX_THREADS_SM : MAX_THREADS)
+__global__ void __launch_bounds__(SLOT_MAJOR ? (WALK ? 896 : MAX_THREADS_SM) : MAX_THREADS)
 pt_sweep_kernel(const InstDesc* __restrict__ insts, const Bundle* __restrict__ bundles,
                 int nbundles, uint32_t sweep0, int nsweeps, int xevery, int mode,
                 int* __restrict__ queue)
