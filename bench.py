@@ -436,6 +436,55 @@ def run_mixing(args):
     return 0
 
 
+def run_surrogate(args):
+    """Surrogate training step (config 4's shape): forward, backward and Adam on
+    a batch of 256 seeded C_8 instances with random log10-TTS targets.  Reports
+    steps/s, graphs/s and the GEMM rate of the step's linear maps against the
+    measured BF16 peak (the maps are K = 128 -> N = 64, HBM-bound; DRAM
+    throughput comes from the ncu summary)."""
+    import torch
+    import paper_1605_03607_gb300 as P
+    from paper_1605_03607_gb300 import build as B
+    B.build()
+    L, Bsz, H, layers = 8, 256, 64, 4
+    N, E = 8 * L * L, W.chimera_n_edges(L)
+    J = np.stack([W.random_couplers(L, 20160514, i) for i in range(Bsz)])
+    t = np.random.default_rng(20160514).uniform(1.0, 4.0, Bsz)
+    m = P.Surrogate(hidden=H, layers=layers)
+    m.set_params(W.surrogate_init_params(20160514, H, layers))
+    for _ in range(args.warmup):
+        m.train_step(L, J, t)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(0)
+    sampler.start()
+    w0 = time.perf_counter()
+    e0.record()
+    for _ in range(args.steps):
+        m.train_step(L, J, t)
+    e1.record()
+    e1.synchronize()
+    wall = time.perf_counter() - w0
+    clocks = sampler.stop()
+    # the step's own launches run on the library's stream; the host waits for
+    # each step's loss, so the wall clock bounds the device time
+    ms = wall * 1e3 / args.steps
+    flops = 3.0 * layers * 2.0 * 2 * H * H * Bsz * (3 * E + N)     # fwd + dX + dW of the 3 maps per layer
+    peaks, kind = load_peaks()
+    achieved = flops / (ms / 1e3) / 1e12
+    print(json.dumps({
+        "workload": f"surrogate train step: {Bsz} C_8 graphs (N={N}, E={E}), hidden {H}, {layers} layers",
+        "metric": "surrogate training steps/s", "value": 1e3 / ms, "unit": "steps/s",
+        "graphs_per_s": Bsz * 1e3 / ms, "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
+        "dtype": "bf16 (fp32 accumulate)",
+        "tensor": {"gemm_tflops": achieved, "peak": float(peaks.get("bf16_tflops", 1900.0)),
+                   "frac": achieved / float(peaks.get("bf16_tflops", 1900.0)), "flops_per_step": flops,
+                   "peak_source": kind},
+        "clocks": clocks, "data": "synthetic"}))
+    m.close()
+    return 0
+
+
 def run_guided_experiment(args):
     """Surrogate-guided vs plain engineering at equal GPU time.
 
@@ -550,7 +599,8 @@ def run_profile_case(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="c8_single", choices=["c8_single", "batched_256", "guided", "mixing"])
+    ap.add_argument("--workload", default="c8_single", choices=["c8_single", "batched_256", "guided", "mixing",
+                                                                      "surrogate"])
     ap.add_argument("--mixing-runs", type=int, default=1024, help="mixing workload: independent PT chains")
     ap.add_argument("--mixing-emcs", type=int, default=1 << 14, help="mixing workload: EMCS per run")
     ap.add_argument("--guided-S", type=int, default=1 << 14)
@@ -588,6 +638,8 @@ def main():
         return run_batched(args)
     if args.workload == "mixing":
         return run_mixing(args)
+    if args.workload == "surrogate":
+        return run_surrogate(args)
     if args.workload == "guided":
         return run_guided_experiment(args)
     return run_gpu(args)

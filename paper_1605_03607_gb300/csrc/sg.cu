@@ -131,9 +131,14 @@ __global__ void __launch_bounds__(256) lin_fwd_kernel(int rows, RowSrc src, cons
 }
 
 // ------------------------------------------------ backward: dX = dZ . W
-// dZ [rows][64] BF16; W^T staged as [128][64]; dX [rows][128] FP32.
+// dZ [rows][64] BF16; W^T staged as [128][64].  EPI 0: dX [rows][128] FP32.
+// EPI 1 (the node and edge updates, whose input halves have separate
+// gradients): out0 = base + dX[:, :64] (base may be out0 or NULL) and
+// out1 = dX[:, 64:], both [rows][64] FP32, without materialising dX.
+template <int EPI>
 __global__ void __launch_bounds__(256) lin_bwd_input_kernel(int rows, const bf16* __restrict__ dZ,
-                                                            const bf16* __restrict__ W, float* __restrict__ dX)
+                                                            const bf16* __restrict__ W, float* __restrict__ dX,
+                                                            const float* base, float* out0, float* __restrict__ out1)
 {
     __shared__ uint32_t WT[KIN][HD / 2 + 4];
     for (int i = threadIdx.x; i < KIN * HD / 2; i += blockDim.x) {
@@ -167,74 +172,149 @@ __global__ void __launch_bounds__(256) lin_bwd_input_kernel(int rows, const bf16
 #pragma unroll
         for (int n = 0; n < 16; ++n) {
             const int c = n * 8 + 2 * t;
-            if (va) reinterpret_cast<float2*>(dX + (size_t)ra * KIN)[c / 2] = make_float2(acc[n][0], acc[n][1]);
-            if (vb) reinterpret_cast<float2*>(dX + (size_t)rb * KIN)[c / 2] = make_float2(acc[n][2], acc[n][3]);
+            if (EPI == 0) {
+                if (va) reinterpret_cast<float2*>(dX + (size_t)ra * KIN)[c / 2] = make_float2(acc[n][0], acc[n][1]);
+                if (vb) reinterpret_cast<float2*>(dX + (size_t)rb * KIN)[c / 2] = make_float2(acc[n][2], acc[n][3]);
+            } else if (n < 8) {
+#pragma unroll
+                for (int hh = 0; hh < 2; ++hh) {
+                    const int r = hh ? rb : ra;
+                    if (!(hh ? vb : va)) continue;
+                    float2 v = make_float2(acc[n][2 * hh], acc[n][2 * hh + 1]);
+                    if (base) {
+                        const float2 b = reinterpret_cast<const float2*>(base + (size_t)r * HD)[c / 2];
+                        v.x = b.x + v.x;
+                        v.y = b.y + v.y;
+                    }
+                    reinterpret_cast<float2*>(out0 + (size_t)r * HD)[c / 2] = v;
+                }
+            } else {
+                if (va) reinterpret_cast<float2*>(out1 + (size_t)ra * HD)[c / 2 - HD / 2] = make_float2(acc[n][0], acc[n][1]);
+                if (vb) reinterpret_cast<float2*>(out1 + (size_t)rb * HD)[c / 2 - HD / 2] = make_float2(acc[n][2], acc[n][3]);
+            }
         }
     }
 }
 
-// ------------------------------------- backward: dW += dZ^T X, db += sum dZ
-// Each block walks a contiguous range of rows in chunks of 32, staging dZ^T
-// [64][32] and X^T [128][32] in shared memory; warp w owns output rows
-// 16*(w/2)..+16 and columns 64*(w%2)..+64 (8 n-tiles), accumulated in
-// registers and added to the FP32 gradient once per block.
-__global__ void __launch_bounds__(256) lin_bwd_weight_kernel(int rows, int rows_per_block, const bf16* __restrict__ dZ,
-                                                             RowSrc src, float* __restrict__ dW, float* __restrict__ db)
+// ------------------------------- backward: dW = dZ^T . X, db = column sums of dZ
+// Persistent blocks take 64-row chunks c = blockIdx.x, c += gridDim.x.  A
+// chunk is staged row-major with 16-byte loads (dZ [64][64], X [64][128] from
+// its two gathered halves), the next chunk's loads are issued into registers
+// before the current chunk's MMAs, and ldmatrix.trans transposes the 8x8
+// sub-tiles on their way into the mma.sync fragments (A = dZ^T, B = X).
+// Warp w accumulates output rows 16*(w/2)..+16 and columns 64*(w%2)..+64;
+// the even warps also sum their rows of dZ (one extra MMA against ones).
+// Each block writes its partial [64][128] + [64] to `part`, and
+// lin_wgrad_reduce adds all blocks' partials into dW and db in a fixed order.
+constexpr int WCH = 64;                  // rows per chunk
+constexpr int ZP = HD + 8;               // shared row pitches (bf16): 16 bytes of padding
+constexpr int XP = KIN + 8;              // make every ldmatrix phase conflict-free
+constexpr int WPART = HD * KIN + HD;     // floats of one block's partial
+
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3, const void* p)
 {
-    constexpr int CH = 32;
-    __shared__ bf16 Zt[HD][CH + 8];
-    __shared__ bf16 Xt[KIN][CH + 8];
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3, w = threadIdx.x >> 5;
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(a));
+}
+
+struct WChunk {                          // one thread's share of a chunk: 2 + 4 16-byte words
+    uint4 z[2], x[4];
+};
+
+__device__ __forceinline__ void wgrad_load(WChunk& v, int rows, int r0, const bf16* __restrict__ dZ,
+                                           const RowSrc& src)
+{
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const int i = threadIdx.x + j * 256, rr = i >> 3, q = i & 7, r = r0 + rr;
+        v.z[j] = r < rows ? reinterpret_cast<const uint4*>(dZ + (size_t)r * HD)[q] : make_uint4(0u, 0u, 0u, 0u);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int i = threadIdx.x + j * 256, rr = i >> 4, seg = i & 15, r = r0 + rr;
+        v.x[j] = r < rows ? reinterpret_cast<const uint4*>(src.half(r, seg >> 3))[seg & 7] : make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
+__global__ void __launch_bounds__(256, 2) lin_wgrad_kernel(int rows, const bf16* __restrict__ dZ, RowSrc src,
+                                                           float* __restrict__ part)
+{
+    __shared__ __align__(16) bf16 Zs[WCH][ZP];
+    __shared__ __align__(16) bf16 Xs[WCH][XP];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+    const int lr = lane & 7, lq = lane >> 3;          // ldmatrix: row inside an 8x8 tile, tile index
     const int mrow = (w >> 1) * 16, ncol = (w & 1) * 64;
-    float acc[8][4];
+    const uint32_t ones = 0x3F803F80u;                // two bf16 1.0
+    float acc[8][4], accb[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int n = 0; n < 8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-    float dbl = 0.f;
-    const int r_begin = blockIdx.x * rows_per_block;
-    const int r_end = min(rows, r_begin + rows_per_block);
-    for (int r0 = r_begin; r0 < r_end; r0 += CH) {
-        __syncthreads();
-        // stage: 256 threads; dZ^T needs 64 x 32, X^T needs 128 x 32 values
-        for (int i = threadIdx.x; i < CH * HD; i += blockDim.x) {
-            const int rr = i / HD, c = i % HD, r = r0 + rr;
-            Zt[c][rr] = r < r_end ? dZ[(size_t)r * HD + c] : __float2bfloat16_rn(0.f);
+    const int nchunks = (rows + WCH - 1) / WCH;
+    WChunk v;
+    int c = blockIdx.x;
+    if (c < nchunks) wgrad_load(v, rows, c * WCH, dZ, src);
+    for (; c < nchunks; c += gridDim.x) {
+        __syncthreads();                              // the previous chunk's MMAs are done
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int i = threadIdx.x + j * 256;
+            *reinterpret_cast<uint4*>(&Zs[i >> 3][(i & 7) * 8]) = v.z[j];
         }
-        for (int i = threadIdx.x; i < CH * KIN / 2; i += blockDim.x) {
-            const int rr = i / (KIN / 2), cw = i % (KIN / 2), r = r0 + rr;
-            uint32_t v = 0u;
-            if (r < r_end) v = src.half(r, cw >= HD / 2)[cw % (HD / 2)];
-            const __nv_bfloat162 p = *reinterpret_cast<__nv_bfloat162*>(&v);
-            Xt[2 * cw][rr] = p.x;
-            Xt[2 * cw + 1][rr] = p.y;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int i = threadIdx.x + j * 256;
+            *reinterpret_cast<uint4*>(&Xs[i >> 4][(i & 15) * 8]) = v.x[j];
         }
         __syncthreads();
-        if (threadIdx.x < HD)
-            for (int rr = 0; rr < CH; ++rr) dbl += __bfloat162float(Zt[threadIdx.x][rr]);
+        if (c + (int)gridDim.x < nchunks) wgrad_load(v, rows, (c + gridDim.x) * WCH, dZ, src);
 #pragma unroll
-        for (int ks = 0; ks < CH / 16; ++ks) {
-            const int k0 = ks * 16 + 2 * t;
-            const uint32_t a0 = *reinterpret_cast<const uint32_t*>(&Zt[mrow + g][k0]);
-            const uint32_t a1 = *reinterpret_cast<const uint32_t*>(&Zt[mrow + g + 8][k0]);
-            const uint32_t a2 = *reinterpret_cast<const uint32_t*>(&Zt[mrow + g][k0 + 8]);
-            const uint32_t a3 = *reinterpret_cast<const uint32_t*>(&Zt[mrow + g + 8][k0 + 8]);
+        for (int ks = 0; ks < WCH / 16; ++ks) {
+            const int k0 = ks * 16;
+            uint32_t a0, a1, a2, a3;                  // (m0-7,k0-7) (m8-15,k0-7) (m0-7,k8-15) (m8-15,k8-15)
+            ldsm_x4_trans(a0, a1, a2, a3, &Zs[k0 + (lq >> 1) * 8 + lr][mrow + (lq & 1) * 8]);
+            if ((w & 1) == 0) mma_bf16(accb, a0, a1, a2, a3, ones, ones);
 #pragma unroll
-            for (int n = 0; n < 8; ++n) {
-                const int col = ncol + n * 8 + g;
-                const uint32_t b0 = *reinterpret_cast<const uint32_t*>(&Xt[col][k0]);
-                const uint32_t b1 = *reinterpret_cast<const uint32_t*>(&Xt[col][k0 + 8]);
-                mma_bf16(acc[n], a0, a1, a2, a3, b0, b1);
+            for (int np = 0; np < 4; ++np) {          // n-tiles n0 and n0 + 8
+                const int n0 = ncol + np * 16;
+                uint32_t b0, b1, b2, b3;              // (k0-7,n0) (k8-15,n0) (k0-7,n0+8) (k8-15,n0+8)
+                ldsm_x4_trans(b0, b1, b2, b3, &Xs[k0 + (lq & 1) * 8 + lr][n0 + (lq >> 1) * 8]);
+                mma_bf16(acc[2 * np], a0, a1, a2, a3, b0, b1);
+                mma_bf16(acc[2 * np + 1], a0, a1, a2, a3, b2, b3);
             }
         }
     }
+    float* P = part + (size_t)blockIdx.x * WPART;
 #pragma unroll
     for (int n = 0; n < 8; ++n) {
-        const int c = ncol + n * 8 + 2 * t;
-        atomicAdd(&dW[(mrow + g) * KIN + c], acc[n][0]);
-        atomicAdd(&dW[(mrow + g) * KIN + c + 1], acc[n][1]);
-        atomicAdd(&dW[(mrow + g + 8) * KIN + c], acc[n][2]);
-        atomicAdd(&dW[(mrow + g + 8) * KIN + c + 1], acc[n][3]);
+        const int col = ncol + n * 8 + 2 * t;
+        *reinterpret_cast<float2*>(&P[(mrow + g) * KIN + col]) = make_float2(acc[n][0], acc[n][1]);
+        *reinterpret_cast<float2*>(&P[(mrow + g + 8) * KIN + col]) = make_float2(acc[n][2], acc[n][3]);
     }
-    if (threadIdx.x < HD) atomicAdd(&db[threadIdx.x], dbl);
+    if ((w & 1) == 0 && t == 0) {                     // every column of the ones tile is the row sum
+        P[HD * KIN + mrow + g] = accb[0];
+        P[HD * KIN + mrow + g + 8] = accb[2];
+    }
+}
+
+// dW += sum over blocks of the partials (and db likewise), blocks in order.
+__global__ void lin_wgrad_reduce(int nblocks, const float* __restrict__ part, float* __restrict__ dW,
+                                 float* __restrict__ db)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= WPART) return;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+    int b = 0;
+    for (; b + 4 <= nblocks; b += 4) {
+        s0 += part[(size_t)b * WPART + i];
+        s1 += part[(size_t)(b + 1) * WPART + i];
+        s2 += part[(size_t)(b + 2) * WPART + i];
+        s3 += part[(size_t)(b + 3) * WPART + i];
+    }
+    for (; b < nblocks; ++b) s0 += part[(size_t)b * WPART + i];
+    const float s = (s0 + s1) + (s2 + s3);
+    if (i < HD * KIN) dW[i] += s;
+    else db[i - HD * KIN] += s;
 }
 
 // ------------------------------------------------------- elementwise kernels
@@ -306,17 +386,6 @@ __global__ void relu_mask_kernel(int rows, const float* __restrict__ G, const in
         const float2 gv = reinterpret_cast<const float2*>(G + gr * HD)[cp];
         const float2 z = unpack_bf2(reinterpret_cast<const uint32_t*>(Z + (size_t)r * HD)[cp]);
         reinterpret_cast<uint32_t*>(dZ + (size_t)r * HD)[cp] = pack_bf2(z.x > 0.f ? gv.x : 0.f, z.y > 0.f ? gv.y : 0.f);
-    }
-}
-
-// out[row] = base[row] + dX[row][off .. off+63]  (base may alias out)
-__global__ void add_half_kernel(size_t rows, const float* base, const float* __restrict__ dX, int off, float* out)
-{
-    const size_t total = rows * HD;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t r = i / HD;
-        const int c = (int)(i % HD);
-        out[i] = (base ? base[i] : 0.f) + dX[r * KIN + off + c];
     }
 }
 
@@ -467,6 +536,8 @@ struct sg_model {
     std::vector<bf16*> h, e, m, s, zm, zu, ze;
     float *R = nullptr, *dX = nullptr, *dh = nullptr, *dh2 = nullptr, *de = nullptr, *dm = nullptr, *ds = nullptr;
     bf16* dZ = nullptr;
+    float* wpart = nullptr;       // weight-gradient partials, one WPART block per persistent CTA
+    int wblocks = 0;              // persistent CTAs of the weight-gradient kernel
     uint64_t launches = 0;
     std::string err = "no error";
 };
@@ -503,6 +574,7 @@ void free_graph(sg_model* M)
     float** fl[] = {&M->d_t, &M->d_y, &M->d_g, &M->d_z, &M->R, &M->dX, &M->dh, &M->dh2, &M->de, &M->dm, &M->ds};
     for (float** p : fl) { cudaFree(*p); *p = nullptr; }
     cudaFree(M->dZ); M->dZ = nullptr;
+    cudaFree(M->wpart); M->wpart = nullptr;
     for (auto* v : {&M->h, &M->e, &M->m, &M->s, &M->zm, &M->zu, &M->ze}) {
         for (bf16* p : *v) cudaFree(p);
         v->clear();
@@ -589,6 +661,13 @@ int prepare(sg_model* M, int L, int B)
     SK(salloc(&M->R, nM * HD), "cudaMalloc R");
     SK(salloc(&M->dX, nM * KIN), "cudaMalloc dX");
     SK(salloc(&M->dZ, nM * HD), "cudaMalloc dZ");
+    {
+        int dev = 0, sms = 0;
+        SK(cudaGetDevice(&dev), "cudaGetDevice");
+        SK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device attribute");
+        M->wblocks = 2 * sms;                 // two resident CTAs per SM (launch bounds)
+        SK(salloc(&M->wpart, (size_t)M->wblocks * WPART), "cudaMalloc wpart");
+    }
     SK(salloc(&M->dh, nN * HD), "cudaMalloc dh");
     SK(salloc(&M->dh2, nN * HD), "cudaMalloc dh2");
     SK(salloc(&M->dm, nN * HD), "cudaMalloc dm");
@@ -610,6 +689,15 @@ int lin_grid(int rows)
     const int tiles = (rows + 15) / 16;
     const int g = (tiles + 7) / 8;
     return g > 4096 ? 4096 : (g < 1 ? 1 : g);
+}
+
+// dW += dZ^T X, db += column sums of dZ over `rows` rows (two launches).
+void lin_wgrad(sg_model* M, int rows, const RowSrc& src, float* dW, float* db)
+{
+    const int nchunks = (rows + WCH - 1) / WCH;
+    const int grid = nchunks < M->wblocks ? (nchunks > 0 ? nchunks : 1) : M->wblocks;
+    lin_wgrad_kernel<<<grid, 256, 0, M->stream>>>(rows, M->dZ, src, M->wpart);
+    lin_wgrad_reduce<<<(WPART + 255) / 256, 256, 0, M->stream>>>(grid, M->wpart, dW, db);
 }
 
 int forward(sg_model* M, int B, bool train)
@@ -657,29 +745,29 @@ int backward_all(sg_model* M, int B)
     for (int l = M->layers - 1; l >= 0; --l) {
         // edge update: e' = e + relu(ze), ze = We [e | s] + be
         relu_mask_kernel<<<grid_for(nE * HD / 2), 256, 0, st>>>(B * E, M->de, nullptr, 1, 1, M->ze[l], M->dZ);
-        lin_bwd_input_kernel<<<lin_grid(B * E), 256, 0, st>>>(B * E, M->dZ, W + M->oWe[l], M->dX);
+        // de += dX[:, :64] (into e), ds = dX[:, 64:]
+        lin_bwd_input_kernel<1><<<lin_grid(B * E), 256, 0, st>>>(B * E, M->dZ, W + M->oWe[l], nullptr, M->de,
+                                                                 M->de, M->ds);
         const RowSrc es = rows_of(M->e[l], M->d_iden, E, M->s[l], M->d_iden, E, E);
-        lin_bwd_weight_kernel<<<(B * E + 1023) / 1024, 256, 0, st>>>(B * E, 1024, M->dZ, es, G + M->oWe[l], G + M->obe[l]);
-        add_half_kernel<<<grid_for(nE * HD), 256, 0, st>>>(nE, M->de, M->dX, 0, M->de);         // de (into e)
-        add_half_kernel<<<grid_for(nE * HD), 256, 0, st>>>(nE, nullptr, M->dX, HD, M->ds);      // ds
+        lin_wgrad(M, B * E, es, G + M->oWe[l], G + M->obe[l]);
         SK(cudaMemcpyAsync(M->dh2, M->dh, sizeof(float) * nN * HD, cudaMemcpyDeviceToDevice, st), "copy dh");
         gather_add_kernel<<<grid_for(nN * HD), 256, 0, st>>>(B, N, E, M->d_inc, M->ds, HD, 0, M->dh2);
         // node update: h' = h + relu(zu), zu = Wu [h | m] + bu
         relu_mask_kernel<<<grid_for(nN * HD / 2), 256, 0, st>>>(B * N, M->dh2, nullptr, 1, 1, M->zu[l], M->dZ);
-        lin_bwd_input_kernel<<<lin_grid(B * N), 256, 0, st>>>(B * N, M->dZ, W + M->oWu[l], M->dX);
+        // dh = dh2 + dX[:, :64] (into h), dm = dX[:, 64:]
+        lin_bwd_input_kernel<1><<<lin_grid(B * N), 256, 0, st>>>(B * N, M->dZ, W + M->oWu[l], nullptr, M->dh2,
+                                                                 M->dh, M->dm);
         const RowSrc ns = rows_of(M->h[l], M->d_iden, N, M->m[l], M->d_iden, N, N);
-        lin_bwd_weight_kernel<<<(B * N + 1023) / 1024, 256, 0, st>>>(B * N, 1024, M->dZ, ns, G + M->oWu[l], G + M->obu[l]);
-        add_half_kernel<<<grid_for(nN * HD), 256, 0, st>>>(nN, M->dh2, M->dX, 0, M->dh);        // dh (into h)
-        add_half_kernel<<<grid_for(nN * HD), 256, 0, st>>>(nN, nullptr, M->dX, HD, M->dm);      // dm
+        lin_wgrad(M, B * N, ns, G + M->oWu[l], G + M->obu[l]);
         // messages: m_i = sum relu(zm) over rows into i
         relu_mask_kernel<<<grid_for(nE * 2 * HD / 2), 256, 0, st>>>(B * 2 * E, M->dm, M->d_tgt, 2 * E, N, M->zm[l], M->dZ);
-        lin_bwd_input_kernel<<<lin_grid(B * 2 * E), 256, 0, st>>>(B * 2 * E, M->dZ, W + M->oWm[l], M->dX);
+        lin_bwd_input_kernel<0><<<lin_grid(B * 2 * E), 256, 0, st>>>(B * 2 * E, M->dZ, W + M->oWm[l], M->dX,
+                                                                     nullptr, nullptr, nullptr);
         const RowSrc ms = rows_of(M->h[l], M->d_src, N, M->e[l], M->d_eid, E, 2 * E);
-        lin_bwd_weight_kernel<<<(B * 2 * E + 1023) / 1024, 256, 0, st>>>(B * 2 * E, 1024, M->dZ, ms, G + M->oWm[l],
-                                                                         G + M->obm[l]);
+        lin_wgrad(M, B * 2 * E, ms, G + M->oWm[l], G + M->obm[l]);
         gather_add_kernel<<<grid_for(nN * HD), 256, 0, st>>>(B, N, 2 * E, M->d_out_rows, M->dX, KIN, 0, M->dh);
         edge_from_messages_kernel<<<grid_for(nE * HD), 256, 0, st>>>(B, E, M->dX, M->de);
-        M->launches += 16;
+        M->launches += 15;
     }
     embed_bwd_kernel<<<256, 256, 0, st>>>(B, N, E, M->d_u, M->d_J, M->dh, M->de, G + M->oX, G + M->oJ);
     M->launches++;
