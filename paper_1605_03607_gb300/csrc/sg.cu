@@ -130,8 +130,18 @@ __global__ void __launch_bounds__(256) lin_fwd_kernel(int rows, RowSrc src, cons
     }
 }
 
+__device__ __forceinline__ void ldsm_x4(uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3, const void* p)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(a));
+}
+
 // ------------------------------------------------ backward: dX = dZ . W
-// dZ [rows][64] BF16; W^T staged as [128][64].  EPI 0: dX [rows][128] FP32.
+// dZ [rows][64] BF16, each warp's 16-row tile staged in shared memory with
+// 16-byte loads and read by ldmatrix; W^T staged as [128][64].  Launched
+// with 256 threads (8 warps).  EPI 0: dX [rows][128] FP32.
 // EPI 1 (the node and edge updates, whose input halves have separate
 // gradients): out0 = base + dX[:, :64] (base may be out0 or NULL) and
 // out1 = dX[:, 64:], both [rows][64] FP32, without materialising dX.
@@ -149,26 +159,34 @@ __global__ void __launch_bounds__(256) lin_bwd_input_kernel(int rows, const bf16
         WT[in][op] = *reinterpret_cast<uint32_t*>(&v);
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    __shared__ __align__(16) bf16 Zs[8][16][HD + 8];
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3, w = threadIdx.x >> 5;
+    const int lr = lane & 7, lq = lane >> 3;
+    bf16 (*Zt)[HD + 8] = Zs[w];
     const int warps = blockDim.x >> 5;
     const int ntiles = (rows + 15) / 16;
-    for (int tile = blockIdx.x * warps + (threadIdx.x >> 5); tile < ntiles; tile += gridDim.x * warps) {
+    for (int tile = blockIdx.x * warps + w; tile < ntiles; tile += gridDim.x * warps) {
         const int ra = tile * 16 + g, rb = ra + 8;
         const bool va = ra < rows, vb = rb < rows;
-        const uint32_t* za = reinterpret_cast<const uint32_t*>(dZ + (size_t)(va ? ra : 0) * HD);
-        const uint32_t* zb = reinterpret_cast<const uint32_t*>(dZ + (size_t)(vb ? rb : 0) * HD);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {                 // 16 rows x 8 16-byte words of dZ
+            const int i = lane + 32 * j, rr = i >> 3, q = i & 7, r = tile * 16 + rr;
+            const uint4 v = r < rows ? reinterpret_cast<const uint4*>(dZ + (size_t)r * HD)[q] : make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4*>(&Zt[rr][q * 8]) = v;
+        }
+        __syncwarp();
         float acc[16][4];
 #pragma unroll
         for (int n = 0; n < 16; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
 #pragma unroll
         for (int ks = 0; ks < 4; ++ks) {
-            const int cw = ks * 8 + t;
-            const uint32_t a0 = va ? za[cw] : 0u, a2 = va ? za[cw + 4] : 0u;
-            const uint32_t a1 = vb ? zb[cw] : 0u, a3 = vb ? zb[cw + 4] : 0u;
+            uint32_t a0, a1, a2, a3;
+            ldsm_x4(a0, a1, a2, a3, &Zt[(lq & 1) * 8 + lr][ks * 16 + (lq >> 1) * 8]);
 #pragma unroll
             for (int n = 0; n < 16; ++n)
                 mma_bf16(acc[n], a0, a1, a2, a3, WT[n * 8 + g][ks * 8 + t], WT[n * 8 + g][ks * 8 + 4 + t]);
         }
+        __syncwarp();                                 // the tile is read before it is restaged
 #pragma unroll
         for (int n = 0; n < 16; ++n) {
             const int c = n * 8 + 2 * t;
