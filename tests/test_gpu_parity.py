@@ -297,15 +297,20 @@ def test_zero_sweeps_and_single_run(P):
     assert h.tts() == ref.tts()
 
 
-def test_single_instance_config_launch_shape(P):
-    """C_8, 32 temperatures in [0.1, 4], 64 runs in bench's launch configuration:
-    a prefix compared element by element, then a full 4x pass checked through
-    properties that hold at any length."""
+@pytest.mark.parametrize("mapping", [None, (4, 32, 1)])
+def test_single_instance_config_launch_shape(P, mapping):
+    """C_8, 32 temperatures in [0.1, 4], 64 runs, with the default schedule and
+    with the one the bench's autotuner picks (slot-major, team 4, 32 teams, one
+    run per CTA, 4096 sweeps per launch): a prefix compared element by element,
+    then a full 4x pass checked through properties that hold at any length."""
     cfg = W.CONFIGS["c8_single"]
     L, NT, R = cfg["L"], cfg["n_temps"], cfg["n_runs"]
     J = W.random_couplers(L, cfg["seed"], 0)
     betas = W.beta_ladder(NT, cfg["beta_min"], cfg["beta_max"])
     h = P.PTHandle(L, J, betas, R, cfg["seed"], 0)
+    if mapping:
+        h.set_mapping(*mapping)
+        h.set_schedule(0, 0, 4096)
     ref = oracle.PTState(L, J, betas, R, cfg["seed"], 0)
     h.sweep(96, 1)
     ref.sweeps(96, 1)
