@@ -529,9 +529,11 @@ def run_guided_experiment(args):
        `--guided-train-instances` C_8 seed instances, every evaluated candidate
        kept as (couplers, log10 TTS).
     2. Training: the GPU surrogate, minibatch 256, Adam lr 1e-3, 20 epochs.
-    3. From one fresh C_8 instance: plain loop, guided loop (64 proposals,
-       top 16 PT-evaluated) with the trained network, and the same guided loop
-       with an untrained network, each for `--guided-seconds` of GPU time.
+    3. From each of `--guided-test-instances` fresh C_8 instances: plain loop,
+       guided loop (64 proposals, top 16 PT-evaluated) with the trained
+       network, and the same guided loop with an untrained network, each for
+       `--guided-seconds` of GPU time; per-arm mean and standard error, and
+       the paired differences.
     """
     import paper_1605_03607_gb300 as P
     from paper_1605_03607_gb300 import build as B
@@ -565,22 +567,36 @@ def run_guided_experiment(args):
 
     untrained = P.Surrogate()
     untrained.set_params(W.surrogate_init_params(1))
-    test_uid = 999
-    Jt = W.random_couplers(L, seed, test_uid)
     out = {}
     Sc = args.guided_cmp_S
-    for name in ("plain", "guided", "guided_untrained"):
-        with P.PTHandle(L, Jt, betas, R, seed, test_uid) as h:
-            h.engineer_begin(S=Sc, pass_mult=pm, exchange_every=1, base_uid=test_uid)
-            if name == "plain":
-                tr_ = G.run_plain(h, args.guided_seconds, speculation=16)
-            else:
-                tr_ = G.run_guided(h, model if name == "guided" else untrained, args.guided_seconds,
-                                   n_prop=64, top=16)
-            out[name] = {"gain_log10_tts_per_gpu_s": G.gain_per_second(tr_, cap=Sc + 1),
-                         "tts_initial": int(tr_[0][1]), "tts_final": int(tr_[-1][1]), "gpu_s": tr_[-1][0],
-                         "steps": tr_[-1][2],
-                         "trace": [(round(t, 2), int(v)) for t, v, _ in tr_[:: max(1, len(tr_) // 12)]]}
+    arms = ("plain", "guided", "guided_untrained")
+    per_inst = {a: [] for a in arms}
+    for k in range(args.guided_test_instances):
+        test_uid = 999 + k
+        Jt = W.random_couplers(L, seed, test_uid)
+        for name in arms:
+            with P.PTHandle(L, Jt, betas, R, seed, test_uid) as h:
+                h.engineer_begin(S=Sc, pass_mult=pm, exchange_every=1, base_uid=test_uid)
+                if name == "plain":
+                    tr_ = G.run_plain(h, args.guided_seconds, speculation=16)
+                else:
+                    tr_ = G.run_guided(h, model if name == "guided" else untrained, args.guided_seconds,
+                                       n_prop=64, top=16)
+                gain = G.gain_per_second(tr_, cap=Sc + 1)
+                per_inst[name].append(gain)
+                out.setdefault(name, {"instances": []})["instances"].append(
+                    {"uid": test_uid, "gain_log10_tts_per_gpu_s": gain, "tts_initial": int(tr_[0][1]),
+                     "tts_final": int(tr_[-1][1]), "gpu_s": tr_[-1][0], "steps": tr_[-1][2],
+                     "trace": [(round(t, 2), int(v)) for t, v, _ in tr_[:: max(1, len(tr_) // 8)]]})
+
+    def mean_se(v):
+        v = np.asarray(v, np.float64)
+        return float(v.mean()), (float(v.std(ddof=1) / np.sqrt(len(v))) if len(v) > 1 else None)
+
+    for name in arms:
+        out[name]["gain_mean"], out[name]["gain_se"] = mean_se(per_inst[name])
+    d_sp = np.asarray(per_inst["guided"]) - np.asarray(per_inst["plain"])
+    d_tu = np.asarray(per_inst["guided"]) - np.asarray(per_inst["guided_untrained"])
     print(json.dumps({
         "workload": "guided_vs_plain", "metric": "log-TTS gain per GPU-s, surrogate vs plain",
         "config": {"instance": "C_8, 32 temps beta [0.1,4], 64 runs", "S_train": S, "S_compare": Sc,
@@ -592,9 +608,9 @@ def run_guided_experiment(args):
                      "data_s": t_data, "train_s": t_train,
                      "unsolved_fraction": float(np.mean(tts > S))},
         "loops": out,
-        "surrogate_over_plain": out["guided"]["gain_log10_tts_per_gpu_s"] - out["plain"]["gain_log10_tts_per_gpu_s"],
-        "trained_over_untrained": out["guided"]["gain_log10_tts_per_gpu_s"] -
-                                  out["guided_untrained"]["gain_log10_tts_per_gpu_s"]}))
+        "surrogate_over_plain": dict(zip(("mean", "se"), mean_se(d_sp))),
+        "trained_over_untrained": dict(zip(("mean", "se"), mean_se(d_tu))),
+        "test_instances": args.guided_test_instances}))
     return 0
 
 
@@ -645,6 +661,7 @@ def main():
     ap.add_argument("--guided-train-steps", type=int, default=48)
     ap.add_argument("--guided-seconds", type=float, default=60.0)
     ap.add_argument("--guided-cmp-S", type=int, default=1 << 15)
+    ap.add_argument("--guided-test-instances", type=int, default=3)
     ap.add_argument("--batch-sweeps", type=int, default=1 << 14)
     ap.add_argument("--batch-mapping", default="",
                     help="batched workload: 'L:team,slot_parallel,runs_per_cta;...' instead of the autotuner")
