@@ -205,6 +205,61 @@ int engineer_run(pt_handle *h, uint32_t step0, int32_t n_steps, int32_t speculat
 /* Current loop state: TTS of the current couplers. */
 int engineer_current_tts(const pt_handle *h, int32_t *tts);
 
+/* ---------------------------------------------------------------------
+ * Planted-solution instances and loop adaptive optimisation (Sec. IV,
+ * Algorithm 2).  An instance is a sum of frustrated loops along Chimera
+ * edges, each with the planted configuration as a ground state, so the
+ * planted configuration is a ground state of the sum and its energy
+ * E_GS = sum over loops of -w (len - 2) is known: PT-TTS evaluations use it
+ * as the target (one pass of S sweeps).  Loops: simple cycles of length 4
+ * (probability 0.1) or 6, weight w uniform in 1..w_max (w_max <= 3), every
+ * edge satisfied by the planted state except one; couplers of overlapping
+ * loops add, and a draw that would take a coupler outside [-3, 3] is
+ * redrawn.  Random draws: Philox kind 4 with key (seed, uid); the counters
+ * are documented with lao_plant below.
+ * --------------------------------------------------------------------- */
+#define PT_LOOP_WORDS 9   /* loop record: len, w, frustrated position, edges[6] (-1 unused) */
+
+typedef struct {
+    int32_t removed;              /* index of the loop taken out */
+    int32_t loop[PT_LOOP_WORDS];  /* the loop put in */
+    int32_t E_gs_new;             /* the candidate's ground-state energy */
+    int32_t tts_old, tts_new, accepted;
+    uint32_t cand_uid;            /* the candidate's PT key */
+} pt_lao_result;
+
+/* Host-only (no GPU work): the planted state s (N = 8 L^2 values +-1; spin
+ * i from counter (0, 0xFFFFFFF0, i>>2, 4), word i&3, -1 if its top bit is
+ * set), n_loops loop records ([n_loops][PT_LOOP_WORDS]) placed one by one
+ * (loop m: counters (0, m, a<<2 | j>>2, 4) for attempt a, words j: j0 of
+ * attempt 0 the length, j1 the start vertex, j2.. the walk in ascending
+ * neighbour order, j8 the weight, j9 the frustrated position), the summed
+ * couplers J (n_edges, the order of pt_create) and E_GS.  PT_ERR_ARG for
+ * bad sizes, PT_ERR_STATE if no admissible loop is found in 2^16 attempts. */
+int lao_plant(int32_t chimera_L, uint32_t seed, uint32_t uid, int32_t n_loops, int32_t w_max,
+              int8_t *planted, int32_t *loops, int8_t *J, int32_t *E_gs);
+
+/* Replaces the handle's couplers by the planted instance (seed = the
+ * handle's seed) and evaluates its TTS against E_GS (rule: S, exchange_every,
+ * direction, beta_rao; pass_mult is ignored) with PT key w2 of counter
+ * (0, 0xFFFFFFFE, 0, 4).  The handle is then in LAO mode (engineer_begin
+ * switches it back). */
+int lao_begin(pt_handle *h, const pt_rule *rule, uint32_t uid, int32_t n_loops, int32_t w_max,
+              int32_t *tts0);
+
+/* LAO steps step0 .. step0+n_steps-1 (step0 >= 1): step t removes loop
+ * floor(w0 M / 2^32), puts in loop (t, 0xFFFFFFFF) drawn against the
+ * remaining couplers, evaluates the candidate against its own E_GS with PT
+ * key w2, and keeps it under Algorithm 1's rule (Boltzmann uniform w1); w0..w2
+ * come from counter (t, 0xFFFFFFFE, 0, 4).  Candidates are PT-evaluated up to
+ * `speculation` (1..16) at a time; results equal the step-by-step loop.
+ * out: n_steps records (may be NULL). */
+int lao_run(pt_handle *h, uint32_t step0, int32_t n_steps, int32_t speculation, pt_lao_result *out);
+
+/* Current planted state (N), loops ([n_loops][PT_LOOP_WORDS]), couplers,
+ * E_GS and TTS (any pointer may be NULL).  PT_ERR_STATE outside LAO mode. */
+int lao_state(const pt_handle *h, int8_t *planted, int32_t *loops, int8_t *J, int32_t *E_gs, int32_t *tts);
+
 /* Checkpoint of the complete PT state and couplers.  With buf == NULL only
  * *len is set; otherwise *len must be at least that size. */
 int pt_checkpoint(pt_handle *h, void *buf, size_t *len);

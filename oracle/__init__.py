@@ -71,6 +71,12 @@ def _declare(L):
                                                              _p(np.uint8)]
     L.or_pt_exchange_walk.argtypes = L.or_pt_exchange.argtypes + [_p(np.int32), _p(np.uint64), _p(np.uint64),
                                                                  _p(np.uint8)]
+    L.or_lao_plant.argtypes = [c.c_int, c.c_uint32, c.c_uint32, c.c_int, c.c_int, _p(np.int8), _p(np.int32),
+                               _p(np.int8), c.POINTER(c.c_int32)]
+    L.or_lao_run.argtypes = [c.c_int, c.c_int, _p(np.float64), c.c_int, c.c_uint32, c.c_uint32, c.c_int, c.c_int,
+                             c.c_int32, c.c_int, c.c_double, c.c_int, c.c_uint32, c.c_int, _p(np.int8),
+                             _p(np.int32), _p(np.int8), c.POINTER(c.c_int32), c.POINTER(c.c_int32),
+                             _p(np.int32), _p(np.int32), _p(np.int32), _p(np.int32)]
     L.or_tts.argtypes = [c.c_int, _p(np.int32), _p(np.int32), c.c_int32, c.c_int32,
                          c.POINTER(c.c_int32), c.POINTER(c.c_int32), c.POINTER(c.c_int32)]
     L.or_tts_eval.argtypes = [c.c_int, _p(np.int8), c.c_int, _p(np.float64), c.c_int,
@@ -246,3 +252,45 @@ def engineer_run(L, J, betas, n_runs, seed, base_uid, S, pass_mult, exchange_eve
 
 def ground_energy_bipartite(L, J):
     return int(lib().or_ground_energy_bipartite(L, np.ascontiguousarray(J, np.int8)))
+
+
+# --------------------------------------------------------------------------
+# Planted-solution instances and loop adaptive optimisation (Sec. IV,
+# Algorithm 2); definitions of the draws in pt_oracle.c.
+LOOP_WORDS = 9
+
+
+def lao_plant(L, seed, uid, n_loops, w_max=3):
+    """(planted spins [N], loops [n_loops][9], couplers [E], E_GS)."""
+    N, E = 8 * L * L, 16 * L * L + 8 * L * (L - 1)
+    planted = np.zeros(N, np.int8)
+    loops = np.zeros((n_loops, LOOP_WORDS), np.int32)
+    J = np.zeros(E, np.int8)
+    eg = ctypes.c_int32()
+    if lib().or_lao_plant(L, _u32(seed), _u32(uid), int(n_loops), int(w_max), planted, loops, J, ctypes.byref(eg)):
+        raise ValueError("no admissible loop found")
+    return planted, loops, J, eg.value
+
+
+class LAOState:
+    """Oracle loop adaptive optimisation on one planted instance."""
+
+    def __init__(self, L, betas, n_runs, seed, uid, n_loops, w_max=3, S=1024, exchange_every=1,
+                 beta_rao=-1.0, direction=1):
+        self.L, self.betas, self.R, self.seed, self.uid = L, np.ascontiguousarray(betas, np.float64), n_runs, seed, uid
+        self.M, self.w_max, self.S, self.x, self.beta, self.direction = n_loops, w_max, S, exchange_every, beta_rao, direction
+        self.planted, self.loops, self.J, self.E_gs = lao_plant(L, seed, uid, n_loops, w_max)
+        self.tts = -1
+
+    def run(self, step0, n_steps):
+        eg, tc = ctypes.c_int32(self.E_gs), ctypes.c_int32(self.tts)
+        logs = [np.zeros(max(n_steps, 1), np.int32) for _ in range(4)]
+        rc = lib().or_lao_run(self.L, len(self.betas), self.betas, self.R, _u32(self.seed), _u32(self.uid), self.M,
+                              self.w_max, int(self.S), int(self.x), float(self.beta), int(self.direction),
+                              _u32(step0), int(n_steps), self.planted, self.loops, self.J, ctypes.byref(eg),
+                              ctypes.byref(tc), *logs)
+        if rc:
+            raise ValueError("oracle LAO failed")
+        self.E_gs, self.tts = eg.value, tc.value
+        return {"removed": logs[0][:n_steps], "tts": logs[1][:n_steps], "E_gs": logs[2][:n_steps],
+                "accepted": logs[3][:n_steps]}

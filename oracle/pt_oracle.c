@@ -588,3 +588,217 @@ int32_t or_ground_energy_bipartite(int L, const int8_t *J)
     free(s); free(nl);
     return bestE;
 }
+
+/* ------------------------------------------------------------------ */
+/* Planted-solution instances and loop adaptive optimisation            */
+/* (Sec. IV, Algorithm 2).                                              */
+/* The instance is a sum of frustrated loops along Chimera edges, each   */
+/* built to have the planted configuration as a ground state, so the     */
+/* planted configuration is a ground state of the sum and                */
+/* E_GS = sum over loops of -w (len - 2).  Readings (the loop rules are  */
+/* only outlined in the paper): a loop is a simple cycle of length 4     */
+/* (probability 0.1) or 6, weight w uniform in 1..w_max; every edge is   */
+/* satisfied by the planted state except one, frustrated, edge.          */
+/* Couplers of overlapping loops add; a draw that would take a coupler   */
+/* outside [-3, 3] is rejected and redrawn.                              */
+/* Draws use key (seed, uid), kind 4:                                    */
+/*   planted spin i: counter (0, 0xFFFFFFF0, i>>2, 4), word i&3, s = -1  */
+/*     if the top bit is set;                                            */
+/*   loop (c0, c1), attempt a: words j = 0..15 from counters             */
+/*     (c0, c1, a<<2 | j>>2, 4): j0 of attempt 0 fixes the length for    */
+/*     every attempt (u < floor(0.1 2^32) -> 4, else 6, the size chosen  */
+/*     before the placement), j1 start vertex floor(u N / 2^32), j2..    */
+/*     the walk (neighbour                                               */
+/*     floor(u deg / 2^32) in ascending vertex order), j8 weight          */
+/*     1 + floor(u w_max / 2^32), j9 frustrated position                 */
+/*     floor(u len / 2^32); an attempt that revisits a vertex, does not  */
+/*     close, or overflows a coupler is rejected;                        */
+/*   initial loop m: (c0, c1) = (0, m); step t: removed loop             */
+/*     floor(w0 M / 2^32), Boltzmann uniform w1 and candidate PT key w2  */
+/*     from counter (t, 0xFFFFFFFE, 0, 4), the new loop (c0, c1) =       */
+/*     (t, 0xFFFFFFFF); the initial instance's PT key is w2 of step 0.   */
+/* A loop record is {len, w, frustrated position, edges[6] (-1 unused)}. */
+/* ------------------------------------------------------------------ */
+#define OR_LOOP_WORDS 9
+#define OR_LAO_P4 429496730u
+#define OR_LAO_ATTEMPTS (1 << 16)
+
+typedef struct { int N, E; int32_t *ei, *ej; int deg[2048]; int nb[2048][6]; int ne[2048][6]; } or_lgraph;
+
+static or_lgraph *lgraph_open(int L)
+{
+    or_lgraph *g = calloc(1, sizeof(or_lgraph));
+    g->N = 8 * L * L;
+    g->E = or_chimera_n_edges(L);
+    g->ei = malloc(sizeof(int32_t) * g->E);
+    g->ej = malloc(sizeof(int32_t) * g->E);
+    or_chimera_edges(L, g->ei, g->ej);
+    for (int e = 0; e < g->E; ++e) {
+        int a = g->ei[e], b = g->ej[e];
+        g->nb[a][g->deg[a]] = b; g->ne[a][g->deg[a]++] = e;
+        g->nb[b][g->deg[b]] = a; g->ne[b][g->deg[b]++] = e;
+    }
+    for (int v = 0; v < g->N; ++v)                    /* ascending neighbour order */
+        for (int i = 1; i < g->deg[v]; ++i)
+            for (int k = i; k > 0 && g->nb[v][k - 1] > g->nb[v][k]; --k) {
+                int t = g->nb[v][k]; g->nb[v][k] = g->nb[v][k - 1]; g->nb[v][k - 1] = t;
+                t = g->ne[v][k]; g->ne[v][k] = g->ne[v][k - 1]; g->ne[v][k - 1] = t;
+            }
+    return g;
+}
+
+static void lgraph_close(or_lgraph *g) { free(g->ei); free(g->ej); free(g); }
+
+static int lgraph_edge(const or_lgraph *g, int a, int b)
+{
+    for (int k = 0; k < g->deg[a]; ++k) if (g->nb[a][k] == b) return g->ne[a][k];
+    return -1;
+}
+
+static uint32_t mulhi32(uint32_t u, uint32_t n) { return (uint32_t)(((uint64_t)u * n) >> 32); }
+
+/* Coupler contribution of a loop record to its m-th edge. */
+static int loop_term(const or_lgraph *g, const int8_t *planted, const int32_t *rec, int m)
+{
+    int e = rec[3 + m];
+    int sgn = (m == rec[2]) ? 1 : -1;
+    return sgn * rec[1] * planted[g->ei[e]] * planted[g->ej[e]];
+}
+
+static void loop_apply(const or_lgraph *g, const int8_t *planted, const int32_t *rec, int8_t *J, int sign)
+{
+    for (int m = 0; m < rec[0]; ++m) J[rec[3 + m]] = (int8_t)(J[rec[3 + m]] + sign * loop_term(g, planted, rec, m));
+}
+
+static int lao_draw_loop(const or_lgraph *g, const int8_t *planted, const int8_t *J, uint32_t seed,
+                         uint32_t uid, uint32_t c0, uint32_t c1, int w_max, int32_t *rec)
+{
+    const int len = draw(seed, uid, c0, c1, 0u, 4u, 0) < OR_LAO_P4 ? 4 : 6;   /* fixed for every attempt */
+    for (uint32_t a = 0; a < OR_LAO_ATTEMPTS; ++a) {
+        uint32_t u[16];
+        for (int j = 0; j < 16; ++j) u[j] = draw(seed, uid, c0, c1, (a << 2) | (uint32_t)(j >> 2), 4u, j & 3);
+        int v[6], ok = 1;
+        v[0] = (int)mulhi32(u[1], (uint32_t)g->N);
+        for (int m = 1; m < len && ok; ++m) {
+            int p = v[m - 1];
+            v[m] = g->nb[p][mulhi32(u[1 + m], (uint32_t)g->deg[p])];
+            for (int q = 0; q < m; ++q) if (v[q] == v[m]) ok = 0;
+        }
+        if (!ok) continue;
+        int32_t r[OR_LOOP_WORDS];
+        r[0] = len;
+        r[1] = 1 + (int)mulhi32(u[8], (uint32_t)w_max);
+        r[2] = (int)mulhi32(u[9], (uint32_t)len);
+        for (int m = 0; m < 6; ++m) r[3 + m] = -1;
+        for (int m = 0; m < len; ++m) {
+            r[3 + m] = lgraph_edge(g, v[m], v[(m + 1) % len]);
+            if (r[3 + m] < 0) ok = 0;
+        }
+        if (!ok) continue;
+        for (int m = 0; m < len && ok; ++m) {
+            int x = J[r[3 + m]] + loop_term(g, planted, r, m);
+            if (x < -3 || x > 3) ok = 0;
+        }
+        if (!ok) continue;
+        memcpy(rec, r, sizeof(r));
+        return 0;
+    }
+    return -1;
+}
+
+static int32_t loops_gs(const int32_t *loops, int n_loops)
+{
+    int32_t e = 0;
+    for (int m = 0; m < n_loops; ++m) e -= loops[m * OR_LOOP_WORDS + 1] * (loops[m * OR_LOOP_WORDS] - 2);
+    return e;
+}
+
+int or_lao_plant(int L, uint32_t seed, uint32_t uid, int n_loops, int w_max, int8_t *planted,
+                 int32_t *loops, int8_t *J, int32_t *E_gs)
+{
+    or_lgraph *g = lgraph_open(L);
+    for (int i = 0; i < g->N; ++i)
+        planted[i] = (draw(seed, uid, 0u, 0xFFFFFFF0u, (uint32_t)(i >> 2), 4u, i & 3) >> 31) ? -1 : 1;
+    memset(J, 0, (size_t)g->E);
+    for (int m = 0; m < n_loops; ++m) {
+        if (lao_draw_loop(g, planted, J, seed, uid, 0u, (uint32_t)m, w_max, loops + m * OR_LOOP_WORDS)) {
+            lgraph_close(g);
+            return -1;
+        }
+        loop_apply(g, planted, loops + m * OR_LOOP_WORDS, J, 1);
+    }
+    *E_gs = loops_gs(loops, n_loops);
+    lgraph_close(g);
+    return 0;
+}
+
+/* PT-TTS against a known target (pass of S sweeps, horizon S). */
+static int tts_known(int L, const int8_t *J, int n_temps, const double *betas, int n_runs, uint32_t seed,
+                     uint32_t uid, int32_t S, int exchange_every, int32_t target, int32_t *tts)
+{
+    int N = 8 * L * L;
+    size_t nrep = (size_t)n_runs * n_temps;
+    int8_t *spins = malloc(nrep * N);
+    int32_t *E = malloc(sizeof(int32_t) * nrep);
+    int32_t *best = malloc(sizeof(int32_t) * n_runs), *first = malloc(sizeof(int32_t) * n_runs);
+    uint64_t *macc = calloc(nrep, sizeof(uint64_t));
+    uint64_t *xacc = calloc((size_t)n_runs * (n_temps > 1 ? n_temps - 1 : 1), sizeof(uint64_t));
+    or_pt_init_spins(L, n_temps, n_runs, seed, uid, spins);
+    or_pt_start(L, J, n_temps, n_runs, spins, E, best, first);
+    int rc = or_pt_sweeps(L, J, n_temps, betas, n_runs, seed, uid, spins, E, best, first, macc, xacc, 0u, S,
+                          exchange_every);
+    int32_t nh, tg;
+    if (rc == 0) or_tts(n_runs, best, first, target, S, tts, &nh, &tg);
+    free(spins); free(E); free(best); free(first); free(macc); free(xacc);
+    return rc;
+}
+
+/* LAO steps step0 .. step0+n_steps-1 (step0 >= 1) in place on (loops, J,
+ * E_gs, tts_cur); tts_cur < 0 on entry: evaluate the instance first (key w2
+ * of step 0).  Acceptance as in Algorithm 1 (direction, beta_rao < 0:
+ * greedy).  Per step the logs get the removed loop, the candidate's TTS,
+ * ground-state energy and acceptance (any log may be NULL). */
+int or_lao_run(int L, int n_temps, const double *betas, int n_runs, uint32_t seed, uint32_t uid, int n_loops,
+               int w_max, int32_t S, int exchange_every, double beta_rao, int direction, uint32_t step0,
+               int n_steps, const int8_t *planted, int32_t *loops, int8_t *J, int32_t *E_gs, int32_t *tts_cur,
+               int32_t *log_removed, int32_t *log_tts, int32_t *log_egs, int32_t *log_accept)
+{
+    or_lgraph *g = lgraph_open(L);
+    int rc = 0;
+    int8_t *Jc = malloc((size_t)g->E);
+    if (*tts_cur < 0) {
+        uint32_t u0 = draw(seed, uid, 0u, 0xFFFFFFFEu, 0u, 4u, 2);
+        rc = tts_known(L, J, n_temps, betas, n_runs, seed, u0, S, exchange_every, *E_gs, tts_cur);
+    }
+    for (int a = 0; a < n_steps && rc == 0; ++a) {
+        uint32_t t = step0 + (uint32_t)a;
+        uint32_t ctl[3];
+        for (int w = 0; w < 3; ++w) ctl[w] = draw(seed, uid, t, 0xFFFFFFFEu, 0u, 4u, w);
+        int r = (int)mulhi32(ctl[0], (uint32_t)n_loops);
+        int32_t *old = loops + r * OR_LOOP_WORDS, rec[OR_LOOP_WORDS];
+        memcpy(Jc, J, (size_t)g->E);
+        loop_apply(g, planted, old, Jc, -1);
+        if (lao_draw_loop(g, planted, Jc, seed, uid, t, 0xFFFFFFFFu, w_max, rec)) { rc = -1; break; }
+        loop_apply(g, planted, rec, Jc, 1);
+        int32_t eg = *E_gs + old[1] * (old[0] - 2) - rec[1] * (rec[0] - 2), tn;
+        rc = tts_known(L, Jc, n_temps, betas, n_runs, seed, ctl[2], S, exchange_every, eg, &tn);
+        if (rc) break;
+        int64_t gain = (int64_t)direction * ((int64_t)tn - (int64_t)*tts_cur);
+        int accept = gain > 0;
+        if (!accept && beta_rao >= 0.0)
+            accept = ctl[1] < prob_to_u32(exp(-beta_rao * fabs((double)tn - (double)*tts_cur)));
+        if (accept) {
+            memcpy(J, Jc, (size_t)g->E);
+            memcpy(old, rec, sizeof(rec));
+            *E_gs = eg;
+            *tts_cur = tn;
+        }
+        if (log_removed) log_removed[a] = r;
+        if (log_tts) log_tts[a] = tn;
+        if (log_egs) log_egs[a] = eg;
+        if (log_accept) log_accept[a] = accept;
+    }
+    free(Jc);
+    lgraph_close(g);
+    return rc;
+}

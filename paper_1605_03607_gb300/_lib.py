@@ -38,6 +38,14 @@ class pt_step_result(C.Structure):
                 ("cand_uid", C.c_uint32)]
 
 
+PT_LOOP_WORDS = 9
+
+
+class pt_lao_result(C.Structure):
+    _fields_ = [("removed", C.c_int32), ("loop", C.c_int32 * PT_LOOP_WORDS), ("E_gs_new", C.c_int32),
+                ("tts_old", C.c_int32), ("tts_new", C.c_int32), ("accepted", C.c_int32), ("cand_uid", C.c_uint32)]
+
+
 # (name, restype, argtypes) of every entry point declared in include/pt.h
 _VP = C.c_void_p
 _I32P = C.POINTER(C.c_int32)
@@ -59,6 +67,10 @@ SIGNATURES = [
     ("engineer_begin", C.c_int, [_VP, C.POINTER(pt_rule), C.c_uint32, _I32P]),
     ("engineer_step", C.c_int, [_VP, C.c_uint32, C.POINTER(pt_step_result)]),
     ("engineer_run", C.c_int, [_VP, C.c_uint32, C.c_int32, C.c_int32, C.POINTER(pt_step_result)]),
+    ("lao_plant", C.c_int, [C.c_int32, C.c_uint32, C.c_uint32, C.c_int32, C.c_int32, _VP, _VP, _VP, _I32P]),
+    ("lao_begin", C.c_int, [_VP, C.POINTER(pt_rule), C.c_uint32, C.c_int32, C.c_int32, _I32P]),
+    ("lao_run", C.c_int, [_VP, C.c_uint32, C.c_int32, C.c_int32, C.POINTER(pt_lao_result)]),
+    ("lao_state", C.c_int, [_VP, _VP, _VP, _VP, _I32P, _I32P]),
     ("engineer_current_tts", C.c_int, [_VP, _I32P]),
     ("pt_checkpoint", C.c_int, [_VP, _VP, C.POINTER(C.c_size_t)]),
     ("pt_restore", C.c_int, [_VP, _VP, C.c_size_t]),
@@ -254,6 +266,31 @@ class PTHandle:
 
     def engineer_step(self, step):
         return self.engineer_run(step, 1, 1)
+
+    def lao_begin(self, S, uid, n_loops, w_max=3, exchange_every=1, beta_rao=-1.0, direction=1):
+        """Planted instance with n_loops loops (Algorithm 2); returns its TTS against E_GS."""
+        rule = pt_rule(int(S), 1, int(exchange_every), int(direction), float(beta_rao))
+        t = C.c_int32()
+        _check(load().lao_begin(self.h, C.byref(rule), int(uid) & 0xFFFFFFFF, int(n_loops), int(w_max), C.byref(t)),
+               self.h)
+        self.n_loops = int(n_loops)
+        return t.value
+
+    def lao_run(self, step0, n_steps, speculation=1):
+        out = (pt_lao_result * max(n_steps, 1))()
+        _check(load().lao_run(self.h, int(step0) & 0xFFFFFFFF, int(n_steps), int(speculation), out), self.h)
+        keys = ("removed", "E_gs_new", "tts_old", "tts_new", "accepted", "cand_uid")
+        res = {k: np.array([getattr(out[i], k) for i in range(n_steps)], np.int64) for k in keys}
+        res["loop"] = np.array([list(out[i].loop) for i in range(n_steps)], np.int32).reshape(n_steps, PT_LOOP_WORDS)
+        return res
+
+    def lao_state(self):
+        planted = np.zeros(self.N, np.int8)
+        loops = np.zeros((self.n_loops, PT_LOOP_WORDS), np.int32)
+        J = np.zeros(self.n_edges, np.int8)
+        eg, t = C.c_int32(), C.c_int32()
+        _check(load().lao_state(self.h, _ptr(planted), _ptr(loops), _ptr(J), C.byref(eg), C.byref(t)), self.h)
+        return dict(planted=planted, loops=loops, J=J, E_gs=eg.value, tts=t.value)
 
     def engineer_guided_step(self, model, step, n_prop=64, top=4):
         """One surrogate-guided step; returns (results in rank order, predictions, ranked indices)."""
@@ -507,3 +544,15 @@ class Surrogate:
 
     def launch_count(self):
         return int(load().sg_launch_count(self.m))
+
+
+def lao_plant(L, seed, uid, n_loops, w_max=3):
+    """Host-side planted instance (no GPU work): (planted, loops, J, E_GS)."""
+    N, E = 8 * L * L, 16 * L * L + 8 * L * (L - 1)
+    planted = np.zeros(N, np.int8)
+    loops = np.zeros((n_loops, PT_LOOP_WORDS), np.int32)
+    J = np.zeros(E, np.int8)
+    eg = C.c_int32()
+    _check(load().lao_plant(int(L), int(seed) & 0xFFFFFFFF, int(uid) & 0xFFFFFFFF, int(n_loops), int(w_max),
+                            _ptr(planted), _ptr(loops), _ptr(J), C.byref(eg)), None)
+    return planted, loops, J, eg.value

@@ -7,6 +7,7 @@
 // accept/reject bookkeeping of the engineering loop.  Every sweep, energy and
 // TTS reduction runs in the kernels of pt_kernels.cu.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -42,6 +43,7 @@ struct Group {
     int2* d_items = nullptr;
     Bundle* d_bundles = nullptr;
     int32_t* d_tts = nullptr;        // [n_inst][3]
+    int32_t* d_targets = nullptr;    // [n_inst] per-instance TTS targets (LAO)
     int* d_queue = nullptr;
     std::vector<InstDesc> desc;
     std::vector<Bundle> bundles;
@@ -86,6 +88,13 @@ struct pt_handle {
     uint64_t evals = 0, batches = 0;
     double eval_ms = 0.0;
     cudaEvent_t eb0 = nullptr, eb1 = nullptr;
+    // loop adaptive optimisation (planted instance)
+    bool lao = false;
+    uint32_t lao_uid = 0;
+    int lao_w_max = 3;
+    std::vector<int8_t> planted;
+    std::vector<int32_t> loops;      // [n_loops][PT_LOOP_WORDS]
+    int32_t E_gs = 0;
     // engineering loop
     bool eng = false;
     pt_rule rule{};
@@ -129,7 +138,7 @@ void free_group(Group& g)
     cudaFree(g.spins); cudaFree(g.E); cudaFree(g.perm); cudaFree(g.best); cudaFree(g.first);
     cudaFree(g.macc); cudaFree(g.xacc); cudaFree(g.jw); cudaFree(g.d_desc); cudaFree(g.d_items);
     cudaFree(g.d_bundles); cudaFree(g.d_tts); cudaFree(g.d_queue);
-    cudaFree(g.whot); cudaFree(g.wtrips); cudaFree(g.wstate);
+    cudaFree(g.whot); cudaFree(g.wtrips); cudaFree(g.wstate); cudaFree(g.d_targets);
     g = Group();
 }
 
@@ -181,6 +190,7 @@ int group_alloc(pt_handle* h, Group& g, int n_inst)
     CK(dalloc(&g.d_desc, (size_t)n_inst), "cudaMalloc desc");
     CK(dalloc(&g.d_items, runs), "cudaMalloc items");
     CK(dalloc(&g.d_tts, (size_t)n_inst * 3), "cudaMalloc tts");
+    CK(dalloc(&g.d_targets, (size_t)n_inst), "cudaMalloc targets");
     CK(dalloc(&g.d_queue, 1), "cudaMalloc queue");
     g.desc.resize(n_inst);
     for (int i = 0; i < n_inst; ++i) {
@@ -336,8 +346,9 @@ int group_tts(pt_handle* h, Group& g, int32_t target, int32_t horizon, std::vect
 }
 
 // Full evaluation of every instance of g: fresh runs, pass_mult*S sweeps, TTS at horizon S.
+// targets (host, one per instance, may be NULL): per-instance TTS targets.
 int group_eval(pt_handle* h, Group& g, int32_t S, int32_t pass_mult, int32_t xevery,
-               std::vector<int32_t>& out)
+               std::vector<int32_t>& out, int32_t target = PT_TARGET_BEST, const int32_t* targets = nullptr)
 {
     int rc;
     if (!h->eb0) {
@@ -348,7 +359,11 @@ int group_eval(pt_handle* h, Group& g, int32_t S, int32_t pass_mult, int32_t xev
     CK(cudaEventRecord(h->eb0, h->stream), "event");
     if ((rc = group_reset(h, g, true))) return rc;
     if ((rc = group_sweeps(h, g, (int64_t)S * pass_mult, xevery))) return rc;
-    CK(launch_tts(g.d_desc, g.n_inst, PT_TARGET_BEST, S, g.d_tts, h->stream), "tts kernel");
+    if (targets)
+        CK(cudaMemcpyAsync(g.d_targets, targets, sizeof(int32_t) * g.n_inst, cudaMemcpyHostToDevice, h->stream),
+           "upload targets");
+    CK(launch_tts(g.d_desc, g.n_inst, target, S, g.d_tts, h->stream, targets ? g.d_targets : nullptr),
+       "tts kernel");
     ++h->launches;
     CK(cudaEventRecord(h->eb1, h->stream), "event");
     out.assign((size_t)g.n_inst * 3, 0);
@@ -399,7 +414,8 @@ int ensure_candidates(pt_handle* h, int k);
 
 // PT-TTS evaluation of k candidate coupler vectors (host [k][n_edges]) with
 // PT keys uids[0..k-1], as one batched launch sequence; res = k x {tts, hits, target}.
-int eval_candidates(pt_handle* h, int k, const int8_t* Jc, const uint32_t* uids, std::vector<int32_t>& res)
+int eval_candidates(pt_handle* h, int k, const int8_t* Jc, const uint32_t* uids, std::vector<int32_t>& res,
+                    int32_t target = PT_TARGET_BEST, const int32_t* targets = nullptr)
 {
     int rc = ensure_candidates(h, k);
     if (rc) return rc;
@@ -417,7 +433,7 @@ int eval_candidates(pt_handle* h, int k, const int8_t* Jc, const uint32_t* uids,
     std::vector<Bundle> sub;
     for (const Bundle& b : keep) if (b.inst < k) sub.push_back(b);
     g.bundles = sub;
-    rc = group_eval(h, g, h->rule.S, h->rule.pass_mult, h->rule.exchange_every, res);
+    rc = group_eval(h, g, h->rule.S, h->rule.pass_mult, h->rule.exchange_every, res, target, targets);
     g.n_inst = n_full;
     g.bundles = keep;
     return rc;
@@ -430,6 +446,123 @@ int ensure_candidates(pt_handle* h, int k)
     int rc = group_alloc(h, h->cand, k);
     if (rc) return rc;
     return group_schedule(h, h->cand);
+}
+
+// ------------------------------------------------ planted instances, LAO
+// Chimera adjacency with every vertex's neighbours in ascending order (the
+// order the loop walks index into) and the edge index of each neighbour.
+struct LaoGraph {
+    int N = 0, E = 0;
+    std::vector<int32_t> ei, ej;
+    std::vector<std::array<int, 6>> nb, ne;
+    std::vector<int> deg;
+    explicit LaoGraph(int L)
+    {
+        N = 8 * L * L;
+        E = n_edges_of(L);
+        ei.resize(E); ej.resize(E);
+        int e = 0;
+        auto sp = [&](int r, int c, int u, int k) { return 8 * (r * L + c) + 4 * u + k; };
+        for (int r = 0; r < L; ++r)
+            for (int c = 0; c < L; ++c)
+                for (int kv = 0; kv < 4; ++kv)
+                    for (int kh = 0; kh < 4; ++kh) { ei[e] = sp(r, c, 0, kv); ej[e] = sp(r, c, 1, kh); ++e; }
+        for (int r = 0; r + 1 < L; ++r)
+            for (int c = 0; c < L; ++c)
+                for (int k = 0; k < 4; ++k) { ei[e] = sp(r, c, 0, k); ej[e] = sp(r + 1, c, 0, k); ++e; }
+        for (int r = 0; r < L; ++r)
+            for (int c = 0; c + 1 < L; ++c)
+                for (int k = 0; k < 4; ++k) { ei[e] = sp(r, c, 1, k); ej[e] = sp(r, c + 1, 1, k); ++e; }
+        nb.assign(N, {}); ne.assign(N, {}); deg.assign(N, 0);
+        std::vector<std::vector<std::pair<int, int>>> adj(N);
+        for (int x = 0; x < E; ++x) {
+            adj[ei[x]].push_back({ej[x], x});
+            adj[ej[x]].push_back({ei[x], x});
+        }
+        for (int v = 0; v < N; ++v) {
+            std::sort(adj[v].begin(), adj[v].end());
+            deg[v] = (int)adj[v].size();
+            for (int k = 0; k < deg[v]; ++k) { nb[v][k] = adj[v][k].first; ne[v][k] = adj[v][k].second; }
+        }
+    }
+    int edge(int a, int b) const
+    {
+        for (int k = 0; k < deg[a]; ++k) if (nb[a][k] == b) return ne[a][k];
+        return -1;
+    }
+};
+
+constexpr uint32_t LAO_P4 = 429496730u;      // floor(0.1 * 2^32): length-4 loops, else length 6
+constexpr uint32_t LAO_ATTEMPTS = 1u << 16;
+
+uint32_t lao_word(uint32_t seed, uint32_t uid, uint32_t c0, uint32_t c1, uint32_t c2, int w)
+{
+    const uint32_t ctr[4] = {c0, c1, c2, 4u};
+    uint32_t out[4];
+    philox_host(ctr, seed, uid, out);
+    return out[w];
+}
+
+uint32_t mulhi(uint32_t u, uint32_t n) { return (uint32_t)(((uint64_t)u * n) >> 32); }
+
+int loop_term(const LaoGraph& g, const int8_t* planted, const int32_t* rec, int m)
+{
+    const int e = rec[3 + m];
+    return (m == rec[2] ? 1 : -1) * rec[1] * planted[g.ei[e]] * planted[g.ej[e]];
+}
+
+void loop_apply(const LaoGraph& g, const int8_t* planted, const int32_t* rec, int8_t* J, int sign)
+{
+    for (int m = 0; m < rec[0]; ++m) J[rec[3 + m]] = (int8_t)(J[rec[3 + m]] + sign * loop_term(g, planted, rec, m));
+}
+
+// Loop (c0, c1) against couplers J: the length is fixed by attempt 0, then
+// placements are drawn until one closes a simple cycle without taking a
+// coupler outside [-3, 3].  false when none is found.
+bool lao_draw_loop(const LaoGraph& g, const int8_t* planted, const int8_t* J, uint32_t seed, uint32_t uid,
+                   uint32_t c0, uint32_t c1, int w_max, int32_t* rec)
+{
+    const int len = lao_word(seed, uid, c0, c1, 0u, 0) < LAO_P4 ? 4 : 6;
+    for (uint32_t a = 0; a < LAO_ATTEMPTS; ++a) {
+        uint32_t u[16];
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t ctr[4] = {c0, c1, (a << 2) | (uint32_t)q, 4u};
+            philox_host(ctr, seed, uid, u + 4 * q);
+        }
+        int v[6];
+        bool ok = true;
+        v[0] = (int)mulhi(u[1], (uint32_t)g.N);
+        for (int m = 1; m < len && ok; ++m) {
+            const int p = v[m - 1];
+            v[m] = g.nb[p][mulhi(u[1 + m], (uint32_t)g.deg[p])];
+            for (int q = 0; q < m; ++q) if (v[q] == v[m]) ok = false;
+        }
+        if (!ok) continue;
+        int32_t r[PT_LOOP_WORDS];
+        r[0] = len;
+        r[1] = 1 + (int)mulhi(u[8], (uint32_t)w_max);
+        r[2] = (int)mulhi(u[9], (uint32_t)len);
+        for (int m = 0; m < 6; ++m) r[3 + m] = -1;
+        for (int m = 0; m < len && ok; ++m) {
+            r[3 + m] = g.edge(v[m], v[(m + 1) % len]);
+            if (r[3 + m] < 0) ok = false;
+        }
+        for (int m = 0; m < len && ok; ++m) {
+            const int x = J[r[3 + m]] + loop_term(g, planted, r, m);
+            if (x < -3 || x > 3) ok = false;
+        }
+        if (!ok) continue;
+        std::memcpy(rec, r, sizeof(r));
+        return true;
+    }
+    return false;
+}
+
+int32_t loops_gs(const int32_t* loops, int n)
+{
+    int32_t e = 0;
+    for (int m = 0; m < n; ++m) e -= loops[m * PT_LOOP_WORDS + 1] * (loops[m * PT_LOOP_WORDS] - 2);
+    return e;
 }
 
 }  // namespace
@@ -690,6 +823,7 @@ int engineer_begin(pt_handle* h, const pt_rule* rule, uint32_t base_uid, int32_t
     if (rc) return rc;
     h->tts_cur = t;
     h->eng = true;
+    h->lao = false;
     if (tts0) *tts0 = t;
     return PT_OK;
 }
@@ -746,6 +880,142 @@ int engineer_run(pt_handle* h, uint32_t step0, int32_t n_steps, int32_t spec, pt
 int engineer_step(pt_handle* h, uint32_t step, pt_step_result* out)
 {
     return engineer_run(h, step, 1, 1, out);
+}
+
+int lao_plant(int32_t chimera_L, uint32_t seed, uint32_t uid, int32_t n_loops, int32_t w_max, int8_t* planted,
+              int32_t* loops, int8_t* J, int32_t* E_gs)
+{
+    if (!planted || !loops || !J || !E_gs) return fail(nullptr, PT_ERR_ARG, "NULL argument");
+    if (chimera_L < 1 || chimera_L > MAX_L || n_loops < 1 || w_max < 1 || w_max > 3)
+        return fail(nullptr, PT_ERR_ARG, "need 1 <= L <= 16, n_loops >= 1, 1 <= w_max <= 3");
+    const LaoGraph g(chimera_L);
+    for (int i = 0; i < g.N; ++i)
+        planted[i] = (lao_word(seed, uid, 0u, 0xFFFFFFF0u, (uint32_t)(i >> 2), i & 3) >> 31) ? -1 : 1;
+    std::memset(J, 0, (size_t)g.E);
+    for (int m = 0; m < n_loops; ++m) {
+        int32_t* rec = loops + (size_t)m * PT_LOOP_WORDS;
+        if (!lao_draw_loop(g, planted, J, seed, uid, 0u, (uint32_t)m, (int)w_max, rec))
+            return fail(nullptr, PT_ERR_STATE, "no admissible loop (too many loops for the graph and |J| <= 3)");
+        loop_apply(g, planted, rec, J, 1);
+    }
+    *E_gs = loops_gs(loops, n_loops);
+    return PT_OK;
+}
+
+int lao_begin(pt_handle* h, const pt_rule* rule, uint32_t uid, int32_t n_loops, int32_t w_max, int32_t* tts0)
+{
+    if (!h || !rule) return fail(h, PT_ERR_ARG, "NULL argument");
+    if (rule->S < 1 || rule->exchange_every < 0 || (rule->direction != 1 && rule->direction != -1) ||
+        rule->S > (1 << 30))
+        return fail(h, PT_ERR_ARG, "invalid pt_rule");
+    std::vector<int8_t> planted(h->N), J(h->n_edges);
+    std::vector<int32_t> loops((size_t)std::max(n_loops, 1) * PT_LOOP_WORDS);
+    int32_t eg = 0;
+    if (lao_plant(h->L, h->seed, uid, n_loops, w_max, planted.data(), loops.data(), J.data(), &eg) != PT_OK)
+        return fail(h, PT_ERR_ARG, pt_last_error(nullptr));
+    h->rule = *rule;
+    h->rule.pass_mult = 1;                   // the target is known: no longer pass
+    h->planted = planted;
+    h->loops = loops;
+    h->J = J;
+    h->E_gs = eg;
+    h->lao_uid = uid;
+    h->lao_w_max = w_max;
+    int rc = upload_couplers(h, h->main, 0, h->J.data());
+    if (rc) return rc;
+    const uint32_t u0 = lao_word(h->seed, uid, 0u, 0xFFFFFFFEu, 0u, 2);
+    std::vector<int32_t> res;
+    if ((rc = eval_candidates(h, 1, h->J.data(), &u0, res, h->E_gs))) return rc;
+    h->tts_cur = res[0];
+    h->lao = true;
+    h->eng = false;
+    if (tts0) *tts0 = h->tts_cur;
+    return PT_OK;
+}
+
+int lao_run(pt_handle* h, uint32_t step0, int32_t n_steps, int32_t spec, pt_lao_result* out)
+{
+    if (!h) return PT_ERR_ARG;
+    if (!h->lao) return fail(h, PT_ERR_STATE, "lao_begin not called");
+    if (step0 < 1 || n_steps < 0 || spec < 1 || spec > 16)
+        return fail(h, PT_ERR_ARG, "need step0 >= 1, n_steps >= 0, speculation in [1, 16]");
+    int rc = ensure_candidates(h, spec);
+    if (rc) return rc;
+    const LaoGraph g(h->L);
+    const int M = (int)(h->loops.size() / PT_LOOP_WORDS);
+    std::vector<int8_t> Jc((size_t)spec * h->n_edges);
+    std::vector<int32_t> rem(spec), egs(spec), recs((size_t)spec * PT_LOOP_WORDS);
+    std::vector<uint32_t> cu(spec), ua(spec);
+    int32_t done = 0;
+    bool changed = false;
+    while (done < n_steps) {
+        // k candidates drawn against the current instance: after the first
+        // accepted one the rest are stale and redrawn (same results as one by one)
+        const int k = std::min<int>(spec, n_steps - done);
+        for (int j = 0; j < k; ++j) {
+            const uint32_t t = step0 + (uint32_t)(done + j);
+            uint32_t ctl[3];
+            for (int w = 0; w < 3; ++w) ctl[w] = lao_word(h->seed, h->lao_uid, t, 0xFFFFFFFEu, 0u, w);
+            rem[j] = (int)mulhi(ctl[0], (uint32_t)M);
+            ua[j] = ctl[1];
+            cu[j] = ctl[2];
+            const int32_t* old = h->loops.data() + (size_t)rem[j] * PT_LOOP_WORDS;
+            int8_t* Jj = Jc.data() + (size_t)j * h->n_edges;
+            int32_t* rec = recs.data() + (size_t)j * PT_LOOP_WORDS;
+            std::memcpy(Jj, h->J.data(), h->n_edges);
+            loop_apply(g, h->planted.data(), old, Jj, -1);
+            if (!lao_draw_loop(g, h->planted.data(), Jj, h->seed, h->lao_uid, t, 0xFFFFFFFFu, h->lao_w_max, rec))
+                return fail(h, PT_ERR_STATE, "no admissible replacement loop");
+            loop_apply(g, h->planted.data(), rec, Jj, 1);
+            egs[j] = h->E_gs + old[1] * (old[0] - 2) - rec[1] * (rec[0] - 2);
+        }
+        // one batched evaluation, each candidate against its own ground-state energy
+        std::vector<int32_t> res;
+        if ((rc = eval_candidates(h, k, Jc.data(), cu.data(), res, PT_TARGET_BEST, egs.data()))) return rc;
+        std::vector<int32_t> tts(k);
+        for (int j = 0; j < k; ++j) tts[j] = res[(size_t)j * 3];
+        int used = k;
+        for (int j = 0; j < k; ++j) {
+            const bool acc = engineer_accept(h->rule, h->tts_cur, tts[j], ua[j]);
+            if (out) {
+                pt_lao_result& o = out[done + j];
+                o.removed = rem[j];
+                std::memcpy(o.loop, recs.data() + (size_t)j * PT_LOOP_WORDS, sizeof(o.loop));
+                o.E_gs_new = egs[j];
+                o.tts_old = h->tts_cur;
+                o.tts_new = tts[j];
+                o.accepted = acc ? 1 : 0;
+                o.cand_uid = cu[j];
+            }
+            if (acc) {
+                std::memcpy(h->J.data(), Jc.data() + (size_t)j * h->n_edges, h->n_edges);
+                std::memcpy(h->loops.data() + (size_t)rem[j] * PT_LOOP_WORDS, recs.data() + (size_t)j * PT_LOOP_WORDS,
+                            sizeof(int32_t) * PT_LOOP_WORDS);
+                h->E_gs = egs[j];
+                h->tts_cur = tts[j];
+                changed = true;
+                used = j + 1;
+                break;
+            }
+        }
+        done += used;
+    }
+    if (changed) {
+        rc = upload_couplers(h, h->main, 0, h->J.data());
+        if (rc) return rc;
+    }
+    return PT_OK;
+}
+
+int lao_state(const pt_handle* h, int8_t* planted, int32_t* loops, int8_t* J, int32_t* E_gs, int32_t* tts)
+{
+    if (!h || !h->lao) return PT_ERR_STATE;
+    if (planted) std::memcpy(planted, h->planted.data(), h->planted.size());
+    if (loops) std::memcpy(loops, h->loops.data(), sizeof(int32_t) * h->loops.size());
+    if (J) std::memcpy(J, h->J.data(), h->J.size());
+    if (E_gs) *E_gs = h->E_gs;
+    if (tts) *tts = h->tts_cur;
+    return PT_OK;
 }
 
 int engineer_guided_step(pt_handle* h, sg_model* m, uint32_t step, int32_t n_prop, int32_t top,

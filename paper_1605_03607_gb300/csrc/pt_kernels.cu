@@ -754,9 +754,10 @@ __global__ void pt_energy_kernel(const InstDesc* __restrict__ insts, const int2*
 // best <= target and first <= horizon, lower median (rank ceil(R/2)) of hit
 // sweeps with misses as +inf, horizon + 1 when unsolved.  One block per instance.
 __global__ void pt_tts_kernel(const InstDesc* __restrict__ insts, int32_t target, int32_t horizon,
-                              int32_t* __restrict__ out)
+                              int32_t* __restrict__ out, const int32_t* __restrict__ targets)
 {
     const InstDesc& in = insts[blockIdx.x];
+    if (targets) target = targets[blockIdx.x];
     const int R = in.R;
     __shared__ long long v[1024];
     __shared__ int s_min, s_hits;
@@ -868,10 +869,10 @@ cudaError_t launch_sweeps(const InstDesc* insts, const Bundle* bundles, int nbun
 }
 
 cudaError_t launch_tts(const InstDesc* insts, int ninst, int32_t target, int32_t horizon,
-                       int32_t* out, cudaStream_t st)
+                       int32_t* out, cudaStream_t st, const int32_t* targets)
 {
     if (ninst <= 0) return cudaSuccess;
-    pt_tts_kernel<<<ninst, 256, 0, st>>>(insts, target, horizon, out);
+    pt_tts_kernel<<<ninst, 256, 0, st>>>(insts, target, horizon, out, targets);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,56 @@
+"""Loop adaptive optimisation (Algorithm 2) on the GPU against the oracle:
+planted instance, known-target TTS of every candidate, and every decision,
+bit-exact; speculative batches give the step-by-step results."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_1605_03607_gb300 as pkg
+    from paper_1605_03607_gb300 import build as b
+    b.build()
+    pkg.load()
+    return pkg
+
+
+@pytest.mark.parametrize("L,NT,R,M,S,beta,spec", [(2, 6, 4, 10, 128, -1.0, 1), (4, 8, 8, 40, 256, 0.05, 4),
+                                                  (4, 8, 8, 40, 256, -1.0, 16)])
+def test_lao_matches_oracle(P, L, NT, R, M, S, beta, spec):
+    seed, uid, steps = 20160516, 21, 14
+    betas = W.beta_ladder(NT, 0.1, 3.0)
+    ref = oracle.LAOState(L, betas, R, seed, uid, M, S=S, beta_rao=beta)
+    log = ref.run(1, steps)
+    with P.PTHandle(L, np.zeros(W.chimera_n_edges(L), np.int8), betas, R, seed, 0) as h:
+        t0 = h.lao_begin(S, uid, M, 3, 1, beta)
+        res = h.lao_run(1, steps, spec)
+        st = h.lao_state()
+    assert np.array_equal(res["removed"], log["removed"])
+    assert np.array_equal(res["tts_new"], log["tts"])
+    assert np.array_equal(res["E_gs_new"], log["E_gs"])
+    assert np.array_equal(res["accepted"], log["accepted"])
+    assert np.array_equal(st["loops"], ref.loops) and np.array_equal(st["J"], ref.J)
+    assert st["E_gs"] == ref.E_gs and st["tts"] == ref.tts
+    assert t0 == res["tts_old"][0]
+    assert oracle.energy(L, st["J"], st["planted"]) == st["E_gs"]
+
+
+def test_lao_c8_shape_known_target(P):
+    """C_8 with 350 loops: the planted energy is a lower bound every run respects,
+    and runs that reach it count as hits (a short pass, properties only)."""
+    cfg = W.CONFIGS["c8_single"]
+    betas = W.beta_ladder(cfg["n_temps"], cfg["beta_min"], cfg["beta_max"])
+    with P.PTHandle(8, np.zeros(W.chimera_n_edges(8), np.int8), betas, cfg["n_runs"], cfg["seed"], 0) as h:
+        h.lao_begin(1 << 12, 7, 350, 3)
+        st = h.lao_state()
+        h.reset(0)                                   # fresh runs on the planted couplers
+        h.sweep(512, 1)
+        s = h.state()
+        assert np.all(s["best"] >= st["E_gs"]) and np.all(s["E"] >= st["E_gs"])
+        tts, nhit, target = h.tts(st["E_gs"], 512)
+        assert target == st["E_gs"] and 0 <= nhit <= cfg["n_runs"]
