@@ -567,12 +567,19 @@ def run_lao(args):
     peak_ops = sms * INT_LANES_PER_SM_CLK * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     achieved = attempts * OPS_PER_ATTEMPT / (sweep_ms / 1e3)
     st = h.lao_state()
+    # ground / first-excited overlaps of the engineered instance (Sec. III.B): one
+    # fresh PT pass of the handle's runs, one coldest-slot sample per run
+    h.reset(1)
+    h.sweep(S, 1)
+    ov = h.overlaps(st["E_gs"])
+    ov["ratio_gs_es_over_gs_gs"] = (ov["q_gs_es"] / ov["q_gs_gs"]) if ov["q_gs_gs"] > 0 and ov["q_gs_es"] >= 0 else None
     print(json.dumps({
         "workload": f"lao: planted C_8 ({M} loops, w <= 3), 32 temps beta [0.1,4], 64 runs, S=2^14 known target",
         "metric": "LAO steps/s", "value": args.steps * spec / wall, "unit": "steps/s",
         "pt_tts_evals_per_s": evals / wall, "attempts_per_s": attempts / (eval_ms / 1e3),
         "steps": args.steps, "warmup": args.warmup, "speculation": spec, "accepted": accepted,
         "tts_initial": tts0, "tts_final": st["tts"], "E_gs_initial": e_gs0, "E_gs_final": st["E_gs"],
+        "overlaps_final": ov,
         "schedule": list(h.schedule()), "team": h.mapping(),
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                      "unit": "Tops/s (int32 issue)", "frac": achieved / peak_ops, "kernel": "pt_sweep_kernel",

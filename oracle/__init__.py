@@ -294,3 +294,34 @@ class LAOState:
         self.E_gs, self.tts = eg.value, tc.value
         return {"removed": logs[0][:n_steps], "tts": logs[1][:n_steps], "E_gs": logs[2][:n_steps],
                 "accepted": logs[3][:n_steps]}
+
+
+def overlaps(spins0, E0, E_gs):
+    """Ground / first-excited overlaps (Sec. III.B) of one sample per run:
+    spins0 [R][N] (+-1), energies E0 [R].  Ground samples have E0 == E_gs; the
+    first excited level is the lowest sampled energy above E_gs; overlap
+    |1 - 2 h / N| for Hamming distance h; lower medians over the distinct
+    ground pairs and over all (ground, excited) pairs (-1 without a pair)."""
+    spins0 = np.asarray(spins0)
+    E0 = np.asarray(E0)
+    R, N = spins0.shape
+    gs = [r for r in range(R) if E0[r] == E_gs]
+    above = [int(e) for e in E0 if e > E_gs]
+    E1 = min(above) if above else 2**31 - 1
+    es = [r for r in range(R) if E0[r] == E1]
+
+    def q(a, b):
+        h = int(np.sum(spins0[a] != spins0[b]))
+        return abs(N - 2 * h)
+
+    def lower_median(v):
+        if not v:
+            return -1
+        v = sorted(v)
+        return v[(len(v) + 1) // 2 - 1]
+
+    a = [q(gs[i], gs[j]) for i in range(len(gs)) for j in range(i + 1, len(gs))]
+    b = [q(x, y) for x in gs for y in es]
+    ma, mb = lower_median(a), lower_median(b)
+    return dict(n_gs=len(gs), n_es=len(es), E1=E1, q_gs_gs=-1.0 if ma < 0 else ma / N,
+                q_gs_es=-1.0 if mb < 0 else mb / N)

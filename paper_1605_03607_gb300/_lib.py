@@ -71,6 +71,7 @@ SIGNATURES = [
     ("lao_begin", C.c_int, [_VP, C.POINTER(pt_rule), C.c_uint32, C.c_int32, C.c_int32, _I32P]),
     ("lao_run", C.c_int, [_VP, C.c_uint32, C.c_int32, C.c_int32, C.POINTER(pt_lao_result)]),
     ("lao_state", C.c_int, [_VP, _VP, _VP, _VP, _I32P, _I32P]),
+    ("pt_overlaps", C.c_int, [_VP, C.c_int32, _I32P, _I32P, _I32P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("engineer_current_tts", C.c_int, [_VP, _I32P]),
     ("pt_checkpoint", C.c_int, [_VP, _VP, C.POINTER(C.c_size_t)]),
     ("pt_restore", C.c_int, [_VP, _VP, C.c_size_t]),
@@ -283,6 +284,15 @@ class PTHandle:
         res = {k: np.array([getattr(out[i], k) for i in range(n_steps)], np.int64) for k in keys}
         res["loop"] = np.array([list(out[i].loop) for i in range(n_steps)], np.int32).reshape(n_steps, PT_LOOP_WORDS)
         return res
+
+    def overlaps(self, E_gs):
+        """Ground / first-excited overlaps of the runs' coldest-slot configurations:
+        dict(n_gs, n_es, E1, q_gs_gs, q_gs_es)."""
+        a, b, e1 = C.c_int32(), C.c_int32(), C.c_int32()
+        qa, qb = C.c_double(), C.c_double()
+        _check(load().pt_overlaps(self.h, int(E_gs), C.byref(a), C.byref(b), C.byref(e1), C.byref(qa), C.byref(qb)),
+               self.h)
+        return dict(n_gs=a.value, n_es=b.value, E1=e1.value, q_gs_gs=qa.value, q_gs_es=qb.value)
 
     def lao_state(self):
         planted = np.zeros(self.N, np.int8)

@@ -1007,6 +1007,53 @@ int lao_run(pt_handle* h, uint32_t step0, int32_t n_steps, int32_t spec, pt_lao_
     return PT_OK;
 }
 
+int pt_overlaps(pt_handle* h, int32_t E_gs, int32_t* n_gs, int32_t* n_es, int32_t* E1, double* q_gs_gs,
+                double* q_gs_es)
+{
+    if (!h) return PT_ERR_ARG;
+    Group& g = h->main;
+    const int R = h->R, NT = h->NT;
+    int32_t* d = nullptr;
+    CK(dalloc(&d, (size_t)R * R), "cudaMalloc overlaps");
+    std::vector<int32_t> dist((size_t)R * R), E((size_t)R * NT);
+    cudaError_t e = launch_hamming(g.d_desc, R, d, h->stream);
+    ++h->launches;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dist.data(), d, sizeof(int32_t) * dist.size(), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(E.data(), g.E, sizeof(int32_t) * E.size(), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(h, e, "overlaps");
+    // samples: each run's coldest slot; the first excited level is the lowest sampled energy above E_gs
+    int32_t e1 = INT32_MAX;
+    std::vector<int> gs, es;
+    for (int r = 0; r < R; ++r) {
+        const int32_t er = E[(size_t)r * NT];
+        if (er == E_gs) gs.push_back(r);
+        else if (er > E_gs && er < e1) e1 = er;
+    }
+    for (int r = 0; r < R; ++r) if (E[(size_t)r * NT] == e1) es.push_back(r);
+    // |q| = |1 - 2 h / N| (global flip symmetry), lower medians of the integers |N - 2 h|
+    auto lower_median = [](std::vector<int32_t>& v) -> int32_t {
+        if (v.empty()) return -1;
+        std::sort(v.begin(), v.end());
+        return v[(v.size() + 1) / 2 - 1];
+    };
+    std::vector<int32_t> a, b;
+    for (size_t i = 0; i < gs.size(); ++i)
+        for (size_t j = i + 1; j < gs.size(); ++j) a.push_back(std::abs(h->N - 2 * dist[(size_t)gs[i] * R + gs[j]]));
+    for (int x : gs)
+        for (int y : es) b.push_back(std::abs(h->N - 2 * dist[(size_t)x * R + y]));
+    const int32_t ma = lower_median(a), mb = lower_median(b);
+    if (n_gs) *n_gs = (int32_t)gs.size();
+    if (n_es) *n_es = (int32_t)es.size();
+    if (E1) *E1 = e1;
+    if (q_gs_gs) *q_gs_gs = ma < 0 ? -1.0 : (double)ma / h->N;
+    if (q_gs_es) *q_gs_es = mb < 0 ? -1.0 : (double)mb / h->N;
+    return PT_OK;
+}
+
 int lao_state(const pt_handle* h, int8_t* planted, int32_t* loops, int8_t* J, int32_t* E_gs, int32_t* tts)
 {
     if (!h || !h->lao) return PT_ERR_STATE;

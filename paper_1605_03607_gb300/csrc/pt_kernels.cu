@@ -792,6 +792,23 @@ __global__ void pt_tts_kernel(const InstDesc* __restrict__ insts, int32_t target
     }
 }
 
+// Hamming distances between the coldest-slot configurations of every pair
+// of runs of instance 0: dist[r][r2] (block r, thread r2).  Spins are +-1
+// bytes, so two differ exactly when their XOR is 0xFE (7 bits).
+__global__ void pt_hamming_kernel(const InstDesc* __restrict__ insts, int32_t* __restrict__ dist)
+{
+    const InstDesc& in = insts[0];
+    const int R = in.R, NT = in.NT, NW = 2 * in.L * in.L;
+    const int r = blockIdx.x;
+    const uint32_t* a = reinterpret_cast<const uint32_t*>(in.spins + ((size_t)r * NT + in.perm[(size_t)r * NT]) * 4 * NW);
+    for (int r2 = threadIdx.x; r2 < R; r2 += blockDim.x) {
+        const uint32_t* b = reinterpret_cast<const uint32_t*>(in.spins + ((size_t)r2 * NT + in.perm[(size_t)r2 * NT]) * 4 * NW);
+        int bits = 0;
+        for (int w = 0; w < NW; ++w) bits += __popc(a[w] ^ b[w]);
+        dist[(size_t)r * R + r2] = bits / 7;
+    }
+}
+
 }  // namespace
 
 cudaError_t sweep_smem_capacity(int* bytes)
@@ -865,6 +882,13 @@ cudaError_t launch_sweeps(const InstDesc* insts, const Bundle* bundles, int nbun
     else
         pt_sweep_kernel<false, false><<<grid, block, smem_bytes, st>>>(insts, bundles, nbundles, sweep0, nsweeps,
                                                                        xevery, mode, queue);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hamming(const InstDesc* insts, int R, int32_t* dist, cudaStream_t st)
+{
+    if (R <= 0) return cudaSuccess;
+    pt_hamming_kernel<<<R, 256, 0, st>>>(insts, dist);
     return cudaGetLastError();
 }
 

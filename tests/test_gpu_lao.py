@@ -54,3 +54,24 @@ def test_lao_c8_shape_known_target(P):
         assert np.all(s["best"] >= st["E_gs"]) and np.all(s["E"] >= st["E_gs"])
         tts, nhit, target = h.tts(st["E_gs"], 512)
         assert target == st["E_gs"] and 0 <= nhit <= cfg["n_runs"]
+
+
+@pytest.mark.parametrize("planted", [True, False])
+def test_overlaps_match_oracle(P, planted):
+    """Ground / first-excited overlaps of the runs' coldest configurations
+    (pairwise distances on the GPU) against the oracle's definition."""
+    L, NT, R, seed = 4, 16, 32, 20160517
+    betas = W.beta_ladder(NT, 0.1, 3.0)
+    if planted:
+        _, _, J, E_gs = oracle.lao_plant(L, seed, 3, 40)
+    else:
+        J, E_gs = W.random_couplers(L, seed, 3), None
+    with P.PTHandle(L, J, betas, R, seed, 5) as h:
+        h.sweep(1500, 1)
+        st = h.state()
+        if E_gs is None:
+            E_gs = int(st["best"].min())
+        r = h.overlaps(E_gs)
+    ref = oracle.overlaps(st["spins"][:, 0, :], st["E"][:, 0], E_gs)
+    assert r == ref
+    assert r["n_gs"] >= 1
