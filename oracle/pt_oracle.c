@@ -22,6 +22,11 @@
  *   - one step of random adaptive optimisation (Algorithm 1): perturb one
  *     coupler, re-measure TTS, keep the change if TTS increased, otherwise keep
  *     it with probability exp(-beta_RAO |dTTS|) (greedy when beta_RAO = inf).
+ *   - the temperature random walk of every system copy (Sec. III.B): passes
+ *     spent in the hot half of the ladder and completed round trips;
+ *   - planted-solution instances built from frustrated loops and one step of
+ *     loop adaptive optimisation (Sec. IV, Algorithm 2), with the TTS taken
+ *     against the known ground-state energy.
  *
  * Readings where the paper is silent (all fixed identically on both sides):
  *   - spin index i = 8*(r*L + c) + 4*u + k (u = 0 vertical, u = 1 horizontal);
