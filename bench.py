@@ -568,7 +568,8 @@ def run_lao(args):
     achieved = attempts * OPS_PER_ATTEMPT / (sweep_ms / 1e3)
     st = h.lao_state()
     # ground / first-excited overlaps of the engineered instance (Sec. III.B): one
-    # fresh PT pass of the handle's runs, one coldest-slot sample per run
+    # fresh PT pass of the handle's runs, then per run its coldest replica at
+    # each of the two levels
     h.reset(1)
     h.sweep(S, 1)
     ov = h.overlaps(st["E_gs"])

@@ -257,15 +257,16 @@ int lao_begin(pt_handle *h, const pt_rule *rule, uint32_t uid, int32_t n_loops, 
 int lao_run(pt_handle *h, uint32_t step0, int32_t n_steps, int32_t speculation, pt_lao_result *out);
 
 /* Ground-state / first-excited-state overlaps (Sec. III.B) of the runs'
- * current coldest-slot configurations, one sample per run.  Samples with
- * energy E_gs are ground states; the first excited level *E1 is the lowest
- * sampled energy above E_gs (INT32_MAX if none) and its samples are the
- * excited states.  The overlap of two configurations is 1 - 2 h / N (h: the
- * Hamming distance), taken in absolute value (zero fields: a configuration
- * and its global flip are the same state).  *q_gs_gs: lower median over the
- * distinct pairs of ground-state samples, *q_gs_es: over all (ground,
- * excited) pairs; -1 where there is no pair.  The paper reports
- * q_gs_es / q_gs_gs.  Pairwise distances are computed on the GPU. */
+ * current replicas.  The first excited level *E1 is the lowest replica
+ * energy above E_gs (INT32_MAX if none).  Samples: per run, its coldest
+ * replica at energy E_gs (a ground state) and its coldest replica at *E1 (an
+ * excited state), where present.  The overlap of two configurations is
+ * 1 - 2 h / N (h: the Hamming distance), taken in absolute value (zero
+ * fields: a configuration and its global flip are the same state).
+ * *q_gs_gs: lower median over the distinct pairs of ground samples,
+ * *q_gs_es: over all (ground, excited) pairs; -1 where there is no pair.  The
+ * paper reports q_gs_es / q_gs_gs.  Pairwise distances are computed on the
+ * GPU. */
 int pt_overlaps(pt_handle *h, int32_t E_gs, int32_t *n_gs, int32_t *n_es, int32_t *E1, double *q_gs_gs,
                 double *q_gs_es);
 

@@ -296,23 +296,33 @@ class LAOState:
                 "accepted": logs[3][:n_steps]}
 
 
-def overlaps(spins0, E0, E_gs):
-    """Ground / first-excited overlaps (Sec. III.B) of one sample per run:
-    spins0 [R][N] (+-1), energies E0 [R].  Ground samples have E0 == E_gs; the
-    first excited level is the lowest sampled energy above E_gs; overlap
-    |1 - 2 h / N| for Hamming distance h; lower medians over the distinct
-    ground pairs and over all (ground, excited) pairs (-1 without a pair)."""
-    spins0 = np.asarray(spins0)
-    E0 = np.asarray(E0)
-    R, N = spins0.shape
-    gs = [r for r in range(R) if E0[r] == E_gs]
-    above = [int(e) for e in E0 if e > E_gs]
+def overlaps(spins, E, E_gs):
+    """Ground / first-excited overlaps (Sec. III.B) of PT replicas: spins
+    [R][N_T][N] (+-1, slot order), energies E [R][N_T].  The first excited level
+    is the lowest replica energy above E_gs; samples: per run, its coldest
+    replica at E_gs (ground) and its coldest replica at that level (excited);
+    overlap |1 - 2 h / N| for Hamming distance h; lower medians over the
+    distinct ground pairs and over all (ground, excited) pairs (-1 without a
+    pair)."""
+    spins = np.asarray(spins)
+    E = np.asarray(E)
+    R, NT, N = spins.shape
+    above = [int(e) for e in E.ravel() if e > E_gs]
     E1 = min(above) if above else 2**31 - 1
-    es = [r for r in range(R) if E0[r] == E1]
+
+    def pick(level):
+        out = []
+        for r in range(R):
+            for t in range(NT):
+                if E[r, t] == level:
+                    out.append(spins[r, t])
+                    break
+        return out
+
+    gs, es = pick(E_gs), pick(E1)
 
     def q(a, b):
-        h = int(np.sum(spins0[a] != spins0[b]))
-        return abs(N - 2 * h)
+        return abs(N - 2 * int(np.sum(a != b)))
 
     def lower_median(v):
         if not v:

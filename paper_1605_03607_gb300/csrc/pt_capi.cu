@@ -1013,41 +1013,57 @@ int pt_overlaps(pt_handle* h, int32_t E_gs, int32_t* n_gs, int32_t* n_es, int32_
     if (!h) return PT_ERR_ARG;
     Group& g = h->main;
     const int R = h->R, NT = h->NT;
-    int32_t* d = nullptr;
-    CK(dalloc(&d, (size_t)R * R), "cudaMalloc overlaps");
-    std::vector<int32_t> dist((size_t)R * R), E((size_t)R * NT);
-    cudaError_t e = launch_hamming(g.d_desc, R, d, h->stream);
-    ++h->launches;
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(dist.data(), d, sizeof(int32_t) * dist.size(), cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(E.data(), g.E, sizeof(int32_t) * E.size(), cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    cudaFree(d);
-    if (e != cudaSuccess) return cuda_fail(h, e, "overlaps");
-    // samples: each run's coldest slot; the first excited level is the lowest sampled energy above E_gs
+    std::vector<int32_t> E((size_t)R * NT);
+    CK(cudaMemcpyAsync(E.data(), g.E, sizeof(int32_t) * E.size(), cudaMemcpyDeviceToHost, h->stream), "download E");
+    CK(cudaStreamSynchronize(h->stream), "sync overlaps");
+    // E1: the lowest replica energy above E_gs; per run at most one sample of
+    // each level, its coldest replica at that energy
     int32_t e1 = INT32_MAX;
-    std::vector<int> gs, es;
-    for (int r = 0; r < R; ++r) {
-        const int32_t er = E[(size_t)r * NT];
-        if (er == E_gs) gs.push_back(r);
-        else if (er > E_gs && er < e1) e1 = er;
+    for (int32_t x : E) if (x > E_gs && x < e1) e1 = x;
+    std::vector<int32_t> run, slot;
+    int ngs = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        const int32_t level = pass == 0 ? E_gs : e1;
+        for (int r = 0; r < R; ++r)
+            for (int t = 0; t < NT; ++t)
+                if (E[(size_t)r * NT + t] == level) {
+                    run.push_back(r);
+                    slot.push_back(t);
+                    break;
+                }
+        if (pass == 0) ngs = (int)run.size();
     }
-    for (int r = 0; r < R; ++r) if (E[(size_t)r * NT] == e1) es.push_back(r);
-    // |q| = |1 - 2 h / N| (global flip symmetry), lower medians of the integers |N - 2 h|
+    const int n = (int)run.size(), nes = n - ngs;
+    std::vector<int32_t> dist((size_t)n * n);
+    if (n > 0) {
+        int32_t *d = nullptr, *dr = nullptr, *ds = nullptr;
+        cudaError_t e = dalloc(&d, (size_t)n * n);
+        if (e == cudaSuccess) e = dalloc(&dr, (size_t)n);
+        if (e == cudaSuccess) e = dalloc(&ds, (size_t)n);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dr, run.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ds, slot.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = launch_hamming(g.d_desc, n, dr, ds, d, h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dist.data(), d, sizeof(int32_t) * dist.size(), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        ++h->launches;
+        cudaFree(d); cudaFree(dr); cudaFree(ds);
+        if (e != cudaSuccess) return cuda_fail(h, e, "overlaps");
+    }
+    // |q| = |1 - 2 h / N| (global flip symmetry); lower medians of the integers |N - 2 h|
     auto lower_median = [](std::vector<int32_t>& v) -> int32_t {
         if (v.empty()) return -1;
         std::sort(v.begin(), v.end());
         return v[(v.size() + 1) / 2 - 1];
     };
     std::vector<int32_t> a, b;
-    for (size_t i = 0; i < gs.size(); ++i)
-        for (size_t j = i + 1; j < gs.size(); ++j) a.push_back(std::abs(h->N - 2 * dist[(size_t)gs[i] * R + gs[j]]));
-    for (int x : gs)
-        for (int y : es) b.push_back(std::abs(h->N - 2 * dist[(size_t)x * R + y]));
+    for (int i = 0; i < ngs; ++i)
+        for (int j = i + 1; j < ngs; ++j) a.push_back(std::abs(h->N - 2 * dist[(size_t)i * n + j]));
+    for (int i = 0; i < ngs; ++i)
+        for (int j = ngs; j < n; ++j) b.push_back(std::abs(h->N - 2 * dist[(size_t)i * n + j]));
     const int32_t ma = lower_median(a), mb = lower_median(b);
-    if (n_gs) *n_gs = (int32_t)gs.size();
-    if (n_es) *n_es = (int32_t)es.size();
+    if (n_gs) *n_gs = ngs;
+    if (n_es) *n_es = nes;
     if (E1) *E1 = e1;
     if (q_gs_gs) *q_gs_gs = ma < 0 ? -1.0 : (double)ma / h->N;
     if (q_gs_es) *q_gs_es = mb < 0 ? -1.0 : (double)mb / h->N;

@@ -792,20 +792,25 @@ __global__ void pt_tts_kernel(const InstDesc* __restrict__ insts, int32_t target
     }
 }
 
-// Hamming distances between the coldest-slot configurations of every pair
-// of runs of instance 0: dist[r][r2] (block r, thread r2).  Spins are +-1
-// bytes, so two differ exactly when their XOR is 0xFE (7 bits).
-__global__ void pt_hamming_kernel(const InstDesc* __restrict__ insts, int32_t* __restrict__ dist)
+// Hamming distances between n sampled configurations of instance 0, sample
+// k being slot slot[k] of run run[k]: dist[k][k2] (block k, thread k2).
+// Spins are +-1 bytes, so two differ exactly when their XOR is 0xFE (7 bits).
+__global__ void pt_hamming_kernel(const InstDesc* __restrict__ insts, int n, const int32_t* __restrict__ run,
+                                  const int32_t* __restrict__ slot, int32_t* __restrict__ dist)
 {
     const InstDesc& in = insts[0];
-    const int R = in.R, NT = in.NT, NW = 2 * in.L * in.L;
-    const int r = blockIdx.x;
-    const uint32_t* a = reinterpret_cast<const uint32_t*>(in.spins + ((size_t)r * NT + in.perm[(size_t)r * NT]) * 4 * NW);
-    for (int r2 = threadIdx.x; r2 < R; r2 += blockDim.x) {
-        const uint32_t* b = reinterpret_cast<const uint32_t*>(in.spins + ((size_t)r2 * NT + in.perm[(size_t)r2 * NT]) * 4 * NW);
+    const int NT = in.NT, NW = 2 * in.L * in.L;
+    auto conf = [&](int k) {
+        const size_t rep = (size_t)run[k] * NT;
+        return reinterpret_cast<const uint32_t*>(in.spins + (rep + in.perm[rep + slot[k]]) * 4 * NW);
+    };
+    const int k = blockIdx.x;
+    const uint32_t* a = conf(k);
+    for (int k2 = threadIdx.x; k2 < n; k2 += blockDim.x) {
+        const uint32_t* b = conf(k2);
         int bits = 0;
         for (int w = 0; w < NW; ++w) bits += __popc(a[w] ^ b[w]);
-        dist[(size_t)r * R + r2] = bits / 7;
+        dist[(size_t)k * n + k2] = bits / 7;
     }
 }
 
@@ -885,10 +890,11 @@ cudaError_t launch_sweeps(const InstDesc* insts, const Bundle* bundles, int nbun
     return cudaGetLastError();
 }
 
-cudaError_t launch_hamming(const InstDesc* insts, int R, int32_t* dist, cudaStream_t st)
+cudaError_t launch_hamming(const InstDesc* insts, int n, const int32_t* run, const int32_t* slot, int32_t* dist,
+                           cudaStream_t st)
 {
-    if (R <= 0) return cudaSuccess;
-    pt_hamming_kernel<<<R, 256, 0, st>>>(insts, dist);
+    if (n <= 0) return cudaSuccess;
+    pt_hamming_kernel<<<n, 256, 0, st>>>(insts, n, run, slot, dist);
     return cudaGetLastError();
 }
 

@@ -24,9 +24,10 @@ cudaError_t launch_sweeps(const InstDesc* insts, const Bundle* bundles, int nbun
                           int block, int smem_bytes, uint32_t sweep0, int nsweeps, int xevery,
                           int mode, int* queue, cudaStream_t st, bool slot_major = false,
                           bool walk = false);
-// dist [R][R]: spins differing between the coldest-slot configurations of
-// runs r and r2 of instance 0.
-cudaError_t launch_hamming(const InstDesc* insts, int R, int32_t* dist, cudaStream_t st);
+// dist [n][n]: spins differing between sampled configurations of instance 0
+// (sample k: run run[k], slot slot[k]; device arrays).
+cudaError_t launch_hamming(const InstDesc* insts, int n, const int32_t* run, const int32_t* slot, int32_t* dist,
+                           cudaStream_t st);
 // targets (device, one per instance, may be NULL): per-instance target
 // energies instead of `target`.
 cudaError_t launch_tts(const InstDesc* insts, int ninst, int32_t target, int32_t horizon,

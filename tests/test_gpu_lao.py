@@ -58,8 +58,8 @@ def test_lao_c8_shape_known_target(P):
 
 @pytest.mark.parametrize("planted", [True, False])
 def test_overlaps_match_oracle(P, planted):
-    """Ground / first-excited overlaps of the runs' coldest configurations
-    (pairwise distances on the GPU) against the oracle's definition."""
+    """Ground / first-excited overlaps of the runs' replicas (pairwise distances
+    on the GPU) against the oracle's definition."""
     L, NT, R, seed = 4, 16, 32, 20160517
     betas = W.beta_ladder(NT, 0.1, 3.0)
     if planted:
@@ -72,6 +72,6 @@ def test_overlaps_match_oracle(P, planted):
         if E_gs is None:
             E_gs = int(st["best"].min())
         r = h.overlaps(E_gs)
-    ref = oracle.overlaps(st["spins"][:, 0, :], st["E"][:, 0], E_gs)
+    ref = oracle.overlaps(st["spins"], st["E"], E_gs)
     assert r == ref
-    assert r["n_gs"] >= 1
+    assert r["n_gs"] >= 1 and r["n_es"] >= 1
