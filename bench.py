@@ -66,6 +66,19 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def measured_int_issue(P, stream, peak_ops, iters=1 << 18, reps=3):
+    """The integer-issue microbenchmark (pt_int_issue_rate) of every kind, run
+    outside the timed region: measured T ops/s and the fraction of the
+    derived peak, so the derived roofline can be read against the sustained
+    rate of the instruction kinds the sweep is made of."""
+    out = {}
+    for kind in P.INT_ISSUE_KINDS:
+        ops, ms = P.int_issue_rate(kind, iters=iters, reps=reps, stream=stream)
+        out[kind] = {"Tops_s": ops / 1e12, "of_derived_peak": ops / peak_ops if peak_ops else None,
+                     "ms_per_launch": ms}
+    return out
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -319,6 +332,7 @@ def run_gpu(args):
     if rank != 0:
         h.close()
         return 0
+    issue = measured_int_issue(P, stream.cuda_stream, peak_ops)
     cpu = None
     if ws == 1 and not args.no_cpu:
         v1, att1, dt1 = oracle_sample(cfg, args.cpu_sweeps, R)
@@ -355,7 +369,8 @@ def run_gpu(args):
                      "ops_per_attempt": OPS_PER_ATTEMPT,
                      "avg_launch_ms": sweep_ms / max(sweep_launches, 1), "launches": sweep_launches,
                      "peak_source": f"{sms} SMs x {INT_LANES_PER_SM_CLK} lanes x "
-                                    f"{peaks.get('sm_max_mhz', 2070.0)} MHz ({peak_kind} max clock)"},
+                                    f"{peaks.get('sm_max_mhz', 2070.0)} MHz ({peak_kind} max clock)",
+                     "measured_int_issue": issue},
         "cpu_baseline": cpu,
         "clocks": clocks,
     }
@@ -411,6 +426,7 @@ def run_batched(args):
     peak_ops = sms * INT_LANES_PER_SM_CLK * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     achieved = attempts * args.steps * OPS_PER_ATTEMPT / (kern_ms / 1e3)
     sched = {L: b.schedule(L) + (b.mapping(L),) for L in (4, 8, 12, 16)}
+    issue = measured_int_issue(P, stream.cuda_stream, peak_ops)
     print(json.dumps({
         "workload": "batched_256", "metric": METRIC, "value": attempts * args.steps / (wall),
         "unit": UNIT, "steps": args.steps, "warmup": args.warmup, "sweeps_per_step": sweeps,
@@ -418,7 +434,8 @@ def run_batched(args):
         "pt_tts_evals_per_s": 256 * args.steps / wall,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                      "unit": "Tops/s (int32 issue)", "frac": achieved / peak_ops,
-                     "kernel": "pt_sweep_kernel (persistent)", "ops_per_attempt": OPS_PER_ATTEMPT},
+                     "kernel": "pt_sweep_kernel (persistent)", "ops_per_attempt": OPS_PER_ATTEMPT,
+                     "measured_int_issue": issue},
         "schedule": {str(k): v for k, v in sched.items()}, "info": b.info(), "clocks": clocks,
         "peak_source": peak_kind}))
     b.close()
@@ -689,6 +706,34 @@ def run_guided_experiment(args):
     return 0
 
 
+def run_int_issue(args):
+    """The integer-issue microbenchmark alone: every kind, with the SM clock
+    sampled while it runs."""
+    import torch
+    import paper_1605_03607_gb300 as P
+    from paper_1605_03607_gb300 import build as B
+    B.build()
+    stream = torch.cuda.current_stream()
+    peaks, peak_kind = load_peaks()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_ops = sms * INT_LANES_PER_SM_CLK * max_mhz * 1e6
+    P.int_issue_rate(0, iters=1 << 16, reps=args.warmup or 1, stream=stream.cuda_stream)
+    sampler = ClockSampler(0)
+    sampler.start()
+    issue = measured_int_issue(P, stream.cuda_stream, peak_ops, reps=max(args.steps, 1) * 5)
+    clocks = sampler.stop()
+    mhz = (clocks or {}).get("sm_mhz") or max_mhz
+    for v in issue.values():
+        v["lanes_per_sm_clk"] = v["Tops_s"] * 1e12 / (sms * mhz * 1e6)
+    print(json.dumps({"workload": "int_issue", "metric": "32-bit integer operations/s by instruction kind",
+                      "unit": "Tops/s", "derived_peak": peak_ops / 1e12,
+                      "derived_peak_source": f"{sms} SMs x {INT_LANES_PER_SM_CLK} lanes x {max_mhz} MHz "
+                                             f"({peak_kind} max clock)",
+                      "kinds": issue, "clocks": clocks}))
+    return 0
+
+
 def run_profile_case(args):
     """A fixed, small sequence of sweep-kernel launches (for ncu captures):
     fresh runs, then `profile_sweeps` launches of sweeps_per_launch sweeps each,
@@ -728,7 +773,7 @@ def run_profile_case(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="c8_single", choices=["c8_single", "batched_256", "guided", "mixing",
-                                                                      "surrogate", "lao"])
+                                                                      "surrogate", "lao", "int_issue"])
     ap.add_argument("--mixing-runs", type=int, default=1024, help="mixing workload: independent PT chains")
     ap.add_argument("--mixing-emcs", type=int, default=1 << 14, help="mixing workload: EMCS per run")
     ap.add_argument("--guided-S", type=int, default=1 << 14)
@@ -774,6 +819,8 @@ def main():
         return run_lao(args)
     if args.workload == "guided":
         return run_guided_experiment(args)
+    if args.workload == "int_issue":
+        return run_int_issue(args)
     return run_gpu(args)
 
 

@@ -359,6 +359,25 @@ int pt_eval_stats(pt_handle *h, uint64_t *evals, uint64_t *batches, double *devi
  * call, summed (ms, CUDA events on the handle's stream), and their count. */
 int pt_last_sweep_timing(const pt_handle *h, double *ms, int32_t *launches);
 
+/* Integer-issue microbenchmark: the measured counterpart of the sweep
+ * kernel's roofline peak (the sweep is bound by 32-bit integer instruction
+ * issue; the paper has no counterpart).  Runs `kind` on the current device,
+ * 8 CTAs of 256 threads per SM, each thread `iters` loop iterations of
+ * independent dependency chains:
+ *   0 LOP3 (three-input xor), 1 IMAD (32-bit multiply-add), 2 LOP3 and IMAD
+ *   interleaved one to one, 3 DP4A (int8 dot product), each 8 operations per
+ *   iteration; 4 Philox4x32-10 rounds of two states sharing one key schedule
+ *   (4 widening multiplies, 4 three-input xors, 2 key adds: 10 operations).
+ * One untimed launch, then `reps` launches timed with CUDA events on `stream`
+ * (a cudaStream_t; NULL is the default stream).  Writes *ops_per_s (thread
+ * operations per second over the whole device) and, if not NULL,
+ * *ms_per_launch.  Allocates and frees one small device buffer.
+ * Errors: PT_ERR_ARG (kind outside [0, 4], iters outside [1, 2^22], reps
+ * outside [1, 1000], NULL ops_per_s), PT_ERR_OOM, PT_ERR_CUDA; failures are
+ * reported by pt_last_error(NULL). */
+int pt_int_issue_rate(int32_t kind, int32_t iters, int32_t reps, double *ops_per_s,
+                      double *ms_per_launch, void *stream);
+
 /* ---------------------------------------------------------------------
  * Batched PT: many instances of uneven size and temperature count, each
  * with n_runs independent runs (Sec. II), in one graph replay.  Instances

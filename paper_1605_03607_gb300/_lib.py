@@ -89,6 +89,8 @@ SIGNATURES = [
     ("pt_sweep_timing_total", C.c_int, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_uint64)]),
     ("pt_eval_stats", C.c_int, [_VP, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64),
                                 C.POINTER(C.c_double), C.c_int]),
+    ("pt_int_issue_rate", C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double), _VP]),
     ("pt_tts_eval_noalloc", C.c_int, [C.c_int32, _VP, C.c_int32, _VP, C.c_int32, C.c_int32,
                                       C.c_uint32, C.c_uint32, C.c_int32, C.c_int32, C.c_int32, _VP,
                                       _I32P, _I32P, _I32P]),
@@ -146,6 +148,20 @@ def load():
 def select_device(device):
     """Current device of the library's CUDA runtime for this host thread."""
     _check(load().pt_select_device(int(device)), None)
+
+
+INT_ISSUE_KINDS = ("lop3", "imad", "lop3_imad", "dp4a", "philox_round")
+
+
+def int_issue_rate(kind, iters=1 << 16, reps=3, stream=None):
+    """Measured 32-bit integer operations per second of one instruction kind
+    over the whole current device (pt_int_issue_rate); returns (ops_per_s,
+    ms_per_launch).  `kind` is an index or a name of INT_ISSUE_KINDS."""
+    k = INT_ISSUE_KINDS.index(kind) if isinstance(kind, str) else int(kind)
+    ops, ms = C.c_double(), C.c_double()
+    _check(load().pt_int_issue_rate(k, int(iters), int(reps), C.byref(ops), C.byref(ms),
+                                    None if stream is None else C.c_void_p(stream)), None)
+    return ops.value, ms.value
 
 
 def _ptr(a):

@@ -87,6 +87,19 @@ def test_argument_validation_without_gpu(P):
     assert rc == 1 and "2^22" in msg
 
 
+def test_int_issue_microbenchmark_validates_arguments(P):
+    C = ctypes
+    lib = P.load()
+    ops, ms = C.c_double(), C.c_double()
+    for kind, iters, reps in [(-1, 16, 1), (5, 16, 1), (0, 0, 1), (0, (1 << 22) + 1, 1), (0, 16, 0),
+                              (0, 16, 1001)]:
+        assert lib.pt_int_issue_rate(kind, iters, reps, C.byref(ops), C.byref(ms), None) == 1
+    assert lib.pt_int_issue_rate(0, 16, 1, None, C.byref(ms), None) == 1
+    assert "ops_per_s" in lib.pt_last_error(None).decode()
+    with pytest.raises(ValueError):
+        P.int_issue_rate("fp32")
+
+
 def test_python_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     import paper_1605_03607_gb300._lib as lib
     monkeypatch.setattr(lib, "_lib", None)
