@@ -215,27 +215,37 @@ int group_alloc(pt_handle* h, Group& g, int n_inst)
     return PT_OK;
 }
 
+// The new bundle list replaces the group's only when every step succeeded, so
+// a failure leaves the previous schedule in place and launchable.
 int group_schedule(pt_handle* h, Group& g)
 {
-    g.bundles.clear();
+    std::vector<Bundle> bundles;
     const int L2 = g.L * g.L;
     for (int i = 0; i < g.n_inst; ++i)
         for (int r = 0; r < g.R; r += h->ipc) {
             Bundle b;
             b.inst = i; b.run0 = r; b.nitems = std::min(h->ipc, g.R - r); b.sp = h->sp; b.team = h->team;
-            g.bundles.push_back(b);
+            bundles.push_back(b);
         }
-    g.block = (h->team > 0 ? h->sp * h->team : h->sp * L2) * h->ipc;
-    g.smem = (int)bundle_smem_bytes(g.L, g.NT, h->ipc, h->team, g.walk);
-    cudaFree(g.d_bundles);
-    g.d_bundles = nullptr;
-    CK(dalloc(&g.d_bundles, g.bundles.size()), "cudaMalloc bundles");
-    CK(cudaMemcpyAsync(g.d_bundles, g.bundles.data(), sizeof(Bundle) * g.bundles.size(),
-                       cudaMemcpyHostToDevice, h->stream), "upload bundles");
+    const int block = (h->team > 0 ? h->sp * h->team : h->sp * L2) * h->ipc;
+    const int smem = (int)bundle_smem_bytes(g.L, g.NT, h->ipc, h->team, g.walk);
     int cap = 0;
     CK(sweep_smem_capacity(&cap), "shared memory capacity");
-    if (g.smem > cap) return fail(h, PT_ERR_ARG, "bundle needs more shared memory than a CTA can have");
+    if (smem > cap) return fail(h, PT_ERR_ARG, "bundle needs more shared memory than a CTA can have");
     CK(set_sweep_smem_limit(cap), "cudaFuncSetAttribute");
+    Bundle* d = nullptr;
+    CK(dalloc(&d, bundles.size()), "cudaMalloc bundles");
+    const cudaError_t e = cudaMemcpyAsync(d, bundles.data(), sizeof(Bundle) * bundles.size(),
+                                          cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return cuda_fail(h, e, "upload bundles");
+    }
+    cudaFree(g.d_bundles);
+    g.d_bundles = d;
+    g.bundles.swap(bundles);
+    g.block = block;
+    g.smem = smem;
     return PT_OK;
 }
 
@@ -444,8 +454,11 @@ int ensure_candidates(pt_handle* h, int k)
     if (h->cand.n_inst >= k) return PT_OK;
     free_group(h->cand);
     int rc = group_alloc(h, h->cand, k);
-    if (rc) return rc;
-    return group_schedule(h, h->cand);
+    if (!rc) rc = group_schedule(h, h->cand);
+    // a half-built group (n_inst already set, some buffers missing) must not
+    // pass the size check above on a later call
+    if (rc) free_group(h->cand);
+    return rc;
 }
 
 // ------------------------------------------------ planted instances, LAO
@@ -563,6 +576,27 @@ int32_t loops_gs(const int32_t* loops, int n)
     int32_t e = 0;
     for (int m = 0; m < n; ++m) e -= loops[m * PT_LOOP_WORDS + 1] * (loops[m * PT_LOOP_WORDS] - 2);
     return e;
+}
+
+// Mapping (team, slot_parallel, runs_per_cta) of every group of the handle.
+// On failure the handle keeps its previous mapping: a group whose new bundle
+// list could not be built keeps its old one (group_schedule), and the groups
+// already switched are switched back.
+int apply_schedule(pt_handle* h, int team, int sp, int ipc)
+{
+    const int ot = h->team, osp = h->sp, oipc = h->ipc;
+    h->team = team;
+    h->sp = sp;
+    h->ipc = std::min(ipc, h->R);
+    int rc = group_schedule(h, h->main);
+    if (!rc && h->cand.n_inst > 0 && (rc = group_schedule(h, h->cand))) {
+        const std::string why = h->err;
+        h->team = ot; h->sp = osp; h->ipc = oipc;
+        group_schedule(h, h->main);
+        h->err = why;
+    }
+    if (rc) { h->team = ot; h->sp = osp; h->ipc = oipc; }
+    return rc;
 }
 
 }  // namespace
@@ -1230,11 +1264,8 @@ int pt_set_schedule(pt_handle* h, int32_t sp, int32_t ipc, int32_t spl)
     if (spl < 0) return fail(h, PT_ERR_ARG, "sweeps_per_launch must be >= 0");
     int rc = check_schedule(h, h->L, h->NT, nsp, nipc, h->team);
     if (rc) return rc;
-    h->sp = nsp;
-    h->ipc = std::min(nipc, h->R);
+    if ((rc = apply_schedule(h, h->team, nsp, nipc))) return rc;
     if (spl > 0) h->spl = spl;
-    if ((rc = group_schedule(h, h->main))) return rc;
-    if (h->cand.n_inst > 0 && (rc = group_schedule(h, h->cand))) return rc;
     CK(cudaStreamSynchronize(h->stream), "sync schedule");
     return PT_OK;
 }
@@ -1245,11 +1276,7 @@ int pt_set_mapping(pt_handle* h, int32_t team, int32_t slot_parallel, int32_t ru
     const int nsp = slot_parallel > 0 ? slot_parallel : h->sp, nipc = runs_per_cta > 0 ? runs_per_cta : h->ipc;
     int rc = check_schedule(h, h->L, h->NT, nsp, nipc, team);
     if (rc) return rc;
-    h->team = team;
-    h->sp = nsp;
-    h->ipc = std::min(nipc, h->R);
-    if ((rc = group_schedule(h, h->main))) return rc;
-    if (h->cand.n_inst > 0 && (rc = group_schedule(h, h->cand))) return rc;
+    if ((rc = apply_schedule(h, team, nsp, nipc))) return rc;
     CK(cudaStreamSynchronize(h->stream), "sync mapping");
     return PT_OK;
 }
@@ -1272,9 +1299,16 @@ int pt_set_walk_stats(pt_handle* h, int32_t on)
         CK(sweep_smem_capacity(&cap), "shared memory capacity");
         if (bundle_smem_bytes(g.L, g.NT, h->ipc, h->team, true) > cap)
             return fail(h, PT_ERR_ARG, "the current schedule leaves no shared memory for the walk counters");
-        CK(dalloc(&g.whot, reps), "cudaMalloc walk");
-        CK(dalloc(&g.wtrips, reps), "cudaMalloc walk");
-        CK(dalloc(&g.wstate, reps), "cudaMalloc walk");
+        unsigned long long *whot = nullptr, *wtrips = nullptr;
+        uint8_t* wstate = nullptr;
+        cudaError_t e = dalloc(&whot, reps);
+        if (e == cudaSuccess) e = dalloc(&wtrips, reps);
+        if (e == cudaSuccess) e = dalloc(&wstate, reps);
+        if (e != cudaSuccess) {                 // nothing half-allocated stays behind
+            cudaFree(whot); cudaFree(wtrips); cudaFree(wstate);
+            return cuda_fail(h, e, "cudaMalloc walk");
+        }
+        g.whot = whot; g.wtrips = wtrips; g.wstate = wstate;
         g.walk = true;
         for (int i = 0; i < g.n_inst; ++i) {
             const size_t r0 = (size_t)i * g.R * g.NT;
@@ -1292,6 +1326,20 @@ int pt_set_walk_stats(pt_handle* h, int32_t on)
     }
     int rc = upload_desc(h, g);
     if (!rc) rc = group_schedule(h, g);
+    if (rc && g.walk && on) {
+        // the walk kernels need the enlarged shared-memory block of the new
+        // schedule: without it, go back to untracked runs
+        cudaStreamSynchronize(h->stream);
+        cudaFree(g.whot); cudaFree(g.wtrips); cudaFree(g.wstate);
+        g.whot = g.wtrips = nullptr;
+        g.wstate = nullptr;
+        g.walk = false;
+        for (auto& d : g.desc) d.whot = d.wtrips = nullptr, d.wstate = nullptr;
+        const std::string why = h->err;
+        upload_desc(h, g);
+        h->err = why;
+        return rc;
+    }
     if (!rc) rc = walk_clear(h, g);
     if (rc) return rc;
     CK(cudaStreamSynchronize(h->stream), "sync walk");
@@ -1355,8 +1403,12 @@ int pt_autotune(pt_handle* h, int32_t n_inst, int32_t trial_sweeps)
             h->team = team;
             h->sp = sp;
             h->ipc = ipc;
-            if ((rc = group_schedule(h, g))) { h->timing = old_timing; return rc; }
-            if ((rc = group_sweeps(h, g, trial_sweeps, 1))) { h->timing = old_timing; return rc; }
+            if (!(rc = group_schedule(h, g))) rc = group_sweeps(h, g, trial_sweeps, 1);
+            if (rc) {
+                h->timing = old_timing;
+                h->team = old_team; h->sp = old_sp; h->ipc = old_ipc;
+                return rc;
+            }
             CK(cudaStreamSynchronize(h->stream), "sync autotune");
             double ms = 0.0;
             for (int i = 0; i < h->ev_used; ++i) {
@@ -1369,11 +1421,8 @@ int pt_autotune(pt_handle* h, int32_t n_inst, int32_t trial_sweeps)
         }
     }
     h->timing = old_timing;
-    h->team = best_team;
-    h->sp = best_sp;
-    h->ipc = best_ipc;
-    if ((rc = group_schedule(h, h->main))) return rc;
-    if ((rc = group_schedule(h, g))) return rc;
+    h->team = old_team; h->sp = old_sp; h->ipc = old_ipc;
+    if ((rc = apply_schedule(h, best_team, best_sp, best_ipc))) return rc;
     CK(cudaStreamSynchronize(h->stream), "sync autotune");
     return PT_OK;
 }
