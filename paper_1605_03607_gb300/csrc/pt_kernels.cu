@@ -20,6 +20,7 @@
 //     the host-built table, which is non-increasing), so the serial ascending
 //     swap chain is a subtract and compare per pair.
 //   * No tensor cores: this is integer ALU / shared-memory work.
+#include <climits>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -266,6 +267,104 @@ __device__ __forceinline__ int exchange_chain(int32_t* Es, uint8_t* perm, uint8_
     return m;
 }
 
+// The same exchange sweep run by all 32 lanes of one warp (NT <= 64).  Only
+// the carried energy is serial: the warp runs that recurrence uniformly (an
+// instruction issues once for all lanes) and records the accepted pairs as a
+// bit mask.  The slot contents then follow from the mask in parallel: after
+// the pass slot s holds the old content of slot s+1 when pair s was accepted,
+// and otherwise the configuration carried into s, which started at the lowest
+// slot of the run of accepted pairs ending at pair s-1 (s itself when pair s-1
+// was rejected).  The pair criteria cc of this sweep are overwritten with the
+// acceptance bounds E_{p+1} - 2 c_p.  Returns the lowest slot energy.
+template <bool INV>
+__device__ __forceinline__ int exchange_chain_warp(int32_t* Es, uint8_t* perm, uint8_t* inv, uint32_t* xacc,
+                                                   int32_t* cc, int NT, int lane)
+{
+    constexpr int B = 4;
+    const int np = NT - 1;
+    int m = INT_MAX;
+    for (int t = lane; t < NT; t += 32) {
+        const int e = Es[t];
+        m = min(m, e);
+        if (t >= 1) cc[t - 1] = e - 2 * cc[t - 1];
+    }
+    m = __reduce_min_sync(FULL, m);
+    __syncwarp();
+    // serial recurrence of the carried energy, bounds and energies read ahead
+    int ce = Es[0];
+    uint32_t lo = 0u, hi = 0u;
+    int nxe[B], nxt[B];
+#pragma unroll
+    for (int i = 0; i < B; ++i) {
+        nxe[i] = i < np ? Es[i + 1] : 0;
+        nxt[i] = i < np ? cc[i] : 0;
+    }
+    for (int p0 = 0; p0 < np; p0 += B) {
+        int ne[B], tt[B];
+#pragma unroll
+        for (int i = 0; i < B; ++i) {
+            ne[i] = nxe[i];
+            tt[i] = nxt[i];
+        }
+#pragma unroll
+        for (int i = 0; i < B; ++i) {
+            const int q = p0 + B + i;
+            nxe[i] = q < np ? Es[q + 1] : 0;
+            nxt[i] = q < np ? cc[q] : 0;
+        }
+        uint32_t nib = 0u;
+#pragma unroll
+        for (int i = 0; i < B; ++i) {
+            if (p0 + i < np) {
+                const bool a = tt[i] <= ce;          // E_{p+1} - E_carried <= 2 c_p
+                ce = a ? ce : ne[i];
+                nib |= (uint32_t)a << i;
+            }
+        }
+        if (p0 < 32) lo |= nib << p0;
+        else hi |= nib << (p0 - 32);
+    }
+    // every slot's new content from the mask, gathered before any slot is rewritten
+    const unsigned long long mask = ((unsigned long long)hi << 32) | lo;
+    int e_new[2] = {0, 0}, b_new[2] = {0, 0};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int s = lane + 32 * h;
+        if (s < NT) {
+            int src;
+            if (s < np && ((mask >> s) & 1ull)) {
+                src = s + 1;
+            } else {
+                const unsigned long long below = ~mask & ((1ull << s) - 1ull);
+                src = below ? 64 - __clzll((long long)below) : 0;
+            }
+            e_new[h] = Es[src];
+            b_new[h] = perm[src];
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int s = lane + 32 * h;
+        if (s < NT) {
+            Es[s] = e_new[h];
+            perm[s] = (uint8_t)b_new[h];
+            if (INV) inv[b_new[h]] = (uint8_t)s;
+            if (s < np) xacc[s] += (uint32_t)((mask >> s) & 1ull);
+        }
+    }
+    __syncwarp();
+    return m;
+}
+
+// Lowest slot energy of a run, by all 32 lanes of one warp.
+__device__ __forceinline__ int slot_min_warp(const int32_t* Es, int NT, int lane)
+{
+    int m = INT_MAX;
+    for (int t = lane; t < NT; t += 32) m = min(m, Es[t]);
+    return __reduce_min_sync(FULL, m);
+}
+
 template <bool WALK>
 __device__ void process_bundle(const InstDesc* __restrict__ insts, const Bundle bd,
                                uint32_t sweep0, int nsweeps, int xevery, int mode,
@@ -347,6 +446,9 @@ __device__ void process_bundle(const InstDesc* __restrict__ insts, const Bundle 
     const uint32_t k0 = __reduce_or_sync(FULL, in.seed), k1 = __reduce_or_sync(FULL, in.uid);
     const uint32_t runbits = (uint32_t)run << 16;
     const int prep_warp_j0 = TPI - 32;          // last warp of the run prepares exchanges
+    // a run whose threads start on a warp boundary passes its exchange chain
+    // with its first warp; otherwise one thread does
+    const bool warp_pass = ((item * TPI) & 31) == 0;
     auto exch = [&](uint32_t sw_) {
         return (NT > 1) && ((mode == 1) || (xevery > 0 && (sw_ % (uint32_t)xevery) == 0u));
     };
@@ -374,18 +476,21 @@ __device__ void process_bundle(const InstDesc* __restrict__ insts, const Bundle 
             }
         }
         __syncthreads();
-        if (active && j == 0) {
+        if (active && (warp_pass ? j < 32 : j == 0)) {
             int m;
             if (do_x) {
-                m = exchange_chain<false>(Es, perm, nullptr, xacc, ccrit + (s & 1u) * NT, NT);
-                if (WALK)
+                m = warp_pass ? exchange_chain_warp<false>(Es, perm, nullptr, xacc, ccrit + (s & 1u) * NT, NT, j)
+                              : exchange_chain<false>(Es, perm, nullptr, xacc, ccrit + (s & 1u) * NT, NT);
+                if (WALK && j == 0)
                     walk_update(perm, reinterpret_cast<uint32_t*>(ib + lay.whot),
                                 reinterpret_cast<uint32_t*>(ib + lay.wtrips), ib + lay.wstate, NT);
+            } else if (warp_pass) {
+                m = slot_min_warp(Es, NT, j);
             } else {
                 m = Es[0];
                 for (int p = 1; p < NT; ++p) m = min(m, Es[p]);
             }
-            if (mode == 0 && m < misc[0]) {
+            if (j == 0 && mode == 0 && m < misc[0]) {
                 misc[0] = m;
                 misc[1] = (int32_t)s;
             }
@@ -550,6 +655,9 @@ __device__ void process_bundle_sm(const InstDesc* __restrict__ insts, const Bund
     const uint32_t k0 = __reduce_or_sync(FULL, in.seed), k1 = __reduce_or_sync(FULL, in.uid);
     const uint32_t runbits = (uint32_t)run << 16;
     const int prep_warp_j0 = TPI >= 32 ? TPI - 32 : 0;
+    // a run whose threads start on a warp boundary passes its exchange chain
+    // with its first warp; otherwise one thread does
+    const bool warp_pass = TPI >= 32 && ((item * TPI) & 31) == 0;
     auto exch = [&](uint32_t sw_) {
         return (NT > 1) && ((mode == 1) || (xevery > 0 && (sw_ % (uint32_t)xevery) == 0u));
     };
@@ -592,18 +700,21 @@ __device__ void process_bundle_sm(const InstDesc* __restrict__ insts, const Bund
             }
         }
         __syncthreads();
-        if (active && j == 0) {
+        if (active && (warp_pass ? j < 32 : j == 0)) {
             int m;
             if (do_x) {
-                m = exchange_chain<true>(Es, perm, inv, xacc, ccrit + (s & 1u) * NT, NT);
-                if (WALK)
+                m = warp_pass ? exchange_chain_warp<true>(Es, perm, inv, xacc, ccrit + (s & 1u) * NT, NT, j)
+                              : exchange_chain<true>(Es, perm, inv, xacc, ccrit + (s & 1u) * NT, NT);
+                if (WALK && j == 0)
                     walk_update(perm, reinterpret_cast<uint32_t*>(ib + lay.whot),
                                 reinterpret_cast<uint32_t*>(ib + lay.wtrips), ib + lay.wstate, NT);
+            } else if (warp_pass) {
+                m = slot_min_warp(Es, NT, j);
             } else {
                 m = Es[0];
                 for (int p = 1; p < NT; ++p) m = min(m, Es[p]);
             }
-            if (mode == 0 && m < misc[0]) {
+            if (j == 0 && mode == 0 && m < misc[0]) {
                 misc[0] = m;
                 misc[1] = (int32_t)s;
             }
@@ -644,12 +755,11 @@ __device__ void process_bundle_sm(const InstDesc* __restrict__ insts, const Bund
 // SLOT_MAJOR selects the mapping of every bundle of the launch, WALK whether
 // the launch tracks the temperature random walk of every copy (separate
 // instantiations, so each keeps its own register allocation and the untracked
-// kernels carry no walk code).  The slot-major walk kernel is bounded to the
-// untracked kernel's register count (896 threads: <= 72 registers), so
-// tracking keeps the same CTAs per SM; the host still caps slot-major CTAs
-// at 768 threads.
+// kernels carry no walk code).  Both slot-major kernels are bounded to 72
+// registers (as if for 896 threads), which keeps 7 CTAs of 128 threads per SM;
+// the host still caps slot-major CTAs at 768 threads.
 template <bool SLOT_MAJOR, bool WALK>
-__global__ void __launch_bounds__(SLOT_MAJOR ? (WALK ? 896 : MAX_THREADS_SM) : MAX_THREADS)
+__global__ void __launch_bounds__(SLOT_MAJOR ? 896 : MAX_THREADS)
 pt_sweep_kernel(const InstDesc* __restrict__ insts, const Bundle* __restrict__ bundles,
                 int nbundles, uint32_t sweep0, int nsweeps, int xevery, int mode,
                 int* __restrict__ queue)
