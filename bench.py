@@ -55,7 +55,7 @@ INT_LANES_PER_SM_CLK = 128
 # slot_parallel, runs_per_cta, runs).  A launch reads the runs' state once and
 # its write-back stays in L2, so the figure does not depend on the sweeps per
 # launch.  Any other schedule reports null.
-PROFILED_TRAFFIC = {(4, 32, 1, 1024): 17554944}
+PROFILED_TRAFFIC = {(4, 32, 1, 1024): 17564160}
 
 
 def load_peaks():
