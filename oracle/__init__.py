@@ -89,6 +89,7 @@ def _declare(L):
                                   c.c_uint32, c.c_uint32, c.c_int32, c.c_int32, c.c_int,
                                   c.c_uint32, c.c_int, c.c_double, c.c_int,
                                   c.POINTER(c.c_int32)] + [c.c_void_p] * 5
+    L.or_rao_accept.argtypes = [c.c_int32, c.c_int32, c.c_int, c.c_double, c.c_uint32]
     L.or_ground_energy_bipartite.argtypes = [c.c_int, _p(np.int8)]
     L.or_ground_energy_bipartite.restype = c.c_int32
 
@@ -232,6 +233,11 @@ def engineer_draw(L, J, seed, base_uid, step, proposal=0):
                            _u32(step), _u32(proposal), ctypes.byref(e), ctypes.byref(v),
                            ctypes.byref(cu), ctypes.byref(ua))
     return e.value, v.value, cu.value, ua.value
+
+
+def rao_accept(tts_cur, tts_new, direction=1, beta_rao=-1.0, u=0):
+    """Algorithm 1's decision for one candidate (beta_rao < 0: greedy)."""
+    return bool(lib().or_rao_accept(int(tts_cur), int(tts_new), int(direction), float(beta_rao), _u32(u)))
 
 
 def engineer_run(L, J, betas, n_runs, seed, base_uid, S, pass_mult, exchange_every,

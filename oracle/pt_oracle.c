@@ -523,6 +523,20 @@ void or_engineer_draw(int L, const int8_t *J, uint32_t seed, uint32_t base_uid, 
     *u_accept = w[3];
 }
 
+/* Acceptance of a candidate in Algorithm 1: a move that makes the instance
+ * harder (direction +1) or easier (direction -1, the reversed optimisation
+ * of Sec. III.A) is kept; otherwise it is kept with probability
+ * exp(-beta_rao |TTS' - TTS|), decided by the uniform u < floor(p 2^32).
+ * beta_rao < 0 stands for beta = infinity (greedy: never). */
+int or_rao_accept(int32_t tts_cur, int32_t tts_new, int direction, double beta_rao, uint32_t u)
+{
+    int64_t gain = (int64_t)direction * ((int64_t)tts_new - (int64_t)tts_cur);
+    if (gain > 0) return 1;
+    if (beta_rao < 0.0) return 0;
+    double dt = fabs((double)tts_new - (double)tts_cur);
+    return u < prob_to_u32(exp(-beta_rao * dt));
+}
+
 /* Runs n_steps RAO steps t = step0 .. step0+n_steps-1 on J (in place).
  * tts_cur: in = TTS of the current J (if < 0 it is measured with uid = base_uid);
  * out = TTS of the final J.  beta_rao < 0 means greedy (beta = inf).
@@ -551,12 +565,7 @@ int or_engineer_run(int L, int8_t *J, int n_temps, const double *betas, int n_ru
         int rc = or_tts_eval(L, J, n_temps, betas, n_runs, seed, cuid, S, pass_mult,
                              exchange_every, &tn, &nh, &tg);
         if (rc) { J[e] = old; return rc; }
-        int64_t gain = (int64_t)direction * ((int64_t)tn - (int64_t)cur);
-        int accept = gain > 0;
-        if (!accept && beta_rao >= 0.0) {
-            double dt = fabs((double)tn - (double)cur);
-            accept = uacc < prob_to_u32(exp(-beta_rao * dt));
-        }
+        int accept = or_rao_accept(cur, tn, direction, beta_rao, uacc);
         if (accept) cur = tn; else J[e] = old;
         if (log_edge) log_edge[a] = e;
         if (log_old) log_old[a] = old;
@@ -788,10 +797,7 @@ int or_lao_run(int L, int n_temps, const double *betas, int n_runs, uint32_t see
         int32_t eg = *E_gs + old[1] * (old[0] - 2) - rec[1] * (rec[0] - 2), tn;
         rc = tts_known(L, Jc, n_temps, betas, n_runs, seed, ctl[2], S, exchange_every, eg, &tn);
         if (rc) break;
-        int64_t gain = (int64_t)direction * ((int64_t)tn - (int64_t)*tts_cur);
-        int accept = gain > 0;
-        if (!accept && beta_rao >= 0.0)
-            accept = ctl[1] < prob_to_u32(exp(-beta_rao * fabs((double)tn - (double)*tts_cur)));
+        int accept = or_rao_accept(*tts_cur, tn, direction, beta_rao, ctl[1]);
         if (accept) {
             memcpy(J, Jc, (size_t)g->E);
             memcpy(old, rec, sizeof(rec));

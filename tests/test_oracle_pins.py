@@ -358,3 +358,124 @@ def test_engineer_run_replay_and_monotone():
     J1, t1, _ = oracle.engineer_run(L, J0, betas, 4, cfg["seed"], 0, 256, 1, 1, 1, 5)
     J2, t2, _ = oracle.engineer_run(L, J1, betas, 4, cfg["seed"], 0, 256, 1, 1, 6, 7, tts_cur=t1)
     assert t2 == ta and np.array_equal(J2, Ja)
+
+
+# --------------------------------------------------------------------------
+# Records (best energy, first sweep reaching it) against a per-sweep trace.
+# --------------------------------------------------------------------------
+def test_best_first_records_match_min_energy_trace():
+    """first[r] must be the EARLIEST sweep whose lowest replica energy equals
+    the run's final best (0 if the initial state already holds it).  The trace
+    is built by stepping the oracle one sweep at a time; an exchange permutes
+    energies, so the per-sweep minimum is read after it.  The instance is cold
+    enough that the best is revisited many times, so recording the last hit
+    instead of the first fails."""
+    L, R, n = 2, 6, 300
+    J = W.random_couplers(L, 91, 0)
+    betas = W.beta_ladder(6, 0.3, 3.0)
+    straight = oracle.PTState(L, J, betas, R, seed=91, uid=3)
+    straight.sweeps(n, 1)
+    stepped = oracle.PTState(L, J, betas, R, seed=91, uid=3)
+    trace = [stepped.E.min(axis=1).copy()]
+    for _ in range(n):
+        stepped.sweeps(1, 1)
+        trace.append(stepped.E.min(axis=1).copy())
+    trace = np.array(trace)                                   # [n+1, R]; row s = after sweep s
+    revisits = 0
+    for r in range(R):
+        best = trace[:, r].min()
+        hits = np.flatnonzero(trace[:, r] == best)
+        assert straight.best[r] == best
+        assert straight.first[r] == hits[0]
+        revisits += len(hits) > 1 and hits[-1] != hits[0]
+    assert revisits == R                                      # every run revisits its best
+
+
+# --------------------------------------------------------------------------
+# Algorithm 1's acceptance: greedy, Boltzmann branch, reversed direction.
+# --------------------------------------------------------------------------
+def test_rao_accept_greedy_and_reversed():
+    for direction in (1, -1):
+        for cur, new in ((100, 101), (100, 99), (100, 100), (513, 2**16 + 1)):
+            want = direction * (new - cur) > 0          # strictly better in the chosen direction
+            for u in (0, 2**31, 2**32 - 1):
+                assert oracle.rao_accept(cur, new, direction, -1.0, u) == want
+
+
+@pytest.mark.parametrize("direction", [1, -1])
+def test_rao_boltzmann_branch_frequency(direction):
+    """A move that does not improve TTS is kept with probability
+    exp(-beta |dTTS|) (Algorithm 1).  The uniforms are word 3 of the proposal
+    draws of consecutive steps, as in the engineering loop; over n steps the
+    kept fraction must lie within 5 standard errors of the exact value."""
+    L = 4
+    J = W.random_couplers(L, 83, 0)
+    n = 20000
+    us = [oracle.engineer_draw(L, J, 83, 0, t)[3] for t in range(n)]
+    beta = 0.01
+    for dtts in (30, 120, 400):
+        p = math.exp(-beta * dtts)
+        cur = 1000
+        new = cur - direction * dtts                   # worse by dtts in the chosen direction
+        kept = sum(oracle.rao_accept(cur, new, direction, beta, u) for u in us)
+        assert abs(kept / n - p) <= 5 * math.sqrt(p * (1 - p) / n), (dtts, kept / n, p)
+        # the improving move is always kept, whatever the uniform
+        assert all(oracle.rao_accept(cur, cur + direction * dtts, direction, beta, u) for u in us[:200])
+    # a tie has dTTS = 0: probability exp(0) = 1 keeps it under the Boltzmann rule
+    assert all(oracle.rao_accept(500, 500, direction, beta, u) for u in us[:200] if u != 2**32 - 1)
+
+
+def test_engineer_run_decisions_follow_rule():
+    """Every logged decision of a Boltzmann, reversed RAO run equals the
+    pinned acceptance rule applied to the logged TTS values and the step's
+    uniform (word 3 of its proposal draw)."""
+    L = 4
+    J0 = W.random_couplers(L, 85, 0)
+    betas = W.beta_ladder(8, 0.1, 3.0)
+    S, R, seed, base = 128, 4, 85, 0
+    beta_rao = 0.02
+    Jf, tf, log = oracle.engineer_run(L, J0, betas, R, seed, base, S, 1, 1, 0, 16, beta_rao=beta_rao, direction=-1)
+    cur = oracle.tts_eval(L, J0, betas, R, seed, base, S, 1, 1)[0]
+    J = J0.copy()
+    n_boltzmann = 0
+    for a in range(16):
+        e, v, _, u = oracle.engineer_draw(L, J, seed, base, a)
+        assert (e, v) == (log["edge"][a], log["new"][a])
+        want = oracle.rao_accept(cur, log["tts"][a], -1, beta_rao, u)
+        assert bool(log["accept"][a]) == want
+        n_boltzmann += want and log["tts"][a] >= cur
+        if want:
+            cur = log["tts"][a]
+            J[e] = v
+    assert cur == tf and np.array_equal(J, Jf)
+    assert n_boltzmann >= 1                          # the Boltzmann branch was taken at least once
+
+
+# --------------------------------------------------------------------------
+# Proposal draws: coupler uniform over the edges, new value uniform over the
+# five values other than the current one (chi-square at a fixed seed).
+# --------------------------------------------------------------------------
+def test_engineer_draws_uniform():
+    from scipy.stats import chi2
+    L = 4
+    J = W.random_couplers(L, 87, 0)
+    E = len(J)
+    n = 60000
+    edges = np.zeros(E, np.int64)
+    ranks = np.zeros(5, np.int64)
+    for t in range(n):
+        e, v, _, _ = oracle.engineer_draw(L, J, 87, 0, t, proposal=t % 7)
+        allowed = [x for x in (-3, -2, -1, 1, 2, 3) if x != J[e]]
+        assert v in allowed
+        edges[e] += 1
+        ranks[allowed.index(v)] += 1
+    def stat(c):
+        exp = c.sum() / len(c)
+        return float(((c - exp) ** 2 / exp).sum())
+    assert stat(ranks) < chi2.ppf(0.999, 4), ranks
+    assert stat(edges) < chi2.ppf(0.999, E - 1)
+    # a biased draw (mulhi over 6 values, the current one skipped by moving up)
+    # puts twice the mass on one value and is caught by the same bound
+    biased = ranks.copy()
+    biased[0] += ranks[0]
+    assert stat(biased) > chi2.ppf(0.999, 4)
