@@ -115,33 +115,56 @@ struct Tables {
     std::vector<float> xhint;      // [NT-1]
 };
 
+// Writes the FP64 acceptance tables into caller buffers, allocating nothing:
+// thr [NT][KT], xoff [NT], xhint [max(NT-1, 1)], and the ragged exchange
+// thresholds into xthr (capacity xcap entries; xthr NULL only counts them).
+// Returns the exchange-table length, or -1 with *why set when the ladder's
+// tables are too long or not monotone.
+inline int64_t fill_tables(int NT, const double* betas, uint32_t* thr, int64_t* xoff, float* xhint, uint32_t* xthr,
+                           int64_t xcap, const char** why)
+{
+    for (int t = 0; t < NT; ++t) {
+        thr[(size_t)t * KT] = 0xFFFFFFFFu;   // k <= 0 always accepts; entry unused for decisions
+        for (int k = 1; k < KT; ++k)
+            thr[(size_t)t * KT + k] = to_u32_threshold(std::exp(-2.0 * (double)k * betas[t]));
+    }
+    int64_t n = 0;
+    xhint[0] = 0.f;
+    for (int p = 0; p + 1 < NT; ++p) {
+        const double db = betas[p] - betas[p + 1];
+        xoff[p] = n;
+        xhint[p] = (float)(std::log(2.0) / (2.0 * db));
+        uint32_t prev = 0xFFFFFFFFu;
+        for (int64_t h = 1;; ++h) {
+            const uint32_t v = to_u32_threshold(std::exp(-2.0 * (double)h * db));
+            if (v == 0u) break;
+            if (h > (1 << 22)) { *why = "exchange table longer than 2^22 entries (beta gap too small)"; return -1; }
+            if (h > 1 && v > prev) { *why = "exchange table not monotone (host libm)"; return -1; }
+            if (xthr) {
+                if (n >= xcap) { *why = "exchange tables exceed the table capacity"; return -1; }
+                xthr[n] = v;
+            }
+            prev = v;
+            ++n;
+        }
+    }
+    if (NT > 0) xoff[NT - 1] = n;
+    return n;
+}
+
 // Returns an empty string or the reason the ladder is rejected.
 inline std::string build_tables(int NT, const double* betas, Tables& tb)
 {
     tb.thr.assign((size_t)NT * KT, 0u);
-    for (int t = 0; t < NT; ++t) {
-        tb.thr[(size_t)t * KT] = 0xFFFFFFFFu;   // k <= 0 always accepts; entry unused for decisions
-        for (int k = 1; k < KT; ++k)
-            tb.thr[(size_t)t * KT + k] = to_u32_threshold(std::exp(-2.0 * (double)k * betas[t]));
-    }
     tb.xoff.assign((size_t)NT, 0);
-    tb.xthr.clear();
     tb.xhint.assign((size_t)(NT > 1 ? NT - 1 : 1), 0.f);
-    for (int p = 0; p + 1 < NT; ++p) {
-        const double db = betas[p] - betas[p + 1];
-        tb.xoff[p] = (int64_t)tb.xthr.size();
-        tb.xhint[p] = (float)(std::log(2.0) / (2.0 * db));
-        for (int64_t h = 1;; ++h) {
-            const uint32_t v = to_u32_threshold(std::exp(-2.0 * (double)h * db));
-            if (v == 0u) break;
-            if (h > (1 << 22)) return "exchange table longer than 2^22 entries (beta gap too small)";
-            if (!tb.xthr.empty() && h > 1 && v > tb.xthr.back())
-                return "exchange table not monotone (host libm)";
-            tb.xthr.push_back(v);
-        }
-    }
-    if (NT > 0) tb.xoff[NT - 1] = (int64_t)tb.xthr.size();
-    if (tb.xthr.size() > (size_t)INT32_MAX / 2) return "exchange tables too large";
+    const char* why = "";
+    const int64_t n = fill_tables(NT, betas, tb.thr.data(), tb.xoff.data(), tb.xhint.data(), nullptr, 0, &why);
+    if (n < 0) return why;
+    if (n > (int64_t)INT32_MAX / 2) return "exchange tables too large";
+    tb.xthr.assign((size_t)n, 0u);
+    if (fill_tables(NT, betas, tb.thr.data(), tb.xoff.data(), tb.xhint.data(), tb.xthr.data(), n, &why) < 0)
+        return why;
     return "";
 }
 

@@ -18,8 +18,12 @@
 //
 // Every call shares the array, which keeps the previous call's contents; the
 // initialisation kernel rewrites every spin, slot map, energy, record and
-// counter before use.  Calls that overlap on the GPU (different streams or
-// host threads) race on the array and on the host staging buffers.
+// counter before use.  Calls whose GPU work overlaps would race on the array
+// and on the host staging buffers.  Inside one process that cannot happen
+// through this entry point: a call holds a process-wide lock from staging to
+// the final stream synchronisation (also on every error path once work is
+// queued), so calls from several host threads or streams run one after the
+// other.  Two processes each have their own copy of the array.
 //
 // Set-up: the first call on a device (with that device current) resolves the
 // array's device address with cudaGetSymbolAddress and raises the sweep
@@ -27,12 +31,14 @@
 // capture.
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 
 #include <cuda_runtime.h>
 
 #include "../../include/pt.h"
+#include "pt_host.h"
 #include "pt_internal.h"
 #include "pt_kernels.h"
 
@@ -51,6 +57,7 @@ static __device__ __align__(256) unsigned char g_scratch[PT_NOALLOC_BYTES];
 
 // host staging (static: no allocation)
 uint32_t h_thr[MAX_TEMPS * KT];
+int64_t h_xoff64[MAX_TEMPS];
 int32_t h_xoff[MAX_TEMPS];
 float h_xhint[MAX_TEMPS];
 uint32_t h_xthr[MAX_XTHR];
@@ -71,86 +78,17 @@ int noalloc_fail(int code, const char* msg)
     return code;
 }
 
-uint32_t prob_u32(double p)
+// A failed CUDA call: its name and the runtime's message go to
+// pt_last_error(NULL).  Once work may be queued on the stream, the stream is
+// drained first, so the shared array is idle when the call returns and the
+// lock is released.
+int noalloc_cuda_fail(const char* what, cudaError_t e, cudaStream_t st, bool queued)
 {
-    const double x = std::floor(std::ldexp(p, 32));
-    if (x >= 4294967295.0) return 0xFFFFFFFFu;
-    if (x <= 0.0) return 0u;
-    return (uint32_t)x;
-}
-
-int pack(int b0, int b1, int b2, int b3)
-{
-    return (int)((uint32_t)(uint8_t)(int8_t)b0 | ((uint32_t)(uint8_t)(int8_t)b1 << 8) |
-                 ((uint32_t)(uint8_t)(int8_t)b2 << 16) | ((uint32_t)(uint8_t)(int8_t)b3 << 24));
-}
-
-// Kernel layout of the couplers (negated, per cell and colour) and neighbour cells.
-void stage_couplers(int L, const int8_t* J)
-{
-    const int base_v = 16 * L * L, base_h = 16 * L * L + 4 * L * (L - 1);
-    for (int r = 0; r < L; ++r)
-        for (int c = 0; c < L; ++c) {
-            const int cell = r * L + c;
-            for (int col = 0; col < 2; ++col) {
-                const int u = (r + c + col) & 1;
-                uint32_t* w = h_jw + (cell * 2 + col) * 8;
-                for (int k = 0; k < 4; ++k) {
-                    int b[4];
-                    for (int kp = 0; kp < 4; ++kp)
-                        b[kp] = -(u == 0 ? J[16 * cell + 4 * k + kp] : J[16 * cell + 4 * kp + k]);
-                    w[k] = (uint32_t)pack(b[0], b[1], b[2], b[3]);
-                }
-                int jm[4], jp[4], m = cell, p = cell;
-                for (int k = 0; k < 4; ++k) {
-                    if (u == 0) {
-                        jm[k] = r >= 1 ? -J[base_v + ((r - 1) * L + c) * 4 + k] : 0;
-                        jp[k] = r + 1 < L ? -J[base_v + (r * L + c) * 4 + k] : 0;
-                    } else {
-                        jm[k] = c >= 1 ? -J[base_h + (r * (L - 1) + c - 1) * 4 + k] : 0;
-                        jp[k] = c + 1 < L ? -J[base_h + (r * (L - 1) + c) * 4 + k] : 0;
-                    }
-                }
-                if (u == 0) {
-                    if (r >= 1) m = (r - 1) * L + c;
-                    if (r + 1 < L) p = (r + 1) * L + c;
-                } else {
-                    if (c >= 1) m = r * L + c - 1;
-                    if (c + 1 < L) p = r * L + c + 1;
-                }
-                w[4] = (uint32_t)pack(jm[0], jp[0], 0, 0);
-                w[5] = (uint32_t)pack(0, 0, jm[1], jp[1]);
-                w[6] = (uint32_t)pack(jm[2], jp[2], 0, 0);
-                w[7] = (uint32_t)pack(0, 0, jm[3], jp[3]);
-                h_nbr[(cell * 2 + col) * 2 + 0] = (int16_t)m;
-                h_nbr[(cell * 2 + col) * 2 + 1] = (int16_t)p;
-            }
-        }
-}
-
-// FP64 acceptance tables into the static staging; returns the exchange-table
-// length, or -1 (too long / not monotone).
-int64_t stage_tables(int NT, const double* betas)
-{
-    for (int t = 0; t < NT; ++t) {
-        h_thr[t * KT] = 0xFFFFFFFFu;
-        for (int k = 1; k < KT; ++k) h_thr[t * KT + k] = prob_u32(std::exp(-2.0 * (double)k * betas[t]));
-    }
-    int64_t n = 0;
-    for (int p = 0; p + 1 < NT; ++p) {
-        const double db = betas[p] - betas[p + 1];
-        h_xoff[p] = (int32_t)n;
-        h_xhint[p] = (float)(std::log(2.0) / (2.0 * db));
-        for (int64_t h = 1;; ++h) {
-            const uint32_t v = prob_u32(std::exp(-2.0 * (double)h * db));
-            if (v == 0u) break;
-            if (n >= MAX_XTHR) return -1;
-            if (h > 1 && v > h_xthr[n - 1]) return -1;
-            h_xthr[n++] = v;
-        }
-    }
-    h_xoff[NT - 1] = (int32_t)n;
-    return n;
+    static char msg[256];
+    if (queued) cudaStreamSynchronize(st);
+    std::snprintf(msg, sizeof(msg), "pt_tts_eval_noalloc: %s: %s", what, cudaGetErrorString(e));
+    set_global_error(msg);
+    return e == cudaErrorMemoryAllocation ? PT_ERR_OOM : PT_ERR_CUDA;
 }
 
 size_t carve(size_t& off, size_t bytes)
@@ -191,20 +129,24 @@ extern "C" int pt_tts_eval_noalloc(int32_t L, const int8_t* J, int32_t n_edges, 
         return noalloc_fail(PT_ERR_CUDA, "no usable current CUDA device");
     if (!g_base[dev]) {                                   // once per device, this device current
         void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p)
-            return noalloc_fail(PT_ERR_CUDA, "cudaGetSymbolAddress of the no-alloc scratch failed");
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+        if (e != cudaSuccess || !p) return noalloc_cuda_fail("cudaGetSymbolAddress of the scratch array", e, nullptr, false);
         int cap = 0;
-        if (sweep_smem_capacity(&cap) != cudaSuccess || set_sweep_smem_limit(cap) != cudaSuccess)
-            return noalloc_fail(PT_ERR_CUDA, "setting the sweep kernel's shared-memory limit failed");
+        cudaError_t e2 = sweep_smem_capacity(&cap);
+        if (e2 == cudaSuccess) e2 = set_sweep_smem_limit(cap);
+        if (e2 != cudaSuccess) return noalloc_cuda_fail("setting the sweep kernel's shared-memory limit", e2, nullptr, false);
         g_smem_cap[dev] = cap;
         g_base[dev] = static_cast<unsigned char*>(p);
     }
     unsigned char* base = g_base[dev];
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 
-    const int64_t nx = stage_tables(n_temps, betas);
-    if (nx < 0) return noalloc_fail(PT_ERR_ARG, "exchange tables exceed 2^17 entries (beta gaps too small)");
-    stage_couplers(L, J);
+    const char* why = "";
+    const int64_t nx = fill_tables(n_temps, betas, h_thr, h_xoff64, h_xhint, h_xthr, MAX_XTHR, &why);
+    if (nx < 0) return noalloc_fail(PT_ERR_ARG, "exchange tables exceed 2^17 entries (beta gaps too small) or are invalid");
+    for (int t = 0; t < n_temps; ++t) h_xoff[t] = (int32_t)h_xoff64[t];
+    pack_couplers(L, J, h_jw);
+    build_neighbours(L, h_nbr);
 
     // schedule: about 256 threads per run, a multiple of 32, one run per CTA
     const int L2 = L * L;
@@ -262,18 +204,20 @@ extern "C" int pt_tts_eval_noalloc(int32_t L, const int8_t* J, int32_t n_edges, 
     static InstDesc h_desc;
     h_desc = d;
 
+    cudaError_t ce = cudaSuccess;
     auto up = [&](size_t o, const void* src, size_t bytes) {
         return cudaMemcpyAsync(base + o, src, bytes, cudaMemcpyHostToDevice, st);
     };
-    if (up(o_jw, h_jw, 4 * (size_t)L2 * 16) != cudaSuccess) return PT_ERR_CUDA;
-    if (up(o_nbr, h_nbr, 2 * (size_t)L2 * 4) != cudaSuccess) return PT_ERR_CUDA;
-    if (up(o_thr, h_thr, 4 * (size_t)n_temps * KT) != cudaSuccess) return PT_ERR_CUDA;
-    if (up(o_xoff, h_xoff, 4 * (size_t)n_temps) != cudaSuccess) return PT_ERR_CUDA;
-    if (up(o_xhint, h_xhint, 4 * (size_t)n_temps) != cudaSuccess) return PT_ERR_CUDA;
-    if (nx > 0 && up(o_xthr, h_xthr, 4 * (size_t)nx) != cudaSuccess) return PT_ERR_CUDA;
-    if (up(o_desc, &h_desc, sizeof(InstDesc)) != cudaSuccess) return PT_ERR_CUDA;
-    if (up(o_items, h_items, sizeof(int2) * (size_t)n_runs) != cudaSuccess) return PT_ERR_CUDA;
-    if (up(o_bund, h_bundles, sizeof(Bundle) * (size_t)n_runs) != cudaSuccess) return PT_ERR_CUDA;
+    if ((ce = up(o_jw, h_jw, 4 * (size_t)L2 * 16)) != cudaSuccess) return noalloc_cuda_fail("cudaMemcpyAsync (staging upload)", ce, st, true);
+    if ((ce = up(o_nbr, h_nbr, 2 * (size_t)L2 * 4)) != cudaSuccess) return noalloc_cuda_fail("cudaMemcpyAsync (staging upload)", ce, st, true);
+    if ((ce = up(o_thr, h_thr, 4 * (size_t)n_temps * KT)) != cudaSuccess) return noalloc_cuda_fail("cudaMemcpyAsync (staging upload)", ce, st, true);
+    if ((ce = up(o_xoff, h_xoff, 4 * (size_t)n_temps)) != cudaSuccess) return noalloc_cuda_fail("cudaMemcpyAsync (staging upload)", ce, st, true);
+    if ((ce = up(o_xhint, h_xhint, 4 * (size_t)n_temps)) != cudaSuccess) return noalloc_cuda_fail("cudaMemcpyAsync (staging upload)", ce, st, true);
+    if (nx > 0 && (ce = up(o_xthr, h_xthr, 4 * (size_t)nx)) != cudaSuccess)
+        return noalloc_cuda_fail("cudaMemcpyAsync (staging upload)", ce, st, true);
+    if ((ce = up(o_desc, &h_desc, sizeof(InstDesc))) != cudaSuccess) return noalloc_cuda_fail("cudaMemcpyAsync (staging upload)", ce, st, true);
+    if ((ce = up(o_items, h_items, sizeof(int2) * (size_t)n_runs)) != cudaSuccess) return noalloc_cuda_fail("cudaMemcpyAsync (staging upload)", ce, st, true);
+    if ((ce = up(o_bund, h_bundles, sizeof(Bundle) * (size_t)n_runs)) != cudaSuccess) return noalloc_cuda_fail("cudaMemcpyAsync (staging upload)", ce, st, true);
 
     const InstDesc* dd = reinterpret_cast<const InstDesc*>(base + o_desc);
     const int2* di = reinterpret_cast<const int2*>(base + o_items);
@@ -281,19 +225,20 @@ extern "C" int pt_tts_eval_noalloc(int32_t L, const int8_t* J, int32_t n_edges, 
     int32_t* dout = reinterpret_cast<int32_t*>(base + o_out);
     // fresh runs: the init kernel draws every spin and zeroes every counter,
     // the energy kernel sets energies and records
-    if (launch_init(dd, di, n_runs, true, st) != cudaSuccess) return PT_ERR_CUDA;
-    if (launch_energy(dd, di, n_runs, 0, st) != cudaSuccess) return PT_ERR_CUDA;
+    if ((ce = launch_init(dd, di, n_runs, true, st)) != cudaSuccess) return noalloc_cuda_fail("init kernel", ce, st, true);
+    if ((ce = launch_energy(dd, di, n_runs, 0, st)) != cudaSuccess) return noalloc_cuda_fail("energy kernel", ce, st, true);
     const int64_t total = (int64_t)S * pass_mult;
     for (int64_t done = 0; done < total;) {
         const int chunk = (int)(total - done < 4096 ? total - done : 4096);
-        if (launch_sweeps(dd, db, n_runs, n_runs, block, smem, (uint32_t)done, chunk, exchange_every, 0,
-                          nullptr, st) != cudaSuccess)
-            return PT_ERR_CUDA;
+        if ((ce = launch_sweeps(dd, db, n_runs, n_runs, block, smem, (uint32_t)done, chunk, exchange_every, 0,
+                                nullptr, st)) != cudaSuccess)
+            return noalloc_cuda_fail("sweep kernel", ce, st, true);
         done += chunk;
     }
-    if (launch_tts(dd, 1, PT_TARGET_BEST, S, dout, st) != cudaSuccess) return PT_ERR_CUDA;
-    if (cudaMemcpyAsync(h_out, dout, sizeof(h_out), cudaMemcpyDeviceToHost, st) != cudaSuccess) return PT_ERR_CUDA;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return PT_ERR_CUDA;
+    if ((ce = launch_tts(dd, 1, PT_TARGET_BEST, S, dout, st)) != cudaSuccess) return noalloc_cuda_fail("TTS kernel", ce, st, true);
+    if ((ce = cudaMemcpyAsync(h_out, dout, sizeof(h_out), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return noalloc_cuda_fail("cudaMemcpyAsync (result download)", ce, st, true);
+    if ((ce = cudaStreamSynchronize(st)) != cudaSuccess) return noalloc_cuda_fail("cudaStreamSynchronize", ce, st, false);
     *tts = h_out[0];
     if (n_hit) *n_hit = h_out[1];
     if (target) *target = h_out[2];

@@ -41,6 +41,9 @@ def _noalloc(P, L, J, betas, R, seed, uid, S, pass_mult, x):
 @pytest.mark.parametrize("L,NT,R,S,pm,uids", [
     (4, 16, 8, 512, 1, (0, 7)),       # the tiny configuration's shape
     (8, 32, 16, 256, 4, (3, 3)),      # same uid twice: the reused scratch must not leak state
+    (1, 3, 8, 256, 1, (1, 2)),        # one cell: more thread slots per run than temperatures
+    (3, 16, 6, 256, 1, (4, 5)),       # L^2 = 9: slots per run rounded up past n_temps
+    (2, 1, 4, 128, 2, (6, 6)),        # one temperature: no exchange pairs
 ])
 def test_noalloc_matches_handle_path_twice(P, L, NT, R, S, pm, uids):
     seed = 20160511
