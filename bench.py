@@ -50,11 +50,12 @@ UNIT = "spin-flip attempts/s"
 OPS_PER_ATTEMPT = 31.25
 # Integer issue peak per SM and clock: 4 sub-partitions x 32 lanes.
 INT_LANES_PER_SM_CLK = 128
-# DRAM bytes (read + write) of one sweep-kernel launch, from the ncu capture
-# summarised in profiles/pt_sweep_kernel_c8_1024runs.md, keyed by (team,
-# slot_parallel, runs_per_cta, runs).  A launch reads the runs' state once and
-# its write-back stays in L2, so the figure does not depend on the sweeps per
-# launch.  Any other schedule reports null.
+# DRAM bytes (read + write) of one sweep-kernel launch, taken from one ncu
+# capture of the C_8 / 32-temperature / 1024-run launch (dram__bytes_read.sum +
+# dram__bytes_write.sum), keyed by (team, slot_parallel, runs_per_cta, runs).
+# It is a profiled constant, not measured in the bench run: a launch reads the
+# runs' state once and its write-back stays in L2, so the figure does not
+# depend on the sweeps per launch.  Any other schedule reports null.
 PROFILED_TRAFFIC = {(4, 32, 1, 1024): 17564160}
 
 
@@ -314,6 +315,7 @@ def run_gpu(args):
     barrier(ws)
     clocks = sampler.stop()
     launches = h.launch_count() - n0
+    tts_now, hits_now = h.engineer_state()
     evals, batches, eval_ms = h.eval_stats()
     sweep_ms, sweep_launches = h.sweep_timing_total()
     attempts = evals * R * NT * N * S * pm
@@ -359,12 +361,18 @@ def run_gpu(args):
         "pt_tts_evals_per_s": tot_evals / t_dev,
         "rao_steps_per_s": tot_steps / t_dev,
         "accepted_moves": accepted,
+        "instance_state": {"tts_sweeps": tts_now, "n_hit": hits_now, "runs": R, "horizon_S": S,
+                           "unsolved": bool(tts_now > S),
+                           "note": "TTS of the engineered instance after the timed steps; at the unsolved "
+                                   "cap (TTS = S + 1) no candidate can be kept"},
         "e2e": {"value": tot_attempts / t_wall, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "pt_tts_evals_per_s": tot_evals / t_wall},
         "gpu_launches": int(launches),
         "roofline": {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": peak_ops / 1e12,
                      "unit": "Tops/s (int32 issue)", "frac": achieved_ops / peak_ops if peak_ops else None,
                      "traffic": PROFILED_TRAFFIC.get((h.mapping(), *h.schedule()[:2], R * spec)),
+                     "traffic_source": "profiled constant (one ncu capture of this schedule), not measured "
+                                       "in this run",
                      "kernel": "pt_sweep_kernel",
                      "ops_per_attempt": OPS_PER_ATTEMPT,
                      "avg_launch_ms": sweep_ms / max(sweep_launches, 1), "launches": sweep_launches,
@@ -374,15 +382,20 @@ def run_gpu(args):
         "cpu_baseline": cpu,
         "clocks": clocks,
     }
-    print(json.dumps(line))
     h.close()
+    if ws == 1 and not args.no_batched:
+        # the batched configuration, measured after (outside) the timed region above
+        line["batched"] = measure_batched(args, steps=args.batched_steps, warmup=1)
+    print(json.dumps(line))
     return 0
 
 
-def run_batched(args):
+def measure_batched(args, steps, warmup):
     """Batched workload: 256 instances mixed over C_4/8/12/16 with 24..48
     temperatures, 32 runs each; a step is fresh runs + `batch_sweeps` sweeps of
-    every run (one graph replay of the persistent launch) + per-instance TTS."""
+    every run (one graph replay of the persistent launch) + per-instance TTS.
+    Returns the measurement as a dict (attempts/s, PT-TTS evaluations/s,
+    roofline of the persistent sweep kernel, clocks)."""
     import torch
     import paper_1605_03607_gb300 as P
     from paper_1605_03607_gb300 import build as B
@@ -401,7 +414,7 @@ def run_batched(args):
             b.set_mapping(team, int(Ls), sp, ipc)
     elif not args.no_autotune:
         b.autotune(trial_sweeps=32)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         b.reset()
         b.run(sweeps, cfg["exchange_every"])
     sampler = ClockSampler(0)
@@ -409,36 +422,53 @@ def run_batched(args):
     sampler.start()
     kern_ms, wall = 0.0, 0.0
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for _ in range(args.steps):
+    n_solved = 0
+    for _ in range(steps):
         b.reset()
         torch.cuda.synchronize()
         w0 = time.perf_counter()
         e0.record(stream)
         b.run(sweeps, cfg["exchange_every"])
-        b.tts(sweeps)
+        tts, _, _ = b.tts(sweeps)
         e1.record(stream)
         e1.synchronize()
         wall += time.perf_counter() - w0
         kern_ms += b.info()["last_run_ms"]
+        n_solved = int(np.sum(tts <= sweeps))
     clocks = sampler.stop()
     peaks, peak_kind = load_peaks()
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     peak_ops = sms * INT_LANES_PER_SM_CLK * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-    achieved = attempts * args.steps * OPS_PER_ATTEMPT / (kern_ms / 1e3)
+    achieved = attempts * steps * OPS_PER_ATTEMPT / (kern_ms / 1e3)
     sched = {L: b.schedule(L) + (b.mapping(L),) for L in (4, 8, 12, 16)}
-    issue = measured_int_issue(P, stream.cuda_stream, peak_ops)
-    print(json.dumps({
-        "workload": "batched_256", "metric": METRIC, "value": attempts * args.steps / (wall),
-        "unit": UNIT, "steps": args.steps, "warmup": args.warmup, "sweeps_per_step": sweeps,
-        "kernel_attempts_per_s": attempts * args.steps / (kern_ms / 1e3),
-        "pt_tts_evals_per_s": 256 * args.steps / wall,
+    out = {
+        "workload": "batched_256: 256 instances, 64 each of C_4/C_8/C_12/C_16, 24..48 temps (beta [0.1,4]), "
+                    "32 runs each, 2^14 sweeps, one persistent graph-captured launch per size group",
+        "metric": "spin-flip attempts/s", "value": attempts * steps / wall, "unit": UNIT,
+        "steps": steps, "warmup": warmup, "sweeps_per_step": sweeps,
+        "kernel_attempts_per_s": attempts * steps / (kern_ms / 1e3),
+        "pt_tts_evals_per_s": len(inst) * steps / wall,
+        "instances_solved_within_S": n_solved,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                      "unit": "Tops/s (int32 issue)", "frac": achieved / peak_ops,
                      "kernel": "pt_sweep_kernel (persistent)", "ops_per_attempt": OPS_PER_ATTEMPT,
-                     "measured_int_issue": issue},
+                     "avg_launch_ms": kern_ms / max(steps, 1), "peak_source": peak_kind},
         "schedule": {str(k): v for k, v in sched.items()}, "info": b.info(), "clocks": clocks,
-        "peak_source": peak_kind}))
+        "timing": "value over the host wall clock of reset + run + TTS per step; kernel_attempts_per_s "
+                  "and the roofline over the graph replay's CUDA-event time"}
     b.close()
+    return out
+
+
+def run_batched(args):
+    import torch
+    import paper_1605_03607_gb300 as P
+    out = measure_batched(args, steps=args.steps, warmup=args.warmup)
+    peaks, _ = load_peaks()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak_ops = sms * INT_LANES_PER_SM_CLK * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    out["roofline"]["measured_int_issue"] = measured_int_issue(P, torch.cuda.current_stream().cuda_stream, peak_ops)
+    print(json.dumps(out))
     return 0
 
 
@@ -786,6 +816,10 @@ def main():
     ap.add_argument("--batch-mapping", default="",
                     help="batched workload: 'L:team,slot_parallel,runs_per_cta;...' instead of the autotuner")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="default workload: skip the batched measurement that follows the timed steps")
+    ap.add_argument("--batched-steps", type=int, default=2,
+                    help="default workload: timed steps of the batched measurement")
     ap.add_argument("--profile-sweeps", type=int, default=0,
                     help="profiling case: this many sweep launches on the bench instance, then exit")
     ap.add_argument("--profile-shape", default="", help="profiling case: L,n_temps,runs of a seeded C_L instance")

@@ -205,6 +205,14 @@ int engineer_run(pt_handle *h, uint32_t step0, int32_t n_steps, int32_t speculat
 /* Current loop state: TTS of the current couplers. */
 int engineer_current_tts(const pt_handle *h, int32_t *tts);
 
+/* Current loop state of an engineering (Algorithm 1) or LAO (Algorithm 2)
+ * loop: the TTS of the current instance and how many of its runs reached
+ * the target in the evaluation that measured it (fewer than half: the TTS
+ * is the unsolved value, horizon + 1, and no candidate can be kept by the
+ * greedy rule).  Either pointer may be NULL.  PT_ERR_STATE before
+ * engineer_begin / lao_begin. */
+int engineer_current_state(const pt_handle *h, int32_t *tts, int32_t *n_hit);
+
 /* ---------------------------------------------------------------------
  * Planted-solution instances and loop adaptive optimisation (Sec. IV,
  * Algorithm 2).  An instance is a sum of frustrated loops along Chimera

@@ -73,6 +73,7 @@ SIGNATURES = [
     ("lao_state", C.c_int, [_VP, _VP, _VP, _VP, _I32P, _I32P]),
     ("pt_overlaps", C.c_int, [_VP, C.c_int32, _I32P, _I32P, _I32P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("engineer_current_tts", C.c_int, [_VP, _I32P]),
+    ("engineer_current_state", C.c_int, [_VP, _I32P, _I32P]),
     ("pt_checkpoint", C.c_int, [_VP, _VP, C.POINTER(C.c_size_t)]),
     ("pt_restore", C.c_int, [_VP, _VP, C.c_size_t]),
     ("pt_set_schedule", C.c_int, [_VP, C.c_int32, C.c_int32, C.c_int32]),
@@ -333,6 +334,12 @@ class PTHandle:
         t = C.c_int32()
         _check(load().engineer_current_tts(self.h, C.byref(t)), self.h)
         return t.value
+
+    def engineer_state(self):
+        """(TTS, runs that hit the target) of the loop's current instance."""
+        t, n = C.c_int32(), C.c_int32()
+        _check(load().engineer_current_state(self.h, C.byref(t), C.byref(n)), self.h)
+        return t.value, n.value
 
     # -- checkpoint / schedule / accounting
     def checkpoint(self):

@@ -100,6 +100,7 @@ struct pt_handle {
     pt_rule rule{};
     uint32_t base_uid = 0;
     int32_t tts_cur = 0;
+    int32_t hits_cur = 0;      // runs that reached the target in the current instance's evaluation
     std::string err = "no error";
 };
 
@@ -852,10 +853,11 @@ int engineer_begin(pt_handle* h, const pt_rule* rule, uint32_t base_uid, int32_t
         return fail(h, PT_ERR_ARG, "invalid pt_rule");
     h->rule = *rule;
     h->base_uid = base_uid;
-    int32_t t;
-    int rc = pt_tts_eval(h, base_uid, rule->S, rule->pass_mult, rule->exchange_every, &t, nullptr, nullptr);
+    int32_t t, nh;
+    int rc = pt_tts_eval(h, base_uid, rule->S, rule->pass_mult, rule->exchange_every, &t, &nh, nullptr);
     if (rc) return rc;
     h->tts_cur = t;
+    h->hits_cur = nh;
     h->eng = true;
     h->lao = false;
     if (tts0) *tts0 = t;
@@ -897,6 +899,7 @@ int engineer_run(pt_handle* h, uint32_t step0, int32_t n_steps, int32_t spec, pt
             if (acc) {
                 h->J[e[j]] = (int8_t)v[j];
                 h->tts_cur = tn;
+                h->hits_cur = res[(size_t)j * 3 + 1];
                 changed = true;
                 used = j + 1;
                 break;
@@ -961,6 +964,7 @@ int lao_begin(pt_handle* h, const pt_rule* rule, uint32_t uid, int32_t n_loops, 
     std::vector<int32_t> res;
     if ((rc = eval_candidates(h, 1, h->J.data(), &u0, res, h->E_gs))) return rc;
     h->tts_cur = res[0];
+    h->hits_cur = res[1];
     h->lao = true;
     h->eng = false;
     if (tts0) *tts0 = h->tts_cur;
@@ -1027,6 +1031,7 @@ int lao_run(pt_handle* h, uint32_t step0, int32_t n_steps, int32_t spec, pt_lao_
                             sizeof(int32_t) * PT_LOOP_WORDS);
                 h->E_gs = egs[j];
                 h->tts_cur = tts[j];
+                h->hits_cur = res[(size_t)j * 3 + 1];
                 changed = true;
                 used = j + 1;
                 break;
@@ -1167,6 +1172,7 @@ int engineer_guided_step(pt_handle* h, sg_model* m, uint32_t step, int32_t n_pro
     if (acc) {
         h->J[e[jb]] = (int8_t)v[jb];
         h->tts_cur = res[(size_t)best * 3];
+        h->hits_cur = res[(size_t)best * 3 + 1];
         rc = upload_couplers(h, h->main, 0, h->J.data());
         if (rc) return rc;
     }
@@ -1177,6 +1183,14 @@ int engineer_current_tts(const pt_handle* h, int32_t* tts)
 {
     if (!h || !tts || !h->eng) return PT_ERR_STATE;
     *tts = h->tts_cur;
+    return PT_OK;
+}
+
+int engineer_current_state(const pt_handle* h, int32_t* tts, int32_t* n_hit)
+{
+    if (!h || !(h->eng || h->lao)) return PT_ERR_STATE;
+    if (tts) *tts = h->tts_cur;
+    if (n_hit) *n_hit = h->hits_cur;
     return PT_OK;
 }
 
