@@ -166,6 +166,33 @@ int pt_tts_eval_noalloc(int32_t chimera_L, const int8_t *J, int32_t n_edges, con
                         int32_t pass_mult, int32_t exchange_every, void *stream, int32_t *tts,
                         int32_t *n_hit, int32_t *target);
 
+/* PT-TTS evaluation under a doubling sweep budget.  The TTS of Sec. II
+ * needs a sweep budget that grows with the instance's hardness (the paper
+ * adapts the HFS repeat count n for the same reason, Appendix B); here fresh
+ * runs keyed by (seed, uid) run S0 sweeps and are then continued, on the
+ * same random streams, to 2 S0, 4 S0, ... Smax.  At each level Lv the target
+ * is the best energy any run found within Lv sweeps and the TTS is the lower
+ * median first-hit sweep with horizon Lv (pt_tts); the first level with
+ * TTS <= Lv / 4 gives the result (the target pass is then at least four
+ * times the TTS).  If none does, *tts = Smax + 1 (unsolved) and n_hit /
+ * target are those of level Smax.  *level: the deciding level.  Smax must be
+ * S0 * 2^k (k >= 0), Smax <= 2^30.  Resets the handle's runs.  Any output
+ * but tts may be NULL. */
+int pt_tts_eval_doubling(pt_handle *h, uint32_t uid, int32_t S0, int32_t Smax, int32_t exchange_every,
+                         int32_t *tts, int32_t *n_hit, int32_t *target, int32_t *level);
+
+/* PT-TTS evaluations of k instances of the handle's shape in one batched
+ * launch sequence: J holds k coupler vectors [k][n_edges] (values in
+ * [-3, 3]), instance j uses PT key uids[j].  max_sweeps == 0: the fixed pass
+ * of pt_tts_eval (pass_mult * S sweeps, horizon S); > 0: the doubling budget
+ * of pt_tts_eval_doubling from S to max_sweeps.  Outputs have k entries;
+ * level[j] is the deciding level (pass_mult * S for the fixed pass).  Only
+ * tts is required.  The handle's own runs and loop state are untouched.
+ * 1 <= k <= 256. */
+int pt_tts_eval_many(pt_handle *h, int32_t k, const int8_t *J, const uint32_t *uids, int32_t S,
+                     int32_t pass_mult, int32_t max_sweeps, int32_t exchange_every, int32_t *tts,
+                     int32_t *n_hit, int32_t *target, int32_t *level);
+
 /* Random adaptive optimisation (Algorithm 1). */
 typedef struct {
     int32_t S;               /* TTS horizon in sweeps */
@@ -174,6 +201,10 @@ typedef struct {
     int32_t direction;       /* +1: maximise TTS (hard instances); -1: minimise (easy) */
     double beta_rao;         /* < 0: greedy (keep only strict improvements); else
                                 also keep a worse move with prob. exp(-beta |dTTS|) */
+    int32_t max_sweeps;      /* 0: fixed budget (pass_mult * S sweeps, horizon S).
+                                > 0: doubling budget S, 2S, 4S, ... <= max_sweeps on the
+                                same runs (pt_tts_eval_doubling); max_sweeps = S * 2^k,
+                                pass_mult must be 1; unsolved = max_sweeps + 1 */
 } pt_rule;
 
 typedef struct {
@@ -525,7 +556,9 @@ uint64_t sg_launch_count(const sg_model *m);
  * out: `top` results in rank order (accepted = 1 on the kept one, if any);
  * pred (may be NULL): the n_prop predictions; ranked (may be NULL): the
  * proposal indices of out.  1 <= top <= min(n_prop, 16), n_prop <= 1024.
- * Requires engineer_begin and couplers in {+-1, +-2, +-3}. */
+ * Requires engineer_begin and couplers in {+-1, +-2, +-3}.
+ * m == NULL: no ranking; proposals 0..top-1 are evaluated and kept under the
+ * same best-of-top rule (the plain loop at identical acceptance, pred = 0). */
 int engineer_guided_step(pt_handle *h, sg_model *m, uint32_t step, int32_t n_prop, int32_t top,
                          pt_step_result *out, float *pred, int32_t *ranked);
 

@@ -89,6 +89,14 @@ def _declare(L):
                                   c.c_uint32, c.c_uint32, c.c_int32, c.c_int32, c.c_int,
                                   c.c_uint32, c.c_int, c.c_double, c.c_int,
                                   c.POINTER(c.c_int32)] + [c.c_void_p] * 5
+    L.or_engineer_run_budget.argtypes = [c.c_int, _p(np.int8), c.c_int, _p(np.float64), c.c_int,
+                                         c.c_uint32, c.c_uint32, c.c_int32, c.c_int32, c.c_int32, c.c_int,
+                                         c.c_uint32, c.c_int, c.c_double, c.c_int,
+                                         c.POINTER(c.c_int32)] + [c.c_void_p] * 5
+    L.or_tts_eval_doubling.argtypes = [c.c_int, _p(np.int8), c.c_int, _p(np.float64), c.c_int,
+                                       c.c_uint32, c.c_uint32, c.c_int32, c.c_int32, c.c_int,
+                                       c.POINTER(c.c_int32), c.POINTER(c.c_int32), c.POINTER(c.c_int32),
+                                       c.POINTER(c.c_int32)]
     L.or_rao_accept.argtypes = [c.c_int32, c.c_int32, c.c_int, c.c_double, c.c_uint32]
     L.or_ground_energy_bipartite.argtypes = [c.c_int, _p(np.int8)]
     L.or_ground_energy_bipartite.restype = c.c_int32
@@ -226,6 +234,18 @@ def tts_eval(L, J, betas, n_runs, seed, uid, S, pass_mult=1, exchange_every=1):
     return t.value, h.value, tg.value
 
 
+def tts_eval_doubling(L, J, betas, n_runs, seed, uid, S0, Smax, exchange_every=1):
+    """(tts, n_hit, target, level) under the doubling budget S0, 2 S0, ... Smax."""
+    t, h, tg, lv = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    rc = lib().or_tts_eval_doubling(L, np.ascontiguousarray(J, np.int8), len(betas),
+                                    np.ascontiguousarray(betas, np.float64), n_runs, _u32(seed), _u32(uid),
+                                    int(S0), int(Smax), int(exchange_every),
+                                    ctypes.byref(t), ctypes.byref(h), ctypes.byref(tg), ctypes.byref(lv))
+    if rc:
+        raise ValueError("oracle TTS evaluation failed (bad ladder)")
+    return t.value, h.value, tg.value, lv.value
+
+
 def engineer_draw(L, J, seed, base_uid, step, proposal=0):
     e, v = ctypes.c_int32(), ctypes.c_int32()
     cu, ua = ctypes.c_uint32(), ctypes.c_uint32()
@@ -241,16 +261,17 @@ def rao_accept(tts_cur, tts_new, direction=1, beta_rao=-1.0, u=0):
 
 
 def engineer_run(L, J, betas, n_runs, seed, base_uid, S, pass_mult, exchange_every,
-                 step0, n_steps, beta_rao=-1.0, direction=1, tts_cur=-1):
-    """Returns (J_final, tts_final, log) with log a dict of per-step arrays."""
+                 step0, n_steps, beta_rao=-1.0, direction=1, tts_cur=-1, max_sweeps=0):
+    """Returns (J_final, tts_final, log) with log a dict of per-step arrays.
+    max_sweeps > 0: every evaluation uses the doubling budget S .. max_sweeps."""
     J = np.ascontiguousarray(J, np.int8).copy()
     cur = ctypes.c_int32(int(tts_cur))
     logs = {k: np.zeros(max(n_steps, 1), np.int32) for k in ("edge", "old", "new", "tts", "accept")}
-    rc = lib().or_engineer_run(L, J, len(betas), np.ascontiguousarray(betas, np.float64), n_runs,
-                               _u32(seed), _u32(base_uid), int(S), int(pass_mult),
-                               int(exchange_every), _u32(step0), int(n_steps), float(beta_rao),
-                               int(direction), ctypes.byref(cur),
-                               *(logs[k].ctypes.data for k in ("edge", "old", "new", "tts", "accept")))
+    rc = lib().or_engineer_run_budget(L, J, len(betas), np.ascontiguousarray(betas, np.float64), n_runs,
+                                      _u32(seed), _u32(base_uid), int(S), int(pass_mult), int(max_sweeps),
+                                      int(exchange_every), _u32(step0), int(n_steps), float(beta_rao),
+                                      int(direction), ctypes.byref(cur),
+                                      *(logs[k].ctypes.data for k in ("edge", "old", "new", "tts", "accept")))
     if rc:
         raise ValueError("oracle engineering failed")
     return J, cur.value, {k: v[:n_steps] for k, v in logs.items()}

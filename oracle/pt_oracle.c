@@ -496,6 +496,46 @@ int or_tts_eval(int L, const int8_t *J, int n_temps, const double *betas, int n_
     return rc;
 }
 
+/* A TTS evaluation under a doubling sweep budget (the reading used for the
+ * large instances, where Sec. II's TTS needs a budget that grows with the
+ * hardness, as the budget n of Appendix B does for HFS): fresh runs keyed by
+ * (seed, uid) are run to S0 sweeps, then continued to 2 S0, 4 S0, ... up to
+ * Smax.  At each level Lv the target is the best energy any run found within
+ * Lv sweeps and the TTS is taken with horizon Lv; the first level with
+ * TTS <= Lv / 4 gives the result (the target pass is then at least four
+ * times the TTS, as with the fixed 4x pass).  If no level qualifies, the
+ * instance is unsolved: TTS = Smax + 1, with the hits and target of the last
+ * level.  *level receives the level that decided (Smax when unsolved).
+ * Smax must be S0 times a power of two. */
+int or_tts_eval_doubling(int L, const int8_t *J, int n_temps, const double *betas, int n_runs,
+                         uint32_t seed, uint32_t uid, int32_t S0, int32_t Smax, int exchange_every,
+                         int32_t *tts, int32_t *n_hit, int32_t *target, int32_t *level)
+{
+    int N = 8 * L * L;
+    size_t nrep = (size_t)n_runs * n_temps;
+    int8_t *spins = malloc(nrep * N);
+    int32_t *E = malloc(sizeof(int32_t) * nrep);
+    int32_t *best = malloc(sizeof(int32_t) * n_runs), *first = malloc(sizeof(int32_t) * n_runs);
+    uint64_t *macc = calloc(nrep, sizeof(uint64_t));
+    uint64_t *xacc = calloc((size_t)n_runs * (n_temps > 1 ? n_temps - 1 : 1), sizeof(uint64_t));
+    or_pt_init_spins(L, n_temps, n_runs, seed, uid, spins);
+    or_pt_start(L, J, n_temps, n_runs, spins, E, best, first);
+    int rc = 0;
+    int32_t done = 0;
+    for (int32_t lv = S0;; lv *= 2) {
+        rc = or_pt_sweeps(L, J, n_temps, betas, n_runs, seed, uid, spins, E, best, first,
+                          macc, xacc, (uint32_t)done, lv - done, exchange_every);
+        if (rc) break;
+        done = lv;
+        or_tts(n_runs, best, first, INT32_MAX, lv, tts, n_hit, target);
+        *level = lv;
+        if (*tts <= lv / 4) break;
+        if (lv >= Smax) { *tts = Smax + 1; break; }
+    }
+    free(spins); free(E); free(best); free(first); free(macc); free(xacc);
+    return rc;
+}
+
 /* ------------------------------------------------------------------ */
 /* Random adaptive optimisation (Algorithm 1).                          */
 /* Proposal j of step t: one Philox call, key (seed, base_uid), counter */
@@ -542,17 +582,31 @@ int or_rao_accept(int32_t tts_cur, int32_t tts_new, int direction, double beta_r
  * out = TTS of the final J.  beta_rao < 0 means greedy (beta = inf).
  * direction +1 maximises TTS (hard instances), -1 minimises it (Sec. III.A).
  * Per-step log arrays (length n_steps) may be NULL. */
-int or_engineer_run(int L, int8_t *J, int n_temps, const double *betas, int n_runs,
-                    uint32_t seed, uint32_t base_uid, int32_t S, int32_t pass_mult,
-                    int exchange_every, uint32_t step0, int n_steps, double beta_rao,
-                    int direction, int32_t *tts_cur,
-                    int32_t *log_edge, int32_t *log_old, int32_t *log_new,
-                    int32_t *log_tts, int32_t *log_accept)
+/* One candidate's TTS: the fixed pass (pass_mult * S sweeps, horizon S) or,
+ * with max_sweeps > 0, the doubling budget from S to max_sweeps. */
+static int eval_budget(int L, const int8_t *J, int n_temps, const double *betas, int n_runs,
+                       uint32_t seed, uint32_t uid, int32_t S, int32_t pass_mult, int32_t max_sweeps,
+                       int exchange_every, int32_t *tts)
 {
-    int32_t cur = *tts_cur, nh, tg;
+    int32_t nh, tg, lv;
+    if (max_sweeps > 0)
+        return or_tts_eval_doubling(L, J, n_temps, betas, n_runs, seed, uid, S, max_sweeps,
+                                    exchange_every, tts, &nh, &tg, &lv);
+    return or_tts_eval(L, J, n_temps, betas, n_runs, seed, uid, S, pass_mult, exchange_every,
+                       tts, &nh, &tg);
+}
+
+int or_engineer_run_budget(int L, int8_t *J, int n_temps, const double *betas, int n_runs,
+                           uint32_t seed, uint32_t base_uid, int32_t S, int32_t pass_mult,
+                           int32_t max_sweeps, int exchange_every, uint32_t step0, int n_steps,
+                           double beta_rao, int direction, int32_t *tts_cur,
+                           int32_t *log_edge, int32_t *log_old, int32_t *log_new,
+                           int32_t *log_tts, int32_t *log_accept)
+{
+    int32_t cur = *tts_cur;
     if (cur < 0) {
-        int rc = or_tts_eval(L, J, n_temps, betas, n_runs, seed, base_uid, S, pass_mult,
-                             exchange_every, &cur, &nh, &tg);
+        int rc = eval_budget(L, J, n_temps, betas, n_runs, seed, base_uid, S, pass_mult, max_sweeps,
+                             exchange_every, &cur);
         if (rc) return rc;
     }
     for (int a = 0; a < n_steps; ++a) {
@@ -562,8 +616,8 @@ int or_engineer_run(int L, int8_t *J, int n_temps, const double *betas, int n_ru
         int8_t old = J[e];
         J[e] = (int8_t)v;
         int32_t tn;
-        int rc = or_tts_eval(L, J, n_temps, betas, n_runs, seed, cuid, S, pass_mult,
-                             exchange_every, &tn, &nh, &tg);
+        int rc = eval_budget(L, J, n_temps, betas, n_runs, seed, cuid, S, pass_mult, max_sweeps,
+                             exchange_every, &tn);
         if (rc) { J[e] = old; return rc; }
         int accept = or_rao_accept(cur, tn, direction, beta_rao, uacc);
         if (accept) cur = tn; else J[e] = old;
@@ -575,6 +629,18 @@ int or_engineer_run(int L, int8_t *J, int n_temps, const double *betas, int n_ru
     }
     *tts_cur = cur;
     return 0;
+}
+
+int or_engineer_run(int L, int8_t *J, int n_temps, const double *betas, int n_runs,
+                    uint32_t seed, uint32_t base_uid, int32_t S, int32_t pass_mult,
+                    int exchange_every, uint32_t step0, int n_steps, double beta_rao,
+                    int direction, int32_t *tts_cur,
+                    int32_t *log_edge, int32_t *log_old, int32_t *log_new,
+                    int32_t *log_tts, int32_t *log_accept)
+{
+    return or_engineer_run_budget(L, J, n_temps, betas, n_runs, seed, base_uid, S, pass_mult, 0,
+                                  exchange_every, step0, n_steps, beta_rao, direction, tts_cur,
+                                  log_edge, log_old, log_new, log_tts, log_accept);
 }
 
 /* Exact ground-state energy by enumeration of the colour-0 spins: on the

@@ -29,7 +29,7 @@ class PTError(RuntimeError):
 
 class pt_rule(C.Structure):
     _fields_ = [("S", C.c_int32), ("pass_mult", C.c_int32), ("exchange_every", C.c_int32),
-                ("direction", C.c_int32), ("beta_rao", C.c_double)]
+                ("direction", C.c_int32), ("beta_rao", C.c_double), ("max_sweeps", C.c_int32)]
 
 
 class pt_step_result(C.Structure):
@@ -61,6 +61,10 @@ SIGNATURES = [
     ("pt_get_state", C.c_int, [_VP] + [_VP] * 8),
     ("pt_tts", C.c_int, [_VP, C.c_int32, C.c_int32, _I32P, _I32P, _I32P]),
     ("pt_tts_eval", C.c_int, [_VP, C.c_uint32, C.c_int32, C.c_int32, C.c_int32, _I32P, _I32P, _I32P]),
+    ("pt_tts_eval_many", C.c_int, [_VP, C.c_int32, _VP, _VP, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                   _VP, _VP, _VP, _VP]),
+    ("pt_tts_eval_doubling", C.c_int, [_VP, C.c_uint32, C.c_int32, C.c_int32, C.c_int32, _I32P, _I32P, _I32P,
+                                       _I32P]),
     ("pt_set_coupler", C.c_int, [_VP, C.c_int32, C.c_int8]),
     ("pt_get_couplers", C.c_int, [_VP, _VP]),
     ("pt_get_tables", C.c_int, [_VP, _VP, _VP, _VP, C.c_int64, C.POINTER(C.c_int64)]),
@@ -270,8 +274,31 @@ class PTHandle:
         return thr, xoff, xthr[:n.value]
 
     # -- RAO (Algorithm 1)
-    def engineer_begin(self, S, pass_mult=1, exchange_every=1, base_uid=0, beta_rao=-1.0, direction=1):
-        rule = pt_rule(int(S), int(pass_mult), int(exchange_every), int(direction), float(beta_rao))
+    def tts_eval_doubling(self, uid, S0, Smax, exchange_every=1):
+        """(tts, n_hit, target, level) under the doubling budget S0, 2 S0, ... Smax."""
+        t, h, tg, lv = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        _check(load().pt_tts_eval_doubling(self.h, int(uid) & 0xFFFFFFFF, int(S0), int(Smax), int(exchange_every),
+                                           C.byref(t), C.byref(h), C.byref(tg), C.byref(lv)), self.h)
+        return t.value, h.value, tg.value, lv.value
+
+    def tts_eval_many(self, J, uids, S, pass_mult=1, max_sweeps=0, exchange_every=1):
+        """Batched evaluation of k coupler vectors J [k, n_edges] with PT keys uids:
+        dict of k-arrays tts, n_hit, target, level."""
+        J = np.ascontiguousarray(J, np.int8).reshape(-1, self.n_edges)
+        k = J.shape[0]
+        u = np.ascontiguousarray(np.asarray(uids, np.int64) & 0xFFFFFFFF, np.uint32)
+        if len(u) != k:
+            raise ValueError("one uid per coupler vector")
+        out = {n: np.zeros(k, np.int32) for n in ("tts", "n_hit", "target", "level")}
+        _check(load().pt_tts_eval_many(self.h, k, _ptr(J), _ptr(u), int(S), int(pass_mult), int(max_sweeps),
+                                       int(exchange_every), *(_ptr(out[n]) for n in ("tts", "n_hit", "target",
+                                                                                     "level"))), self.h)
+        return out
+
+    def engineer_begin(self, S, pass_mult=1, exchange_every=1, base_uid=0, beta_rao=-1.0, direction=1,
+                       max_sweeps=0):
+        rule = pt_rule(int(S), int(pass_mult), int(exchange_every), int(direction), float(beta_rao),
+                       int(max_sweeps))
         t = C.c_int32()
         _check(load().engineer_begin(self.h, C.byref(rule), int(base_uid) & 0xFFFFFFFF, C.byref(t)), self.h)
         return t.value
@@ -287,7 +314,7 @@ class PTHandle:
 
     def lao_begin(self, S, uid, n_loops, w_max=3, exchange_every=1, beta_rao=-1.0, direction=1):
         """Planted instance with n_loops loops (Algorithm 2); returns its TTS against E_GS."""
-        rule = pt_rule(int(S), 1, int(exchange_every), int(direction), float(beta_rao))
+        rule = pt_rule(int(S), 1, int(exchange_every), int(direction), float(beta_rao), 0)
         t = C.c_int32()
         _check(load().lao_begin(self.h, C.byref(rule), int(uid) & 0xFFFFFFFF, int(n_loops), int(w_max), C.byref(t)),
                self.h)
@@ -320,12 +347,14 @@ class PTHandle:
         return dict(planted=planted, loops=loops, J=J, E_gs=eg.value, tts=t.value)
 
     def engineer_guided_step(self, model, step, n_prop=64, top=4):
-        """One surrogate-guided step; returns (results in rank order, predictions, ranked indices)."""
+        """One best-of-top step; returns (results in rank order, predictions, ranked indices).
+        model None: no ranking, proposals 0..top-1 are evaluated (the plain
+        loop under the same acceptance rule)."""
         out = (pt_step_result * top)()
         pred = np.zeros(n_prop, np.float32)
         ranked = np.zeros(top, np.int32)
-        _check(load().engineer_guided_step(self.h, model.m, int(step) & 0xFFFFFFFF, int(n_prop), int(top), out,
-                                           _ptr(pred), _ptr(ranked)), self.h)
+        _check(load().engineer_guided_step(self.h, None if model is None else model.m, int(step) & 0xFFFFFFFF,
+                                           int(n_prop), int(top), out, _ptr(pred), _ptr(ranked)), self.h)
         keys = ("edge", "old_value", "new_value", "tts_old", "tts_new", "accepted", "cand_uid")
         res = {k: np.array([getattr(out[i], k) for i in range(top)], np.int64) for k in keys}
         return res, pred, ranked

@@ -42,6 +42,7 @@ struct Group {
     InstDesc* d_desc = nullptr;
     int2* d_items = nullptr;
     Bundle* d_bundles = nullptr;
+    Bundle* d_sub = nullptr;         // a subset of the bundles (doubling budget: undecided instances)
     int32_t* d_tts = nullptr;        // [n_inst][3]
     int32_t* d_targets = nullptr;    // [n_inst] per-instance TTS targets (LAO)
     int* d_queue = nullptr;
@@ -101,6 +102,7 @@ struct pt_handle {
     uint32_t base_uid = 0;
     int32_t tts_cur = 0;
     int32_t hits_cur = 0;      // runs that reached the target in the current instance's evaluation
+    std::vector<int32_t> last_levels;   // deciding levels of the last doubling evaluation of candidates
     std::string err = "no error";
 };
 
@@ -138,9 +140,18 @@ void free_group(Group& g)
 {
     cudaFree(g.spins); cudaFree(g.E); cudaFree(g.perm); cudaFree(g.best); cudaFree(g.first);
     cudaFree(g.macc); cudaFree(g.xacc); cudaFree(g.jw); cudaFree(g.d_desc); cudaFree(g.d_items);
-    cudaFree(g.d_bundles); cudaFree(g.d_tts); cudaFree(g.d_queue);
+    cudaFree(g.d_bundles); cudaFree(g.d_sub); cudaFree(g.d_tts); cudaFree(g.d_queue);
     cudaFree(g.whot); cudaFree(g.wtrips); cudaFree(g.wstate); cudaFree(g.d_targets);
     g = Group();
+}
+
+// A doubling budget S0, 2 S0, ... Smax: Smax = S0 * 2^k, Smax <= 2^30 (pass_mult 1).
+bool doubling_ok(int32_t S0, int32_t Smax, int32_t pass_mult)
+{
+    if (S0 < 1 || Smax < S0 || Smax > (1 << 30) || pass_mult != 1) return false;
+    int64_t x = S0;
+    while (x < Smax) x *= 2;
+    return x == Smax;
 }
 
 // Default schedule: about 256 threads per run, a multiple of 32.
@@ -235,14 +246,19 @@ int group_schedule(pt_handle* h, Group& g)
     if (smem > cap) return fail(h, PT_ERR_ARG, "bundle needs more shared memory than a CTA can have");
     CK(set_sweep_smem_limit(cap), "cudaFuncSetAttribute");
     Bundle* d = nullptr;
+    Bundle* dsub = nullptr;
     CK(dalloc(&d, bundles.size()), "cudaMalloc bundles");
-    const cudaError_t e = cudaMemcpyAsync(d, bundles.data(), sizeof(Bundle) * bundles.size(),
-                                          cudaMemcpyHostToDevice, h->stream);
+    cudaError_t e = dalloc(&dsub, bundles.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d, bundles.data(), sizeof(Bundle) * bundles.size(), cudaMemcpyHostToDevice, h->stream);
     if (e != cudaSuccess) {
         cudaFree(d);
+        cudaFree(dsub);
         return cuda_fail(h, e, "upload bundles");
     }
     cudaFree(g.d_bundles);
+    cudaFree(g.d_sub);
+    g.d_sub = dsub;               // room for any subset of the full list
     g.d_bundles = d;
     g.bundles.swap(bundles);
     g.block = block;
@@ -301,8 +317,10 @@ int ensure_events(pt_handle* h, int n)
     return PT_OK;
 }
 
-int group_sweeps(pt_handle* h, Group& g, int64_t n, int xevery)
+int group_sweeps(pt_handle* h, Group& g, int64_t n, int xevery, const Bundle* dsub = nullptr, int nsub = 0)
 {
+    const Bundle* db = dsub ? dsub : g.d_bundles;
+    const int nb = dsub ? nsub : (int)g.bundles.size();
     const int nl = (int)((n + h->spl - 1) / h->spl);
     if (h->timing) {
         int rc = ensure_events(h, 2 * nl);
@@ -313,8 +331,8 @@ int group_sweeps(pt_handle* h, Group& g, int64_t n, int xevery)
     while (done < n) {
         const int chunk = (int)std::min<int64_t>(h->spl, n - done);
         if (h->timing) CK(cudaEventRecord(h->ev[2 * li], h->stream), "event");
-        CK(launch_sweeps(g.d_desc, g.d_bundles, (int)g.bundles.size(), (int)g.bundles.size(), g.block,
-                         g.smem, (uint32_t)g.sweep, chunk, xevery, 0, nullptr, h->stream, h->team > 0, g.walk),
+        CK(launch_sweeps(g.d_desc, db, nb, nb, g.block, g.smem, (uint32_t)g.sweep, chunk, xevery, 0, nullptr,
+                         h->stream, h->team > 0, g.walk),
            "sweep kernel");
         if (g.walk && g.NT > 1 && xevery > 0)
             g.walk_passes += (g.sweep + chunk) / (uint64_t)xevery - g.sweep / (uint64_t)xevery;
@@ -389,6 +407,69 @@ int group_eval(pt_handle* h, Group& g, int32_t S, int32_t pass_mult, int32_t xev
     return collect_timing(h);
 }
 
+// Evaluation of every instance of g under the doubling budget: fresh runs,
+// then levels S0, 2 S0, ... Smax on the same runs.  After each level the TTS
+// of every instance is taken against its best energy within that level
+// (horizon = level); an instance is decided at the first level with
+// TTS <= level / 4, and later levels sweep only the undecided instances'
+// bundles.  Unsolved after Smax: TTS = Smax + 1.  out = n_inst x {tts, hits,
+// target}; levels = the deciding level of each instance.
+int group_eval_doubling(pt_handle* h, Group& g, int32_t S0, int32_t Smax, int32_t xevery, std::vector<int32_t>& out,
+                        std::vector<int32_t>& levels)
+{
+    int rc;
+    if (!h->eb0) {
+        CK(cudaEventCreate(&h->eb0), "cudaEventCreate");
+        CK(cudaEventCreate(&h->eb1), "cudaEventCreate");
+    }
+    if ((rc = upload_desc(h, g))) return rc;
+    CK(cudaEventRecord(h->eb0, h->stream), "event");
+    if ((rc = group_reset(h, g, true))) return rc;
+    const int n = g.n_inst;
+    std::vector<char> open((size_t)n, 1);
+    out.assign((size_t)n * 3, 0);
+    levels.assign((size_t)n, 0);
+    std::vector<Bundle> sub;
+    std::vector<int32_t> lv_out;
+    double ms_total = 0.0;
+    for (int64_t lv = S0;; lv *= 2) {
+        sub.clear();
+        for (const Bundle& b : g.bundles)
+            if (b.inst < n && open[(size_t)b.inst]) sub.push_back(b);
+        CK(cudaMemcpyAsync(g.d_sub, sub.data(), sizeof(Bundle) * sub.size(), cudaMemcpyHostToDevice, h->stream),
+           "upload bundle subset");
+        if ((rc = group_sweeps(h, g, lv - (int64_t)g.sweep, xevery, g.d_sub, (int)sub.size()))) return rc;
+        if ((rc = group_tts(h, g, PT_TARGET_BEST, (int32_t)lv, lv_out))) return rc;   // synchronises
+        if ((rc = collect_timing(h))) return rc;
+        if (h->timing) ms_total += h->last_ms;
+        bool any = false;
+        for (int i = 0; i < n; ++i) {
+            if (!open[(size_t)i]) continue;
+            const int32_t t = lv_out[(size_t)i * 3];
+            const bool last = lv >= Smax;
+            if (t <= lv / 4 || last) {
+                out[(size_t)i * 3 + 0] = t <= lv / 4 ? t : Smax + 1;
+                out[(size_t)i * 3 + 1] = lv_out[(size_t)i * 3 + 1];
+                out[(size_t)i * 3 + 2] = lv_out[(size_t)i * 3 + 2];
+                levels[(size_t)i] = (int32_t)lv;
+                open[(size_t)i] = 0;
+            } else {
+                any = true;
+            }
+        }
+        if (!any) break;
+    }
+    CK(cudaEventRecord(h->eb1, h->stream), "event");
+    CK(cudaEventSynchronize(h->eb1), "sync eval");
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->eb0, h->eb1), "event time");
+    h->eval_ms += ms;
+    h->evals += (uint64_t)n;
+    h->batches += 1;
+    if (h->timing) h->last_ms = ms_total;
+    return PT_OK;
+}
+
 // Draw of proposal j for step t against couplers J (Algorithm 1, one perturbed edge).
 void engineer_draw(const pt_handle* h, const int8_t* J, uint32_t step, uint32_t proposal,
                    int32_t& edge, int32_t& value, uint32_t& uid, uint32_t& uacc)
@@ -444,7 +525,11 @@ int eval_candidates(pt_handle* h, int k, const int8_t* Jc, const uint32_t* uids,
     std::vector<Bundle> sub;
     for (const Bundle& b : keep) if (b.inst < k) sub.push_back(b);
     g.bundles = sub;
-    rc = group_eval(h, g, h->rule.S, h->rule.pass_mult, h->rule.exchange_every, res, target, targets);
+    if (h->rule.max_sweeps > 0 && !targets && target == PT_TARGET_BEST) {
+        rc = group_eval_doubling(h, g, h->rule.S, h->rule.max_sweeps, h->rule.exchange_every, res, h->last_levels);
+    } else {
+        rc = group_eval(h, g, h->rule.S, h->rule.pass_mult, h->rule.exchange_every, res, target, targets);
+    }
     g.n_inst = n_full;
     g.bundles = keep;
     return rc;
@@ -810,6 +895,55 @@ int pt_tts_eval(pt_handle* h, uint32_t uid, int32_t S, int32_t pass_mult, int32_
     return PT_OK;
 }
 
+int pt_tts_eval_doubling(pt_handle* h, uint32_t uid, int32_t S0, int32_t Smax, int32_t xevery, int32_t* tts,
+                         int32_t* n_hit, int32_t* target, int32_t* level)
+{
+    if (!h || !tts) return fail(h, PT_ERR_ARG, "NULL argument");
+    if (!doubling_ok(S0, Smax, 1) || xevery < 0)
+        return fail(h, PT_ERR_ARG, "need S0 >= 1, Smax = S0 * 2^k <= 2^30, exchange_every >= 0");
+    h->uid = uid;
+    h->main.desc[0].uid = uid;
+    std::vector<int32_t> out, levels;
+    int rc = group_eval_doubling(h, h->main, S0, Smax, xevery, out, levels);
+    if (rc) return rc;
+    *tts = out[0];
+    if (n_hit) *n_hit = out[1];
+    if (target) *target = out[2];
+    if (level) *level = levels[0];
+    return PT_OK;
+}
+
+int pt_tts_eval_many(pt_handle* h, int32_t k, const int8_t* J, const uint32_t* uids, int32_t S, int32_t pass_mult,
+                     int32_t max_sweeps, int32_t xevery, int32_t* tts, int32_t* n_hit, int32_t* target,
+                     int32_t* level)
+{
+    if (!h || !J || !uids || !tts) return fail(h, PT_ERR_ARG, "NULL argument");
+    if (k < 1 || k > 256) return fail(h, PT_ERR_ARG, "need 1 <= k <= 256");
+    if (S < 1 || pass_mult < 1 || xevery < 0 || (int64_t)S * pass_mult > (1 << 30))
+        return fail(h, PT_ERR_ARG, "need S >= 1, pass_mult >= 1, S * pass_mult <= 2^30");
+    if (max_sweeps != 0 && !doubling_ok(S, max_sweeps, pass_mult))
+        return fail(h, PT_ERR_ARG, "max_sweeps must be S * 2^k <= 2^30 with pass_mult 1");
+    for (size_t i = 0; i < (size_t)k * h->n_edges; ++i)
+        if (J[i] < -3 || J[i] > 3) return fail(h, PT_ERR_ARG, "coupler outside [-3, 3]");
+    const pt_rule keep = h->rule;
+    h->rule.S = S;
+    h->rule.pass_mult = pass_mult;
+    h->rule.max_sweeps = max_sweeps;
+    h->rule.exchange_every = xevery;
+    std::vector<int32_t> res;
+    int rc = eval_candidates(h, k, J, uids, res);
+    const std::vector<int32_t> lv = h->last_levels;
+    h->rule = keep;
+    if (rc) return rc;
+    for (int j = 0; j < k; ++j) {
+        tts[j] = res[(size_t)j * 3];
+        if (n_hit) n_hit[j] = res[(size_t)j * 3 + 1];
+        if (target) target[j] = res[(size_t)j * 3 + 2];
+        if (level) level[j] = max_sweeps > 0 ? lv[(size_t)j] : S * pass_mult;
+    }
+    return PT_OK;
+}
+
 int pt_set_coupler(pt_handle* h, int32_t edge, int8_t value)
 {
     if (!h) return PT_ERR_ARG;
@@ -851,10 +985,15 @@ int engineer_begin(pt_handle* h, const pt_rule* rule, uint32_t base_uid, int32_t
     if (rule->S < 1 || rule->pass_mult < 1 || rule->exchange_every < 0 ||
         (rule->direction != 1 && rule->direction != -1) || (int64_t)rule->S * rule->pass_mult > (1 << 30))
         return fail(h, PT_ERR_ARG, "invalid pt_rule");
+    if (rule->max_sweeps != 0 && !doubling_ok(rule->S, rule->max_sweeps, rule->pass_mult))
+        return fail(h, PT_ERR_ARG, "max_sweeps must be S * 2^k <= 2^30 with pass_mult 1");
     h->rule = *rule;
     h->base_uid = base_uid;
     int32_t t, nh;
-    int rc = pt_tts_eval(h, base_uid, rule->S, rule->pass_mult, rule->exchange_every, &t, &nh, nullptr);
+    int rc = rule->max_sweeps > 0
+                 ? pt_tts_eval_doubling(h, base_uid, rule->S, rule->max_sweeps, rule->exchange_every, &t, &nh,
+                                        nullptr, nullptr)
+                 : pt_tts_eval(h, base_uid, rule->S, rule->pass_mult, rule->exchange_every, &t, &nh, nullptr);
     if (rc) return rc;
     h->tts_cur = t;
     h->hits_cur = nh;
@@ -952,6 +1091,7 @@ int lao_begin(pt_handle* h, const pt_rule* rule, uint32_t uid, int32_t n_loops, 
         return fail(h, PT_ERR_ARG, pt_last_error(nullptr));
     h->rule = *rule;
     h->rule.pass_mult = 1;                   // the target is known: no longer pass
+    h->rule.max_sweeps = 0;                  // one pass of S sweeps against E_GS
     h->planted = planted;
     h->loops = loops;
     h->J = J;
@@ -1123,12 +1263,13 @@ int lao_state(const pt_handle* h, int8_t* planted, int32_t* loops, int8_t* J, in
 int engineer_guided_step(pt_handle* h, sg_model* m, uint32_t step, int32_t n_prop, int32_t top,
                          pt_step_result* out, float* pred, int32_t* ranked)
 {
-    if (!h || !m) return fail(h, PT_ERR_ARG, "NULL argument");
+    if (!h) return fail(h, PT_ERR_ARG, "NULL argument");
     if (!h->eng) return fail(h, PT_ERR_STATE, "engineer_begin not called");
     if (n_prop < 1 || n_prop > 1024 || top < 1 || top > 16 || top > n_prop)
         return fail(h, PT_ERR_ARG, "need 1 <= top <= min(n_prop, 16), n_prop <= 1024");
-    for (int e = 0; e < h->n_edges; ++e)
-        if (h->J[e] == 0) return fail(h, PT_ERR_STATE, "the surrogate needs couplers in {+-1, +-2, +-3}");
+    if (m)
+        for (int e = 0; e < h->n_edges; ++e)
+            if (h->J[e] == 0) return fail(h, PT_ERR_STATE, "the surrogate needs couplers in {+-1, +-2, +-3}");
     std::vector<int8_t> Jp((size_t)n_prop * h->n_edges);
     std::vector<int32_t> e(n_prop), v(n_prop);
     std::vector<uint32_t> cu(n_prop), ua(n_prop);
@@ -1138,8 +1279,8 @@ int engineer_guided_step(pt_handle* h, sg_model* m, uint32_t step, int32_t n_pro
         std::memcpy(Jj, h->J.data(), h->n_edges);
         Jj[e[j]] = (int8_t)v[j];
     }
-    std::vector<float> y(n_prop);
-    if (sg_forward(m, h->L, n_prop, Jp.data(), y.data()) != PT_OK)
+    std::vector<float> y(n_prop, 0.f);       // without a model every proposal ties: draw order
+    if (m && sg_forward(m, h->L, n_prop, Jp.data(), y.data()) != PT_OK)
         return fail(h, PT_ERR_CUDA, std::string("surrogate forward: ") + sg_last_error(m));
     std::vector<int> order(n_prop);
     for (int j = 0; j < n_prop; ++j) order[j] = j;

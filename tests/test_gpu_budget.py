@@ -1,0 +1,148 @@
+"""Doubling sweep budget and the plain best-of-k step on the GPU vs the oracle.
+
+The doubling budget (levels S0, 2 S0, ... Smax on the same runs; the first
+level with TTS <= level / 4 decides; unsolved = Smax + 1) is compared
+bit-exactly with the oracle's or_tts_eval_doubling, alone and inside the
+engineering loop (Algorithm 1).  At the C_16 / 48-temperature shape, where
+the oracle is too slow, the result is checked by a property that holds at any
+size: the deciding level's TTS is the TTS of one plain pass of that many
+sweeps on the same random streams.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_1605_03607_gb300 as pkg
+    from paper_1605_03607_gb300 import build as b
+    b.build()
+    pkg.load()
+    return pkg
+
+
+CASES = [(2, 4, 4, 4, 64, 93, 0.5), (4, 8, 6, 8, 512, 93, 0.1), (4, 16, 8, 16, 256, 97, 0.1)]
+
+
+@pytest.mark.parametrize("L,NT,R,S0,Smax,seed,bmin", CASES)
+@pytest.mark.parametrize("mapping", [None, (8, 4, 1)])
+def test_tts_eval_doubling_matches_oracle(P, L, NT, R, S0, Smax, seed, bmin, mapping):
+    J = W.random_couplers(L, seed, 1)
+    betas = W.beta_ladder(NT, bmin, 3.0)
+    seen = set()
+    with P.PTHandle(L, J, betas, R, seed, 0) as h:
+        if mapping:
+            h.set_mapping(*mapping)
+        for uid in range(5):
+            got = h.tts_eval_doubling(uid, S0, Smax, 1)
+            want = oracle.tts_eval_doubling(L, J, betas, R, seed, uid, S0, Smax, 1)
+            assert got == want, (uid, got, want)
+            seen.add(got[3])
+    assert len(seen) >= 1
+
+
+def test_doubling_rejects_bad_budget(P):
+    J = W.random_couplers(2, 1, 0)
+    with P.PTHandle(2, J, W.beta_ladder(4, 0.5, 3.0), 2, 1, 0) as h:
+        for S0, Smax in ((8, 12), (8, 4), (0, 8)):
+            with pytest.raises(P.PTError):
+                h.tts_eval_doubling(0, S0, Smax)
+        with pytest.raises(P.PTError):
+            h.engineer_begin(S=8, pass_mult=2, max_sweeps=64)
+
+
+@pytest.mark.parametrize("spec", [1, 4])
+def test_engineer_run_doubling_matches_oracle(P, spec):
+    L, seed, base, S0, Smax, R = 2, 95, 0, 4, 128, 4
+    J0 = W.random_couplers(L, seed, 0)
+    betas = W.beta_ladder(4, 0.5, 3.0)
+    Jf, tf, log = oracle.engineer_run(L, J0, betas, R, seed, base, S0, 1, 1, 0, 10, max_sweeps=Smax)
+    with P.PTHandle(L, J0, betas, R, seed, base) as h:
+        t0 = h.engineer_begin(S=S0, pass_mult=1, exchange_every=1, base_uid=base, max_sweeps=Smax)
+        assert t0 == oracle.tts_eval_doubling(L, J0, betas, R, seed, base, S0, Smax)[0]
+        res = h.engineer_run(0, 10, spec)
+        assert list(res["tts_new"]) == list(log["tts"])
+        assert list(res["accepted"]) == list(log["accept"])
+        assert h.engineer_tts() == tf and np.array_equal(h.couplers(), Jf)
+        assert h.engineer_state()[0] == tf
+
+
+@pytest.mark.parametrize("max_sweeps", [0, 256])
+def test_plain_best_of_k_matches_oracle(P, max_sweeps):
+    """engineer_guided_step without a model evaluates proposals 0..k-1 and keeps
+    the largest TTS (ties: lower index) if it beats the current one: the plain
+    loop under the guided step's acceptance rule."""
+    L, NT, R, seed, uid, S0 = 4, 8, 4, 20160515, 3, 32
+    J = W.random_couplers(L, seed, uid)
+    betas = W.beta_ladder(NT, 0.1, 3.0)
+
+    def ev(Jc, key):
+        if max_sweeps:
+            return oracle.tts_eval_doubling(L, Jc, betas, R, seed, key, S0, max_sweeps)[0]
+        return oracle.tts_eval(L, Jc, betas, R, seed, key, S0, 2, 1)[0]
+
+    with P.PTHandle(L, J, betas, R, seed, uid) as h:
+        tcur = h.engineer_begin(S=S0, pass_mult=1 if max_sweeps else 2, exchange_every=1, base_uid=uid,
+                                max_sweeps=max_sweeps)
+        assert tcur == ev(J, uid)
+        Jcur, kept = J.copy(), 0
+        for step in range(4):
+            res, pred, ranked = h.engineer_guided_step(None, step, n_prop=16, top=4)
+            assert list(ranked) == [0, 1, 2, 3] and np.all(pred == 0)
+            tts = []
+            for j in range(4):
+                e, v, cu, _ = oracle.engineer_draw(L, Jcur, seed, uid, step, j)
+                Jc = Jcur.copy()
+                Jc[e] = v
+                tts.append((ev(Jc, cu), Jc))
+                assert res["edge"][j] == e and res["new_value"][j] == v
+            assert list(res["tts_new"]) == [t for t, _ in tts]
+            best = max(range(4), key=lambda j: (tts[j][0], -j))
+            keep = tts[best][0] > tcur
+            assert list(res["accepted"]) == [1 if (keep and j == best) else 0 for j in range(4)]
+            if keep:
+                Jcur, tcur = tts[best][1], tts[best][0]
+                kept += 1
+            assert h.engineer_tts() == tcur and np.array_equal(h.couplers(), Jcur)
+
+
+def test_doubling_prefix_property_at_c16(P):
+    """Config-5 shape (C_16, 48 temperatures in [0.05, 5], 32 runs): whatever
+    level decides, its TTS, hits and target equal those of one plain pass of
+    that many sweeps keyed by the same uid."""
+    cfg = W.CONFIGS["c16_guided"]
+    J = W.random_couplers(16, cfg["seed"], 0)
+    betas = W.beta_ladder(cfg["n_temps"], cfg["beta_min"], cfg["beta_max"])
+    S0, Smax = 256, 4096
+    with P.PTHandle(16, J, betas, cfg["n_runs"], cfg["seed"], 0) as h:
+        for uid in (0, 1):
+            t, hits, tg, lv = h.tts_eval_doubling(uid, S0, Smax)
+            assert lv in (256, 512, 1024, 2048, 4096)
+            tp, hp, tgp = h.tts_eval(uid, lv, 1, 1)
+            assert (hits, tg) == (hp, tgp)
+            assert t == (tp if tp <= lv // 4 else Smax + 1)
+            if t <= Smax:
+                assert t <= lv // 4
+
+
+@pytest.mark.parametrize("max_sweeps", [0, 256])
+def test_tts_eval_many_matches_oracle(P, max_sweeps):
+    """Batched evaluation of unrelated coupler vectors, each under its own key."""
+    L, NT, R, seed, S0 = 4, 8, 4, 99, 16
+    betas = W.beta_ladder(NT, 0.1, 3.0)
+    Js = np.stack([W.random_couplers(L, seed, i) for i in range(6)])
+    uids = [7, 3, 3, 100, 2**32 - 1, 12]
+    with P.PTHandle(L, Js[0], betas, R, seed, 0) as h:
+        out = h.tts_eval_many(Js, uids, S0, 1 if max_sweeps else 4, max_sweeps)
+    for j in range(6):
+        if max_sweeps:
+            want = oracle.tts_eval_doubling(L, Js[j], betas, R, seed, uids[j], S0, max_sweeps)
+        else:
+            want = oracle.tts_eval(L, Js[j], betas, R, seed, uids[j], S0, 4, 1) + (4 * S0,)
+        got = tuple(int(out[k][j]) for k in ("tts", "n_hit", "target", "level"))
+        assert got == want, (j, got, want)

@@ -479,3 +479,63 @@ def test_engineer_draws_uniform():
     biased = ranks.copy()
     biased[0] += ranks[0]
     assert stat(biased) > chi2.ppf(0.999, 4)
+
+
+# --------------------------------------------------------------------------
+# Doubling budget (the TTS reading for the large instances): the result is
+# the first level Lv in S0, 2 S0, ... Smax whose TTS against the best energy
+# found within Lv sweeps is <= Lv / 4, else unsolved = Smax + 1.  Checked
+# against the same runs stepped level by level and the pinned TTS statistic.
+# --------------------------------------------------------------------------
+def _doubling_by_levels(L, J, betas, R, seed, uid, S0, Smax):
+    st = oracle.PTState(L, J, betas, R, seed=seed, uid=uid)
+    lv = S0
+    while True:
+        st.sweeps(lv - st.sweep, 1)
+        t, h, tg = oracle.tts(st.best, st.first, oracle.TARGET_BEST, lv)
+        if t <= lv // 4:
+            return t, h, tg, lv
+        if lv >= Smax:
+            return Smax + 1, h, tg, lv
+        lv *= 2
+
+
+@pytest.mark.parametrize("L,NT,R,S0,Smax,seed", [(2, 4, 4, 4, 64, 93), (4, 8, 6, 8, 512, 93)])
+def test_doubling_budget_matches_levels(L, NT, R, S0, Smax, seed):
+    J = W.random_couplers(L, seed, 1 if L == 2 else 0)
+    betas = W.beta_ladder(NT, 0.5 if L == 2 else 0.1, 3.0)
+    levels = set()
+    for uid in range(6):
+        got = oracle.tts_eval_doubling(L, J, betas, R, seed, uid, S0, Smax, 1)
+        assert got == _doubling_by_levels(L, J, betas, R, seed, uid, S0, Smax)
+        levels.add((got[3], got[0] > Smax))
+    assert len(levels) >= 2                    # the cases decide at different levels / outcomes
+    # a single level (Smax = S0) is the plain pass of S0 sweeps with the 4x rule applied to it
+    t, h, tg, lv = oracle.tts_eval_doubling(L, J, betas, R, seed, 0, S0, S0, 1)
+    t1, h1, tg1 = oracle.tts_eval(L, J, betas, R, seed, 0, S0, 1, 1)
+    assert (h, tg, lv) == (h1, tg1, S0) and t == (t1 if t1 <= S0 // 4 else S0 + 1)
+
+
+def test_engineer_run_with_doubling_budget_replays():
+    """Every logged candidate TTS is the doubling evaluation of that candidate
+    under its own PT key, and the decisions follow the greedy rule."""
+    L, seed, base = 2, 95, 0
+    J0 = W.random_couplers(L, seed, 0)
+    betas = W.beta_ladder(4, 0.5, 3.0)
+    S0, Smax, R = 4, 128, 4
+    Jf, tf, log = oracle.engineer_run(L, J0, betas, R, seed, base, S0, 1, 1, 0, 10, max_sweeps=Smax)
+    cur = oracle.tts_eval_doubling(L, J0, betas, R, seed, base, S0, Smax)[0]
+    J = J0.copy()
+    for a in range(10):
+        e, v, cu, _ = oracle.engineer_draw(L, J, seed, base, a)
+        Jc = J.copy()
+        Jc[e] = v
+        assert log["tts"][a] == oracle.tts_eval_doubling(L, Jc, betas, R, seed, cu, S0, Smax)[0]
+        assert bool(log["accept"][a]) == (log["tts"][a] > cur)
+        if log["accept"][a]:
+            J, cur = Jc, log["tts"][a]
+    assert cur == tf and np.array_equal(J, Jf)
+    # without a budget the same entry point is the fixed-pass loop
+    a = oracle.engineer_run(L, J0, betas, R, seed, base, 16, 2, 1, 0, 4)
+    b = oracle.engineer_run(L, J0, betas, R, seed, base, 16, 2, 1, 0, 4, max_sweeps=0)
+    assert a[1] == b[1] and all(np.array_equal(a[2][k], b[2][k]) for k in a[2])
