@@ -27,7 +27,10 @@
  *     spin, then k of the horizontal spin), then the vertical inter-cell
  *     couplers (r, c, 0, k)-(r+1, c, 0, k) ordered by (r, c, k), then the
  *     horizontal ones (r, c, 1, k)-(r, c+1, 1, k) ordered by (r, c, k):
- *     16 L^2 + 8 L (L - 1) couplers.  J values must lie in [-3, 3].
+ *     16 L^2 + 8 L (L - 1) couplers.  J values are int8 in [-127, 127], and
+ *     every spin's sum of |J| over its couplers must be <= 127 (the largest
+ *     local field, which sizes the Metropolis table).  Random instances use
+ *     {+-1, +-2, +-3}; planted instances (Sec. IV) sum loop weights.
  *   - Temperature slots t = 0 .. N_T-1 hold inverse temperatures beta_t,
  *     strictly descending (slot 0 is the coldest).
  *   - Random numbers are Philox4x32-10 (Salmon et al., SC'11) with key
@@ -53,7 +56,8 @@ extern "C" {
 #define PT_ERR_STATE 5    /* call not valid in the handle's current state */
 
 #define PT_TARGET_BEST INT32_MAX   /* pt_tts target: the best energy any run found */
-#define PT_KMAX 18                 /* largest |local field| = 6 neighbours x |J| <= 3 */
+#define PT_KMAX 18                 /* largest |local field| of couplers in {+-1, +-2, +-3} */
+#define PT_KMAX_LIMIT 127          /* largest |local field| any instance may have */
 
 typedef struct pt_handle pt_handle;
 
@@ -129,20 +133,44 @@ int pt_tts(pt_handle *h, int32_t E_target, int32_t horizon, int32_t *tts, int32_
 int pt_tts_eval(pt_handle *h, uint32_t uid, int32_t S, int32_t pass_mult,
                 int32_t exchange_every, int32_t *tts, int32_t *n_hit, int32_t *target);
 
-/* Sets coupler `edge` to `value` (|value| <= 3), recomputes the energies of
- * the current configurations and restarts the best/first record from them
- * (best = min over slots, first = current sweep). */
+/* Sets coupler `edge` to `value` (|value| <= 127, every spin's sum of |J|
+ * still <= 127), recomputes the energies of the current configurations and
+ * restarts the best/first record from them (best = min over slots, first =
+ * current sweep).  A change that needs a larger Metropolis table enlarges it
+ * (pt_get_table_rows). */
 int pt_set_coupler(pt_handle *h, int32_t edge, int8_t value);
 
 /* Copies the current couplers (n_edges int8) to the host. */
 int pt_get_couplers(pt_handle *h, int8_t *J);
 
-/* Copies the host-built acceptance tables: thr [n_temps][PT_KMAX + 1] (entry
- * k = 0 unused), xoff [n_temps] (pair p owns xthr[xoff[p] .. xoff[p+1]-1] for
+/* Copies the host-built acceptance tables: thr [n_temps][rows] with rows
+ * from pt_get_table_rows (entry k = 0 unused; row k = floor(exp(-2 k beta)
+ * 2^32)), xoff [n_temps] (pair p owns xthr[xoff[p] .. xoff[p+1]-1] for
  * h = 1..H_p), xthr (capacity xthr_cap entries; may be NULL to query), and the
  * total exchange-table length in *xthr_len. */
 int pt_get_tables(const pt_handle *h, uint32_t *thr, int64_t *xoff, uint32_t *xthr,
                   int64_t xthr_cap, int64_t *xthr_len);
+
+/* Debug builds.  A library compiled with -DPT_DEBUG (build(debug=True):
+ * libpt_gb300_debug.so) checks every data-dependent shared- and global-memory
+ * index of its kernels: table rows, slot-map entries, exchange-table ranges,
+ * run indexes, neighbour words.  A failed check records a code in a device
+ * word and the access goes to index 0 instead, so no kernel faults or leaves
+ * a barrier early; after every launch the host synchronises the stream, reads
+ * and clears the word and prints the first code to stderr.  pt_debug_enabled
+ * returns 1 in such a build, 0 otherwise; pt_debug_status returns (and
+ * clears) the first code seen since the last call, 0 if none (always 0 in a
+ * release build).  Codes: 1 Metropolis table row, 2 slot map, 3 exchange
+ * table range, 4 run index, 5 neighbour word, 6 more than 1024 runs in a
+ * TTS reduction, 7 slot map in the energy kernel. */
+int pt_debug_enabled(void);
+int pt_debug_status(uint32_t *code);
+
+/* Rows per temperature of the Metropolis table (k = 0 .. rows-1): 19 for
+ * couplers in {+-1, +-2, +-3}; otherwise the largest sum of |J| over a
+ * spin's couplers plus one, rounded up to a multiple of 4.  It grows when a
+ * coupler change or candidate needs more and never shrinks. */
+int pt_get_table_rows(const pt_handle *h, int32_t *rows);
 
 /* The paper has no counterpart to this entry point: it is pt_tts_eval for
  * callers that cannot allocate device memory at call time, for instance code
@@ -183,7 +211,7 @@ int pt_tts_eval_doubling(pt_handle *h, uint32_t uid, int32_t S0, int32_t Smax, i
 
 /* PT-TTS evaluations of k instances of the handle's shape in one batched
  * launch sequence: J holds k coupler vectors [k][n_edges] (values in
- * [-3, 3]), instance j uses PT key uids[j].  max_sweeps == 0: the fixed pass
+ * [-127, 127], every spin's sum of |J| <= 127), instance j uses PT key uids[j].  max_sweeps == 0: the fixed pass
  * of pt_tts_eval (pass_mult * S sweeps, horizon S); > 0: the doubling budget
  * of pt_tts_eval_doubling from S to max_sweeps.  Outputs have k entries;
  * level[j] is the deciding level (pass_mult * S for the fixed pass).  Only
@@ -211,6 +239,8 @@ typedef struct {
     int32_t edge, old_value, new_value;
     int32_t tts_old, tts_new, accepted;
     uint32_t cand_uid;
+    int32_t n_runs;          /* PT runs the candidate's evaluation used */
+    int32_t level;           /* sweeps it used: pass_mult * S, or the deciding doubling level */
 } pt_step_result;
 
 /* Starts a loop on the handle's current couplers: measures their TTS with
@@ -233,6 +263,24 @@ int engineer_step(pt_handle *h, uint32_t step, pt_step_result *out);
 int engineer_run(pt_handle *h, uint32_t step0, int32_t n_steps, int32_t speculation,
                  pt_step_result *out);
 
+/* The adaptive budget of Appendix B for engineer_run.  The paper repeats HFS
+ * until the lowest energy is found n+1 times, halves n (start 512, floor 16)
+ * after a step whose wall-clock time exceeds T_max, and uses beta = 6.5 n.
+ * Here n is the number of PT runs a candidate's evaluation uses (runs
+ * 0 .. n-1 of its streams, so a smaller n is a prefix of a larger one), a
+ * step's cost is n times the sweeps that evaluation used (pass_mult * S, or
+ * the deciding level of the doubling budget) in place of T_step, and after a
+ * step whose cost exceeds cost_max the next step uses max(n_min, n / 2) runs.
+ * beta_per_run > 0 sets the Boltzmann beta of each step to beta_per_run * n
+ * (else pt_rule.beta_rao applies).  A speculative batch is cut after the
+ * candidate that halves n, like after a kept one, so results equal those of
+ * single steps.  The current instance keeps the TTS it was measured with.
+ * n0 = 0 switches the rule off; otherwise 1 <= n_min <= n0 <= n_runs. */
+int engineer_set_adaptive(pt_handle *h, int32_t n0, int32_t n_min, int64_t cost_max, double beta_per_run);
+
+/* Runs the next engineering step will use (n_runs without the adaptive rule). */
+int engineer_adaptive_runs(const pt_handle *h, int32_t *n);
+
 /* Current loop state: TTS of the current couplers. */
 int engineer_current_tts(const pt_handle *h, int32_t *tts);
 
@@ -251,10 +299,12 @@ int engineer_current_state(const pt_handle *h, int32_t *tts, int32_t *n_hit);
  * planted configuration is a ground state of the sum and its energy
  * E_GS = sum over loops of -w (len - 2) is known: PT-TTS evaluations use it
  * as the target (one pass of S sweeps).  Loops: simple cycles of length 4
- * (probability 0.1) or 6, weight w uniform in 1..w_max (w_max <= 3), every
- * edge satisfied by the planted state except one; couplers of overlapping
- * loops add, and a draw that would take a coupler outside [-3, 3] is
- * redrawn.  Random draws: Philox kind 4 with key (seed, uid); the counters
+ * (probability 0.1) or 6, weight w uniform in 1..w_max (the paper uses
+ * integer weights in [1, 5]), every edge satisfied by the planted state
+ * except one; couplers of overlapping loops add.  A placement that would take
+ * a coupler outside [-127, 127] or a spin's sum of |J| above 127 (the
+ * engine's int8 couplers and table bound) is redrawn; at the paper's
+ * parameters no placement reaches these bounds.  Random draws: Philox kind 4 with key (seed, uid); the counters
  * are documented with lao_plant below.
  * --------------------------------------------------------------------- */
 #define PT_LOOP_WORDS 9   /* loop record: len, w, frustrated position, edges[6] (-1 unused) */
@@ -429,7 +479,8 @@ int pt_int_issue_rate(int32_t kind, int32_t iters, int32_t reps, double *ops_per
 typedef struct {
     int32_t chimera_L;       /* 1..16 */
     int32_t n_temps;         /* 1..64 */
-    const int8_t *J;         /* 16 L^2 + 8 L (L-1) couplers in [-3, 3], read during the call */
+    const int8_t *J;         /* 16 L^2 + 8 L (L-1) int8 couplers (|J| <= 127, every spin's sum of
+                                |J| <= 127), read during the call */
     const double *betas;     /* n_temps, strictly descending, > 0 */
     uint32_t uid;            /* second key word of this instance's random streams */
 } pt_instance_desc;

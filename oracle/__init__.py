@@ -54,7 +54,8 @@ def _declare(L):
     L.or_spin_colour.argtypes = [c.c_int, c.c_int]
     L.or_energy.argtypes = [c.c_int, _p(np.int8), _p(np.int8)]
     L.or_energy.restype = c.c_int32
-    L.or_metropolis_thresholds.argtypes = [c.c_int, _p(np.float64), _p(np.uint32)]
+    L.or_metropolis_thresholds.argtypes = [c.c_int, _p(np.float64), c.c_int, _p(np.uint32)]
+    L.or_coupler_kmax.argtypes = [c.c_int, _p(np.int8)]
     L.or_exchange_thresholds.argtypes = [c.c_int, _p(np.float64), c.c_void_p, c.c_void_p]
     L.or_exchange_thresholds.restype = c.c_int64
     L.or_pt_init_spins.argtypes = [c.c_int, c.c_int, c.c_int, c.c_uint32, c.c_uint32, _p(np.int8)]
@@ -93,6 +94,10 @@ def _declare(L):
                                          c.c_uint32, c.c_uint32, c.c_int32, c.c_int32, c.c_int32, c.c_int,
                                          c.c_uint32, c.c_int, c.c_double, c.c_int,
                                          c.POINTER(c.c_int32)] + [c.c_void_p] * 5
+    L.or_engineer_run_adaptive.argtypes = [c.c_int, _p(np.int8), c.c_int, _p(np.float64), c.c_uint32, c.c_uint32,
+                                           c.c_int32, c.c_int32, c.c_int32, c.c_int, c.c_uint32, c.c_int,
+                                           c.c_double, c.c_double, c.c_int, c.c_int32, c.c_int64,
+                                           c.POINTER(c.c_int32), c.POINTER(c.c_int32)] + [c.c_void_p] * 6
     L.or_tts_eval_doubling.argtypes = [c.c_int, _p(np.int8), c.c_int, _p(np.float64), c.c_int,
                                        c.c_uint32, c.c_uint32, c.c_int32, c.c_int32, c.c_int,
                                        c.POINTER(c.c_int32), c.POINTER(c.c_int32), c.POINTER(c.c_int32),
@@ -128,11 +133,17 @@ def energy(L, J, s):
     return int(lib().or_energy(L, np.ascontiguousarray(J, np.int8), np.ascontiguousarray(s, np.int8)))
 
 
-def metropolis_thresholds(betas):
+def metropolis_thresholds(betas, kmax=KMAX):
+    """[n_temps][kmax + 1]: floor(exp(-2 k beta) 2^32), k = 1..kmax (entry 0 unused)."""
     betas = np.ascontiguousarray(betas, np.float64)
-    thr = np.zeros((len(betas), KMAX + 1), np.uint32)
-    lib().or_metropolis_thresholds(len(betas), betas, thr)
+    thr = np.zeros((len(betas), kmax + 1), np.uint32)
+    lib().or_metropolis_thresholds(len(betas), betas, int(kmax), thr)
     return thr
+
+
+def coupler_kmax(L, J):
+    """Largest sum of |J| over one spin's couplers."""
+    return int(lib().or_coupler_kmax(L, np.ascontiguousarray(J, np.int8)))
 
 
 def exchange_thresholds(betas):
@@ -277,6 +288,26 @@ def engineer_run(L, J, betas, n_runs, seed, base_uid, S, pass_mult, exchange_eve
     return J, cur.value, {k: v[:n_steps] for k, v in logs.items()}
 
 
+def engineer_run_adaptive(L, J, betas, seed, base_uid, S, pass_mult, exchange_every, step0, n_steps,
+                          n0, n_min, cost_max, tts_cur, beta_rao=-1.0, beta_per_run=0.0, direction=1,
+                          max_sweeps=0):
+    """RAO with Appendix B's adaptive budget (see or_engineer_run_adaptive):
+    returns (J_final, tts_final, n_after, log) with per-step edge, new, tts,
+    accept, n (runs used) and level (sweeps used)."""
+    J = np.ascontiguousarray(J, np.int8).copy()
+    cur, n = ctypes.c_int32(int(tts_cur)), ctypes.c_int32(int(n0))
+    keys = ("edge", "new", "tts", "accept", "n", "level")
+    logs = {k: np.zeros(max(n_steps, 1), np.int32) for k in keys}
+    rc = lib().or_engineer_run_adaptive(L, J, len(betas), np.ascontiguousarray(betas, np.float64), _u32(seed),
+                                        _u32(base_uid), int(S), int(pass_mult), int(max_sweeps), int(exchange_every),
+                                        _u32(step0), int(n_steps), float(beta_rao), float(beta_per_run),
+                                        int(direction), int(n_min), int(cost_max), ctypes.byref(n),
+                                        ctypes.byref(cur), *(logs[k].ctypes.data for k in keys))
+    if rc:
+        raise ValueError("oracle engineering failed")
+    return J, cur.value, n.value, {k: v[:n_steps] for k, v in logs.items()}
+
+
 def ground_energy_bipartite(L, J):
     return int(lib().or_ground_energy_bipartite(L, np.ascontiguousarray(J, np.int8)))
 
@@ -287,7 +318,7 @@ def ground_energy_bipartite(L, J):
 LOOP_WORDS = 9
 
 
-def lao_plant(L, seed, uid, n_loops, w_max=3):
+def lao_plant(L, seed, uid, n_loops, w_max=5):
     """(planted spins [N], loops [n_loops][9], couplers [E], E_GS)."""
     N, E = 8 * L * L, 16 * L * L + 8 * L * (L - 1)
     planted = np.zeros(N, np.int8)
@@ -302,7 +333,7 @@ def lao_plant(L, seed, uid, n_loops, w_max=3):
 class LAOState:
     """Oracle loop adaptive optimisation on one planted instance."""
 
-    def __init__(self, L, betas, n_runs, seed, uid, n_loops, w_max=3, S=1024, exchange_every=1,
+    def __init__(self, L, betas, n_runs, seed, uid, n_loops, w_max=5, S=1024, exchange_every=1,
                  beta_rao=-1.0, direction=1):
         self.L, self.betas, self.R, self.seed, self.uid = L, np.ascontiguousarray(betas, np.float64), n_runs, seed, uid
         self.M, self.w_max, self.S, self.x, self.beta, self.direction = n_loops, w_max, S, exchange_every, beta_rao, direction

@@ -56,7 +56,7 @@
 #include <string.h>
 #include <math.h>
 
-#define OR_KMAX 18           /* max |h_i| = 6 neighbours x |J| <= 3 */
+#define OR_KMAX_LIMIT 127    /* largest |h_i| an instance may have (sum of |J| over a spin's couplers) */
 #define OR_HMAX (1 << 22)    /* cap on the exchange table length per pair */
 
 /* ------------------------------------------------------------------ */
@@ -175,14 +175,33 @@ static uint32_t prob_to_u32(double p)
     return (uint32_t)x;
 }
 
-/* thr[t*(OR_KMAX+1) + k] = floor(exp(-2 k beta_t) 2^32) for k = 1..OR_KMAX; entry 0 unused (0). */
-void or_metropolis_thresholds(int n_temps, const double *betas, uint32_t *thr)
+/* thr[t*(kmax+1) + k] = floor(exp(-2 k beta_t) 2^32) for k = 1..kmax; entry 0 unused (0). */
+void or_metropolis_thresholds(int n_temps, const double *betas, int kmax, uint32_t *thr)
 {
     for (int t = 0; t < n_temps; ++t) {
-        thr[t * (OR_KMAX + 1)] = 0;
-        for (int k = 1; k <= OR_KMAX; ++k)
-            thr[t * (OR_KMAX + 1) + k] = prob_to_u32(exp(-2.0 * (double)k * betas[t]));
+        thr[t * (kmax + 1)] = 0;
+        for (int k = 1; k <= kmax; ++k)
+            thr[t * (kmax + 1) + k] = prob_to_u32(exp(-2.0 * (double)k * betas[t]));
     }
+}
+
+/* The largest local-field magnitude the couplers allow: max over spins of
+ * the sum of |J| over the spin's couplers (k = -s_i h_i never exceeds it). */
+int or_coupler_kmax(int L, const int8_t *J)
+{
+    int N = 8 * L * L, E = or_chimera_n_edges(L);
+    int32_t *ei = malloc(sizeof(int32_t) * E), *ej = malloc(sizeof(int32_t) * E);
+    int *sum = calloc((size_t)N, sizeof(int));
+    or_chimera_edges(L, ei, ej);
+    for (int e = 0; e < E; ++e) {
+        int a = J[e] < 0 ? -J[e] : J[e];
+        sum[ei[e]] += a;
+        sum[ej[e]] += a;
+    }
+    int m = 0;
+    for (int i = 0; i < N; ++i) if (sum[i] > m) m = sum[i];
+    free(ei); free(ej); free(sum);
+    return m;
 }
 
 /* Length H_p of pair p's exchange table: the largest h with a nonzero entry. */
@@ -250,10 +269,10 @@ void or_pt_start(int L, const int8_t *J, int n_temps, int n_runs, const int8_t *
 }
 
 typedef struct {
-    int L, N, NT, R;
+    int L, N, NT, R, kmax;
     uint32_t seed, uid;
     nbr_list *nl;
-    uint32_t *thr;
+    uint32_t *thr;            /* [NT][kmax + 1] */
     int64_t *xoff;
     uint32_t *xthr;
 } pt_ctx;
@@ -264,8 +283,9 @@ static int ctx_open(pt_ctx *cx, int L, const int8_t *J, int n_temps, const doubl
     cx->L = L; cx->N = 8 * L * L; cx->NT = n_temps; cx->R = n_runs;
     cx->seed = seed; cx->uid = uid;
     cx->nl = build_neighbours(L, J);
-    cx->thr = malloc(sizeof(uint32_t) * (size_t)n_temps * (OR_KMAX + 1));
-    or_metropolis_thresholds(n_temps, betas, cx->thr);
+    cx->kmax = or_coupler_kmax(L, J);
+    cx->thr = malloc(sizeof(uint32_t) * (size_t)n_temps * (cx->kmax + 1));
+    or_metropolis_thresholds(n_temps, betas, cx->kmax, cx->thr);
     cx->xoff = malloc(sizeof(int64_t) * (size_t)(n_temps > 0 ? n_temps : 1));
     int64_t tot = or_exchange_thresholds(n_temps, betas, NULL, NULL);
     if (tot < 0) return -1;
@@ -283,7 +303,7 @@ static void ctx_close(pt_ctx *cx)
 static void metropolis_sweep(const pt_ctx *cx, int run, int slot, uint32_t sweep,
                              int8_t *s, int32_t *E, uint64_t *macc)
 {
-    const uint32_t *thr = cx->thr + (size_t)slot * (OR_KMAX + 1);
+    const uint32_t *thr = cx->thr + (size_t)slot * (cx->kmax + 1);
     for (int colour = 0; colour < 2; ++colour)
         for (int i = 0; i < cx->N; ++i) {
             if (or_spin_colour(cx->L, i) != colour) continue;
@@ -643,6 +663,58 @@ int or_engineer_run(int L, int8_t *J, int n_temps, const double *betas, int n_ru
                                   log_edge, log_old, log_new, log_tts, log_accept);
 }
 
+/* Random adaptive optimisation with the adaptive budget of Appendix B.  The
+ * paper's HFS evaluation repeats until the lowest energy has been found n+1
+ * times; a step whose wall-clock time T_step exceeds T_max halves n (never
+ * below 16, starting at 512), and beta = 6.5 n.  The deterministic
+ * counterpart here: n is the number of PT runs an evaluation uses (runs
+ * 0 .. n-1 of the instance's streams), the step's cost is n times the sweeps
+ * the candidate's evaluation used (pass_mult * S, or the deciding level of
+ * the doubling budget) in place of T_step, and after a step whose cost
+ * exceeds cost_max the next step uses max(n_min, n / 2) runs.  The Boltzmann
+ * branch uses beta = beta_per_run * n when beta_per_run > 0 (else the fixed
+ * beta_rao).  *n_cur: in = runs of the next step, out = after the last step.
+ * log_n / log_level (may be NULL): runs and sweeps of every step. */
+int or_engineer_run_adaptive(int L, int8_t *J, int n_temps, const double *betas, uint32_t seed,
+                             uint32_t base_uid, int32_t S, int32_t pass_mult, int32_t max_sweeps,
+                             int exchange_every, uint32_t step0, int n_steps, double beta_rao,
+                             double beta_per_run, int direction, int32_t n_min, int64_t cost_max,
+                             int32_t *n_cur, int32_t *tts_cur, int32_t *log_edge, int32_t *log_new,
+                             int32_t *log_tts, int32_t *log_accept, int32_t *log_n, int32_t *log_level)
+{
+    int32_t cur = *tts_cur, n = *n_cur;
+    for (int a = 0; a < n_steps; ++a) {
+        uint32_t t = step0 + (uint32_t)a;
+        int32_t e, v; uint32_t cuid, uacc;
+        or_engineer_draw(L, J, seed, base_uid, t, 0u, &e, &v, &cuid, &uacc);
+        int8_t old = J[e];
+        J[e] = (int8_t)v;
+        int32_t tn, nh, tg, level;
+        int rc;
+        if (max_sweeps > 0) {
+            rc = or_tts_eval_doubling(L, J, n_temps, betas, n, seed, cuid, S, max_sweeps, exchange_every,
+                                      &tn, &nh, &tg, &level);
+        } else {
+            rc = or_tts_eval(L, J, n_temps, betas, n, seed, cuid, S, pass_mult, exchange_every, &tn, &nh, &tg);
+            level = S * pass_mult;
+        }
+        if (rc) { J[e] = old; return rc; }
+        double beta = beta_per_run > 0.0 ? beta_per_run * (double)n : beta_rao;
+        int accept = or_rao_accept(cur, tn, direction, beta, uacc);
+        if (accept) cur = tn; else J[e] = old;
+        if (log_edge) log_edge[a] = e;
+        if (log_new) log_new[a] = v;
+        if (log_tts) log_tts[a] = tn;
+        if (log_accept) log_accept[a] = accept;
+        if (log_n) log_n[a] = n;
+        if (log_level) log_level[a] = level;
+        if ((int64_t)n * level > cost_max && n > n_min) n = n / 2 > n_min ? n / 2 : n_min;
+    }
+    *tts_cur = cur;
+    *n_cur = n;
+    return 0;
+}
+
 /* Exact ground-state energy by enumeration of the colour-0 spins: on the
  * bipartite Chimera graph the colour-1 spins are then independent, each
  * contributing -|h_i|.  Feasible while colour 0 has <= 24 spins (L <= 2). */
@@ -679,8 +751,11 @@ int32_t or_ground_energy_bipartite(int L, const int8_t *J)
 /* only outlined in the paper): a loop is a simple cycle of length 4     */
 /* (probability 0.1) or 6, weight w uniform in 1..w_max; every edge is   */
 /* satisfied by the planted state except one, frustrated, edge.          */
-/* Couplers of overlapping loops add; a draw that would take a coupler   */
-/* outside [-3, 3] is rejected and redrawn.                              */
+/* Couplers of overlapping loops add, without a cap of their own; a       */
+/* placement is redrawn only if it would take a coupler outside          */
+/* [-127, 127] or a spin's sum of |J| above 127 (the representable        */
+/* range of the couplers and local fields), which the paper's parameters  */
+/* (weights 1..5, 350 loops on 512 spins) do not reach.                  */
 /* Draws use key (seed, uid), kind 4:                                    */
 /*   planted spin i: counter (0, 0xFFFFFFF0, i>>2, 4), word i&3, s = -1  */
 /*     if the top bit is set;                                            */
@@ -775,9 +850,19 @@ static int lao_draw_loop(const or_lgraph *g, const int8_t *planted, const int8_t
             if (r[3 + m] < 0) ok = 0;
         }
         if (!ok) continue;
+        int Jt[6];
         for (int m = 0; m < len && ok; ++m) {
-            int x = J[r[3 + m]] + loop_term(g, planted, r, m);
-            if (x < -3 || x > 3) ok = 0;
+            Jt[m] = J[r[3 + m]] + loop_term(g, planted, r, m);
+            if (Jt[m] < -127 || Jt[m] > 127) ok = 0;
+        }
+        for (int m = 0; m < len && ok; ++m) {          /* every loop vertex's sum of |J| */
+            int x = v[m], sum = 0;
+            for (int k = 0; k < g->deg[x]; ++k) {
+                int e = g->ne[x][k], val = J[e];
+                for (int q = 0; q < len; ++q) if (r[3 + q] == e) val = Jt[q];
+                sum += val < 0 ? -val : val;
+            }
+            if (sum > OR_KMAX_LIMIT) ok = 0;
         }
         if (!ok) continue;
         memcpy(rec, r, sizeof(r));

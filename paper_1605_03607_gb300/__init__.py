@@ -9,4 +9,5 @@ the Python binding of that ABI.
 """
 from ._lib import (PT_KMAX, PT_TARGET_BEST, PTError, PTHandle, load, pt_rule,  # noqa: F401
                    pt_step_result, SIGNATURES, LIB_PATH, select_device, PTBatch, Surrogate,
-                   PT_LOOP_WORDS, pt_lao_result, lao_plant, int_issue_rate, INT_ISSUE_KINDS)
+                   PT_LOOP_WORDS, pt_lao_result, lao_plant, int_issue_rate, INT_ISSUE_KINDS,
+                   debug_enabled, debug_status)

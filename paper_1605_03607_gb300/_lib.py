@@ -13,6 +13,11 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpt_gb300.so")
+# PT_GB300_DEBUG=1 selects the build with device-side bounds checks
+# (pt_debug_enabled / pt_debug_status); it is built by build.build(debug=True).
+DEBUG_LIB_PATH = os.path.join(_HERE, "libpt_gb300_debug.so")
+if os.environ.get("PT_GB300_DEBUG", "") not in ("", "0"):
+    LIB_PATH = DEBUG_LIB_PATH
 
 PT_OK, PT_ERR_ARG, PT_ERR_CUDA, PT_ERR_TIMEOUT, PT_ERR_OOM, PT_ERR_STATE = range(6)
 PT_TARGET_BEST = 2**31 - 1
@@ -35,7 +40,7 @@ class pt_rule(C.Structure):
 class pt_step_result(C.Structure):
     _fields_ = [("edge", C.c_int32), ("old_value", C.c_int32), ("new_value", C.c_int32),
                 ("tts_old", C.c_int32), ("tts_new", C.c_int32), ("accepted", C.c_int32),
-                ("cand_uid", C.c_uint32)]
+                ("cand_uid", C.c_uint32), ("n_runs", C.c_int32), ("level", C.c_int32)]
 
 
 PT_LOOP_WORDS = 9
@@ -68,6 +73,7 @@ SIGNATURES = [
     ("pt_set_coupler", C.c_int, [_VP, C.c_int32, C.c_int8]),
     ("pt_get_couplers", C.c_int, [_VP, _VP]),
     ("pt_get_tables", C.c_int, [_VP, _VP, _VP, _VP, C.c_int64, C.POINTER(C.c_int64)]),
+    ("pt_get_table_rows", C.c_int, [_VP, _I32P]),
     ("engineer_begin", C.c_int, [_VP, C.POINTER(pt_rule), C.c_uint32, _I32P]),
     ("engineer_step", C.c_int, [_VP, C.c_uint32, C.POINTER(pt_step_result)]),
     ("engineer_run", C.c_int, [_VP, C.c_uint32, C.c_int32, C.c_int32, C.POINTER(pt_step_result)]),
@@ -78,6 +84,8 @@ SIGNATURES = [
     ("pt_overlaps", C.c_int, [_VP, C.c_int32, _I32P, _I32P, _I32P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("engineer_current_tts", C.c_int, [_VP, _I32P]),
     ("engineer_current_state", C.c_int, [_VP, _I32P, _I32P]),
+    ("engineer_set_adaptive", C.c_int, [_VP, C.c_int32, C.c_int32, C.c_int64, C.c_double]),
+    ("engineer_adaptive_runs", C.c_int, [_VP, _I32P]),
     ("pt_checkpoint", C.c_int, [_VP, _VP, C.POINTER(C.c_size_t)]),
     ("pt_restore", C.c_int, [_VP, _VP, C.c_size_t]),
     ("pt_set_schedule", C.c_int, [_VP, C.c_int32, C.c_int32, C.c_int32]),
@@ -125,6 +133,8 @@ SIGNATURES = [
     ("sg_launch_count", C.c_uint64, [_VP]),
     ("engineer_guided_step", C.c_int, [_VP, _VP, C.c_uint32, C.c_int32, C.c_int32,
                                        C.POINTER(pt_step_result), _VP, _VP]),
+    ("pt_debug_enabled", C.c_int, []),
+    ("pt_debug_status", C.c_int, [C.POINTER(C.c_uint32)]),
 ]
 
 
@@ -148,6 +158,18 @@ def load():
             f.argtypes = args
         _lib = lib
     return _lib
+
+
+def debug_enabled():
+    """True when the loaded library is the bounds-checking debug build."""
+    return bool(load().pt_debug_enabled())
+
+
+def debug_status():
+    """First failed device-side bounds check since the last call (0: none)."""
+    c = C.c_uint32()
+    _check(load().pt_debug_status(C.byref(c)), None)
+    return int(c.value)
 
 
 def select_device(device):
@@ -264,10 +286,15 @@ class PTHandle:
         _check(load().pt_get_couplers(self.h, _ptr(J)), self.h)
         return J
 
+    def table_rows(self):
+        r = C.c_int32()
+        _check(load().pt_get_table_rows(self.h, C.byref(r)), self.h)
+        return r.value
+
     def tables(self):
         n = C.c_int64()
         _check(load().pt_get_tables(self.h, None, None, None, 0, C.byref(n)), self.h)
-        thr = np.zeros((self.NT, PT_KMAX + 1), np.uint32)
+        thr = np.zeros((self.NT, self.table_rows()), np.uint32)
         xoff = np.zeros(self.NT, np.int64)
         xthr = np.zeros(max(n.value, 1), np.uint32)
         _check(load().pt_get_tables(self.h, _ptr(thr), _ptr(xoff), _ptr(xthr), len(xthr), C.byref(n)), self.h)
@@ -303,16 +330,31 @@ class PTHandle:
         _check(load().engineer_begin(self.h, C.byref(rule), int(base_uid) & 0xFFFFFFFF, C.byref(t)), self.h)
         return t.value
 
-    def engineer_run(self, step0, n_steps, speculation=1):
+    def engineer_run(self, step0, n_steps, speculation=1, log=None):
+        """n_steps RAO steps from step0.  log (path or writable text file, optional):
+        one JSON record per step appended (see _log_steps)."""
         out = (pt_step_result * max(n_steps, 1))()
+        e0 = self.eval_stats() if log is not None else None
         _check(load().engineer_run(self.h, int(step0) & 0xFFFFFFFF, int(n_steps), int(speculation), out), self.h)
-        keys = ("edge", "old_value", "new_value", "tts_old", "tts_new", "accepted", "cand_uid")
-        return {k: np.array([getattr(out[i], k) for i in range(n_steps)], np.int64) for k in keys}
+        keys = ("edge", "old_value", "new_value", "tts_old", "tts_new", "accepted", "cand_uid", "n_runs", "level")
+        res = {k: np.array([getattr(out[i], k) for i in range(n_steps)], np.int64) for k in keys}
+        if log is not None:
+            _log_steps(log, "rao", step0, res, e0, self.eval_stats(), self.engineer_state()[1])
+        return res
+
+    def set_adaptive(self, n0, n_min=16, cost_max=1 << 40, beta_per_run=0.0):
+        """Appendix B's adaptive budget for engineer_run (n0 = 0: off)."""
+        _check(load().engineer_set_adaptive(self.h, int(n0), int(n_min), int(cost_max), float(beta_per_run)), self.h)
+
+    def adaptive_runs(self):
+        n = C.c_int32()
+        _check(load().engineer_adaptive_runs(self.h, C.byref(n)), self.h)
+        return n.value
 
     def engineer_step(self, step):
         return self.engineer_run(step, 1, 1)
 
-    def lao_begin(self, S, uid, n_loops, w_max=3, exchange_every=1, beta_rao=-1.0, direction=1):
+    def lao_begin(self, S, uid, n_loops, w_max=5, exchange_every=1, beta_rao=-1.0, direction=1):
         """Planted instance with n_loops loops (Algorithm 2); returns its TTS against E_GS."""
         rule = pt_rule(int(S), 1, int(exchange_every), int(direction), float(beta_rao), 0)
         t = C.c_int32()
@@ -321,12 +363,16 @@ class PTHandle:
         self.n_loops = int(n_loops)
         return t.value
 
-    def lao_run(self, step0, n_steps, speculation=1):
+    def lao_run(self, step0, n_steps, speculation=1, log=None):
+        """n_steps LAO steps from step0 (>= 1); log as in engineer_run."""
         out = (pt_lao_result * max(n_steps, 1))()
+        e0 = self.eval_stats() if log is not None else None
         _check(load().lao_run(self.h, int(step0) & 0xFFFFFFFF, int(n_steps), int(speculation), out), self.h)
         keys = ("removed", "E_gs_new", "tts_old", "tts_new", "accepted", "cand_uid")
         res = {k: np.array([getattr(out[i], k) for i in range(n_steps)], np.int64) for k in keys}
         res["loop"] = np.array([list(out[i].loop) for i in range(n_steps)], np.int32).reshape(n_steps, PT_LOOP_WORDS)
+        if log is not None:
+            _log_steps(log, "lao", step0, res, e0, self.eval_stats(), self.engineer_state()[1])
         return res
 
     def overlaps(self, E_gs):
@@ -355,7 +401,7 @@ class PTHandle:
         ranked = np.zeros(top, np.int32)
         _check(load().engineer_guided_step(self.h, None if model is None else model.m, int(step) & 0xFFFFFFFF,
                                            int(n_prop), int(top), out, _ptr(pred), _ptr(ranked)), self.h)
-        keys = ("edge", "old_value", "new_value", "tts_old", "tts_new", "accepted", "cand_uid")
+        keys = ("edge", "old_value", "new_value", "tts_old", "tts_new", "accepted", "cand_uid", "n_runs", "level")
         res = {k: np.array([getattr(out[i], k) for i in range(top)], np.int64) for k in keys}
         return res, pred, ranked
 
@@ -434,6 +480,38 @@ class PTHandle:
         ms, n = C.c_double(), C.c_int32()
         _check(load().pt_last_sweep_timing(self.h, C.byref(ms), C.byref(n)), self.h)
         return ms.value, n.value
+
+
+def _log_steps(log, kind, step0, res, before, after, hits_now):
+    """Appends one JSON line per step of an engineering call: step, the move
+    (coupler and old/new value for RAO, removed loop and new ground-state
+    energy for LAO), TTS before and after, acceptance, the candidate's PT key,
+    and the device time of the call's evaluations divided by the candidates
+    evaluated (speculative candidates that were discarded included).  The
+    last line of a call also carries the current instance's hit count."""
+    import json
+    evals = after[0] - before[0]
+    ms_per_eval = (after[2] - before[2]) / evals if evals > 0 else None
+    n = len(res["tts_new"])
+    recs = []
+    for i in range(n):
+        r = {"kind": kind, "step": int(step0) + i, "tts_old": int(res["tts_old"][i]),
+             "tts_new": int(res["tts_new"][i]), "accepted": bool(res["accepted"][i]),
+             "cand_uid": int(res["cand_uid"][i]), "device_ms_per_eval": ms_per_eval}
+        if kind == "rao":
+            r.update(coupler=int(res["edge"][i]), J_old=int(res["old_value"][i]), J_new=int(res["new_value"][i]),
+                     runs=int(res["n_runs"][i]), sweeps=int(res["level"][i]))
+        else:
+            r.update(removed_loop=int(res["removed"][i]), E_gs_new=int(res["E_gs_new"][i]))
+        if i == n - 1:
+            r.update(call_evals=int(evals), call_batches=int(after[1] - before[1]), n_hit_now=int(hits_now))
+        recs.append(json.dumps(r))
+    text = "".join(x + "\n" for x in recs)
+    if hasattr(log, "write"):
+        log.write(text)
+    else:
+        with open(log, "a") as f:
+            f.write(text)
 
 
 def _check_batch(rc, b=None):
@@ -608,7 +686,7 @@ class Surrogate:
         return int(load().sg_launch_count(self.m))
 
 
-def lao_plant(L, seed, uid, n_loops, w_max=3):
+def lao_plant(L, seed, uid, n_loops, w_max=5):
     """Host-side planted instance (no GPU work): (planted, loops, J, E_GS)."""
     N, E = 8 * L * L, 16 * L * L + 8 * L * (L - 1)
     planted = np.zeros(N, np.int8)

@@ -61,6 +61,7 @@ struct pt_batch {
     std::vector<uint32_t> uid;
     std::vector<std::vector<int8_t>> J;
     std::vector<Tables> tb;
+    int kt = KT_DEFAULT;            // Metropolis table rows per slot, shared by every instance
     // device storage (one allocation per kind)
     int8_t* spins = nullptr;
     int32_t* E = nullptr;
@@ -134,7 +135,7 @@ cudaError_t balloc(T** p, size_t n)
     return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (n ? n : 1));
 }
 
-void default_shape_sched(int L, int NT, int R, bool slot_major, ShapeSched& s)
+void default_shape_sched(int L, int NT, int R, bool slot_major, ShapeSched& s, int kt)
 {
     const int L2 = L * L;
     s.block = 0;
@@ -147,7 +148,7 @@ void default_shape_sched(int L, int NT, int R, bool slot_major, ShapeSched& s)
         while (sp * team < 32 && team < 32) team *= 2;
         while (sp * team > 384 && sp > 1) sp = (sp + 1) / 2;
         int ipc = std::max(1, std::min(384 / (sp * team), R));
-        while (ipc > 1 && bundle_smem_bytes(L, NT, ipc, team) > 110 * 1024) --ipc;
+        while (ipc > 1 && bundle_smem_bytes(L, NT, ipc, team, false, kt) > 110 * 1024) --ipc;
         s.team = team;
         s.sp = sp;
         s.ipc = ipc;
@@ -157,7 +158,7 @@ void default_shape_sched(int L, int NT, int R, bool slot_major, ShapeSched& s)
     int sp = std::max(1, std::min(NT, 512 / L2));
     while (sp * L2 < 32) ++sp;
     int ipc = std::max(1, std::min(512 / (sp * L2), R));
-    while (ipc > 1 && bundle_smem_bytes(L, NT, ipc) > 110 * 1024) --ipc;
+    while (ipc > 1 && bundle_smem_bytes(L, NT, ipc, 0, false, kt) > 110 * 1024) --ipc;
     s.team = 0;
     s.sp = sp;
     s.ipc = ipc;
@@ -178,10 +179,10 @@ void instance_shape(const pt_batch* b, const SizeGroup& g, int NT, int* sp, int*
     const int per = (g.ntmax + s.sp - 1) / s.sp;
     const int spi = std::max((NT + per - 1) / per, (32 + s.team - 1) / s.team);
     const int threads = s.sp * s.team * s.ipc;
-    const int64_t smem_cap = bundle_smem_bytes(g.L, g.ntmax, s.ipc, s.team);
+    const int64_t smem_cap = bundle_smem_bytes(g.L, g.ntmax, s.ipc, s.team, false, b->kt);
     int ipci = std::min(s.ipc, b->R);
     while (ipci < b->R && spi * s.team * (ipci + 1) <= threads &&
-           bundle_smem_bytes(g.L, NT, ipci + 1, s.team) <= smem_cap)
+           bundle_smem_bytes(g.L, NT, ipci + 1, s.team, false, b->kt) <= smem_cap)
         ++ipci;
     *sp = spi;
     *ipc = ipci;
@@ -214,7 +215,7 @@ int build_group(pt_batch* b, int k)
             bundles.push_back(bd);
         }
         threads = std::max(threads, tpr * ipci);
-        smem = std::max<int64_t>(smem, bundle_smem_bytes(g.L, b->NT[i], ipci, s.team));
+        smem = std::max<int64_t>(smem, bundle_smem_bytes(g.L, b->NT[i], ipci, s.team, false, b->kt));
     }
     int block = (threads + 31) / 32 * 32;
     if (s.block > 0) {
@@ -334,6 +335,7 @@ int run_graph(pt_batch* b, int nsweeps, int xevery)
         BK(cudaGraphExecKernelNodeSetParams(b->exec, g.knode, &kp), "patch kernel node");
     }
     BK(cudaGraphLaunch(b->exec, b->stream), "graph launch");
+    BK(debug_check(b->stream, "batched sweep graph"), "debug check");
     b->launches += (uint64_t)b->groups.size();
     return PT_OK;
 }
@@ -367,7 +369,10 @@ int pt_batch_create(pt_batch** out, int32_t n_inst, const pt_instance_desc* d, i
         }
         const int E = n_edges_of(x.chimera_L);
         for (int e = 0; e < E; ++e)
-            if (x.J[e] < -3 || x.J[e] > 3) { b->err = "instance " + std::to_string(i) + ": coupler outside [-3, 3]"; return bail(PT_ERR_ARG); }
+            if (x.J[e] < -J_ABS_MAX) { b->err = "instance " + std::to_string(i) + ": coupler outside [-127, 127]"; return bail(PT_ERR_ARG); }
+        const int km = coupler_kmax(x.chimera_L, x.J);
+        if (km > KT_MAX - 1) { b->err = "instance " + std::to_string(i) + ": a spin's sum of |J| exceeds 127"; return bail(PT_ERR_ARG); }
+        b->kt = std::max(b->kt, table_rows_for(km));
         for (int t = 0; t < x.n_temps; ++t)
             if (!(x.betas[t] > 0.0) || !std::isfinite(x.betas[t]) || (t > 0 && !(x.betas[t] < x.betas[t - 1]))) {
                 b->err = "instance " + std::to_string(i) + ": betas must be finite, > 0, strictly descending";
@@ -378,8 +383,12 @@ int pt_batch_create(pt_batch** out, int32_t n_inst, const pt_instance_desc* d, i
         b->N.push_back(8 * x.chimera_L * x.chimera_L);
         b->uid.push_back(x.uid);
         b->J.emplace_back(x.J, x.J + E);
+    }
+    // one table row count for the whole batch: the largest any instance needs
+    for (int i = 0; i < n_inst; ++i) {
+        const pt_instance_desc& x = d[i];
         Tables tb;
-        std::string why = build_tables(x.n_temps, x.betas, tb);
+        std::string why = build_tables(x.n_temps, b->kt, x.betas, tb);
         if (!why.empty()) { b->err = "instance " + std::to_string(i) + ": " + why; return bail(PT_ERR_ARG); }
         b->tb.push_back(std::move(tb));
     }
@@ -400,7 +409,7 @@ int pt_batch_create(pt_batch** out, int32_t n_inst, const pt_instance_desc* d, i
         reps += (size_t)n_runs * b->NT[i];
         pairs += (size_t)n_runs * std::max(b->NT[i] - 1, 1);
         jws += (size_t)b->L[i] * b->L[i] * 16;
-        thrs += (size_t)b->NT[i] * KT;
+        thrs += (size_t)b->NT[i] * b->kt;
         xts += b->tb[i].xthr.size();
         nts += (size_t)b->NT[i];
     }
@@ -441,6 +450,7 @@ int pt_batch_create(pt_batch** out, int32_t n_inst, const pt_instance_desc* d, i
         InstDesc dd;
         dd.L = L; dd.NT = NT; dd.R = n_runs; dd.n_xpairs = NT - 1;
         dd.seed = seed; dd.uid = b->uid[i];
+        dd.kt = b->kt;
         std::vector<uint32_t> jw((size_t)L * L * 16);
         pack_couplers(L, b->J[i].data(), jw.data());
         BKC(cudaMemcpy(b->jw + o_jw, jw.data(), 4 * jw.size(), cudaMemcpyHostToDevice), "upload jw");
@@ -481,7 +491,7 @@ int pt_batch_create(pt_batch** out, int32_t n_inst, const pt_instance_desc* d, i
         g.ntmax = max_temps_of(b, g.L);
         for (int i = 0; i < n_inst; ++i)
             if (b->L[i] == g.L) g.work += (int64_t)n_runs * b->NT[i] * b->N[i];
-        default_shape_sched(g.L, g.ntmax, n_runs, false, g.s);
+        default_shape_sched(g.L, g.ntmax, n_runs, false, g.s, b->kt);
         b->groups.push_back(g);
     }
     std::stable_sort(b->groups.begin(), b->groups.end(),
@@ -649,7 +659,7 @@ int pt_batch_set_mapping(pt_batch* b, int32_t chimera_L, int32_t team, int32_t s
         for (size_t k = 0; k < b->groups.size(); ++k) {
             SizeGroup& g = b->groups[k];
             ShapeSched s;
-            default_shape_sched(g.L, g.ntmax, b->R, team > 0, s);
+            default_shape_sched(g.L, g.ntmax, b->R, team > 0, s, b->kt);
             const int rc = set_group(b, (int)k, s);
             if (rc) {
                 for (size_t m = 0; m < k; ++m) set_group(b, (int)m, old[m]);
@@ -661,7 +671,7 @@ int pt_batch_set_mapping(pt_batch* b, int32_t chimera_L, int32_t team, int32_t s
         if (k < 0) return bfail(b, PT_ERR_ARG, "no instance of that size");
         SizeGroup& g = b->groups[k];
         ShapeSched s = g.s;
-        if ((s.team > 0) != (team > 0)) default_shape_sched(g.L, g.ntmax, b->R, team > 0, s);
+        if ((s.team > 0) != (team > 0)) default_shape_sched(g.L, g.ntmax, b->R, team > 0, s, b->kt);
         if (team > 0) s.team = team;
         if (slot_parallel > 0) s.sp = slot_parallel;
         if (runs_per_cta > 0) s.ipc = std::min<int>(runs_per_cta, b->R);
@@ -714,7 +724,7 @@ int pt_batch_autotune(pt_batch* b, int32_t trial_sweeps, int32_t* block_out)
             if (sp > NT || tpr > MAX_THREADS) break;
             if (tpr < 32) continue;
             for (int ipc : {1, 2, 4, 8, 16}) {
-                if (tpr * ipc > MAX_THREADS || ipc > b->R || bundle_smem_bytes(g.L, NT, ipc) > cap) break;
+                if (tpr * ipc > MAX_THREADS || ipc > b->R || bundle_smem_bytes(g.L, NT, ipc, 0, false, b->kt) > cap) break;
                 ShapeSched s; s.sp = sp; s.ipc = ipc; s.team = 0;
                 cands.push_back(s);
             }
@@ -727,7 +737,7 @@ int pt_batch_autotune(pt_batch* b, int32_t trial_sweeps, int32_t* block_out)
                 prev = nt;
                 for (int ipc : {1, 2, 4, 8}) {
                     if (nt * team * ipc > MAX_THREADS_SM || ipc > b->R ||
-                        bundle_smem_bytes(g.L, NT, ipc, team) > cap)
+                        bundle_smem_bytes(g.L, NT, ipc, team, false, b->kt) > cap)
                         break;
                     ShapeSched s; s.sp = nt; s.ipc = ipc; s.team = team;
                     cands.push_back(s);

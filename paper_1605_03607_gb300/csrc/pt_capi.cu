@@ -65,6 +65,7 @@ struct pt_handle {
     std::vector<int8_t> J;
     std::vector<double> betas;
     Tables tb;
+    int kt = KT_DEFAULT;       // Metropolis table rows per slot (grows with the couplers, ensure_table_rows)
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     // device tables shared by every group of this handle
@@ -102,6 +103,11 @@ struct pt_handle {
     uint32_t base_uid = 0;
     int32_t tts_cur = 0;
     int32_t hits_cur = 0;      // runs that reached the target in the current instance's evaluation
+    // adaptive budget of Appendix B (engineer_set_adaptive): runs per evaluation
+    bool adapt = false;
+    int32_t n_cur = 0, n_min = 0;
+    int64_t cost_max = 0;
+    double beta_per_run = 0.0;
     std::vector<int32_t> last_levels;   // deciding levels of the last doubling evaluation of candidates
     std::string err = "no error";
 };
@@ -155,7 +161,7 @@ bool doubling_ok(int32_t S0, int32_t Smax, int32_t pass_mult)
 }
 
 // Default schedule: about 256 threads per run, a multiple of 32.
-void default_schedule(int L, int NT, int R, int& sp, int& ipc)
+void default_schedule(int L, int NT, int R, int& sp, int& ipc, int kt)
 {
     const int L2 = L * L;
     sp = std::max(1, 256 / L2);
@@ -164,7 +170,7 @@ void default_schedule(int L, int NT, int R, int& sp, int& ipc)
     const int tpi = sp * L2;
     ipc = std::max(1, 512 / tpi);
     if (ipc > R) ipc = R;
-    while (ipc > 1 && bundle_smem_bytes(L, NT, ipc) > 110 * 1024) --ipc;
+    while (ipc > 1 && bundle_smem_bytes(L, NT, ipc, 0, false, kt) > 110 * 1024) --ipc;
 }
 
 int check_schedule(pt_handle* h, int L, int NT, int sp, int ipc, int team)
@@ -180,7 +186,7 @@ int check_schedule(pt_handle* h, int L, int NT, int sp, int ipc, int team)
         if ((sp * L2) % 32 != 0) return fail(h, PT_ERR_ARG, "slot_parallel * L^2 must be a multiple of 32");
         if (sp * L2 * ipc > MAX_THREADS) return fail(h, PT_ERR_ARG, "more than 1024 threads per CTA");
     }
-    if (bundle_smem_bytes(L, NT, ipc, team, h->main.walk) > 227 * 1024)
+    if (bundle_smem_bytes(L, NT, ipc, team, h->main.walk, h->kt) > 227 * 1024)
         return fail(h, PT_ERR_ARG, "shared memory above 227 KB");
     return PT_OK;
 }
@@ -210,6 +216,7 @@ int group_alloc(pt_handle* h, Group& g, int n_inst)
         const size_t r0 = (size_t)i * h->R;
         d.L = h->L; d.NT = h->NT; d.R = h->R; d.n_xpairs = h->NT - 1;
         d.seed = h->seed; d.uid = h->uid;
+        d.kt = h->kt;
         d.jw = g.jw + (size_t)i * h->L * h->L * 16;
         d.nbr = h->d_nbr; d.thr = h->d_thr; d.xoff = h->d_xoff; d.xthr = h->d_xthr; d.xhint = h->d_xhint;
         d.spins = g.spins + r0 * h->NT * h->N;
@@ -240,7 +247,7 @@ int group_schedule(pt_handle* h, Group& g)
             bundles.push_back(b);
         }
     const int block = (h->team > 0 ? h->sp * h->team : h->sp * L2) * h->ipc;
-    const int smem = (int)bundle_smem_bytes(g.L, g.NT, h->ipc, h->team, g.walk);
+    const int smem = (int)bundle_smem_bytes(g.L, g.NT, h->ipc, h->team, g.walk, h->kt);
     int cap = 0;
     CK(sweep_smem_capacity(&cap), "shared memory capacity");
     if (smem > cap) return fail(h, PT_ERR_ARG, "bundle needs more shared memory than a CTA can have");
@@ -377,7 +384,8 @@ int group_tts(pt_handle* h, Group& g, int32_t target, int32_t horizon, std::vect
 // Full evaluation of every instance of g: fresh runs, pass_mult*S sweeps, TTS at horizon S.
 // targets (host, one per instance, may be NULL): per-instance TTS targets.
 int group_eval(pt_handle* h, Group& g, int32_t S, int32_t pass_mult, int32_t xevery,
-               std::vector<int32_t>& out, int32_t target = PT_TARGET_BEST, const int32_t* targets = nullptr)
+               std::vector<int32_t>& out, int32_t target = PT_TARGET_BEST, const int32_t* targets = nullptr,
+               const Bundle* dsub = nullptr, int nsub = 0)
 {
     int rc;
     if (!h->eb0) {
@@ -387,7 +395,7 @@ int group_eval(pt_handle* h, Group& g, int32_t S, int32_t pass_mult, int32_t xev
     if ((rc = upload_desc(h, g))) return rc;
     CK(cudaEventRecord(h->eb0, h->stream), "event");
     if ((rc = group_reset(h, g, true))) return rc;
-    if ((rc = group_sweeps(h, g, (int64_t)S * pass_mult, xevery))) return rc;
+    if ((rc = group_sweeps(h, g, (int64_t)S * pass_mult, xevery, dsub, nsub))) return rc;
     if (targets)
         CK(cudaMemcpyAsync(g.d_targets, targets, sizeof(int32_t) * g.n_inst, cudaMemcpyHostToDevice, h->stream),
            "upload targets");
@@ -503,14 +511,18 @@ bool engineer_accept(const pt_rule& rule, int32_t cur, int32_t cand, uint32_t ua
 }
 
 int ensure_candidates(pt_handle* h, int k);
+int ensure_table_rows(pt_handle* h, int kmax);
 
 // PT-TTS evaluation of k candidate coupler vectors (host [k][n_edges]) with
 // PT keys uids[0..k-1], as one batched launch sequence; res = k x {tts, hits, target}.
 int eval_candidates(pt_handle* h, int k, const int8_t* Jc, const uint32_t* uids, std::vector<int32_t>& res,
-                    int32_t target = PT_TARGET_BEST, const int32_t* targets = nullptr)
+                    int32_t target = PT_TARGET_BEST, const int32_t* targets = nullptr, int n_eval = 0)
 {
     int rc = ensure_candidates(h, k);
     if (rc) return rc;
+    int kmax = 0;
+    for (int j = 0; j < k; ++j) kmax = std::max(kmax, coupler_kmax(h->L, Jc + (size_t)j * h->n_edges));
+    if ((rc = ensure_table_rows(h, kmax))) return rc;
     Group& g = h->cand;
     std::vector<uint32_t> jw((size_t)k * h->L * h->L * 16);
     for (int j = 0; j < k; ++j) {
@@ -518,18 +530,31 @@ int eval_candidates(pt_handle* h, int k, const int8_t* Jc, const uint32_t* uids,
         g.desc[j].uid = uids[j];
     }
     CK(cudaMemcpyAsync(g.jw, jw.data(), 4 * jw.size(), cudaMemcpyHostToDevice, h->stream), "upload candidates");
-    // evaluate only the first k candidates: shrink the group view temporarily
+    // evaluate only the first k candidates, with their first n_eval runs
+    // (all runs when n_eval is 0): shrink the group view temporarily
+    const int nr = (n_eval > 0 && n_eval < h->R) ? n_eval : h->R;
     const int n_full = g.n_inst;
     std::vector<Bundle> keep = g.bundles;
     g.n_inst = k;
     std::vector<Bundle> sub;
-    for (const Bundle& b : keep) if (b.inst < k) sub.push_back(b);
+    for (Bundle b : keep) {
+        if (b.inst >= k || b.run0 >= nr) continue;
+        b.nitems = std::min(b.nitems, nr - b.run0);
+        sub.push_back(b);
+    }
     g.bundles = sub;
+    for (int j = 0; j < k; ++j) g.desc[j].R = nr;            // the TTS reduction's run count
     if (h->rule.max_sweeps > 0 && !targets && target == PT_TARGET_BEST) {
         rc = group_eval_doubling(h, g, h->rule.S, h->rule.max_sweeps, h->rule.exchange_every, res, h->last_levels);
     } else {
-        rc = group_eval(h, g, h->rule.S, h->rule.pass_mult, h->rule.exchange_every, res, target, targets);
+        rc = cudaMemcpyAsync(g.d_sub, sub.data(), sizeof(Bundle) * sub.size(), cudaMemcpyHostToDevice, h->stream)
+                 == cudaSuccess ? PT_OK : fail(h, PT_ERR_CUDA, "upload bundle subset");
+        if (!rc)
+            rc = group_eval(h, g, h->rule.S, h->rule.pass_mult, h->rule.exchange_every, res, target, targets,
+                            g.d_sub, (int)sub.size());
+        h->last_levels.assign((size_t)k, h->rule.S * h->rule.pass_mult);
     }
+    for (int j = 0; j < k; ++j) g.desc[j].R = h->R;
     g.n_inst = n_full;
     g.bundles = keep;
     return rc;
@@ -646,9 +671,24 @@ bool lao_draw_loop(const LaoGraph& g, const int8_t* planted, const int8_t* J, ui
             r[3 + m] = g.edge(v[m], v[(m + 1) % len]);
             if (r[3 + m] < 0) ok = false;
         }
+        // the engine's bounds: int8 couplers, and every spin's sum of |J| <= 127
+        // (its Metropolis table rows); with the paper's weights (1..5, 350
+        // loops on C_8) no placement reaches them
+        int Jt[6];
         for (int m = 0; m < len && ok; ++m) {
-            const int x = J[r[3 + m]] + loop_term(g, planted, r, m);
-            if (x < -3 || x > 3) ok = false;
+            Jt[m] = J[r[3 + m]] + loop_term(g, planted, r, m);
+            if (Jt[m] < -J_ABS_MAX || Jt[m] > J_ABS_MAX) ok = false;
+        }
+        for (int m = 0; m < len && ok; ++m) {
+            const int x = v[m];
+            int sum = 0;
+            for (int k = 0; k < g.deg[x]; ++k) {
+                const int e = g.ne[x][k];
+                int val = J[e];
+                for (int q = 0; q < len; ++q) if (r[3 + q] == e) val = Jt[q];
+                sum += val < 0 ? -val : val;
+            }
+            if (sum > KT_MAX - 1) ok = false;
         }
         if (!ok) continue;
         std::memcpy(rec, r, sizeof(r));
@@ -685,6 +725,53 @@ int apply_schedule(pt_handle* h, int team, int sp, int ipc)
     return rc;
 }
 
+// Makes the handle's Metropolis table cover local fields up to kmax (rows
+// 0 .. kmax): a coupler change that raises some spin's sum of |J| above the
+// table's last row rebuilds the table with more rows, points every group's
+// instances at it and rebuilds their schedules for the larger shared-memory
+// footprint.  Tables never shrink, so results do not depend on the order of
+// the changes (every row is a function of (beta, k) alone).
+int ensure_table_rows(pt_handle* h, int kmax)
+{
+    if (kmax > KT_MAX - 1) return fail(h, PT_ERR_ARG, "a spin's sum of |J| exceeds 127");
+    const int kt = table_rows_for(kmax);
+    if (kt <= h->kt) return PT_OK;
+    Tables tb;
+    const std::string why = build_tables(h->NT, kt, h->betas.data(), tb);
+    if (!why.empty()) return fail(h, PT_ERR_ARG, why);
+    uint32_t* d = nullptr;
+    CK(dalloc(&d, tb.thr.size()), "cudaMalloc thr");
+    cudaError_t e = cudaMemcpy(d, tb.thr.data(), 4 * tb.thr.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);     // no launch still reads the old table
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return cuda_fail(h, e, "upload thr");
+    }
+    const int old_kt = h->kt;
+    uint32_t* old = h->d_thr;
+    h->d_thr = d;
+    h->kt = kt;
+    for (Group* g : {&h->main, &h->cand}) {
+        for (InstDesc& x : g->desc) { x.thr = d; x.kt = kt; }
+        if (g->n_inst == 0) continue;
+        int rc = upload_desc(h, *g);
+        if (!rc) rc = group_schedule(h, *g);
+        if (rc) {                                   // keep the old, still valid table
+            h->d_thr = old;
+            h->kt = old_kt;
+            for (Group* g2 : {&h->main, &h->cand}) {
+                for (InstDesc& x : g2->desc) { x.thr = old; x.kt = old_kt; }
+                if (g2->n_inst) { upload_desc(h, *g2); group_schedule(h, *g2); }
+            }
+            cudaFree(d);
+            return rc;
+        }
+    }
+    cudaFree(old);
+    h->tb = std::move(tb);
+    return PT_OK;
+}
+
 }  // namespace
 
 void ptg::set_global_error(const char* msg)
@@ -716,7 +803,9 @@ int pt_create(pt_handle** out, int32_t L, const int8_t* J, int32_t n_edges, cons
     if (n_temps < 1 || n_temps > MAX_TEMPS) return fail(nullptr, PT_ERR_ARG, "n_temps must be in [1, 64]");
     if (n_runs < 1 || n_runs > 1024) return fail(nullptr, PT_ERR_ARG, "n_runs must be in [1, 1024]");
     for (int e = 0; e < n_edges; ++e)
-        if (J[e] < -3 || J[e] > 3) return fail(nullptr, PT_ERR_ARG, "coupler outside [-3, 3]");
+        if (J[e] < -J_ABS_MAX) return fail(nullptr, PT_ERR_ARG, "coupler outside [-127, 127]");
+    const int kmax = coupler_kmax(L, J);
+    if (kmax > KT_MAX - 1) return fail(nullptr, PT_ERR_ARG, "a spin's sum of |J| exceeds 127");
     for (int t = 0; t < n_temps; ++t) {
         if (!(betas[t] > 0.0) || !std::isfinite(betas[t])) return fail(nullptr, PT_ERR_ARG, "beta must be finite and > 0");
         if (t > 0 && !(betas[t] < betas[t - 1])) return fail(nullptr, PT_ERR_ARG, "betas must be strictly descending");
@@ -727,7 +816,8 @@ int pt_create(pt_handle** out, int32_t L, const int8_t* J, int32_t n_edges, cons
     h->seed = seed; h->uid = uid;
     h->J.assign(J, J + n_edges);
     h->betas.assign(betas, betas + n_temps);
-    std::string why = build_tables(n_temps, betas, h->tb);
+    h->kt = table_rows_for(kmax);
+    std::string why = build_tables(n_temps, h->kt, betas, h->tb);
     if (!why.empty()) { delete h; return fail(nullptr, PT_ERR_ARG, why); }
     int rc = PT_OK;
     auto bail = [&](int code) { std::string m = h->err; pt_destroy(h); return fail(nullptr, code, m); };
@@ -756,7 +846,7 @@ int pt_create(pt_handle** out, int32_t L, const int8_t* J, int32_t n_edges, cons
     if (xt) CKC(cudaMemcpy(h->d_xthr, h->tb.xthr.data(), 4 * (size_t)xt, cudaMemcpyHostToDevice), "upload xthr");
     CKC(cudaMemcpy(h->d_xhint, h->tb.xhint.data(), 4 * h->tb.xhint.size(), cudaMemcpyHostToDevice), "upload xhint");
     CKC(cudaMemcpy(h->d_nbr, nbr.data(), 2 * nbr.size(), cudaMemcpyHostToDevice), "upload nbr");
-    default_schedule(L, n_temps, n_runs, h->sp, h->ipc);
+    default_schedule(L, n_temps, n_runs, h->sp, h->ipc, h->kt);
     if ((rc = group_alloc(h, h->main, 1))) return bail(rc);
     if ((rc = group_schedule(h, h->main))) return bail(rc);
     if ((rc = upload_couplers(h, h->main, 0, h->J.data()))) return bail(rc);
@@ -924,7 +1014,7 @@ int pt_tts_eval_many(pt_handle* h, int32_t k, const int8_t* J, const uint32_t* u
     if (max_sweeps != 0 && !doubling_ok(S, max_sweeps, pass_mult))
         return fail(h, PT_ERR_ARG, "max_sweeps must be S * 2^k <= 2^30 with pass_mult 1");
     for (size_t i = 0; i < (size_t)k * h->n_edges; ++i)
-        if (J[i] < -3 || J[i] > 3) return fail(h, PT_ERR_ARG, "coupler outside [-3, 3]");
+        if (J[i] < -J_ABS_MAX) return fail(h, PT_ERR_ARG, "coupler outside [-127, 127]");
     const pt_rule keep = h->rule;
     h->rule.S = S;
     h->rule.pass_mult = pass_mult;
@@ -947,9 +1037,14 @@ int pt_tts_eval_many(pt_handle* h, int32_t k, const int8_t* J, const uint32_t* u
 int pt_set_coupler(pt_handle* h, int32_t edge, int8_t value)
 {
     if (!h) return PT_ERR_ARG;
-    if (edge < 0 || edge >= h->n_edges || value < -3 || value > 3)
-        return fail(h, PT_ERR_ARG, "edge out of range or |value| > 3");
+    if (edge < 0 || edge >= h->n_edges || value < -J_ABS_MAX)
+        return fail(h, PT_ERR_ARG, "edge out of range or |value| > 127");
+    const int8_t prev = h->J[edge];
     h->J[edge] = value;
+    if (int rc0 = ensure_table_rows(h, coupler_kmax(h->L, h->J.data()))) {
+        h->J[edge] = prev;
+        return rc0;
+    }
     int rc = upload_couplers(h, h->main, 0, h->J.data());
     if (rc) return rc;
     CK(launch_energy(h->main.d_desc, h->main.d_items, h->R, (int32_t)h->main.sweep, h->stream), "energy kernel");
@@ -976,6 +1071,22 @@ int pt_get_tables(const pt_handle* h, uint32_t* thr, int64_t* xoff, uint32_t* xt
         if (cap < n) return PT_ERR_ARG;
         std::memcpy(xthr, h->tb.xthr.data(), 4 * (size_t)n);
     }
+    return PT_OK;
+}
+
+int pt_debug_enabled(void) { return debug_build() ? 1 : 0; }
+
+int pt_debug_status(uint32_t* code)
+{
+    if (!code) return PT_ERR_ARG;
+    *code = debug_take();
+    return PT_OK;
+}
+
+int pt_get_table_rows(const pt_handle* h, int32_t* rows)
+{
+    if (!h || !rows) return PT_ERR_ARG;
+    *rows = h->kt;
     return PT_OK;
 }
 
@@ -1023,23 +1134,38 @@ int engineer_run(pt_handle* h, uint32_t step0, int32_t n_steps, int32_t spec, pt
             std::memcpy(Jj, h->J.data(), h->n_edges);
             Jj[e[j]] = (int8_t)v[j];
         }
+        // every candidate of the batch uses the runs of the step it stands for;
+        // the batch is cut after a candidate that is kept or that halves them
+        const int n = h->adapt ? h->n_cur : h->R;
         std::vector<int32_t> res;
-        rc = eval_candidates(h, k, Jc.data(), cu.data(), res);
+        rc = eval_candidates(h, k, Jc.data(), cu.data(), res, PT_TARGET_BEST, nullptr, n);
         if (rc) return rc;
+        pt_rule rule = h->rule;
+        if (h->adapt && h->beta_per_run > 0.0) rule.beta_rao = h->beta_per_run * (double)n;
         int used = k;
         for (int j = 0; j < k; ++j) {
             const int32_t tn = res[(size_t)j * 3];
-            const bool acc = engineer_accept(h->rule, h->tts_cur, tn, ua[j]);
+            const int32_t level = h->last_levels[(size_t)j];
+            const bool acc = engineer_accept(rule, h->tts_cur, tn, ua[j]);
             if (out) {
                 pt_step_result& o = out[done + j];
                 o.edge = e[j]; o.old_value = h->J[e[j]]; o.new_value = v[j];
                 o.tts_old = h->tts_cur; o.tts_new = tn; o.accepted = acc ? 1 : 0; o.cand_uid = cu[j];
+                o.n_runs = n; o.level = level;
             }
+            bool stop = false;
             if (acc) {
                 h->J[e[j]] = (int8_t)v[j];
                 h->tts_cur = tn;
                 h->hits_cur = res[(size_t)j * 3 + 1];
                 changed = true;
+                stop = true;
+            }
+            if (h->adapt && (int64_t)n * level > h->cost_max && n > h->n_min) {
+                h->n_cur = std::max(h->n_min, n / 2);
+                stop = true;
+            }
+            if (stop) {
                 used = j + 1;
                 break;
             }
@@ -1062,8 +1188,8 @@ int lao_plant(int32_t chimera_L, uint32_t seed, uint32_t uid, int32_t n_loops, i
               int32_t* loops, int8_t* J, int32_t* E_gs)
 {
     if (!planted || !loops || !J || !E_gs) return fail(nullptr, PT_ERR_ARG, "NULL argument");
-    if (chimera_L < 1 || chimera_L > MAX_L || n_loops < 1 || w_max < 1 || w_max > 3)
-        return fail(nullptr, PT_ERR_ARG, "need 1 <= L <= 16, n_loops >= 1, 1 <= w_max <= 3");
+    if (chimera_L < 1 || chimera_L > MAX_L || n_loops < 1 || w_max < 1 || w_max > J_ABS_MAX)
+        return fail(nullptr, PT_ERR_ARG, "need 1 <= L <= 16, n_loops >= 1, 1 <= w_max <= 127");
     const LaoGraph g(chimera_L);
     for (int i = 0; i < g.N; ++i)
         planted[i] = (lao_word(seed, uid, 0u, 0xFFFFFFF0u, (uint32_t)(i >> 2), i & 3) >> 31) ? -1 : 1;
@@ -1071,7 +1197,7 @@ int lao_plant(int32_t chimera_L, uint32_t seed, uint32_t uid, int32_t n_loops, i
     for (int m = 0; m < n_loops; ++m) {
         int32_t* rec = loops + (size_t)m * PT_LOOP_WORDS;
         if (!lao_draw_loop(g, planted, J, seed, uid, 0u, (uint32_t)m, (int)w_max, rec))
-            return fail(nullptr, PT_ERR_STATE, "no admissible loop (too many loops for the graph and |J| <= 3)");
+            return fail(nullptr, PT_ERR_STATE, "no admissible loop (the couplers would leave the engine's bounds)");
         loop_apply(g, planted, rec, J, 1);
     }
     *E_gs = loops_gs(loops, n_loops);
@@ -1306,6 +1432,7 @@ int engineer_guided_step(pt_handle* h, sg_model* m, uint32_t step, int32_t n_pro
             o.edge = e[j]; o.old_value = h->J[e[j]]; o.new_value = v[j];
             o.tts_old = h->tts_cur; o.tts_new = res[(size_t)r * 3];
             o.accepted = (acc && r == best) ? 1 : 0; o.cand_uid = cu[j];
+            o.n_runs = h->R; o.level = h->last_levels[(size_t)r];
         }
         if (ranked) ranked[r] = j;
     }
@@ -1324,6 +1451,30 @@ int engineer_current_tts(const pt_handle* h, int32_t* tts)
 {
     if (!h || !tts || !h->eng) return PT_ERR_STATE;
     *tts = h->tts_cur;
+    return PT_OK;
+}
+
+int engineer_set_adaptive(pt_handle* h, int32_t n0, int32_t n_min, int64_t cost_max, double beta_per_run)
+{
+    if (!h) return PT_ERR_ARG;
+    if (n0 == 0) {
+        h->adapt = false;
+        return PT_OK;
+    }
+    if (n_min < 1 || n0 < n_min || n0 > h->R || cost_max < 1 || !(beta_per_run >= 0.0) || !std::isfinite(beta_per_run))
+        return fail(h, PT_ERR_ARG, "need 1 <= n_min <= n0 <= n_runs, cost_max >= 1, beta_per_run >= 0");
+    h->adapt = true;
+    h->n_cur = n0;
+    h->n_min = n_min;
+    h->cost_max = cost_max;
+    h->beta_per_run = beta_per_run;
+    return PT_OK;
+}
+
+int engineer_adaptive_runs(const pt_handle* h, int32_t* n)
+{
+    if (!h || !n) return PT_ERR_ARG;
+    *n = h->adapt ? h->n_cur : h->R;
     return PT_OK;
 }
 
@@ -1373,7 +1524,12 @@ int pt_restore(pt_handle* h, const void* buf, size_t len)
         return fail(h, PT_ERR_ARG, "checkpoint shape does not match this handle");
     p += 64;
     for (int e = 0; e < h->n_edges; ++e)
-        if ((int8_t)p[e] < -3 || (int8_t)p[e] > 3) return fail(h, PT_ERR_ARG, "corrupt couplers in checkpoint");
+        if ((int8_t)p[e] < -J_ABS_MAX) return fail(h, PT_ERR_ARG, "corrupt couplers in checkpoint");
+    {
+        const int km = coupler_kmax(h->L, reinterpret_cast<const int8_t*>(p));
+        if (km > KT_MAX - 1) return fail(h, PT_ERR_ARG, "corrupt couplers in checkpoint");
+        if (int rc0 = ensure_table_rows(h, km)) return rc0;
+    }
     Group& g = h->main;
     const size_t reps = (size_t)h->R * h->NT, npair = (size_t)h->R * (h->NT > 1 ? h->NT - 1 : 1);
     {
@@ -1452,7 +1608,7 @@ int pt_set_walk_stats(pt_handle* h, int32_t on)
         // the walk arrays enlarge each run's shared-memory block: check first
         int cap = 0;
         CK(sweep_smem_capacity(&cap), "shared memory capacity");
-        if (bundle_smem_bytes(g.L, g.NT, h->ipc, h->team, true) > cap)
+        if (bundle_smem_bytes(g.L, g.NT, h->ipc, h->team, true, h->kt) > cap)
             return fail(h, PT_ERR_ARG, "the current schedule leaves no shared memory for the walk counters");
         unsigned long long *whot = nullptr, *wtrips = nullptr;
         uint8_t* wstate = nullptr;
@@ -1554,7 +1710,7 @@ int pt_autotune(pt_handle* h, int32_t n_inst, int32_t trial_sweeps)
         const int tpr = team > 0 ? sp * team : sp * L2;
         for (int ipc : {1, 2, 4}) {
             if (tpr * ipc > (team > 0 ? MAX_THREADS_SM : MAX_THREADS) || ipc > h->R) break;
-            if (bundle_smem_bytes(h->L, h->NT, ipc, team) > cap) break;
+            if (bundle_smem_bytes(h->L, h->NT, ipc, team, false, h->kt) > cap) break;
             h->team = team;
             h->sp = sp;
             h->ipc = ipc;

@@ -4,6 +4,7 @@
 #pragma once
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <string>
 #include <vector>
 
@@ -108,25 +109,67 @@ inline void build_neighbours(int L, int16_t* nbr)
         }
 }
 
+// Largest local-field magnitude an instance can produce: max over spins of
+// sum_j |J_ij| (the Metropolis table needs rows k = 0 .. K).
+inline int coupler_kmax(int L, const int8_t* J)
+{
+    const int N = 8 * L * L;
+    std::vector<int> s((size_t)N, 0);
+    for (int r = 0; r < L; ++r)
+        for (int c = 0; c < L; ++c) {
+            const int cell = r * L + c;
+            for (int kv = 0; kv < 4; ++kv)
+                for (int kh = 0; kh < 4; ++kh) {
+                    const int a = std::abs((int)J[intra_edge(L, cell, kv, kh)]);
+                    s[(size_t)8 * cell + kv] += a;
+                    s[(size_t)8 * cell + 4 + kh] += a;
+                }
+            for (int k = 0; k < 4; ++k) {
+                if (r + 1 < L) {
+                    const int a = std::abs((int)J[vert_edge(L, r, c, k)]);
+                    s[(size_t)8 * cell + k] += a;
+                    s[(size_t)8 * (cell + L) + k] += a;
+                }
+                if (c + 1 < L) {
+                    const int a = std::abs((int)J[horiz_edge(L, r, c, k)]);
+                    s[(size_t)8 * cell + 4 + k] += a;
+                    s[(size_t)8 * (cell + 1) + 4 + k] += a;
+                }
+            }
+        }
+    int m = 0;
+    for (int v : s) m = v > m ? v : m;
+    return m;
+}
+
+// Table rows for an instance: the default 19, or K + 1 rounded up to a
+// multiple of 4 when its couplers need more.
+inline int table_rows_for(int kmax)
+{
+    if (kmax + 1 <= KT_DEFAULT) return KT_DEFAULT;
+    return (kmax + 1 + 3) & ~3;
+}
+
 struct Tables {
-    std::vector<uint32_t> thr;     // [NT][KT]
+    int kt = KT_DEFAULT;           // rows per slot
+    std::vector<uint32_t> thr;     // [NT][kt]
     std::vector<int64_t> xoff;     // [NT]
     std::vector<uint32_t> xthr;
     std::vector<float> xhint;      // [NT-1]
 };
 
 // Writes the FP64 acceptance tables into caller buffers, allocating nothing:
-// thr [NT][KT], xoff [NT], xhint [max(NT-1, 1)], and the ragged exchange
+// thr [NT][kt], xoff [NT], xhint [max(NT-1, 1)], and the ragged exchange
 // thresholds into xthr (capacity xcap entries; xthr NULL only counts them).
 // Returns the exchange-table length, or -1 with *why set when the ladder's
 // tables are too long or not monotone.
-inline int64_t fill_tables(int NT, const double* betas, uint32_t* thr, int64_t* xoff, float* xhint, uint32_t* xthr,
-                           int64_t xcap, const char** why)
+inline int64_t fill_tables(int NT, int kt, const double* betas, uint32_t* thr, int64_t* xoff, float* xhint,
+                           uint32_t* xthr, int64_t xcap, const char** why)
 {
     for (int t = 0; t < NT; ++t) {
-        thr[(size_t)t * KT] = 0xFFFFFFFFu;   // k <= 0 always accepts; entry unused for decisions
-        for (int k = 1; k < KT; ++k)
-            thr[(size_t)t * KT + k] = to_u32_threshold(std::exp(-2.0 * (double)k * betas[t]));
+        thr[(size_t)t * kt] = 0xFFFFFFFFu;   // k <= 0 always accepts; entry unused for decisions
+        for (int k = 1; k < kt; ++k)
+            thr[(size_t)t * kt + k] = to_u32_threshold(std::exp(-2.0 * (double)k * betas[t]));
     }
     int64_t n = 0;
     xhint[0] = 0.f;
@@ -153,17 +196,18 @@ inline int64_t fill_tables(int NT, const double* betas, uint32_t* thr, int64_t* 
 }
 
 // Returns an empty string or the reason the ladder is rejected.
-inline std::string build_tables(int NT, const double* betas, Tables& tb)
+inline std::string build_tables(int NT, int kt, const double* betas, Tables& tb)
 {
-    tb.thr.assign((size_t)NT * KT, 0u);
+    tb.kt = kt;
+    tb.thr.assign((size_t)NT * kt, 0u);
     tb.xoff.assign((size_t)NT, 0);
     tb.xhint.assign((size_t)(NT > 1 ? NT - 1 : 1), 0.f);
     const char* why = "";
-    const int64_t n = fill_tables(NT, betas, tb.thr.data(), tb.xoff.data(), tb.xhint.data(), nullptr, 0, &why);
+    const int64_t n = fill_tables(NT, kt, betas, tb.thr.data(), tb.xoff.data(), tb.xhint.data(), nullptr, 0, &why);
     if (n < 0) return why;
     if (n > (int64_t)INT32_MAX / 2) return "exchange tables too large";
     tb.xthr.assign((size_t)n, 0u);
-    if (fill_tables(NT, betas, tb.thr.data(), tb.xoff.data(), tb.xhint.data(), tb.xthr.data(), n, &why) < 0)
+    if (fill_tables(NT, kt, betas, tb.thr.data(), tb.xoff.data(), tb.xhint.data(), tb.xthr.data(), n, &why) < 0)
         return why;
     return "";
 }

@@ -9,7 +9,13 @@
 
 namespace ptg {
 
-constexpr int KT = 19;             // Metropolis table entries per slot: k = 0..18
+// Metropolis table rows per temperature slot: k = 0 .. kt-1 where kt - 1 is
+// the largest local-field magnitude K = max_i sum_j |J_ij| an instance can
+// produce.  Couplers in {+-1, +-2, +-3} give K <= 18 (the default row count);
+// planted instances with summed loop weights need more, up to KT_MAX - 1.
+constexpr int KT_DEFAULT = 19;
+constexpr int KT_MAX = 128;
+constexpr int J_ABS_MAX = 127;     // couplers are int8
 constexpr int MAX_TEMPS = 64;
 constexpr int MAX_L = 16;
 constexpr int MAX_THREADS = 1024;
@@ -31,9 +37,10 @@ constexpr int MAX_THREADS_SM = 768;
 struct InstDesc {
     int32_t L, NT, R, n_xpairs;
     uint32_t seed, uid;
+    int32_t kt;               // Metropolis table rows per slot (> every spin's sum of |J|)
     const uint32_t* jw;
     const int16_t* nbr;
-    const uint32_t* thr;      // [NT][KT]; entry 0 = 0xFFFFFFFF (unused: k <= 0 always accepts)
+    const uint32_t* thr;      // [NT][kt]; entry 0 = 0xFFFFFFFF (unused: k <= 0 always accepts)
     const int32_t* xoff;      // [NT]  pair p owns xthr[xoff[p] .. xoff[p+1]-1], h = 1..H_p
     const uint32_t* xthr;
     const float* xhint;       // [NT-1] ln2 / (2 dbeta_p): start point of the exact table search
@@ -111,9 +118,9 @@ __host__ __device__ inline int sm_pad(int L, int team)
     return ((team & 31) - (NW & 31) + 64) & 31;
 }
 
-// Instance tables staged per bundle: thr [NT][KT], then exchange offsets [NT]
+// Instance tables staged per bundle: thr [NT][kt], then exchange offsets [NT]
 // and search hints [NT].
-__host__ __device__ inline int64_t table_bytes(int NT) { return pad16(4LL * NT * KT + 8LL * NT); }
+__host__ __device__ inline int64_t table_bytes(int NT, int kt) { return pad16(4LL * NT * kt + 8LL * NT); }
 
 // Sets the message pt_last_error(NULL) returns (defined with the C ABI).
 void set_global_error(const char* msg);
@@ -126,12 +133,12 @@ void set_global_error(const char* msg);
 constexpr int CELL_REC = 12;
 __host__ __device__ inline int64_t cell_table_bytes(int L) { return 4LL * CELL_REC * 2 * L * L; }
 
-inline int64_t bundle_smem_bytes(int L, int NT, int nitems, int team = 0, bool walk = false)
+inline int64_t bundle_smem_bytes(int L, int NT, int nitems, int team = 0, bool walk = false, int kt = KT_DEFAULT)
 {
     if (team > 0)
-        return table_bytes(NT) + cell_table_bytes(L) +
+        return table_bytes(NT, kt) + cell_table_bytes(L) +
                (int64_t)nitems * item_layout(L, NT, sm_pad(L, team), walk).bytes;
-    return table_bytes(NT) + (int64_t)nitems * item_layout(L, NT, 0, walk).bytes;
+    return table_bytes(NT, kt) + (int64_t)nitems * item_layout(L, NT, 0, walk).bytes;
 }
 
 }  // namespace ptg

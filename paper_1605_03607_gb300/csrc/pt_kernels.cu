@@ -20,8 +20,10 @@
 //     the host-built table, which is non-increasing), so the serial ascending
 //     swap chain is a subtract and compare per pair.
 //   * No tensor cores: this is integer ALU / shared-memory work.
+#include <atomic>
 #include <climits>
 #include <cstdint>
+#include <cstdio>
 #include <cuda_runtime.h>
 
 #include "pt_internal.h"
@@ -29,6 +31,31 @@
 #include "pt_philox.cuh"
 
 namespace ptg {
+
+// Debug builds (-DPT_DEBUG): every data-dependent shared or global index of
+// the kernels below is checked.  A failed check records its code in a device
+// word (the first failure wins) and the access goes to index 0 instead, so
+// the kernel neither faults nor leaves a barrier early; the launchers then
+// synchronise the stream and read the word (debug_check).  Codes:
+//   1 Metropolis table row >= rows per slot     2 slot map entry >= n_temps
+//   3 exchange table range outside the tables   4 run index >= runs
+//   5 neighbour spin word outside the buffer    6 TTS over more than 1024 runs
+//   7 energy kernel: slot map entry >= n_temps
+// Release builds compile the checks away.
+#ifdef PT_DEBUG
+__device__ unsigned int g_pt_debug_code;
+__device__ __forceinline__ int dbg_idx(int i, int n, unsigned code)
+{
+    if ((unsigned)i >= (unsigned)n) {
+        atomicCAS(&g_pt_debug_code, 0u, code);
+        return 0;
+    }
+    return i;
+}
+#define PT_IDX(i, n, code) ::ptg::dbg_idx((i), (n), (code))
+#else
+#define PT_IDX(i, n, code) (i)
+#endif
 
 namespace {
 
@@ -43,7 +70,13 @@ __device__ __forceinline__ int critical_half_gap(const InstDesc& in, const int32
                                                  const float* xhint_sm, int p, uint32_t u)
 {
     const int o = xoff_sm[p];
+#ifdef PT_DEBUG
+    const int total = xoff_sm[in.NT - 1];
+    const int H = (o < 0 || xoff_sm[p + 1] < o || xoff_sm[p + 1] > total)
+                      ? (atomicCAS(&g_pt_debug_code, 0u, 3u), 0) : xoff_sm[p + 1] - o;
+#else
     const int H = xoff_sm[p + 1] - o;
+#endif
     const uint32_t* tab = in.xthr + o - 1;       // tab[h], h = 1..H
     int c = H;
     if (u != 0u) {
@@ -106,7 +139,7 @@ struct WarpSeg {
 
 // One Metropolis half-sweep (one colour) over this thread's slots.
 __device__ __forceinline__ void colour_phase(const CellRegs& cr, uint32_t* sw, int NW,
-                                             const uint32_t* thr_sm, int32_t* Es, uint32_t* macc,
+                                             const uint32_t* thr_sm, int kt, int32_t* Es, uint32_t* macc,
                                              const uint8_t* perm, int NT, int SP, int sp,
                                              int iters, uint32_t s, uint32_t runbits,
                                              uint32_t k0, uint32_t k1, const WarpSeg& ws, int lane)
@@ -116,12 +149,12 @@ __device__ __forceinline__ void colour_phase(const CellRegs& cr, uint32_t* sw, i
         const int t = sp + i * SP;
         int packed = 0;
         if (t < NT) {
-            uint32_t* bw = sw + perm[t] * NW;
+            uint32_t* bw = sw + PT_IDX((int)perm[t], NT, 2u) * NW;
             const uint32_t own = bw[cr.own];
             const int opp = (int)bw[cr.opp];
-            const uint32_t mw = bw[cr.mn], pw = bw[cr.pl];
+            const uint32_t mw = bw[PT_IDX(cr.mn, NW, 5u)], pw = bw[PT_IDX(cr.pl, NW, 5u)];
             const uint4 rn = philox_slot(pre, runbits | (uint32_t)t, k0, k1);
-            const uint32_t* th = thr_sm + t * KT;
+            const uint32_t* th = thr_sm + t * kt;
             const int x01 = (int)__byte_perm(mw, pw, 0x5140);
             const int x23 = (int)__byte_perm(mw, pw, 0x7362);
             // -h_i for the 4 spins (couplers are stored negated)
@@ -134,10 +167,10 @@ __device__ __forceinline__ void colour_phase(const CellRegs& cr, uint32_t* sw, i
             const int kk1 = (int)(int8_t)(own >> 8) * h1;
             const int kk2 = (int)(int8_t)(own >> 16) * h2;
             const int kk3 = (int)(int8_t)(own >> 24) * h3;
-            const bool a0 = (kk0 <= 0) | (rn.x < th[max(kk0, 0)]);
-            const bool a1 = (kk1 <= 0) | (rn.y < th[max(kk1, 0)]);
-            const bool a2 = (kk2 <= 0) | (rn.z < th[max(kk2, 0)]);
-            const bool a3 = (kk3 <= 0) | (rn.w < th[max(kk3, 0)]);
+            const bool a0 = (kk0 <= 0) | (rn.x < th[PT_IDX(max(kk0, 0), kt, 1u)]);
+            const bool a1 = (kk1 <= 0) | (rn.y < th[PT_IDX(max(kk1, 0), kt, 1u)]);
+            const bool a2 = (kk2 <= 0) | (rn.z < th[PT_IDX(max(kk2, 0), kt, 1u)]);
+            const bool a3 = (kk3 <= 0) | (rn.w < th[PT_IDX(max(kk3, 0), kt, 1u)]);
             uint32_t flip = 0u;
             int dk = 0;
             if (a0) { flip |= 0x000000FEu; dk += kk0; }
@@ -170,9 +203,9 @@ __device__ __forceinline__ void exchange_prepare(const InstDesc& in, const uint3
                                                  uint32_t s, uint32_t runbits, uint32_t k0, uint32_t k1,
                                                  int NT, int32_t* cc)
 {
-    // bundle tables: thr [NT][KT], then exchange offsets [NT] and search hints [NT]
-    const int32_t* xoff_sm = reinterpret_cast<const int32_t*>(thr_sm + NT * KT);
-    const float* xhint_sm = reinterpret_cast<const float*>(thr_sm + NT * KT + NT);
+    // bundle tables: thr [NT][kt], then exchange offsets [NT] and search hints [NT]
+    const int32_t* xoff_sm = reinterpret_cast<const int32_t*>(thr_sm + NT * in.kt);
+    const float* xhint_sm = reinterpret_cast<const float*>(thr_sm + NT * in.kt + NT);
     const int npairs = NT - 1;
     for (int call = lane; call * 4 < npairs; call += 32) {
         const uint4 w = philox10(s, runbits, (uint32_t)call, 1u, k0, k1);
@@ -377,13 +410,14 @@ __device__ void process_bundle(const InstDesc* __restrict__ insts, const Bundle 
     const int item = tid / TPI, j = tid - item * TPI;
     const bool active = item < bd.nitems;
     const int q = j % L2, sp = j / L2;
-    const int run = bd.run0 + (active ? item : 0);
+    const int run = PT_IDX(bd.run0 + (active ? item : 0), in.R, 4u);
     constexpr bool walk = WALK;
     const ItemLayout lay = item_layout(L, NT, 0, walk);
 
-    // bundle tables: thr [NT][KT], then exchange offsets [NT] and search hints [NT]
+    // bundle tables: thr [NT][kt], then exchange offsets [NT] and search hints [NT]
+    const int KTI = in.kt;
     uint32_t* thr_sm = reinterpret_cast<uint32_t*>(smem);
-    unsigned char* ib = smem + table_bytes(NT) + (active ? item : 0) * lay.bytes;
+    unsigned char* ib = smem + table_bytes(NT, KTI) + (active ? item : 0) * lay.bytes;
     uint32_t* sw = reinterpret_cast<uint32_t*>(ib + lay.spins);
     int32_t* Es = reinterpret_cast<int32_t*>(ib + lay.E);
     int32_t* ccrit = reinterpret_cast<int32_t*>(ib + lay.ccrit);     // 2 x NT, by sweep parity
@@ -393,10 +427,10 @@ __device__ void process_bundle(const InstDesc* __restrict__ insts, const Bundle 
     int32_t* misc = reinterpret_cast<int32_t*>(ib + lay.misc);
 
     // ---- load the instance table and this bundle's runs into shared memory
-    for (int w = tid; w < NT * KT; w += blockDim.x) thr_sm[w] = in.thr[w];
+    for (int w = tid; w < NT * KTI; w += blockDim.x) thr_sm[w] = in.thr[w];
     for (int p = tid; p < NT; p += blockDim.x) {
-        reinterpret_cast<int32_t*>(thr_sm + NT * KT)[p] = in.xoff[p];
-        reinterpret_cast<float*>(thr_sm + NT * KT + NT)[p] = p < NT - 1 ? in.xhint[p] : 0.0f;
+        reinterpret_cast<int32_t*>(thr_sm + NT * KTI)[p] = in.xoff[p];
+        reinterpret_cast<float*>(thr_sm + NT * KTI + NT)[p] = p < NT - 1 ? in.xhint[p] : 0.0f;
     }
     const size_t rep0 = (size_t)run * NT;
     if (active) {
@@ -464,13 +498,13 @@ __device__ void process_bundle(const InstDesc* __restrict__ insts, const Bundle 
         const bool do_x = exch(s);
         if (mode == 0) {
             if (active) {
-                colour_phase(cr, sw, NW, thr_sm, Es, macc, perm, NT, SP, sp, iters, s, runbits,
+                colour_phase(cr, sw, NW, thr_sm, KTI, Es, macc, perm, NT, SP, sp, iters, s, runbits,
                              k0, k1, ws, lane);
                 load_cell(in, q, 1, L2, L, cr);
             }
             __syncthreads();
             if (active) {
-                colour_phase(cr, sw, NW, thr_sm, Es, macc, perm, NT, SP, sp, iters, s, runbits,
+                colour_phase(cr, sw, NW, thr_sm, KTI, Es, macc, perm, NT, SP, sp, iters, s, runbits,
                              k0, k1, ws, lane);
                 load_cell(in, q, 0, L2, L, cr);
             }
@@ -534,14 +568,14 @@ __device__ void process_bundle(const InstDesc* __restrict__ insts, const Bundle 
 // spin against its uniform in `rn`, flips written back, energy change and
 // flip bits accumulated.
 __device__ __forceinline__ void sm_word(const uint32_t* rec, uint32_t meta, uint32_t* bw, int col, int L2, int q,
-                                        const uint4 rn, const uint32_t* th, int& dk, int& pc)
+                                        const uint4 rn, const uint32_t* th, int kt, int& dk, int& pc)
 {
     const uint4 jin = *reinterpret_cast<const uint4*>(rec);
     const uint4 jud = *reinterpret_cast<const uint4*>(rec + 4);
     const int ow = col * L2 + q;
     const uint32_t own = bw[ow];
     const int opp = (int)bw[(1 - col) * L2 + q];
-    const uint32_t mw = bw[(meta >> 10) & 1023u], pw = bw[meta >> 20];
+    const uint32_t mw = bw[PT_IDX((int)((meta >> 10) & 1023u), 2 * L2, 5u)], pw = bw[PT_IDX((int)(meta >> 20), 2 * L2, 5u)];
     const int x01 = (int)__byte_perm(mw, pw, 0x5140);
     const int x23 = (int)__byte_perm(mw, pw, 0x7362);
     const int h0 = __dp4a((int)jin.x, opp, __dp4a((int)jud.x, x01, 0));
@@ -552,10 +586,10 @@ __device__ __forceinline__ void sm_word(const uint32_t* rec, uint32_t meta, uint
     const int kk1 = (int)(int8_t)(own >> 8) * h1;
     const int kk2 = (int)(int8_t)(own >> 16) * h2;
     const int kk3 = (int)(int8_t)(own >> 24) * h3;
-    const bool a0 = (kk0 <= 0) | (rn.x < th[max(kk0, 0)]);
-    const bool a1 = (kk1 <= 0) | (rn.y < th[max(kk1, 0)]);
-    const bool a2 = (kk2 <= 0) | (rn.z < th[max(kk2, 0)]);
-    const bool a3 = (kk3 <= 0) | (rn.w < th[max(kk3, 0)]);
+    const bool a0 = (kk0 <= 0) | (rn.x < th[PT_IDX(max(kk0, 0), kt, 1u)]);
+    const bool a1 = (kk1 <= 0) | (rn.y < th[PT_IDX(max(kk1, 0), kt, 1u)]);
+    const bool a2 = (kk2 <= 0) | (rn.z < th[PT_IDX(max(kk2, 0), kt, 1u)]);
+    const bool a3 = (kk3 <= 0) | (rn.w < th[PT_IDX(max(kk3, 0), kt, 1u)]);
     uint32_t flip = 0u;
     if (a0) { flip |= 0x000000FEu; dk += kk0; }
     if (a1) { flip |= 0x0000FE00u; dk += kk1; }
@@ -588,13 +622,14 @@ __device__ void process_bundle_sm(const InstDesc* __restrict__ insts, const Bund
     const int item = tid / TPI, j = tid - item * TPI;
     const bool active = item < bd.nitems;
     const int team = j / G, tl = j - team * G;
-    const int run = bd.run0 + (active ? item : 0);
+    const int run = PT_IDX(bd.run0 + (active ? item : 0), in.R, 4u);
     constexpr bool walk = WALK;
     const ItemLayout lay = item_layout(L, NT, sm_pad(L, G), walk);
 
+    const int KTI = in.kt;
     uint32_t* thr_sm = reinterpret_cast<uint32_t*>(smem);
-    uint32_t* rec_sm = reinterpret_cast<uint32_t*>(smem + table_bytes(NT));   // [2][L2][CELL_REC]
-    unsigned char* ib = smem + table_bytes(NT) + cell_table_bytes(L) + (active ? item : 0) * lay.bytes;
+    uint32_t* rec_sm = reinterpret_cast<uint32_t*>(smem + table_bytes(NT, KTI));   // [2][L2][CELL_REC]
+    unsigned char* ib = smem + table_bytes(NT, KTI) + cell_table_bytes(L) + (active ? item : 0) * lay.bytes;
     uint32_t* sw = reinterpret_cast<uint32_t*>(ib + lay.spins);
     int32_t* Es = reinterpret_cast<int32_t*>(ib + lay.E);
     int32_t* ccrit = reinterpret_cast<int32_t*>(ib + lay.ccrit);
@@ -605,10 +640,10 @@ __device__ void process_bundle_sm(const InstDesc* __restrict__ insts, const Bund
     int32_t* misc = reinterpret_cast<int32_t*>(ib + lay.misc);
 
     // ---- tables, couplers, per-group offsets and this bundle's runs
-    for (int w = tid; w < NT * KT; w += blockDim.x) thr_sm[w] = in.thr[w];
+    for (int w = tid; w < NT * KTI; w += blockDim.x) thr_sm[w] = in.thr[w];
     for (int p = tid; p < NT; p += blockDim.x) {
-        reinterpret_cast<int32_t*>(thr_sm + NT * KT)[p] = in.xoff[p];
-        reinterpret_cast<float*>(thr_sm + NT * KT + NT)[p] = p < NT - 1 ? in.xhint[p] : 0.0f;
+        reinterpret_cast<int32_t*>(thr_sm + NT * KTI)[p] = in.xoff[p];
+        reinterpret_cast<float*>(thr_sm + NT * KTI + NT)[p] = p < NT - 1 ? in.xhint[p] : 0.0f;
     }
     for (int w = tid; w < L2 * 4; w += blockDim.x) {  // global: [cell][colour][in 4 | inter 4]
         const int qc = w >> 1, half = w & 1, q = qc >> 1, col = qc & 1;
@@ -674,9 +709,9 @@ __device__ void process_bundle_sm(const InstDesc* __restrict__ insts, const Bund
         if (mode == 0 && active) {
             const PhiloxSweep ps = philox_sweep_pre(s, k0, k1);
             for (int b = team; b < NT; b += NTEAM) {
-                const int t = inv[b];
+                const int t = PT_IDX((int)inv[b], NT, 2u);
                 uint32_t* bw = sw + b * NWP;
-                const uint32_t* th = thr_sm + t * KT;
+                const uint32_t* th = thr_sm + t * KTI;
                 const uint32_t c1 = runbits | (uint32_t)t;
                 int dk = 0, pc = 0;
 #pragma unroll
@@ -685,7 +720,7 @@ __device__ void process_bundle_sm(const InstDesc* __restrict__ insts, const Bund
                         const uint32_t* rec = rec_sm + (col * L2 + q) * CELL_REC;
                         const uint32_t meta = rec[8];
                         const uint4 rn = philox_group(ps, c1, meta & 1023u, k0, k1);
-                        sm_word(rec, meta, bw, col, L2, q, rn, th, dk, pc);
+                        sm_word(rec, meta, bw, col, L2, q, rn, th, KTI, dk, pc);
                     }
                     __syncwarp(tmask);                  // colour 0 of this buffer done by the whole team
                 }
@@ -829,7 +864,7 @@ __global__ void pt_energy_kernel(const InstDesc* __restrict__ insts, const int2*
     if (threadIdx.x == 0) s_min = INT32_MAX;
     __syncthreads();
     for (int t = warp; t < NT; t += nwarps) {
-        const int buf = in.perm[rep0 + t];
+        const int buf = PT_IDX((int)in.perm[rep0 + t], NT, 7u);
         const uint32_t* w = reinterpret_cast<const uint32_t*>(in.spins + (rep0 + buf) * 8 * L2);
         int acc = 0;
         for (int q = lane; q < L2; q += 32) {
@@ -868,7 +903,11 @@ __global__ void pt_tts_kernel(const InstDesc* __restrict__ insts, int32_t target
 {
     const InstDesc& in = insts[blockIdx.x];
     if (targets) target = targets[blockIdx.x];
+#ifdef PT_DEBUG
+    const int R = in.R > 1024 ? (atomicCAS(&g_pt_debug_code, 0u, 6u), 1024) : in.R;
+#else
     const int R = in.R;
+#endif
     __shared__ long long v[1024];
     __shared__ int s_min, s_hits;
     __shared__ long long s_med;
@@ -926,6 +965,37 @@ __global__ void pt_hamming_kernel(const InstDesc* __restrict__ insts, int n, con
 
 }  // namespace
 
+#ifdef PT_DEBUG
+namespace {
+std::atomic<unsigned> g_debug_sticky{0};
+}
+bool debug_build() { return true; }
+cudaError_t debug_check(cudaStream_t st, const char* what)
+{
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess || cap != cudaStreamCaptureStatusNone) return e;   // checked after the graph replay
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+    unsigned code = 0;
+    if ((e = cudaMemcpyFromSymbol(&code, g_pt_debug_code, sizeof(code))) != cudaSuccess) return e;
+    if (code) {
+        const unsigned zero = 0;
+        if ((e = cudaMemcpyToSymbol(g_pt_debug_code, &zero, sizeof(zero))) != cudaSuccess) return e;
+        unsigned expect = 0;
+        g_debug_sticky.compare_exchange_strong(expect, code);
+        std::fprintf(stderr, "PT_DEBUG: bounds check %u failed in %s\n", code, what);
+    }
+    return cudaSuccess;
+}
+unsigned debug_take() { return g_debug_sticky.exchange(0u); }
+#define DBG(e, st, what) ((e) == cudaSuccess ? debug_check((st), (what)) : (e))
+#else
+bool debug_build() { return false; }
+cudaError_t debug_check(cudaStream_t, const char*) { return cudaSuccess; }
+unsigned debug_take() { return 0u; }
+#define DBG(e, st, what) (e)
+#endif
+
 cudaError_t sweep_smem_capacity(int* bytes)
 {
     int dev = 0, optin = 0;
@@ -969,7 +1039,7 @@ cudaError_t launch_init(const InstDesc* insts, const int2* items, int nitems, bo
 {
     if (nitems <= 0) return cudaSuccess;
     pt_init_kernel<<<nitems, 256, 0, st>>>(insts, items, draw ? 1 : 0);
-    return cudaGetLastError();
+    return DBG(cudaGetLastError(), st, "init kernel");
 }
 
 cudaError_t launch_energy(const InstDesc* insts, const int2* items, int nitems, int32_t first_value,
@@ -977,7 +1047,7 @@ cudaError_t launch_energy(const InstDesc* insts, const int2* items, int nitems, 
 {
     if (nitems <= 0) return cudaSuccess;
     pt_energy_kernel<<<nitems, 256, 0, st>>>(insts, items, first_value);
-    return cudaGetLastError();
+    return DBG(cudaGetLastError(), st, "energy kernel");
 }
 
 cudaError_t launch_sweeps(const InstDesc* insts, const Bundle* bundles, int nbundles, int grid,
@@ -997,7 +1067,7 @@ cudaError_t launch_sweeps(const InstDesc* insts, const Bundle* bundles, int nbun
     else
         pt_sweep_kernel<false, false><<<grid, block, smem_bytes, st>>>(insts, bundles, nbundles, sweep0, nsweeps,
                                                                        xevery, mode, queue);
-    return cudaGetLastError();
+    return DBG(cudaGetLastError(), st, "sweep kernel");
 }
 
 cudaError_t launch_hamming(const InstDesc* insts, int n, const int32_t* run, const int32_t* slot, int32_t* dist,
@@ -1005,7 +1075,7 @@ cudaError_t launch_hamming(const InstDesc* insts, int n, const int32_t* run, con
 {
     if (n <= 0) return cudaSuccess;
     pt_hamming_kernel<<<n, 256, 0, st>>>(insts, n, run, slot, dist);
-    return cudaGetLastError();
+    return DBG(cudaGetLastError(), st, "hamming kernel");
 }
 
 cudaError_t launch_tts(const InstDesc* insts, int ninst, int32_t target, int32_t horizon,
@@ -1013,7 +1083,7 @@ cudaError_t launch_tts(const InstDesc* insts, int ninst, int32_t target, int32_t
 {
     if (ninst <= 0) return cudaSuccess;
     pt_tts_kernel<<<ninst, 256, 0, st>>>(insts, target, horizon, out, targets);
-    return cudaGetLastError();
+    return DBG(cudaGetLastError(), st, "TTS kernel");
 }
 
 }  // namespace ptg

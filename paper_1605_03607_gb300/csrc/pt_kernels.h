@@ -33,4 +33,13 @@ cudaError_t launch_hamming(const InstDesc* insts, int n, const int32_t* run, con
 cudaError_t launch_tts(const InstDesc* insts, int ninst, int32_t target, int32_t horizon,
                        int32_t* out, cudaStream_t st, const int32_t* targets = nullptr);
 
+// Debug builds (-DPT_DEBUG): the kernels check their data-dependent indexes
+// and record the first failure in a device word.  debug_check synchronises
+// `st` and reads (and clears) that word, printing and remembering the code;
+// it does nothing in release builds or while `st` is being captured.
+// debug_take returns and clears the remembered code (0: none).
+bool debug_build();
+cudaError_t debug_check(cudaStream_t st, const char* what);
+unsigned debug_take();
+
 }  // namespace ptg

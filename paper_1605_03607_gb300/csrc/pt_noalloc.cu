@@ -56,7 +56,7 @@ constexpr int MAX_DEVICES = 64;
 static __device__ __align__(256) unsigned char g_scratch[PT_NOALLOC_BYTES];
 
 // host staging (static: no allocation)
-uint32_t h_thr[MAX_TEMPS * KT];
+uint32_t h_thr[MAX_TEMPS * KT_MAX];
 int64_t h_xoff64[MAX_TEMPS];
 int32_t h_xoff[MAX_TEMPS];
 float h_xhint[MAX_TEMPS];
@@ -118,7 +118,10 @@ extern "C" int pt_tts_eval_noalloc(int32_t L, const int8_t* J, int32_t n_edges, 
         return noalloc_fail(PT_ERR_ARG, "problem exceeds the fixed no-alloc scratch: need n_runs * n_temps * 8 L^2 "
                                         "<= 2^21 and n_runs * n_temps <= 16384");
     for (int e = 0; e < n_edges; ++e)
-        if (J[e] < -3 || J[e] > 3) return noalloc_fail(PT_ERR_ARG, "coupler outside [-3, 3]");
+        if (J[e] < -J_ABS_MAX) return noalloc_fail(PT_ERR_ARG, "coupler outside [-127, 127]");
+    const int kmax = coupler_kmax(L, J);
+    if (kmax > KT_MAX - 1) return noalloc_fail(PT_ERR_ARG, "a spin's sum of |J| exceeds 127");
+    const int kt = table_rows_for(kmax);
     for (int t = 0; t < n_temps; ++t)
         if (!(betas[t] > 0.0) || !std::isfinite(betas[t]) || (t > 0 && !(betas[t] < betas[t - 1])))
             return noalloc_fail(PT_ERR_ARG, "betas must be finite, > 0 and strictly descending");
@@ -142,7 +145,7 @@ extern "C" int pt_tts_eval_noalloc(int32_t L, const int8_t* J, int32_t n_edges, 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 
     const char* why = "";
-    const int64_t nx = fill_tables(n_temps, betas, h_thr, h_xoff64, h_xhint, h_xthr, MAX_XTHR, &why);
+    const int64_t nx = fill_tables(n_temps, kt, betas, h_thr, h_xoff64, h_xhint, h_xthr, MAX_XTHR, &why);
     if (nx < 0) return noalloc_fail(PT_ERR_ARG, "exchange tables exceed 2^17 entries (beta gaps too small) or are invalid");
     for (int t = 0; t < n_temps; ++t) h_xoff[t] = (int32_t)h_xoff64[t];
     pack_couplers(L, J, h_jw);
@@ -154,7 +157,7 @@ extern "C" int pt_tts_eval_noalloc(int32_t L, const int8_t* J, int32_t n_edges, 
     if (sp > n_temps) sp = n_temps;
     while ((sp * L2) % 32 != 0) ++sp;
     const int block = sp * L2;
-    const int smem = (int)bundle_smem_bytes(L, n_temps, 1);
+    const int smem = (int)bundle_smem_bytes(L, n_temps, 1, 0, false, kt);
     if (block > MAX_THREADS || smem > g_smem_cap[dev])
         return noalloc_fail(PT_ERR_ARG, "one run needs more shared memory than a CTA can have");
     for (int r = 0; r < n_runs; ++r) {
@@ -175,7 +178,7 @@ extern "C" int pt_tts_eval_noalloc(int32_t L, const int8_t* J, int32_t n_edges, 
     const size_t o_xacc = carve(off, 8 * (size_t)n_runs * npair);
     const size_t o_jw = carve(off, 4 * (size_t)L2 * 16);
     const size_t o_nbr = carve(off, 2 * (size_t)L2 * 4);
-    const size_t o_thr = carve(off, 4 * (size_t)n_temps * KT);
+    const size_t o_thr = carve(off, 4 * (size_t)n_temps * kt);
     const size_t o_xoff = carve(off, 4 * (size_t)n_temps);
     const size_t o_xhint = carve(off, 4 * (size_t)n_temps);
     const size_t o_xthr = carve(off, 4 * (size_t)(nx > 0 ? nx : 1));
@@ -188,6 +191,7 @@ extern "C" int pt_tts_eval_noalloc(int32_t L, const int8_t* J, int32_t n_edges, 
     InstDesc d;
     d.L = L; d.NT = n_temps; d.R = n_runs; d.n_xpairs = n_temps - 1;
     d.seed = seed; d.uid = uid;
+    d.kt = kt;
     d.jw = reinterpret_cast<const uint32_t*>(base + o_jw);
     d.nbr = reinterpret_cast<const int16_t*>(base + o_nbr);
     d.thr = reinterpret_cast<const uint32_t*>(base + o_thr);
@@ -210,7 +214,7 @@ extern "C" int pt_tts_eval_noalloc(int32_t L, const int8_t* J, int32_t n_edges, 
     };
     if ((ce = up(o_jw, h_jw, 4 * (size_t)L2 * 16)) != cudaSuccess) return noalloc_cuda_fail("cudaMemcpyAsync (staging upload)", ce, st, true);
     if ((ce = up(o_nbr, h_nbr, 2 * (size_t)L2 * 4)) != cudaSuccess) return noalloc_cuda_fail("cudaMemcpyAsync (staging upload)", ce, st, true);
-    if ((ce = up(o_thr, h_thr, 4 * (size_t)n_temps * KT)) != cudaSuccess) return noalloc_cuda_fail("cudaMemcpyAsync (staging upload)", ce, st, true);
+    if ((ce = up(o_thr, h_thr, 4 * (size_t)n_temps * kt)) != cudaSuccess) return noalloc_cuda_fail("cudaMemcpyAsync (staging upload)", ce, st, true);
     if ((ce = up(o_xoff, h_xoff, 4 * (size_t)n_temps)) != cudaSuccess) return noalloc_cuda_fail("cudaMemcpyAsync (staging upload)", ce, st, true);
     if ((ce = up(o_xhint, h_xhint, 4 * (size_t)n_temps)) != cudaSuccess) return noalloc_cuda_fail("cudaMemcpyAsync (staging upload)", ce, st, true);
     if (nx > 0 && (ce = up(o_xthr, h_xthr, 4 * (size_t)nx)) != cudaSuccess)

@@ -73,9 +73,13 @@ def test_argument_validation_without_gpu(P):
     assert _create(P, L=17)[0] == 1
     assert _create(P, J=J[:-1])[0] == 1
     bad = J.copy()
-    bad[5] = 4
+    bad[5] = -128                                   # int8 but outside [-127, 127]
     rc, msg = _create(P, J=bad)
     assert rc == 1 and "coupler" in msg
+    big = J.copy()
+    big[0:4] = 60                                   # spin 0: four couplers summing to 240 > 127
+    rc, msg = _create(P, J=big)
+    assert rc == 1 and "sum of |J|" in msg
     rc, msg = _create(P, betas=np.array([1.0, 2.0, 0.5]))
     assert rc == 1 and "descending" in msg
     assert _create(P, betas=np.array([1.0, 0.0]))[0] == 1

@@ -146,3 +146,52 @@ def test_tts_eval_many_matches_oracle(P, max_sweeps):
             want = oracle.tts_eval(L, Js[j], betas, R, seed, uids[j], S0, 4, 1) + (4 * S0,)
         got = tuple(int(out[k][j]) for k in ("tts", "n_hit", "target", "level"))
         assert got == want, (j, got, want)
+
+
+def test_engineer_run_step_log(P, tmp_path):
+    """Per-step JSON records of engineer_run and lao_run match the returned results."""
+    import json
+    L, NT, R, seed = 2, 4, 4, 95
+    J0 = W.random_couplers(L, seed, 0)
+    betas = W.beta_ladder(NT, 0.5, 3.0)
+    path = tmp_path / "steps.jsonl"
+    with P.PTHandle(L, J0, betas, R, seed, 0) as h:
+        h.engineer_begin(S=8, pass_mult=1, max_sweeps=64)
+        res = h.engineer_run(0, 6, 3, log=str(path))
+        recs = [json.loads(x) for x in path.read_text().splitlines()]
+        assert [r["step"] for r in recs] == list(range(6))
+        for i, r in enumerate(recs):
+            assert (r["coupler"], r["J_old"], r["J_new"], r["tts_new"], r["accepted"]) == (
+                res["edge"][i], res["old_value"][i], res["new_value"][i], res["tts_new"][i], bool(res["accepted"][i]))
+            assert r["device_ms_per_eval"] > 0
+        assert recs[-1]["n_hit_now"] == h.engineer_state()[1]
+        h.lao_begin(64, 3, 6, 5)
+        with open(path, "a") as f:
+            lres = h.lao_run(1, 4, 2, log=f)
+    recs = [json.loads(x) for x in path.read_text().splitlines()][6:]
+    assert [r["kind"] for r in recs] == ["lao"] * 4
+    assert [r["removed_loop"] for r in recs] == list(lres["removed"])
+
+
+@pytest.mark.parametrize("spec,max_sweeps", [(1, 0), (4, 0), (4, 64)])
+def test_adaptive_budget_matches_oracle(P, spec, max_sweeps):
+    """Appendix B's rule in runs and sweeps: the run count of every step, its
+    TTS and decision, and the halvings equal the oracle's; speculative
+    batches are cut where the run count changes."""
+    L, seed, base, NT = 2, 101, 0, 4
+    J0 = W.random_couplers(L, seed, 0)
+    betas = W.beta_ladder(NT, 0.5, 3.0)
+    S, pm, n0, nmin = (16, 2, 32, 4) if not max_sweeps else (8, 1, 32, 4)
+    cost_max = 10 * S * pm if not max_sweeps else 12 * 16
+    with P.PTHandle(L, J0, betas, n0, seed, base) as h:
+        t0 = h.engineer_begin(S=S, pass_mult=pm, base_uid=base, max_sweeps=max_sweeps)
+        h.set_adaptive(n0, nmin, cost_max, beta_per_run=0.05)
+        res = h.engineer_run(0, 10, spec)
+        n_after = h.adaptive_runs()
+        J_gpu, t_gpu = h.couplers(), h.engineer_tts()
+    Jf, tf, n2, log = oracle.engineer_run_adaptive(L, J0, betas, seed, base, S, pm, 1, 0, 10, n0, nmin, cost_max, t0,
+                                                   beta_per_run=0.05, max_sweeps=max_sweeps)
+    assert list(res["n_runs"]) == list(log["n"]) and list(res["level"]) == list(log["level"])
+    assert list(res["tts_new"]) == list(log["tts"]) and list(res["accepted"]) == list(log["accept"])
+    assert n_after == n2 and t_gpu == tf and np.array_equal(J_gpu, Jf)
+    assert len(set(log["n"])) >= 2                    # the run count did change

@@ -19,17 +19,21 @@ def P():
     return pkg
 
 
-@pytest.mark.parametrize("L,NT,R,M,S,beta,spec", [(2, 6, 4, 10, 128, -1.0, 1), (4, 8, 8, 40, 256, 0.05, 4),
-                                                  (4, 8, 8, 40, 256, -1.0, 16)])
-def test_lao_matches_oracle(P, L, NT, R, M, S, beta, spec):
+@pytest.mark.parametrize("L,NT,R,M,S,beta,spec,w", [(2, 6, 4, 10, 128, -1.0, 1, 3), (4, 8, 8, 40, 256, 0.05, 4, 3),
+                                                    (4, 8, 8, 40, 256, -1.0, 16, 3), (2, 6, 4, 10, 128, -1.0, 1, 5),
+                                                    (4, 8, 8, 60, 256, 0.05, 4, 5), (4, 8, 8, 60, 256, -1.0, 16, 5)])
+def test_lao_matches_oracle(P, L, NT, R, M, S, beta, spec, w):
+    """Weights 1..w (the paper's [1, 5]); couplers of overlapping loops sum past
+    +-3, so the handle's Metropolis table grows beyond 19 rows."""
     seed, uid, steps = 20160516, 21, 14
     betas = W.beta_ladder(NT, 0.1, 3.0)
-    ref = oracle.LAOState(L, betas, R, seed, uid, M, S=S, beta_rao=beta)
+    ref = oracle.LAOState(L, betas, R, seed, uid, M, w_max=w, S=S, beta_rao=beta)
     log = ref.run(1, steps)
     with P.PTHandle(L, np.zeros(W.chimera_n_edges(L), np.int8), betas, R, seed, 0) as h:
-        t0 = h.lao_begin(S, uid, M, 3, 1, beta)
+        t0 = h.lao_begin(S, uid, M, w, 1, beta)
         res = h.lao_run(1, steps, spec)
         st = h.lao_state()
+        rows = h.table_rows()
     assert np.array_equal(res["removed"], log["removed"])
     assert np.array_equal(res["tts_new"], log["tts"])
     assert np.array_equal(res["E_gs_new"], log["E_gs"])
@@ -38,6 +42,8 @@ def test_lao_matches_oracle(P, L, NT, R, M, S, beta, spec):
     assert st["E_gs"] == ref.E_gs and st["tts"] == ref.tts
     assert t0 == res["tts_old"][0]
     assert oracle.energy(L, st["J"], st["planted"]) == st["E_gs"]
+    if w == 5 and L == 4:
+        assert np.abs(st["J"]).max() > 3 and rows > 19
 
 
 def test_lao_c8_shape_known_target(P):
@@ -46,7 +52,7 @@ def test_lao_c8_shape_known_target(P):
     cfg = W.CONFIGS["c8_single"]
     betas = W.beta_ladder(cfg["n_temps"], cfg["beta_min"], cfg["beta_max"])
     with P.PTHandle(8, np.zeros(W.chimera_n_edges(8), np.int8), betas, cfg["n_runs"], cfg["seed"], 0) as h:
-        h.lao_begin(1 << 12, 7, 350, 3)
+        h.lao_begin(1 << 12, 7, 350, 5)
         st = h.lao_state()
         h.reset(0)                                   # fresh runs on the planted couplers
         h.sweep(512, 1)

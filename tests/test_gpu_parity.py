@@ -266,7 +266,11 @@ def test_checkpoint_resume(P):
     for k in ("spins", "E", "perm", "best", "first", "macc", "xacc"):
         assert np.array_equal(straight[k], resumed[k]), k
     bad = buf.copy()
-    bad[64 + 3] = 9                                    # corrupt a coupler byte
+    bad[64 + 3] = 0x80                                 # a coupler byte of -128: outside [-127, 127]
+    with pytest.raises(P.PTError):
+        h3.restore(bad)
+    bad = buf.copy()
+    bad[64 + 3] = 125                                  # its spins' sums of |J| would exceed 127
     with pytest.raises(P.PTError):
         h3.restore(bad)
     with pytest.raises(P.PTError):
@@ -325,3 +329,37 @@ def test_single_instance_config_launch_shape(P, mapping):
     assert (tts, nhit, target) == oracle.tts(st["best"], st["first"], oracle.TARGET_BEST, cfg["sweeps"])
     assert np.all(np.sort(st["perm"], axis=1) == np.arange(NT))
     assert st["macc"].sum() > 0 and st["xacc"].sum() > 0
+
+
+def test_large_couplers_and_table_growth(P):
+    """Couplers beyond +-3 (planted instances sum loop weights): the Metropolis
+    table has one row per local-field value up to the largest sum of |J| over a
+    spin's couplers.  A handle created on +-3 couplers (19 rows) whose coupler
+    change needs more rows enlarges its table; fresh runs on the changed
+    couplers then match the oracle bit-exactly."""
+    L, NT, R, seed = 4, 8, 4, 20160518
+    betas = W.beta_ladder(NT, 0.1, 3.0)
+    rng = np.random.default_rng(3)
+    Jbig = rng.integers(-9, 10, size=W.chimera_n_edges(L)).astype(np.int8)
+    with P.PTHandle(L, Jbig, betas, R, seed, 4) as h:
+        assert h.table_rows() >= oracle.coupler_kmax(L, Jbig) + 1 > 19
+        h.sweep(120, 1)
+        ref = oracle.PTState(L, Jbig, betas, R, seed, 4)
+        ref.sweeps(120, 1)
+        _assert_state_equal(h.state(), ref, "couplers in [-9, 9]")
+    J = W.random_couplers(L, seed, 0)
+    with P.PTHandle(L, J, betas, R, seed, 5) as h:
+        assert h.table_rows() == 19
+        h.set_coupler(0, 90)                 # spin 0 (and 4): sum of |J| well above 18
+        J2 = J.copy()
+        J2[0] = 90
+        rows = h.table_rows()
+        assert rows >= oracle.coupler_kmax(L, J2) + 1
+        h.reset(5)
+        h.sweep(80, 1)
+        ref = oracle.PTState(L, J2, betas, R, seed, 5)
+        ref.sweeps(80, 1)
+        _assert_state_equal(h.state(), ref, "after table growth")
+        with pytest.raises(P.PTError):
+            h.set_coupler(1, 100)           # spin 0's sum would exceed 127
+        assert h.table_rows() == rows and np.array_equal(h.couplers(), J2)

@@ -539,3 +539,45 @@ def test_engineer_run_with_doubling_budget_replays():
     a = oracle.engineer_run(L, J0, betas, R, seed, base, 16, 2, 1, 0, 4)
     b = oracle.engineer_run(L, J0, betas, R, seed, base, 16, 2, 1, 0, 4, max_sweeps=0)
     assert a[1] == b[1] and all(np.array_equal(a[2][k], b[2][k]) for k in a[2])
+
+
+# --------------------------------------------------------------------------
+# Appendix B's adaptive budget, in runs and sweeps.
+# --------------------------------------------------------------------------
+def test_adaptive_budget_rule():
+    """The run count halves after every step whose cost (runs x sweeps used)
+    exceeds the cap, never below n_min; the Boltzmann beta follows 6.5 n; an
+    evaluation with n runs is the first n runs of a full evaluation (each
+    run's streams are keyed by its own index)."""
+    L, seed, base = 2, 101, 0
+    J0 = W.random_couplers(L, seed, 0)
+    betas = W.beta_ladder(4, 0.5, 3.0)
+    S, pm, n0, nmin = 16, 2, 32, 4
+    cost_max = 20 * S * pm                 # exceeded while n > 20
+    t0 = oracle.tts_eval(L, J0, betas, n0, seed, base, S, pm, 1)[0]
+    Jf, tf, n_after, log = oracle.engineer_run_adaptive(L, J0, betas, seed, base, S, pm, 1, 0, 8, n0, nmin, cost_max,
+                                                        t0, beta_per_run=0.05)
+    assert list(log["n"]) == [32, 16, 16, 16, 16, 16, 16, 16] and n_after == 16
+    assert np.all(log["level"] == S * pm)
+    Jf2, _, n2, log2 = oracle.engineer_run_adaptive(L, J0, betas, seed, base, S, pm, 1, 0, 8, n0, nmin, 1, t0,
+                                                    beta_per_run=0.05)
+    assert list(log2["n"]) == [32, 16, 8, 4, 4, 4, 4, 4] and n2 == 4
+    # replay: every step's TTS is an n-run evaluation and the rule uses beta = 0.05 n
+    cur, J = t0, J0.copy()
+    for a in range(8):
+        e, v, cu, u = oracle.engineer_draw(L, J, seed, base, a)
+        Jc = J.copy()
+        Jc[e] = v
+        n = int(log2["n"][a])
+        tn = oracle.tts_eval(L, Jc, betas, n, seed, cu, S, pm, 1)[0]
+        assert tn == log2["tts"][a]
+        st = oracle.PTState(L, Jc, betas, 32, seed, cu)      # first n of 32 runs: same trajectories
+        st.sweeps(S * pm, 1)
+        assert oracle.tts(st.best[:n], st.first[:n], oracle.TARGET_BEST, S)[0] == tn
+        acc = oracle.rao_accept(cur, tn, 1, 0.05 * n, u)
+        assert bool(log2["accept"][a]) == acc
+        if acc:
+            cur, J = tn, Jc
+    assert cur == oracle.engineer_run_adaptive(L, J0, betas, seed, base, S, pm, 1, 0, 8, n0, nmin, 1, t0,
+                                               beta_per_run=0.05)[1]
+    assert np.array_equal(J, Jf2)
