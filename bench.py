@@ -665,8 +665,10 @@ def run_guided_experiment(args):
       plain      proposals 0..3 (no ranking);
       untrained  the 4 ranked best by a network with initial weights;
       online     the 4 ranked best by a network retrained every 8 steps on
-                 the loop's own evaluations (differences candidate - base,
-                 guided.train_pairs); training time counts against its budget.
+                 the loop's 1024 most recent evaluations (differences
+                 candidate - base, guided.train_pairs), the plain choice
+                 until its first training; training time counts against its
+                 budget.
     From each of --guided-test-instances seeded instances every arm runs for
     --guided-seconds; reported: gain in log10 TTS per GPU-second (up to the
     first unsolved TTS), per-arm mean and standard error, paired differences,
@@ -722,7 +724,8 @@ def run_guided_experiment(args):
         "metric": "log-TTS gain per GPU-s, surrogate vs plain", "unit": "log10 TTS / GPU-s",
         "config": {"shape": {k: v for k, v in sh.items()}, "proposals": 64, "evaluated_per_step": 4,
                    "acceptance": "best of the 4 evaluated, kept if its TTS beats the current one (all arms)",
-                   "online_training": "every 8 steps, 4 epochs of train_pairs over all pairs so far, lr 1e-3",
+                   "online_training": "every 8 steps, 4 epochs of train_pairs over the 1024 most recent pairs, "
+                                      "lr 1e-3; no ranking before the first training",
                    "gpu_seconds_per_arm": args.guided_seconds, "instances": args.guided_test_instances,
                    "gain": "until the TTS first reaches the unsolved value, or the budget ends"},
         "noise_floor": noise,

@@ -10,8 +10,10 @@
 //   readout:   y = w2 . relu(W1 mean_i(h_i) + b1) + b2
 // Hidden width 64.  Weights and activations are BF16, accumulation FP32; the
 // three per-layer linear maps (K = 128 -> 64 outputs over every message,
-// node or edge row) run on tensor cores (mma.sync m16n8k16 BF16).  Gradients
-// are FP32 buffers; master weights and Adam moments are FP32.
+// node or edge row), their input gradients and their weight gradients run on
+// the 5th-generation tensor cores (tcgen05.mma, accumulators in tensor
+// memory).  Gradients are FP32 buffers; master weights and Adam moments are
+// FP32.
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -43,16 +45,6 @@ __device__ __forceinline__ float2 unpack_bf2(uint32_t u)
     return __bfloat1622float2(v);
 }
 
-__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                         uint32_t b0, uint32_t b1)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
 // Row r of a linear map's input is [P0[idx0(r)] | P1[idx1(r)]] with
 // idx(r) = (r / R_local) * S + map[r % R_local] (64 BF16 per row each).
 struct RowSrc {
@@ -71,268 +63,508 @@ struct RowSrc {
     }
 };
 
-// ------------------------------------------------------------ forward GEMM
-// Z = W X + bias for 16 rows per warp, W [64][128] BF16 staged in shared
-// memory.  EPI 0 (messages): Z -> Zout (BF16), relu(Z) -> Rout (FP32).
-// EPI 1 (residual): Z -> Zout, Yout = P0 row + relu(Z) (BF16).
-template <int EPI>
-__global__ void __launch_bounds__(256) lin_fwd_kernel(int rows, RowSrc src, const bf16* __restrict__ W,
-                                                      const float* __restrict__ bias, bf16* __restrict__ Zout,
-                                                      float* __restrict__ Rout, bf16* __restrict__ Yout)
-{
-    __shared__ uint32_t Ws[HD][KIN / 2 + 4];
-    for (int i = threadIdx.x; i < HD * KIN / 2; i += blockDim.x)
-        Ws[i / (KIN / 2)][i % (KIN / 2)] = reinterpret_cast<const uint32_t*>(W)[i];
-    __syncthreads();
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const int warps = blockDim.x >> 5;
-    const int ntiles = (rows + 15) / 16;
-    for (int tile = blockIdx.x * warps + (threadIdx.x >> 5); tile < ntiles; tile += gridDim.x * warps) {
-        const int ra = tile * 16 + g, rb = ra + 8;
-        const bool va = ra < rows, vb = rb < rows;
-        const uint32_t* pa0 = va ? src.half(ra, 0) : nullptr;
-        const uint32_t* pa1 = va ? src.half(ra, 1) : nullptr;
-        const uint32_t* pb0 = vb ? src.half(rb, 0) : nullptr;
-        const uint32_t* pb1 = vb ? src.half(rb, 1) : nullptr;
-        float acc[8][4];
-#pragma unroll
-        for (int n = 0; n < 8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-#pragma unroll
-        for (int ks = 0; ks < 8; ++ks) {
-            const int cw = (ks & 3) * 8 + t;          // u32 index inside the 64-wide half
-            const uint32_t* sa = ks < 4 ? pa0 : pa1;
-            const uint32_t* sb = ks < 4 ? pb0 : pb1;
-            const uint32_t a0 = va ? sa[cw] : 0u, a2 = va ? sa[cw + 4] : 0u;
-            const uint32_t a1 = vb ? sb[cw] : 0u, a3 = vb ? sb[cw + 4] : 0u;
-#pragma unroll
-            for (int n = 0; n < 8; ++n)
-                mma_bf16(acc[n], a0, a1, a2, a3, Ws[n * 8 + g][ks * 8 + t], Ws[n * 8 + g][ks * 8 + 4 + t]);
-        }
-#pragma unroll
-        for (int n = 0; n < 8; ++n) {
-            const int c = n * 8 + 2 * t;
-            const float b0 = bias[c], b1 = bias[c + 1];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int r = h ? rb : ra;
-                if (!(h ? vb : va)) continue;
-                const float z0 = acc[n][2 * h] + b0, z1 = acc[n][2 * h + 1] + b1;
-                reinterpret_cast<uint32_t*>(Zout + (size_t)r * HD)[c / 2] = pack_bf2(z0, z1);
-                if (EPI == 0) {
-                    reinterpret_cast<float2*>(Rout + (size_t)r * HD)[c / 2] = make_float2(fmaxf(z0, 0.f), fmaxf(z1, 0.f));
-                } else {
-                    const float2 base = unpack_bf2((h ? pb0 : pa0)[c / 2]);
-                    reinterpret_cast<uint32_t*>(Yout + (size_t)r * HD)[c / 2] =
-                        pack_bf2(base.x + fmaxf(z0, 0.f), base.y + fmaxf(z1, 0.f));
-                }
-            }
-        }
-    }
-}
+// Floats of one CTA's weight-gradient partial: dW [64][128] then db [64].
+constexpr int WPART = HD * KIN + HD;
 
-__device__ __forceinline__ void ldsm_x4(uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3, const void* p)
-{
-    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(a));
-}
-
-// ------------------------------------------------ backward: dX = dZ . W
-// dZ [rows][64] BF16, each warp's 16-row tile staged in shared memory with
-// 16-byte loads and read by ldmatrix; W^T staged as [128][64].  Launched
-// with 256 threads (8 warps).  EPI 0: dX [rows][128] FP32.
-// EPI 1 (the node and edge updates, whose input halves have separate
-// gradients): out0 = base + dX[:, :64] (base may be out0 or NULL) and
-// out1 = dX[:, 64:], both [rows][64] FP32, without materialising dX.
-template <int EPI>
-__global__ void __launch_bounds__(256) lin_bwd_input_kernel(int rows, const bf16* __restrict__ dZ,
-                                                            const bf16* __restrict__ W, float* __restrict__ dX,
-                                                            const float* base, float* out0, float* __restrict__ out1)
-{
-    __shared__ uint32_t WT[KIN][HD / 2 + 4];
-    for (int i = threadIdx.x; i < KIN * HD / 2; i += blockDim.x) {
-        const int in = i / (HD / 2), op = i % (HD / 2);        // pair of outputs 2op, 2op+1
-        const float w0 = __bfloat162float(W[(2 * op) * KIN + in]);
-        const float w1 = __bfloat162float(W[(2 * op + 1) * KIN + in]);
-        __nv_bfloat162 v = __floats2bfloat162_rn(w0, w1);
-        WT[in][op] = *reinterpret_cast<uint32_t*>(&v);
-    }
-    __syncthreads();
-    __shared__ __align__(16) bf16 Zs[8][16][HD + 8];
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3, w = threadIdx.x >> 5;
-    const int lr = lane & 7, lq = lane >> 3;
-    bf16 (*Zt)[HD + 8] = Zs[w];
-    const int warps = blockDim.x >> 5;
-    const int ntiles = (rows + 15) / 16;
-    for (int tile = blockIdx.x * warps + w; tile < ntiles; tile += gridDim.x * warps) {
-        const int ra = tile * 16 + g, rb = ra + 8;
-        const bool va = ra < rows, vb = rb < rows;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {                 // 16 rows x 8 16-byte words of dZ
-            const int i = lane + 32 * j, rr = i >> 3, q = i & 7, r = tile * 16 + rr;
-            const uint4 v = r < rows ? reinterpret_cast<const uint4*>(dZ + (size_t)r * HD)[q] : make_uint4(0u, 0u, 0u, 0u);
-            *reinterpret_cast<uint4*>(&Zt[rr][q * 8]) = v;
-        }
-        __syncwarp();
-        float acc[16][4];
-#pragma unroll
-        for (int n = 0; n < 16; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-#pragma unroll
-        for (int ks = 0; ks < 4; ++ks) {
-            uint32_t a0, a1, a2, a3;
-            ldsm_x4(a0, a1, a2, a3, &Zt[(lq & 1) * 8 + lr][ks * 16 + (lq >> 1) * 8]);
-#pragma unroll
-            for (int n = 0; n < 16; ++n)
-                mma_bf16(acc[n], a0, a1, a2, a3, WT[n * 8 + g][ks * 8 + t], WT[n * 8 + g][ks * 8 + 4 + t]);
-        }
-        __syncwarp();                                 // the tile is read before it is restaged
-#pragma unroll
-        for (int n = 0; n < 16; ++n) {
-            const int c = n * 8 + 2 * t;
-            if (EPI == 0) {
-                if (va) reinterpret_cast<float2*>(dX + (size_t)ra * KIN)[c / 2] = make_float2(acc[n][0], acc[n][1]);
-                if (vb) reinterpret_cast<float2*>(dX + (size_t)rb * KIN)[c / 2] = make_float2(acc[n][2], acc[n][3]);
-            } else if (n < 8) {
-#pragma unroll
-                for (int hh = 0; hh < 2; ++hh) {
-                    const int r = hh ? rb : ra;
-                    if (!(hh ? vb : va)) continue;
-                    float2 v = make_float2(acc[n][2 * hh], acc[n][2 * hh + 1]);
-                    if (base) {
-                        const float2 b = reinterpret_cast<const float2*>(base + (size_t)r * HD)[c / 2];
-                        v.x = b.x + v.x;
-                        v.y = b.y + v.y;
-                    }
-                    reinterpret_cast<float2*>(out0 + (size_t)r * HD)[c / 2] = v;
-                }
-            } else {
-                if (va) reinterpret_cast<float2*>(out1 + (size_t)ra * HD)[c / 2 - HD / 2] = make_float2(acc[n][0], acc[n][1]);
-                if (vb) reinterpret_cast<float2*>(out1 + (size_t)rb * HD)[c / 2 - HD / 2] = make_float2(acc[n][2], acc[n][3]);
-            }
-        }
-    }
-}
-
-// ------------------------------- backward: dW = dZ^T . X, db = column sums of dZ
-// Persistent blocks take 64-row chunks c = blockIdx.x, c += gridDim.x.  A
-// chunk is staged row-major with 16-byte loads (dZ [64][64], X [64][128] from
-// its two gathered halves), the next chunk's loads are issued into registers
-// before the current chunk's MMAs, and ldmatrix.trans transposes the 8x8
-// sub-tiles on their way into the mma.sync fragments (A = dZ^T, B = X).
-// Warp w accumulates output rows 16*(w/2)..+16 and columns 64*(w%2)..+64;
-// the even warps also sum their rows of dZ (one extra MMA against ones).
-// Each block writes its partial [64][128] + [64] to `part`, and
-// lin_wgrad_reduce adds all blocks' partials into dW and db in a fixed order.
-constexpr int WCH = 64;                  // rows per chunk
-constexpr int ZP = HD + 8;               // shared row pitches (bf16): 16 bytes of padding
-constexpr int XP = KIN + 8;              // make every ldmatrix phase conflict-free
-constexpr int WPART = HD * KIN + HD;     // floats of one block's partial
-
-__device__ __forceinline__ void ldsm_x4_trans(uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3, const void* p)
-{
-    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(a));
-}
-
-struct WChunk {                          // one thread's share of a chunk: 2 + 4 16-byte words
-    uint4 z[2], x[4];
-};
-
-__device__ __forceinline__ void wgrad_load(WChunk& v, int rows, int r0, const bf16* __restrict__ dZ,
-                                           const RowSrc& src)
-{
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-        const int i = threadIdx.x + j * 256, rr = i >> 3, q = i & 7, r = r0 + rr;
-        v.z[j] = r < rows ? reinterpret_cast<const uint4*>(dZ + (size_t)r * HD)[q] : make_uint4(0u, 0u, 0u, 0u);
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int i = threadIdx.x + j * 256, rr = i >> 4, seg = i & 15, r = r0 + rr;
-        v.x[j] = r < rows ? reinterpret_cast<const uint4*>(src.half(r, seg >> 3))[seg & 7] : make_uint4(0u, 0u, 0u, 0u);
-    }
-}
-
-__global__ void __launch_bounds__(256, 2) lin_wgrad_kernel(int rows, const bf16* __restrict__ dZ, RowSrc src,
-                                                           float* __restrict__ part)
-{
-    __shared__ __align__(16) bf16 Zs[WCH][ZP];
-    __shared__ __align__(16) bf16 Xs[WCH][XP];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
-    const int lr = lane & 7, lq = lane >> 3;          // ldmatrix: row inside an 8x8 tile, tile index
-    const int mrow = (w >> 1) * 16, ncol = (w & 1) * 64;
-    const uint32_t ones = 0x3F803F80u;                // two bf16 1.0
-    float acc[8][4], accb[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int n = 0; n < 8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-    const int nchunks = (rows + WCH - 1) / WCH;
-    WChunk v;
-    int c = blockIdx.x;
-    if (c < nchunks) wgrad_load(v, rows, c * WCH, dZ, src);
-    for (; c < nchunks; c += gridDim.x) {
-        __syncthreads();                              // the previous chunk's MMAs are done
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int i = threadIdx.x + j * 256;
-            *reinterpret_cast<uint4*>(&Zs[i >> 3][(i & 7) * 8]) = v.z[j];
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int i = threadIdx.x + j * 256;
-            *reinterpret_cast<uint4*>(&Xs[i >> 4][(i & 15) * 8]) = v.x[j];
-        }
-        __syncthreads();
-        if (c + (int)gridDim.x < nchunks) wgrad_load(v, rows, (c + gridDim.x) * WCH, dZ, src);
-#pragma unroll
-        for (int ks = 0; ks < WCH / 16; ++ks) {
-            const int k0 = ks * 16;
-            uint32_t a0, a1, a2, a3;                  // (m0-7,k0-7) (m8-15,k0-7) (m0-7,k8-15) (m8-15,k8-15)
-            ldsm_x4_trans(a0, a1, a2, a3, &Zs[k0 + (lq >> 1) * 8 + lr][mrow + (lq & 1) * 8]);
-            if ((w & 1) == 0) mma_bf16(accb, a0, a1, a2, a3, ones, ones);
-#pragma unroll
-            for (int np = 0; np < 4; ++np) {          // n-tiles n0 and n0 + 8
-                const int n0 = ncol + np * 16;
-                uint32_t b0, b1, b2, b3;              // (k0-7,n0) (k8-15,n0) (k0-7,n0+8) (k8-15,n0+8)
-                ldsm_x4_trans(b0, b1, b2, b3, &Xs[k0 + (lq & 1) * 8 + lr][n0 + (lq >> 1) * 8]);
-                mma_bf16(acc[2 * np], a0, a1, a2, a3, b0, b1);
-                mma_bf16(acc[2 * np + 1], a0, a1, a2, a3, b2, b3);
-            }
-        }
-    }
-    float* P = part + (size_t)blockIdx.x * WPART;
-#pragma unroll
-    for (int n = 0; n < 8; ++n) {
-        const int col = ncol + n * 8 + 2 * t;
-        *reinterpret_cast<float2*>(&P[(mrow + g) * KIN + col]) = make_float2(acc[n][0], acc[n][1]);
-        *reinterpret_cast<float2*>(&P[(mrow + g + 8) * KIN + col]) = make_float2(acc[n][2], acc[n][3]);
-    }
-    if ((w & 1) == 0 && t == 0) {                     // every column of the ones tile is the row sum
-        P[HD * KIN + mrow + g] = accb[0];
-        P[HD * KIN + mrow + g + 8] = accb[2];
-    }
-}
-
-// dW += sum over blocks of the partials (and db likewise), blocks in order.
-__global__ void lin_wgrad_reduce(int nblocks, const float* __restrict__ part, float* __restrict__ dW,
-                                 float* __restrict__ db)
+// dW += sum over blocks of the partials (and db likewise), in a fixed order:
+// stage 1 (grid.y = WRED_GROUPS) sums consecutive ranges of the partials
+// into `tmp`, stage 2 adds the group sums in order.
+constexpr int WRED_GROUPS = 16;
+__global__ void lin_wgrad_reduce1(int nblocks, const float* __restrict__ part, float* __restrict__ tmp)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= WPART) return;
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-    int b = 0;
-    for (; b + 4 <= nblocks; b += 4) {
+    const int per = (nblocks + WRED_GROUPS - 1) / WRED_GROUPS;
+    const int b0 = blockIdx.y * per, b1 = min(nblocks, b0 + per);
+    float s0 = 0.f, s1 = 0.f;
+    int b = b0;
+    for (; b + 2 <= b1; b += 2) {
         s0 += part[(size_t)b * WPART + i];
         s1 += part[(size_t)(b + 1) * WPART + i];
-        s2 += part[(size_t)(b + 2) * WPART + i];
-        s3 += part[(size_t)(b + 3) * WPART + i];
     }
-    for (; b < nblocks; ++b) s0 += part[(size_t)b * WPART + i];
-    const float s = (s0 + s1) + (s2 + s3);
+    if (b < b1) s0 += part[(size_t)b * WPART + i];
+    tmp[(size_t)blockIdx.y * WPART + i] = s0 + s1;
+}
+
+__global__ void lin_wgrad_reduce2(const float* __restrict__ tmp, float* __restrict__ dW, float* __restrict__ db)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= WPART) return;
+    float s = 0.f;
+    for (int g = 0; g < WRED_GROUPS; ++g) s += tmp[(size_t)g * WPART + i];
     if (i < HD * KIN) dW[i] += s;
     else db[i - HD * KIN] += s;
+}
+
+// ------------------------------------------- tcgen05 (5th-generation tensor core) GEMMs
+// The forward maps Z = X W^T + b (128 rows x K = 128 -> 64 outputs per tile)
+// and the input gradient dX = dZ W (128 rows x K = 64 -> 128 inputs per
+// tile) run on tcgen05.mma with the accumulator in tensor memory:
+//   * one CTA of 128 threads per 128-row tile (persistent over tiles); one
+//     thread issues the MMAs and commits them to an mbarrier;
+//   * operands in shared memory in the canonical K-major layout without
+//     swizzle, built from 8-row x 16-byte core matrices stored as
+//     [8-row group][k-chunk of 8 elements][8 rows][16 bytes]: core matrices
+//     adjacent in K are 128 bytes apart (the leading byte offset) and 8-row
+//     groups (number of k-chunks) x 128 bytes apart (the stride byte offset).
+//     Read with the two offsets the other way round, every address would
+//     still lie inside the 48 KB the kernels allocate;
+//   * the weights, pre-packed in that layout (pack_weights_kernel), arrive by
+//     one bulk asynchronous copy; the gathered input rows by 16-byte cp.async;
+//   * after the commit each warp reads its 32 accumulator rows (TMEM lanes
+//     32w .. 32w+31) with tcgen05.ld, one row per thread, for the epilogue;
+//   * every mbarrier wait is bounded: on a timeout the CTA records it in
+//     *err, stops taking tiles, frees its tensor memory and returns.
+constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;
+constexpr int TC_ROWS = 128;
+// CTAs of 256 threads: all 8 warps stage a tile; in the epilogue warps w and
+// w + 4 read the same 32 tensor-memory lanes (a warp reaches lanes
+// 32 (w mod 4) .. + 31) and split the columns.  Dynamic shared memory:
+// forward A 32 KB + W 16 KB = 48 KB, input gradient dZ 16 KB + W^T 16 KB
+// padded to 48 KB (4 CTAs per SM, 64 or 128 tensor-memory columns each);
+// weight gradient two stages of 24 KB (the next chunk loads while the
+// current one is multiplied) + ones 16 KB = 64 KB (3 CTAs, 128 columns).  The
+// shared memory bounds the resident CTAs, so their tensor memory never
+// exceeds an SM's 512 columns; the persistent grids use exactly that many.
+constexpr int TC_THREADS = 256;
+constexpr int TC_A_FWD = TC_ROWS * KIN * 2, TC_A_BWD = TC_ROWS * HD * 2;
+constexpr int TC_SMEM_FWD = TC_A_FWD + HD * KIN * 2;
+constexpr int TC_SMEM_BWD = TC_SMEM_FWD;
+constexpr int TC_CTAS_FWD = 4, TC_CTAS_BWD = 4, TC_CTAS_WGRAD = 3;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor of tcgen05.mma: start address, leading and
+// stride byte offsets (all >> 4), descriptor version 1 (bits 46-47), no
+// swizzle (layout type 0 in bits 61-63), base offset 0.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor, kind::f16: F32 accumulator (bits 4-5 = 1), BF16 A
+// and B (bits 7-9, 10-12 = 1), both K-major, N >> 3 in bits 17-22, M >> 4 in
+// bits 24-28.
+__host__ __device__ constexpr uint32_t tc_idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+{
+    for (uint32_t i = 0; i < TC_WAIT_LIMIT; ++i) {
+        uint32_t done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done)
+                     : "r"(smem_u32(bar)), "r"(parity)
+                     : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// One bulk asynchronous copy global -> shared of `bytes` (a multiple of 16,
+// both addresses 16-byte aligned), completing on `bar`.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accum)
+{
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                 ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Common prologue: tensor memory (ncols columns, warp 0), the two mbarriers,
+// and the packed weights (bytes) by one bulk copy.  Returns false (for every
+// thread) if the weights did not arrive within the wait limit.
+__device__ __forceinline__ bool tc_setup(uint32_t* tmem_sh, uint64_t* bar_w, uint64_t* bar_mma, uint32_t ncols,
+                                         void* Ws, const void* Wpk, uint32_t bytes)
+{
+    const int tid = threadIdx.x;
+    if ((tid >> 5) == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_sh)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(bar_w, 1);
+        mbar_init(bar_mma, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (bytes == 0) return true;
+    if (tid == 0) bulk_g2s(Ws, Wpk, bytes, bar_w);
+    bool ok = mbar_wait(bar_w, 0);
+    if (!ok) ok = mbar_wait(bar_w, 0);         // second bounded wait for the copy still in flight
+    return !__syncthreads_or(!ok);
+}
+
+__device__ __forceinline__ void tc_teardown(uint32_t tmem, uint32_t ncols, bool failed, int* err)
+{
+    tc_fence_before();
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    }
+    if (failed && threadIdx.x == 0) atomicExch(err, 1);
+}
+
+// Forward: Z = X W^T + bias over `rows` gathered rows (see RowSrc).  EPI 0
+// (messages): Z -> Zout (BF16), relu(Z) -> Rout (FP32).  EPI 1 (residual):
+// Z -> Zout, Yout = P0 row + relu(Z) (BF16).
+template <int EPI>
+__global__ void __launch_bounds__(TC_THREADS) lin_fwd_tc_kernel(int rows, RowSrc src, const bf16* __restrict__ Wpk,
+                                                                const float* __restrict__ bias, bf16* __restrict__ Zout,
+                                                                float* __restrict__ Rout, bf16* __restrict__ Yout,
+                                                                int* err)
+{
+    extern __shared__ __align__(128) unsigned char tc_smem[];
+    unsigned char* As = tc_smem;                         // [16 row groups][16 k-chunks][8 rows][16 B]
+    unsigned char* Ws = tc_smem + TC_A_FWD;              // [8 output groups][16 k-chunks][8 outputs][16 B]
+    __shared__ __align__(8) uint64_t bar_w, bar_mma;
+    __shared__ uint32_t tmem_sh;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    bool failed = !tc_setup(&tmem_sh, &bar_w, &bar_mma, 64, Ws, Wpk, HD * KIN * 2);
+    const uint32_t tmem = tmem_sh;
+    constexpr uint32_t IDESC = tc_idesc_bf16(TC_ROWS, HD);
+    const int ntiles = (rows + TC_ROWS - 1) / TC_ROWS;
+    uint32_t phase = 0;
+    for (int tile = blockIdx.x; !failed && tile < ntiles; tile += gridDim.x) {
+        const int r0 = tile * TC_ROWS;
+        for (int i = tid; i < 16 * TC_ROWS; i += TC_THREADS) {   // chunk i: row (i >> 7) * 8 + (i & 7), k-chunk (i >> 3) & 15
+            const int kc = (i >> 3) & 15, row = ((i >> 7) << 3) | (i & 7), r = r0 + row;
+            const bool v = r < rows;
+            const unsigned char* g = v ? reinterpret_cast<const unsigned char*>(src.half(r, kc >> 3)) + (kc & 7) * 16
+                                       : reinterpret_cast<const unsigned char*>(Wpk);
+            cp_async16(As + i * 16, g, v);
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");     // visible to the tensor core
+        tc_fence_before();
+        __syncthreads();                                    // also: the previous tile's TMEM reads are done
+        tc_fence_after();
+        if (tid == 0) {
+#pragma unroll
+            for (int ks = 0; ks < KIN / 16; ++ks)
+                tc_mma(tmem, tc_desc(smem_u32(As) + ks * 256, 128, 16 * 128), tc_desc(smem_u32(Ws) + ks * 256, 128, 16 * 128),
+                       IDESC, ks > 0 ? 1u : 0u);
+            tc_commit(&bar_mma);
+        }
+        const bool ok = mbar_wait(&bar_mma, phase);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        tc_fence_after();
+        const int q = warp & 3, r = r0 + q * 32 + lane;    // TMEM lane q*32 + lane = this thread's row
+        const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
+#pragma unroll
+        for (int c0 = (warp >> 2) * (HD / 2); c0 < (warp >> 2) * (HD / 2) + HD / 2; c0 += 16) {
+            float z[16];
+            tmem_ld16(tl + c0, z);
+            tmem_ld_wait();
+            if (r < rows) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) z[i] += bias[c0 + i];
+                uint4 zp[2];
+                uint32_t* zw = reinterpret_cast<uint32_t*>(zp);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) zw[i] = pack_bf2(z[2 * i], z[2 * i + 1]);
+                uint4* zo = reinterpret_cast<uint4*>(Zout + (size_t)r * HD + c0);
+                zo[0] = zp[0];
+                zo[1] = zp[1];
+                if (EPI == 0) {
+                    float4* ro = reinterpret_cast<float4*>(Rout + (size_t)r * HD + c0);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        ro[i] = make_float4(fmaxf(z[4 * i], 0.f), fmaxf(z[4 * i + 1], 0.f), fmaxf(z[4 * i + 2], 0.f),
+                                            fmaxf(z[4 * i + 3], 0.f));
+                } else {
+                    const uint4* bp = reinterpret_cast<const uint4*>(reinterpret_cast<const bf16*>(src.half(r, 0)) + c0);
+                    uint4 b4[2] = {bp[0], bp[1]}, yp[2];
+                    const uint32_t* bw = reinterpret_cast<const uint32_t*>(b4);
+                    uint32_t* yw = reinterpret_cast<uint32_t*>(yp);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const float2 bb = unpack_bf2(bw[i]);
+                        yw[i] = pack_bf2(bb.x + fmaxf(z[2 * i], 0.f), bb.y + fmaxf(z[2 * i + 1], 0.f));
+                    }
+                    uint4* yo = reinterpret_cast<uint4*>(Yout + (size_t)r * HD + c0);
+                    yo[0] = yp[0];
+                    yo[1] = yp[1];
+                }
+            }
+        }
+    }
+    tc_teardown(tmem, 64, failed, err);
+}
+
+// Input gradient: dX = dZ W over `rows` rows of dZ [rows][64] (BF16), with
+// W^T pre-packed.  EPI 0: dX [rows][128] FP32.  EPI 1 (node and edge
+// updates): out0 = base + dX[:, :64] (base may be out0 or NULL) and
+// out1 = dX[:, 64:], both [rows][64] FP32.
+template <int EPI>
+__global__ void __launch_bounds__(TC_THREADS) lin_bwd_input_tc_kernel(int rows, const bf16* __restrict__ dZ,
+                                                                      const bf16* __restrict__ WTpk,
+                                                                      float* __restrict__ dX, const float* base,
+                                                                      float* out0, float* __restrict__ out1, int* err)
+{
+    extern __shared__ __align__(128) unsigned char tc_smem[];
+    unsigned char* As = tc_smem;                         // [16 row groups][8 k-chunks][8 rows][16 B]
+    unsigned char* Ws = tc_smem + TC_A_BWD;              // [16 input groups][8 k-chunks][8 inputs][16 B]
+    __shared__ __align__(8) uint64_t bar_w, bar_mma;
+    __shared__ uint32_t tmem_sh;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    bool failed = !tc_setup(&tmem_sh, &bar_w, &bar_mma, 128, Ws, WTpk, KIN * HD * 2);
+    const uint32_t tmem = tmem_sh;
+    constexpr uint32_t IDESC = tc_idesc_bf16(TC_ROWS, KIN);
+    const int ntiles = (rows + TC_ROWS - 1) / TC_ROWS;
+    uint32_t phase = 0;
+    for (int tile = blockIdx.x; !failed && tile < ntiles; tile += gridDim.x) {
+        const int r0 = tile * TC_ROWS;
+        for (int i = tid; i < 8 * TC_ROWS; i += TC_THREADS) {    // chunk i: row (i >> 6) * 8 + (i & 7), k-chunk (i >> 3) & 7
+            const int kc = (i >> 3) & 7, row = ((i >> 6) << 3) | (i & 7), r = r0 + row;
+            const bool v = r < rows;
+            const unsigned char* g = v ? reinterpret_cast<const unsigned char*>(dZ + (size_t)r * HD) + kc * 16
+                                       : reinterpret_cast<const unsigned char*>(WTpk);
+            cp_async16(As + i * 16, g, v);
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) {
+#pragma unroll
+            for (int ks = 0; ks < HD / 16; ++ks)
+                tc_mma(tmem, tc_desc(smem_u32(As) + ks * 256, 128, 8 * 128), tc_desc(smem_u32(Ws) + ks * 256, 128, 8 * 128),
+                       IDESC, ks > 0 ? 1u : 0u);
+            tc_commit(&bar_mma);
+        }
+        const bool ok = mbar_wait(&bar_mma, phase);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        tc_fence_after();
+        const int q = warp & 3, r = r0 + q * 32 + lane;
+        const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
+#pragma unroll
+        for (int c0 = (warp >> 2) * HD; c0 < (warp >> 2) * HD + HD; c0 += 16) {
+            float d[16];
+            tmem_ld16(tl + c0, d);
+            tmem_ld_wait();
+            if (r < rows) {
+                if (EPI == 0) {
+                    float4* o = reinterpret_cast<float4*>(dX + (size_t)r * KIN + c0);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) o[i] = make_float4(d[4 * i], d[4 * i + 1], d[4 * i + 2], d[4 * i + 3]);
+                } else if (c0 < HD) {
+                    float4* o = reinterpret_cast<float4*>(out0 + (size_t)r * HD + c0);
+                    const float4* bs = base ? reinterpret_cast<const float4*>(base + (size_t)r * HD + c0) : nullptr;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        float4 v = make_float4(d[4 * i], d[4 * i + 1], d[4 * i + 2], d[4 * i + 3]);
+                        if (bs) {
+                            const float4 bb = bs[i];
+                            v.x += bb.x; v.y += bb.y; v.z += bb.z; v.w += bb.w;
+                        }
+                        o[i] = v;
+                    }
+                } else {
+                    float4* o = reinterpret_cast<float4*>(out1 + (size_t)r * HD + (c0 - HD));
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) o[i] = make_float4(d[4 * i], d[4 * i + 1], d[4 * i + 2], d[4 * i + 3]);
+                }
+            }
+        }
+    }
+    tc_teardown(tmem, 128, failed, err);
+}
+
+// Weight gradient: dW = dZ^T X and db = column sums of dZ over `rows` rows,
+// as D[in][o] = sum_r X[r][in] dZ[r][o] (M = 128 inputs, N = 64 outputs,
+// K = rows) accumulated in tensor memory over the CTA's 64-row chunks c =
+// blockIdx.x, c += gridDim.x; db the same with a tile of ones in place of X.
+// Both operands are MN-major: a 16-byte chunk of a row of X (8 inputs) or of
+// dZ (8 outputs) is one row of a core matrix, so the rows are staged with
+// 16-byte cp.async and no transposition, as [MN group][k group][8 rows][16 B].
+// Each CTA writes its partial [64][128] + [64] like lin_wgrad_kernel, and
+// lin_wgrad_reduce1/2 add the partials in a fixed order.
+constexpr int TC_WCH = 64;                          // rows per chunk
+constexpr int TC_WSTAGE = TC_WCH * KIN * 2 + TC_WCH * HD * 2;          // X 16 KB + dZ 8 KB
+constexpr int TC_SMEM_WGRAD = 2 * TC_WSTAGE + TC_WCH * KIN * 2;         // two stages + ones 16 KB
+__global__ void __launch_bounds__(TC_THREADS) lin_wgrad_tc_kernel(int rows, const bf16* __restrict__ dZ, RowSrc src,
+                                                                  float* __restrict__ part, int* err)
+{
+    extern __shared__ __align__(128) unsigned char tc_smem[];
+    // stage b: X [16 input groups][8 row groups][8 rows][16 B], then dZ [8 output groups][8 row groups][8][16 B]
+    unsigned char* Os = tc_smem + 2 * TC_WSTAGE;             // ones, the layout of X
+    __shared__ __align__(8) uint64_t bar_w, bar_mma;
+    __shared__ uint32_t tmem_sh;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    bool failed = !tc_setup(&tmem_sh, &bar_w, &bar_mma, 128, nullptr, nullptr, 0);
+    const uint32_t tmem = tmem_sh;
+    for (int i = tid; i < TC_WCH * KIN / 8; i += TC_THREADS)   // 16 bytes of bf16 1.0 each
+        *reinterpret_cast<uint4*>(Os + i * 16) = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    // M = 128 inputs, N = 64 outputs, both operands MN-major (bits 15, 16)
+    constexpr uint32_t IDESC = tc_idesc_bf16(KIN, HD) | (1u << 15) | (1u << 16);
+    const int nchunks = (rows + TC_WCH - 1) / TC_WCH;
+    auto stage = [&](int c, int b) {
+        unsigned char* Xs = tc_smem + b * TC_WSTAGE;
+        unsigned char* Zs = Xs + TC_WCH * KIN * 2;
+        const int r0 = c * TC_WCH;
+        for (int i = tid; i < TC_WCH * KIN / 8; i += TC_THREADS) {   // X: chunk i -> row group (i>>3)&7, inputs (i>>6)*8..
+            const int r = r0 + (((i >> 3) & 7) << 3) + (i & 7), mg = i >> 6;
+            const bool v = r < rows;
+            const unsigned char* g = v ? reinterpret_cast<const unsigned char*>(src.half(r, mg >> 3)) + (mg & 7) * 16
+                                       : reinterpret_cast<const unsigned char*>(dZ);
+            cp_async16(Xs + i * 16, g, v);
+        }
+        for (int i = tid; i < TC_WCH * HD / 8; i += TC_THREADS) {    // dZ: outputs (i>>6)*8..
+            const int r = r0 + (((i >> 3) & 7) << 3) + (i & 7), ng = i >> 6;
+            const bool v = r < rows;
+            const unsigned char* g = v ? reinterpret_cast<const unsigned char*>(dZ + (size_t)r * HD) + ng * 16
+                                       : reinterpret_cast<const unsigned char*>(dZ);
+            cp_async16(Zs + i * 16, g, v);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    uint32_t phase = 0;
+    bool first = true;
+    int it = 0;
+    if (!failed && (int)blockIdx.x < nchunks) stage(blockIdx.x, 0);
+    for (int c = blockIdx.x; !failed && c < nchunks; c += gridDim.x, ++it) {
+        const int b = it & 1;
+        if (c + (int)gridDim.x < nchunks) {
+            stage(c + gridDim.x, b ^ 1);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) {
+            const uint32_t xs = smem_u32(tc_smem + b * TC_WSTAGE), zs = xs + TC_WCH * KIN * 2;
+#pragma unroll
+            for (int ks = 0; ks < TC_WCH / 16; ++ks) {
+                const uint32_t acc = (first && ks == 0) ? 0u : 1u;
+                const uint64_t bz = tc_desc(zs + ks * 256, 128, 8 * 128);
+                tc_mma(tmem, tc_desc(xs + ks * 256, 128, 8 * 128), bz, IDESC, acc);
+                tc_mma(tmem + HD, tc_desc(smem_u32(Os) + ks * 256, 128, 8 * 128), bz, IDESC, acc);
+            }
+            tc_commit(&bar_mma);
+        }
+        first = false;
+        const bool ok = mbar_wait(&bar_mma, phase);            // the chunk's MMAs are done: its stage is reusable
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    if (!failed) {
+        tc_fence_after();
+        float* P = part + (size_t)blockIdx.x * WPART;
+        const int q = warp & 3, in = q * 32 + (tid & 31);      // TMEM lane = input index
+        const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
+        if (warp < 4) {
+#pragma unroll
+            for (int c0 = 0; c0 < HD; c0 += 16) {
+                float d[16];
+                tmem_ld16(tl + c0, d);
+                tmem_ld_wait();
+#pragma unroll
+                for (int i = 0; i < 16; ++i) P[(c0 + i) * KIN + in] = d[i];
+            }
+        } else {
+#pragma unroll
+            for (int c0 = 0; c0 < HD; c0 += 16) {               // every lane holds the column sums
+                float d[16];
+                tmem_ld16(tl + HD + c0, d);
+                tmem_ld_wait();
+                if (in == 0)
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) P[HD * KIN + c0 + i] = d[i];
+            }
+        }
+    }
+    tc_teardown(tmem, 128, failed, err);
+}
+
+// Packs the BF16 matrix W [64 outputs][128 inputs] of every layer map into the
+// tcgen05 operand layouts: Wpk [8 output groups][16 k-chunks][8][8] (forward,
+// B = W, K = inputs) and WTpk [16 input groups][8 k-chunks][8][8] (input
+// gradient, B = W^T, K = outputs).  One thread per packed element.
+__global__ void pack_weights_kernel(int nmat, const bf16* const* __restrict__ Ws, bf16* __restrict__ out)
+{
+    const int per = HD * KIN;
+    const int64_t total = (int64_t)nmat * 2 * per;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int m = (int)(i / (2 * per)), which = (int)((i / per) & 1), e = (int)(i % per);
+        const bf16* W = Ws[m];
+        const int j = e & 7, r8 = (e >> 3) & 7;
+        bf16 v;
+        if (which == 0) {                    // output n = (e >> 10) * 8 + r8, input k = ((e >> 6) & 15) * 8 + j
+            const int n = ((e >> 10) << 3) | r8, k = (((e >> 6) & 15) << 3) | j;
+            v = W[n * KIN + k];
+        } else {                             // input n = (e >> 9) * 8 + r8, output k = ((e >> 6) & 7) * 8 + j
+            const int n = ((e >> 9) << 3) | r8, k = (((e >> 6) & 7) << 3) | j;
+            v = W[k * KIN + n];
+        }
+        out[i] = v;
+    }
 }
 
 // ------------------------------------------------------- elementwise kernels
@@ -541,6 +773,10 @@ struct sg_model {
     bool own_stream = false;
     float *theta = nullptr, *grad = nullptr, *mom1 = nullptr, *mom2 = nullptr, *dloss = nullptr;
     bf16* wbf = nullptr;          // BF16 copy of theta
+    bf16* wpk = nullptr;          // per layer map: W and W^T in the tcgen05 operand layouts (2 x 8192 BF16 each)
+    const bf16** d_wptr = nullptr;// device array: the BF16 matrices of every layer map (pack_weights_kernel input)
+    int* d_err = nullptr;         // set by a tensor-core kernel whose bounded wait ran out
+    int sms = 0;                  // SMs of the device (persistent grids)
     int64_t step = 0;
     // offsets into theta
     int64_t oX = 0, oJ = 0, oW1 = 0, ob1 = 0, ow2 = 0, ob2 = 0;
@@ -555,6 +791,7 @@ struct sg_model {
     float *R = nullptr, *dX = nullptr, *dh = nullptr, *dh2 = nullptr, *de = nullptr, *dm = nullptr, *ds = nullptr;
     bf16* dZ = nullptr;
     float* wpart = nullptr;       // weight-gradient partials, one WPART block per persistent CTA
+    float* wred = nullptr;        // [WRED_GROUPS][WPART] group sums of the partials
     int wblocks = 0;              // persistent CTAs of the weight-gradient kernel
     uint64_t launches = 0;
     std::string err = "no error";
@@ -593,6 +830,7 @@ void free_graph(sg_model* M)
     for (float** p : fl) { cudaFree(*p); *p = nullptr; }
     cudaFree(M->dZ); M->dZ = nullptr;
     cudaFree(M->wpart); M->wpart = nullptr;
+    cudaFree(M->wred); M->wred = nullptr;
     for (auto* v : {&M->h, &M->e, &M->m, &M->s, &M->zm, &M->zu, &M->ze}) {
         for (bf16* p : *v) cudaFree(p);
         v->clear();
@@ -683,8 +921,9 @@ int prepare(sg_model* M, int L, int B)
         int dev = 0, sms = 0;
         SK(cudaGetDevice(&dev), "cudaGetDevice");
         SK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device attribute");
-        M->wblocks = 2 * sms;                 // two resident CTAs per SM (launch bounds)
+        M->wblocks = TC_CTAS_WGRAD * sms;     // persistent weight-gradient CTAs
         SK(salloc(&M->wpart, (size_t)M->wblocks * WPART), "cudaMalloc wpart");
+        SK(salloc(&M->wred, (size_t)WRED_GROUPS * WPART), "cudaMalloc wred");
     }
     SK(salloc(&M->dh, nN * HD), "cudaMalloc dh");
     SK(salloc(&M->dh2, nN * HD), "cudaMalloc dh2");
@@ -702,26 +941,38 @@ RowSrc rows_of(const bf16* P0, const int* map0, int S0, const bf16* P1, const in
     return r;
 }
 
-int lin_grid(int rows)
+// The tcgen05 operand copies of every layer matrix follow the BF16 weights.
+void pack_weights(sg_model* M)
 {
-    const int tiles = (rows + 15) / 16;
-    const int g = (tiles + 7) / 8;
-    return g > 4096 ? 4096 : (g < 1 ? 1 : g);
+    pack_weights_kernel<<<grid_for((size_t)M->layers * 3 * 2 * HD * KIN), 256, 0, M->stream>>>(M->layers * 3,
+                                                                                                  M->d_wptr, M->wpk);
+    M->launches++;
 }
+
+// Packed operands of layer l's map `which` (0 messages, 1 node update, 2 edge update).
+const bf16* wpk_fwd(const sg_model* M, int l, int which) { return M->wpk + ((size_t)(l * 3 + which) * 2) * HD * KIN; }
+const bf16* wpk_bwd(const sg_model* M, int l, int which) { return wpk_fwd(M, l, which) + HD * KIN; }
+
+int tc_grid(const sg_model* M, int rows, int ctas_per_sm)
+{
+    const int tiles = (rows + TC_ROWS - 1) / TC_ROWS, cap = ctas_per_sm * M->sms;
+    return tiles < cap ? (tiles > 0 ? tiles : 1) : cap;
+}
+
 
 // dW += dZ^T X, db += column sums of dZ over `rows` rows (two launches).
 void lin_wgrad(sg_model* M, int rows, const RowSrc& src, float* dW, float* db)
 {
-    const int nchunks = (rows + WCH - 1) / WCH;
+    const int nchunks = (rows + TC_WCH - 1) / TC_WCH;
     const int grid = nchunks < M->wblocks ? (nchunks > 0 ? nchunks : 1) : M->wblocks;
-    lin_wgrad_kernel<<<grid, 256, 0, M->stream>>>(rows, M->dZ, src, M->wpart);
-    lin_wgrad_reduce<<<(WPART + 255) / 256, 256, 0, M->stream>>>(grid, M->wpart, dW, db);
+    lin_wgrad_tc_kernel<<<grid, TC_THREADS, TC_SMEM_WGRAD, M->stream>>>(rows, M->dZ, src, M->wpart, M->d_err);
+    lin_wgrad_reduce1<<<dim3((WPART + 255) / 256, WRED_GROUPS), 256, 0, M->stream>>>(grid, M->wpart, M->wred);
+    lin_wgrad_reduce2<<<(WPART + 255) / 256, 256, 0, M->stream>>>(M->wred, dW, db);
 }
 
 int forward(sg_model* M, int B, bool train)
 {
     const int N = M->N, E = M->E;
-    const bf16* W = M->wbf;
     cudaStream_t st = M->stream;
     embed_kernel<<<grid_for((size_t)B * (N + E) * HD), 256, 0, st>>>(B, N, E, M->d_u, M->d_J, M->theta + M->oX,
                                                                        M->theta + M->oJ, M->h[0], M->e[0]);
@@ -729,16 +980,17 @@ int forward(sg_model* M, int B, bool train)
     for (int l = 0; l < M->layers; ++l) {
         // messages: row 2e / 2e+1 of every graph: [h[src] | e[edge]]
         const RowSrc ms = rows_of(M->h[l], M->d_src, N, M->e[l], M->d_eid, E, 2 * E);
-        lin_fwd_kernel<0><<<lin_grid(B * 2 * E), 256, 0, st>>>(B * 2 * E, ms, W + M->oWm[l], M->theta + M->obm[l],
-                                                              M->zm[l], M->R, nullptr);
+        lin_fwd_tc_kernel<0><<<tc_grid(M, B * 2 * E, TC_CTAS_FWD), TC_THREADS, TC_SMEM_FWD, st>>>(B * 2 * E, ms, wpk_fwd(M, l, 0),
+                                                                           M->theta + M->obm[l], M->zm[l], M->R,
+                                                                           nullptr, M->d_err);
         aggregate_kernel<<<grid_for((size_t)B * N * HD / 2), 256, 0, st>>>(B, N, E, M->d_in_rows, M->R, M->m[l]);
         const RowSrc ns = rows_of(M->h[l], M->d_iden, N, M->m[l], M->d_iden, N, N);
-        lin_fwd_kernel<1><<<lin_grid(B * N), 256, 0, st>>>(B * N, ns, W + M->oWu[l], M->theta + M->obu[l], M->zu[l],
-                                                          nullptr, M->h[l + 1]);
+        lin_fwd_tc_kernel<1><<<tc_grid(M, B * N, TC_CTAS_FWD), TC_THREADS, TC_SMEM_FWD, st>>>(B * N, ns, wpk_fwd(M, l, 1), M->theta + M->obu[l],
+                                                                       M->zu[l], nullptr, M->h[l + 1], M->d_err);
         endpoint_sum_kernel<<<grid_for((size_t)B * E * HD / 2), 256, 0, st>>>(B, N, E, M->d_ei, M->d_ej, M->h[l + 1], M->s[l]);
         const RowSrc es = rows_of(M->e[l], M->d_iden, E, M->s[l], M->d_iden, E, E);
-        lin_fwd_kernel<1><<<lin_grid(B * E), 256, 0, st>>>(B * E, es, W + M->oWe[l], M->theta + M->obe[l], M->ze[l],
-                                                          nullptr, M->e[l + 1]);
+        lin_fwd_tc_kernel<1><<<tc_grid(M, B * E, TC_CTAS_FWD), TC_THREADS, TC_SMEM_FWD, st>>>(B * E, es, wpk_fwd(M, l, 2), M->theta + M->obe[l],
+                                                                       M->ze[l], nullptr, M->e[l + 1], M->d_err);
         M->launches += 5;
     }
     (void)train;
@@ -749,7 +1001,6 @@ int forward(sg_model* M, int B, bool train)
 int backward_all(sg_model* M, int B)
 {
     const int N = M->N, E = M->E;
-    const bf16* W = M->wbf;
     cudaStream_t st = M->stream;
     float* G = M->grad;
     SK(cudaMemsetAsync(G, 0, sizeof(float) * M->nparams, st), "zero grad");
@@ -764,8 +1015,8 @@ int backward_all(sg_model* M, int B)
         // edge update: e' = e + relu(ze), ze = We [e | s] + be
         relu_mask_kernel<<<grid_for(nE * HD / 2), 256, 0, st>>>(B * E, M->de, nullptr, 1, 1, M->ze[l], M->dZ);
         // de += dX[:, :64] (into e), ds = dX[:, 64:]
-        lin_bwd_input_kernel<1><<<lin_grid(B * E), 256, 0, st>>>(B * E, M->dZ, W + M->oWe[l], nullptr, M->de,
-                                                                 M->de, M->ds);
+        lin_bwd_input_tc_kernel<1><<<tc_grid(M, B * E, TC_CTAS_BWD), TC_THREADS, TC_SMEM_BWD, st>>>(B * E, M->dZ, wpk_bwd(M, l, 2), nullptr,
+                                                                             M->de, M->de, M->ds, M->d_err);
         const RowSrc es = rows_of(M->e[l], M->d_iden, E, M->s[l], M->d_iden, E, E);
         lin_wgrad(M, B * E, es, G + M->oWe[l], G + M->obe[l]);
         SK(cudaMemcpyAsync(M->dh2, M->dh, sizeof(float) * nN * HD, cudaMemcpyDeviceToDevice, st), "copy dh");
@@ -773,23 +1024,35 @@ int backward_all(sg_model* M, int B)
         // node update: h' = h + relu(zu), zu = Wu [h | m] + bu
         relu_mask_kernel<<<grid_for(nN * HD / 2), 256, 0, st>>>(B * N, M->dh2, nullptr, 1, 1, M->zu[l], M->dZ);
         // dh = dh2 + dX[:, :64] (into h), dm = dX[:, 64:]
-        lin_bwd_input_kernel<1><<<lin_grid(B * N), 256, 0, st>>>(B * N, M->dZ, W + M->oWu[l], nullptr, M->dh2,
-                                                                 M->dh, M->dm);
+        lin_bwd_input_tc_kernel<1><<<tc_grid(M, B * N, TC_CTAS_BWD), TC_THREADS, TC_SMEM_BWD, st>>>(B * N, M->dZ, wpk_bwd(M, l, 1), nullptr,
+                                                                             M->dh2, M->dh, M->dm, M->d_err);
         const RowSrc ns = rows_of(M->h[l], M->d_iden, N, M->m[l], M->d_iden, N, N);
         lin_wgrad(M, B * N, ns, G + M->oWu[l], G + M->obu[l]);
         // messages: m_i = sum relu(zm) over rows into i
         relu_mask_kernel<<<grid_for(nE * 2 * HD / 2), 256, 0, st>>>(B * 2 * E, M->dm, M->d_tgt, 2 * E, N, M->zm[l], M->dZ);
-        lin_bwd_input_kernel<0><<<lin_grid(B * 2 * E), 256, 0, st>>>(B * 2 * E, M->dZ, W + M->oWm[l], M->dX,
-                                                                     nullptr, nullptr, nullptr);
+        lin_bwd_input_tc_kernel<0><<<tc_grid(M, B * 2 * E, TC_CTAS_BWD), TC_THREADS, TC_SMEM_BWD, st>>>(B * 2 * E, M->dZ, wpk_bwd(M, l, 0),
+                                                                                 M->dX, nullptr, nullptr, nullptr,
+                                                                                 M->d_err);
         const RowSrc ms = rows_of(M->h[l], M->d_src, N, M->e[l], M->d_eid, E, 2 * E);
         lin_wgrad(M, B * 2 * E, ms, G + M->oWm[l], G + M->obm[l]);
         gather_add_kernel<<<grid_for(nN * HD), 256, 0, st>>>(B, N, 2 * E, M->d_out_rows, M->dX, KIN, 0, M->dh);
         edge_from_messages_kernel<<<grid_for(nE * HD), 256, 0, st>>>(B, E, M->dX, M->de);
-        M->launches += 15;
+        M->launches += 18;
     }
     embed_bwd_kernel<<<256, 256, 0, st>>>(B, N, E, M->d_u, M->d_J, M->dh, M->de, G + M->oX, G + M->oJ);
     M->launches++;
     return PT_OK;
+}
+
+// A tensor-core kernel whose bounded mbarrier wait ran out leaves 1 in d_err
+// (its CTA stopped and freed its tensor memory): the call reports a timeout
+// and the word is cleared for the next call.
+int tc_status(sg_model* M, int terr)
+{
+    if (!terr) return PT_OK;
+    SK(cudaMemsetAsync(M->d_err, 0, sizeof(int), M->stream), "clear status");
+    SK(cudaStreamSynchronize(M->stream), "sync status");
+    return sfail(M, PT_ERR_TIMEOUT, "a tensor-core kernel's mbarrier wait ran out (results of this call are invalid)");
 }
 
 int load_batch(sg_model* M, int L, int B, const int8_t* J, const float* t)
@@ -852,6 +1115,37 @@ int sg_create(sg_model** out, int32_t hidden, int32_t layers, void* stream)
     cudaMemset(M->mom1, 0, sizeof(float) * o);
     cudaMemset(M->mom2, 0, sizeof(float) * o);
     cudaMemset(M->wbf, 0, sizeof(bf16) * o);
+    {
+        // tcgen05 operand copies of the layer matrices, their source pointers, the timeout word
+        std::vector<const bf16*> ptrs;
+        for (int l = 0; l < layers; ++l) {
+            ptrs.push_back(M->wbf + M->oWm[l]);
+            ptrs.push_back(M->wbf + M->oWu[l]);
+            ptrs.push_back(M->wbf + M->oWe[l]);
+        }
+        int dev = 0, sms = 0;
+        if (salloc(&M->wpk, (size_t)layers * 3 * 2 * HD * KIN) != cudaSuccess ||
+            salloc(&M->d_wptr, ptrs.size()) != cudaSuccess || salloc(&M->d_err, 1) != cudaSuccess) {
+            M->err = "cudaMalloc tensor-core operands failed";
+            return bail(PT_ERR_OOM);
+        }
+        cudaError_t e = cudaMemcpy(M->d_wptr, ptrs.data(), sizeof(bf16*) * ptrs.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemset(M->wpk, 0, sizeof(bf16) * (size_t)layers * 3 * 2 * HD * KIN);
+        if (e == cudaSuccess) e = cudaMemset(M->d_err, 0, sizeof(int));
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const void* tk[5] = {(const void*)lin_fwd_tc_kernel<0>, (const void*)lin_fwd_tc_kernel<1>,
+                             (const void*)lin_bwd_input_tc_kernel<0>, (const void*)lin_bwd_input_tc_kernel<1>,
+                             (const void*)lin_wgrad_tc_kernel};
+        const int sm_bytes[5] = {TC_SMEM_FWD, TC_SMEM_FWD, TC_SMEM_BWD, TC_SMEM_BWD, TC_SMEM_WGRAD};
+        for (int q = 0; q < 5; ++q)
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(tk[q], cudaFuncAttributeMaxDynamicSharedMemorySize, sm_bytes[q]);
+        if (e != cudaSuccess) {
+            M->err = std::string("tensor-core set-up: ") + cudaGetErrorString(e);
+            return bail(PT_ERR_CUDA);
+        }
+        M->sms = sms;
+    }
     *out = M;
     return PT_OK;
 }
@@ -862,6 +1156,7 @@ void sg_destroy(sg_model* M)
     if (M->stream) cudaStreamSynchronize(M->stream);
     free_graph(M);
     cudaFree(M->theta); cudaFree(M->grad); cudaFree(M->mom1); cudaFree(M->mom2); cudaFree(M->wbf); cudaFree(M->dloss);
+    cudaFree(M->wpk); cudaFree(M->d_wptr); cudaFree(M->d_err);
     if (M->own_stream && M->stream) cudaStreamDestroy(M->stream);
     delete M;
 }
@@ -876,6 +1171,7 @@ int sg_set_params(sg_model* M, const float* theta)
     SK(cudaMemsetAsync(M->mom2, 0, sizeof(float) * M->nparams, M->stream), "zero moments");
     to_bf16_kernel<<<grid_for((size_t)M->nparams), 256, 0, M->stream>>>(M->nparams, M->theta, M->wbf);
     M->launches++;
+    pack_weights(M);
     M->step = 0;
     SK(cudaStreamSynchronize(M->stream), "sync set_params");
     return PT_OK;
@@ -901,8 +1197,10 @@ int sg_forward(sg_model* M, int32_t L, int32_t B, const int8_t* J, float* y)
     M->launches++;
     SK(cudaGetLastError(), "forward kernels");
     SK(cudaMemcpyAsync(y, M->d_y, sizeof(float) * B, cudaMemcpyDeviceToHost, M->stream), "download y");
+    int terr = 0;
+    SK(cudaMemcpyAsync(&terr, M->d_err, sizeof(int), cudaMemcpyDeviceToHost, M->stream), "download status");
     SK(cudaStreamSynchronize(M->stream), "sync forward");
-    return PT_OK;
+    return tc_status(M, terr);
 }
 
 int sg_grad(sg_model* M, int32_t L, int32_t B, const int8_t* J, const float* t, float* loss, float* grad)
@@ -915,10 +1213,12 @@ int sg_grad(sg_model* M, int32_t L, int32_t B, const int8_t* J, const float* t, 
     SK(cudaGetLastError(), "gradient kernels");
     if (grad) SK(cudaMemcpyAsync(grad, M->grad, sizeof(float) * M->nparams, cudaMemcpyDeviceToHost, M->stream), "download grad");
     float lv = 0.f;
+    int terr = 0;
     SK(cudaMemcpyAsync(&lv, M->dloss, sizeof(float), cudaMemcpyDeviceToHost, M->stream), "download loss");
+    SK(cudaMemcpyAsync(&terr, M->d_err, sizeof(int), cudaMemcpyDeviceToHost, M->stream), "download status");
     SK(cudaStreamSynchronize(M->stream), "sync grad");
     if (loss) *loss = lv;
-    return PT_OK;
+    return tc_status(M, terr);
 }
 
 int sg_adam(sg_model* M, float lr)
@@ -931,6 +1231,7 @@ int sg_adam(sg_model* M, float lr)
                                                                         lr, b1, b2, c1, c2, 1e-8f);
     to_bf16_kernel<<<grid_for((size_t)M->nparams), 256, 0, M->stream>>>(M->nparams, M->theta, M->wbf);
     M->launches += 2;
+    pack_weights(M);
     SK(cudaGetLastError(), "adam kernels");
     SK(cudaStreamSynchronize(M->stream), "sync adam");
     return PT_OK;

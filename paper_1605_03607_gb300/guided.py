@@ -90,7 +90,7 @@ def target_scale(y):
 
 
 def run_loop(h, L, seconds, model=None, online=False, step0=0, n_prop=64, top=4, retrain_every=8,
-             min_pairs=32, epochs=4, lr=1e-3, max_steps=10**9):
+             min_pairs=32, epochs=4, lr=1e-3, window=1024, max_steps=10**9):
     """One engineering loop for `seconds` of GPU time (host wall clock around
     the synchronous library calls, training included).  Every step draws
     n_prop proposals, PT-evaluates `top` of them in one batched launch and
@@ -99,17 +99,21 @@ def run_loop(h, L, seconds, model=None, online=False, step0=0, n_prop=64, top=4,
 
     model None: the plain loop (proposals 0..top-1, no ranking).  model given:
     its ranking picks the `top`; with online=True it is retrained every
-    `retrain_every` steps (train_pairs, `epochs` passes) on all pairs the loop
-    has evaluated so far: (candidate, instance it was drawn from, log10 TTS
-    difference).  Returns (trace [(seconds, tts, steps)], pairs evaluated)."""
+    `retrain_every` steps (train_pairs, `epochs` passes) on the `window` most
+    recent pairs the loop has evaluated: (candidate, instance it was drawn
+    from, log10 TTS difference), and until its first training it does not
+    rank (the plain choice), so an untrained network's bias never steers the
+    loop.  Returns (trace [(seconds, tts, steps)], pairs evaluated)."""
     trace = [(0.0, h.engineer_tts(), 0)]
     Jc, Jb, d = [], [], []
     used, step = 0.0, step0
+    trained = False
     while used < seconds and step - step0 < max_steps:
         J = h.couplers()
         tcur = h.engineer_tts()
         t0 = time.perf_counter()
-        res, _, _ = h.engineer_guided_step(model, step, n_prop, top)
+        ranker = model if (model is not None and (trained or not online)) else None
+        res, _, _ = h.engineer_guided_step(ranker, step, n_prop, top)
         for r in range(top):
             c = J.copy()
             c[res["edge"][r]] = res["new_value"][r]
@@ -118,9 +122,10 @@ def run_loop(h, L, seconds, model=None, online=False, step0=0, n_prop=64, top=4,
             d.append(float(log10_tts(res["tts_new"][r]) - log10_tts(tcur)))
         step += 1
         if online and model is not None and (step - step0) % retrain_every == 0 and len(d) >= min_pairs:
-            dd = np.asarray(d)
-            train_pairs(model, L, np.asarray(Jc), np.asarray(Jb), dd / max(dd.std(), 1e-6), epochs=epochs,
-                        batch=64, lr=lr, seed=step)
+            dd = np.asarray(d[-window:])
+            train_pairs(model, L, np.asarray(Jc[-window:]), np.asarray(Jb[-window:]), dd / max(dd.std(), 1e-6),
+                        epochs=epochs, batch=64, lr=lr, seed=step)
+            trained = True
         used += time.perf_counter() - t0
         trace.append((used, h.engineer_tts(), step - step0))
     return trace, len(d)
