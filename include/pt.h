@@ -79,6 +79,27 @@ int pt_create(pt_handle **h, int32_t chimera_L, const int8_t *J, int32_t n_edges
               const double *betas, int32_t n_temps, int32_t n_runs, uint32_t seed,
               uint32_t instance_uid, void *stream);
 
+/* An Ising graph given by its coupler list (Eq. 1).  The kernels work on the
+ * Chimera graph C_L (Appendix A), so the list must be a set of couplers of
+ * C_L: n = 8 L^2 spins, every (ei[e], ej[e]) a Chimera coupler (either
+ * orientation), none repeated.  Couplers of C_L that are not listed are zero:
+ * this is how a device with inoperative qubits, such as the paper's 504 of 512
+ * (Fig. 8), is described.  ei == ej == NULL means the full C_L in the coupler
+ * order above (then n_edges = 16 L^2 + 8 L (L - 1)). */
+typedef struct pt_graph {
+    int32_t n, n_edges;
+    const int32_t *ei, *ej;   /* n_edges endpoints, read during pt_create_graph only */
+    int32_t chimera_L;
+} pt_graph;
+
+/* pt_create for a graph given as a coupler list: J [n_edges] in the list's
+ * order is placed on the listed couplers (pt_get_couplers then returns the
+ * full C_L vector in the library's order).  Errors as pt_create, plus
+ * PT_ERR_ARG for a coupler that is not an edge of C_L, a repeated one, or
+ * n != 8 L^2. */
+int pt_create_graph(pt_handle **h, const pt_graph *g, const int8_t *J, const double *betas, int32_t n_temps,
+                    int32_t n_runs, uint32_t seed, uint32_t instance_uid, void *stream);
+
 /* Frees every device and host resource of h (NULL is ignored). */
 void pt_destroy(pt_handle *h);
 

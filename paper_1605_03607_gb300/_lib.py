@@ -37,6 +37,11 @@ class pt_rule(C.Structure):
                 ("direction", C.c_int32), ("beta_rao", C.c_double), ("max_sweeps", C.c_int32)]
 
 
+class pt_graph(C.Structure):
+    _fields_ = [("n", C.c_int32), ("n_edges", C.c_int32), ("ei", C.c_void_p), ("ej", C.c_void_p),
+                ("chimera_L", C.c_int32)]
+
+
 class pt_step_result(C.Structure):
     _fields_ = [("edge", C.c_int32), ("old_value", C.c_int32), ("new_value", C.c_int32),
                 ("tts_old", C.c_int32), ("tts_new", C.c_int32), ("accepted", C.c_int32),
@@ -83,6 +88,8 @@ SIGNATURES = [
     ("lao_state", C.c_int, [_VP, _VP, _VP, _VP, _I32P, _I32P]),
     ("pt_overlaps", C.c_int, [_VP, C.c_int32, _I32P, _I32P, _I32P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("engineer_current_tts", C.c_int, [_VP, _I32P]),
+    ("pt_create_graph", C.c_int, [C.POINTER(_VP), C.POINTER(pt_graph), _VP, _VP, C.c_int32, C.c_int32, C.c_uint32,
+                                  C.c_uint32, _VP]),
     ("engineer_current_state", C.c_int, [_VP, _I32P, _I32P]),
     ("engineer_set_adaptive", C.c_int, [_VP, C.c_int32, C.c_int32, C.c_int64, C.c_double]),
     ("engineer_adaptive_runs", C.c_int, [_VP, _I32P]),
@@ -204,7 +211,9 @@ def _check(rc, h=None):
 class PTHandle:
     """One instance, n_runs PT runs of len(betas) slots on the GPU (owner of a pt_handle)."""
 
-    def __init__(self, L, J, betas, n_runs, seed, uid, stream=None):
+    def __init__(self, L, J, betas, n_runs, seed, uid, stream=None, edges=None):
+        """edges (optional): (ei, ej) coupler list on C_L for J in that order
+        (pt_create_graph); missing couplers of C_L are zero."""
         lib = load()
         self.L = int(L)
         self.N = 8 * self.L * self.L
@@ -212,11 +221,21 @@ class PTHandle:
         betas = np.ascontiguousarray(betas, np.float64)
         self.NT = len(betas)
         self.R = int(n_runs)
-        self.n_edges = len(J)
         h = C.c_void_p()
-        rc = lib.pt_create(C.byref(h), self.L, _ptr(J), self.n_edges, _ptr(betas), self.NT, self.R,
-                           int(seed) & 0xFFFFFFFF, int(uid) & 0xFFFFFFFF,
-                           None if stream is None else C.c_void_p(stream))
+        st = None if stream is None else C.c_void_p(stream)
+        if edges is None:
+            self.n_edges = len(J)
+            rc = lib.pt_create(C.byref(h), self.L, _ptr(J), self.n_edges, _ptr(betas), self.NT, self.R,
+                               int(seed) & 0xFFFFFFFF, int(uid) & 0xFFFFFFFF, st)
+        else:
+            ei = np.ascontiguousarray(edges[0], np.int32)
+            ej = np.ascontiguousarray(edges[1], np.int32)
+            if len(ei) != len(J) or len(ej) != len(J):
+                raise ValueError("one coupler value per listed edge")
+            g = pt_graph(self.N, len(J), ei.ctypes.data, ej.ctypes.data, self.L)
+            self.n_edges = 16 * self.L * self.L + 8 * self.L * (self.L - 1)
+            rc = lib.pt_create_graph(C.byref(h), C.byref(g), _ptr(J), _ptr(betas), self.NT, self.R,
+                                     int(seed) & 0xFFFFFFFF, int(uid) & 0xFFFFFFFF, st)
         _check(rc, None)
         self.h = h
 

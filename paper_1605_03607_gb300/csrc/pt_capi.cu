@@ -858,6 +858,46 @@ int pt_create(pt_handle** out, int32_t L, const int8_t* J, int32_t n_edges, cons
     return PT_OK;
 }
 
+int pt_create_graph(pt_handle** out, const pt_graph* g, const int8_t* J, const double* betas, int32_t n_temps,
+                    int32_t n_runs, uint32_t seed, uint32_t uid, void* stream)
+{
+    if (!out || !g || !J) return fail(nullptr, PT_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    const int L = g->chimera_L;
+    if (L < 1 || L > MAX_L) return fail(nullptr, PT_ERR_ARG, "chimera_L must be in [1, 16]");
+    if (!g->ei && !g->ej) return pt_create(out, L, J, g->n_edges, betas, n_temps, n_runs, seed, uid, stream);
+    if (!g->ei || !g->ej) return fail(nullptr, PT_ERR_ARG, "ei and ej must both be given or both be NULL");
+    const int N = 8 * L * L, E = n_edges_of(L);
+    if (g->n != N) return fail(nullptr, PT_ERR_ARG, "n must be 8 L^2 (the spins of C_L)");
+    if (g->n_edges < 0 || g->n_edges > E) return fail(nullptr, PT_ERR_ARG, "more couplers than C_L has");
+    // library index of the Chimera coupler (a, b), or -1 when (a, b) is not one
+    auto edge_of = [L, N](int a, int b) -> int {
+        if (a < 0 || b < 0 || a >= N || b >= N || a == b) return -1;
+        int ca = a >> 3, cb = b >> 3, ua = (a >> 2) & 1, ub = (b >> 2) & 1, ka = a & 3, kb = b & 3;
+        if (ca == cb) {
+            if (ua == ub) return -1;
+            const int kv = ua == 0 ? ka : kb, kh = ua == 0 ? kb : ka;
+            return intra_edge(L, ca, kv, kh);
+        }
+        if (ua != ub || ka != kb) return -1;
+        if (ca > cb) { std::swap(ca, cb); }
+        const int r = ca / L, c = ca % L, r2 = cb / L, c2 = cb % L;
+        if (ua == 0 && c == c2 && r2 == r + 1) return vert_edge(L, r, c, ka);
+        if (ua == 1 && r == r2 && c2 == c + 1) return horiz_edge(L, r, c, ka);
+        return -1;
+    };
+    std::vector<int8_t> full((size_t)E, 0);
+    std::vector<char> seen((size_t)E, 0);
+    for (int e = 0; e < g->n_edges; ++e) {
+        const int x = edge_of(g->ei[e], g->ej[e]);
+        if (x < 0) return fail(nullptr, PT_ERR_ARG, "coupler " + std::to_string(e) + " is not an edge of C_L");
+        if (seen[(size_t)x]) return fail(nullptr, PT_ERR_ARG, "coupler " + std::to_string(e) + " is listed twice");
+        seen[(size_t)x] = 1;
+        full[(size_t)x] = J[e];
+    }
+    return pt_create(out, L, full.data(), E, betas, n_temps, n_runs, seed, uid, stream);
+}
+
 void pt_destroy(pt_handle* h)
 {
     if (!h) return;

@@ -110,3 +110,32 @@ def test_python_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(lib, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         lib.load()
+
+
+def test_graph_form_validation_without_gpu(P):
+    """pt_create_graph rejects coupler lists that are not sets of C_L couplers
+    (checked on the host before any device work)."""
+    lib = P.load()
+    L = 2
+    import oracle
+    ei, ej = oracle.chimera_edges(L)
+    betas = W.beta_ladder(4, 0.5, 3.0)
+
+    def create(a, b, n=8 * L * L):
+        a = np.ascontiguousarray(a, np.int32)
+        b = np.ascontiguousarray(b, np.int32)
+        J = np.ones(len(a), np.int8)
+        g = P._lib.pt_graph(n, len(a), a.ctypes.data, b.ctypes.data, L)
+        h = ctypes.c_void_p()
+        rc = lib.pt_create_graph(ctypes.byref(h), ctypes.byref(g), J.ctypes.data_as(ctypes.c_void_p),
+                                 betas.ctypes.data_as(ctypes.c_void_p), len(betas), 2, 1, 0, None)
+        return rc, lib.pt_last_error(None).decode()
+
+    rc, msg = create([0, 0], [1, 2])                  # spins 0-1, 0-2: same orientation in one cell
+    assert rc == 1 and "not an edge" in msg
+    rc, msg = create([0, 4], [4, 0])                  # the same coupler in both orientations
+    assert rc == 1 and "twice" in msg
+    rc, msg = create([0], [8])                        # vertical k=0 of cell (0,0) to horizontal cell (0,1): no
+    assert rc == 1 and "not an edge" in msg
+    rc, msg = create(ei[:3], ej[:3], n=31)
+    assert rc == 1 and "8 L^2" in msg

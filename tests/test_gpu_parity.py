@@ -363,3 +363,30 @@ def test_large_couplers_and_table_growth(P):
         with pytest.raises(P.PTError):
             h.set_coupler(1, 100)           # spin 0's sum would exceed 127
         assert h.table_rows() == rows and np.array_equal(h.couplers(), J2)
+
+
+def test_graph_form_matches_full_vector(P):
+    """pt_create_graph with a shuffled coupler list that omits some couplers
+    (inoperative qubits, as on the paper's 504-qubit device): the handle holds
+    the full C_L vector with zeros where nothing was listed, and its runs
+    match the oracle on that vector bit-exactly."""
+    L, NT, R, seed = 4, 8, 4, 20160520
+    ei, ej = oracle.chimera_edges(L)
+    J = W.random_couplers(L, seed, 0)
+    rng = np.random.default_rng(9)
+    dead = {int(x) for x in rng.choice(8 * L * L, 4, replace=False)}          # four inoperative spins
+    keep = [e for e in range(len(J)) if int(ei[e]) not in dead and int(ej[e]) not in dead]
+    order = rng.permutation(keep)
+    flip = rng.random(len(order)) < 0.5                                        # either orientation
+    a = np.where(flip, ej[order], ei[order])
+    b = np.where(flip, ei[order], ej[order])
+    full = np.zeros_like(J)
+    full[keep] = J[keep]
+    betas = W.beta_ladder(NT, 0.1, 3.0)
+    with P.PTHandle(L, J[order], betas, R, seed, 2, edges=(a, b)) as h:
+        assert np.array_equal(h.couplers(), full)
+        h.sweep(100, 1)
+        st = h.state()
+    ref = oracle.PTState(L, full, betas, R, seed, 2)
+    ref.sweeps(100, 1)
+    _assert_state_equal(st, ref, "graph form")
