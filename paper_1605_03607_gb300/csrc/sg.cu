@@ -268,7 +268,10 @@ __global__ void __launch_bounds__(TC_THREADS) lin_fwd_tc_kernel(int rows, RowSrc
     unsigned char* Ws = tc_smem + TC_A_FWD;              // [8 output groups][16 k-chunks][8 outputs][16 B]
     __shared__ __align__(8) uint64_t bar_w, bar_mma;
     __shared__ uint32_t tmem_sh;
+    __shared__ const unsigned char* rowp[2][TC_ROWS];    // this tile's gathered row halves (NULL past the end)
+    __shared__ float bias_sm[HD];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid < HD) bias_sm[tid] = bias[tid];
     bool failed = !tc_setup(&tmem_sh, &bar_w, &bar_mma, 64, Ws, Wpk, HD * KIN * 2);
     const uint32_t tmem = tmem_sh;
     constexpr uint32_t IDESC = tc_idesc_bf16(TC_ROWS, HD);
@@ -276,12 +279,15 @@ __global__ void __launch_bounds__(TC_THREADS) lin_fwd_tc_kernel(int rows, RowSrc
     uint32_t phase = 0;
     for (int tile = blockIdx.x; !failed && tile < ntiles; tile += gridDim.x) {
         const int r0 = tile * TC_ROWS;
+        {                                                  // one index lookup per row half
+            const int row = tid & (TC_ROWS - 1), hf = tid >> 7, r = r0 + row;
+            rowp[hf][row] = r < rows ? reinterpret_cast<const unsigned char*>(src.half(r, hf)) : nullptr;
+        }
+        __syncthreads();
         for (int i = tid; i < 16 * TC_ROWS; i += TC_THREADS) {   // chunk i: row (i >> 7) * 8 + (i & 7), k-chunk (i >> 3) & 15
-            const int kc = (i >> 3) & 15, row = ((i >> 7) << 3) | (i & 7), r = r0 + row;
-            const bool v = r < rows;
-            const unsigned char* g = v ? reinterpret_cast<const unsigned char*>(src.half(r, kc >> 3)) + (kc & 7) * 16
-                                       : reinterpret_cast<const unsigned char*>(Wpk);
-            cp_async16(As + i * 16, g, v);
+            const int kc = (i >> 3) & 15, row = ((i >> 7) << 3) | (i & 7);
+            const unsigned char* p = rowp[kc >> 3][row];
+            cp_async16(As + i * 16, p ? p + (kc & 7) * 16 : reinterpret_cast<const unsigned char*>(Wpk), p != nullptr);
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");     // visible to the tensor core
@@ -311,7 +317,7 @@ __global__ void __launch_bounds__(TC_THREADS) lin_fwd_tc_kernel(int rows, RowSrc
             tmem_ld_wait();
             if (r < rows) {
 #pragma unroll
-                for (int i = 0; i < 16; ++i) z[i] += bias[c0 + i];
+                for (int i = 0; i < 16; ++i) z[i] += bias_sm[c0 + i];
                 uint4 zp[2];
                 uint32_t* zw = reinterpret_cast<uint32_t*>(zp);
 #pragma unroll
@@ -326,8 +332,10 @@ __global__ void __launch_bounds__(TC_THREADS) lin_fwd_tc_kernel(int rows, RowSrc
                         ro[i] = make_float4(fmaxf(z[4 * i], 0.f), fmaxf(z[4 * i + 1], 0.f), fmaxf(z[4 * i + 2], 0.f),
                                             fmaxf(z[4 * i + 3], 0.f));
                 } else {
-                    const uint4* bp = reinterpret_cast<const uint4*>(reinterpret_cast<const bf16*>(src.half(r, 0)) + c0);
-                    uint4 b4[2] = {bp[0], bp[1]}, yp[2];
+                    // the residual input is half 0 of this row, already staged: k-chunks c0/8 and c0/8 + 1
+                    const int row = q * 32 + lane;
+                    const unsigned char* sb = As + (((row >> 3) * 16 + (c0 >> 3)) * 128) + (row & 7) * 16;
+                    uint4 b4[2] = {*reinterpret_cast<const uint4*>(sb), *reinterpret_cast<const uint4*>(sb + 128)}, yp[2];
                     const uint32_t* bw = reinterpret_cast<const uint32_t*>(b4);
                     uint32_t* yw = reinterpret_cast<uint32_t*>(yp);
 #pragma unroll
@@ -341,6 +349,7 @@ __global__ void __launch_bounds__(TC_THREADS) lin_fwd_tc_kernel(int rows, RowSrc
                 }
             }
         }
+        if (EPI == 1) __syncthreads();                     // the staged tile is read above before it is restaged
     }
     tc_teardown(tmem, 64, failed, err);
 }
@@ -387,6 +396,16 @@ __global__ void __launch_bounds__(TC_THREADS) lin_bwd_input_tc_kernel(int rows, 
                        IDESC, ks > 0 ? 1u : 0u);
             tc_commit(&bar_mma);
         }
+        const int q = warp & 3, r = r0 + q * 32 + lane;
+        // warps 0-3 add this row's base gradient to dX[:, :64]: loaded while the MMAs run
+        float4 bpre[EPI == 1 ? HD / 4 : 1];
+        if (EPI == 1 && warp < 4 && base && r < rows) {
+#pragma unroll
+            for (int i = 0; i < HD / 4; ++i) bpre[i] = reinterpret_cast<const float4*>(base + (size_t)r * HD)[i];
+        } else {
+#pragma unroll
+            for (int i = 0; i < (EPI == 1 ? HD / 4 : 1); ++i) bpre[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         const bool ok = mbar_wait(&bar_mma, phase);
         phase ^= 1u;
         if (__syncthreads_or(!ok)) {
@@ -394,7 +413,6 @@ __global__ void __launch_bounds__(TC_THREADS) lin_bwd_input_tc_kernel(int rows, 
             break;
         }
         tc_fence_after();
-        const int q = warp & 3, r = r0 + q * 32 + lane;
         const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
 #pragma unroll
         for (int c0 = (warp >> 2) * HD; c0 < (warp >> 2) * HD + HD; c0 += 16) {
@@ -408,15 +426,10 @@ __global__ void __launch_bounds__(TC_THREADS) lin_bwd_input_tc_kernel(int rows, 
                     for (int i = 0; i < 4; ++i) o[i] = make_float4(d[4 * i], d[4 * i + 1], d[4 * i + 2], d[4 * i + 3]);
                 } else if (c0 < HD) {
                     float4* o = reinterpret_cast<float4*>(out0 + (size_t)r * HD + c0);
-                    const float4* bs = base ? reinterpret_cast<const float4*>(base + (size_t)r * HD + c0) : nullptr;
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
-                        float4 v = make_float4(d[4 * i], d[4 * i + 1], d[4 * i + 2], d[4 * i + 3]);
-                        if (bs) {
-                            const float4 bb = bs[i];
-                            v.x += bb.x; v.y += bb.y; v.z += bb.z; v.w += bb.w;
-                        }
-                        o[i] = v;
+                        const float4 bb = bpre[(EPI == 1 ? (c0 >> 2) + i : 0)];
+                        o[i] = make_float4(d[4 * i] + bb.x, d[4 * i + 1] + bb.y, d[4 * i + 2] + bb.z, d[4 * i + 3] + bb.w);
                     }
                 } else {
                     float4* o = reinterpret_cast<float4*>(out1 + (size_t)r * HD + (c0 - HD));
@@ -458,16 +471,21 @@ __global__ void __launch_bounds__(TC_THREADS) lin_wgrad_tc_kernel(int rows, cons
     // M = 128 inputs, N = 64 outputs, both operands MN-major (bits 15, 16)
     constexpr uint32_t IDESC = tc_idesc_bf16(KIN, HD) | (1u << 15) | (1u << 16);
     const int nchunks = (rows + TC_WCH - 1) / TC_WCH;
+    __shared__ const unsigned char* rowp[2][2][TC_WCH];       // per stage: the chunk's gathered row halves
     auto stage = [&](int c, int b) {
         unsigned char* Xs = tc_smem + b * TC_WSTAGE;
         unsigned char* Zs = Xs + TC_WCH * KIN * 2;
         const int r0 = c * TC_WCH;
+        {                                                       // one index lookup per row half
+            const int row = tid & (TC_WCH - 1), hf = (tid >> 6) & 1, r = r0 + row;
+            if (tid < 2 * TC_WCH)
+                rowp[b][hf][row] = r < rows ? reinterpret_cast<const unsigned char*>(src.half(r, hf)) : nullptr;
+        }
+        __syncthreads();
         for (int i = tid; i < TC_WCH * KIN / 8; i += TC_THREADS) {   // X: chunk i -> row group (i>>3)&7, inputs (i>>6)*8..
-            const int r = r0 + (((i >> 3) & 7) << 3) + (i & 7), mg = i >> 6;
-            const bool v = r < rows;
-            const unsigned char* g = v ? reinterpret_cast<const unsigned char*>(src.half(r, mg >> 3)) + (mg & 7) * 16
-                                       : reinterpret_cast<const unsigned char*>(dZ);
-            cp_async16(Xs + i * 16, g, v);
+            const int row = (((i >> 3) & 7) << 3) + (i & 7), mg = i >> 6;
+            const unsigned char* p = rowp[b][mg >> 3][row];
+            cp_async16(Xs + i * 16, p ? p + (mg & 7) * 16 : reinterpret_cast<const unsigned char*>(dZ), p != nullptr);
         }
         for (int i = tid; i < TC_WCH * HD / 8; i += TC_THREADS) {    // dZ: outputs (i>>6)*8..
             const int r = r0 + (((i >> 3) & 7) << 3) + (i & 7), ng = i >> 6;
