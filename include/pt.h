@@ -183,7 +183,8 @@ int pt_get_tables(const pt_handle *h, uint32_t *thr, int64_t *xoff, uint32_t *xt
  * clears) the first code seen since the last call, 0 if none (always 0 in a
  * release build).  Codes: 1 Metropolis table row, 2 slot map, 3 exchange
  * table range, 4 run index, 5 neighbour word, 6 more than 1024 runs in a
- * TTS reduction, 7 slot map in the energy kernel. */
+ * TTS reduction, 7 slot map in the energy kernel, 8 a closed-form exchange
+ * criterion that differs from the table search (debug builds evaluate both). */
 int pt_debug_enabled(void);
 int pt_debug_status(uint32_t *code);
 

@@ -41,6 +41,7 @@ namespace ptg {
 //   3 exchange table range outside the tables   4 run index >= runs
 //   5 neighbour spin word outside the buffer    6 TTS over more than 1024 runs
 //   7 energy kernel: slot map entry >= n_temps
+//   8 closed-form exchange criterion differs from the table search
 // Release builds compile the checks away.
 #ifdef PT_DEBUG
 __device__ unsigned int g_pt_debug_code;
@@ -61,11 +62,40 @@ namespace {
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
-// Largest h in [0, H_p] with xthr[p][h'] > u for all 1 <= h' <= h: a swap with
-// energy gap d = 2h > 0 is accepted iff h <= c_p.  Exact for any start point
-// because the table is non-increasing in h (checked on the host); the float
-// estimate only picks where the exact search starts, and both neighbours of
-// the estimate are loaded at once.
+// Exact search of the exchange table from a start point c0 in [0, H]: the
+// largest h in [0, H] with tab[h'] > u for all 1 <= h' <= h.  Exact for any
+// start point because the table is non-increasing in h (checked on the host);
+// both neighbours of the start are loaded at once.
+__device__ __forceinline__ int half_gap_search(const uint32_t* tab, int H, uint32_t u, int c)
+{
+    const uint32_t at = c > 0 ? tab[c] : 0xFFFFFFFFu;
+    const uint32_t above = c < H ? tab[c + 1] : 0u;
+    if (c > 0 && at <= u) {
+        --c;
+        while (c > 0 && tab[c] <= u) --c;
+    } else if (c < H && above > u) {
+        ++c;
+        while (c < H && tab[c + 1] > u) ++c;
+    }
+    return c;
+}
+
+// Critical half-gap c_p of pair p for the uniform u: a swap with energy gap
+// d = 2h > 0 is accepted iff h <= c_p, where c_p is the number of table
+// entries xthr[p][h] = floor(2^32 exp(-2 h dbeta_p)) (h = 1..H_p) above u.
+// Such an entry exceeds u iff 2^32 exp(-2 h dbeta_p) >= u + 1, i.e. iff
+// h <= X = log2(2^32 / (u + 1)) * ln2 / (2 dbeta_p), so c_p = min(H_p, floor X).
+// X is evaluated in single precision from the hint ln2 / (2 dbeta_p):
+// log2f is accurate to 1 ulp of its result (at most X * 2^-23 after the
+// product), the argument u + 1 (or u for u >= 2^24, off by at most 2^-23 in
+// log2) and the hint and product roundings (2^-24 each) add at most
+// X * 1.2e-7 + hint * 1.8e-7, and the host's FP64 tables round 1e-14
+// relative.  When X lies further than twice that bound from an integer the
+// floor is exact and no table entry is read; otherwise (a few times in 10^5)
+// the table is searched, from a separate fast-intrinsic estimate (any start
+// point gives the exact result; keeping the first estimate live through the
+// search measured 1 % slower).  Debug builds also search on the closed-form
+// path and record code 8 if the two ever differ.
 __device__ __forceinline__ int critical_half_gap(const InstDesc& in, const int32_t* xoff_sm,
                                                  const float* xhint_sm, int p, uint32_t u)
 {
@@ -78,21 +108,26 @@ __device__ __forceinline__ int critical_half_gap(const InstDesc& in, const int32
     const int H = xoff_sm[p + 1] - o;
 #endif
     const uint32_t* tab = in.xthr + o - 1;       // tab[h], h = 1..H
-    int c = H;
-    if (u != 0u) {
-        const float est = (32.0f - __log2f((float)u)) * xhint_sm[p];
-        c = est <= 0.0f ? 0 : (est >= (float)H ? H : (int)est);
+    if (u == 0u) return H;                       // every entry is >= 1
+    const float hint = xhint_sm[p];
+    const float x = u < (1u << 24) ? (float)(u + 1u) : (float)u;
+    const float est = -log2f(x * 0x1p-32f) * hint;
+    const float eps = est * 8e-7f + hint * 4e-7f + 2e-6f;
+    if (est >= (float)H + eps) {
+#ifdef PT_DEBUG
+        if (half_gap_search(tab, H, u, H) != H) atomicCAS(&g_pt_debug_code, 0u, 8u);
+#endif
+        return H;
     }
-    const uint32_t at = c > 0 ? tab[c] : 0xFFFFFFFFu;
-    const uint32_t above = c < H ? tab[c + 1] : 0u;
-    if (c > 0 && at <= u) {
-        --c;
-        while (c > 0 && tab[c] <= u) --c;
-    } else if (c < H && above > u) {
-        ++c;
-        while (c < H && tab[c + 1] > u) ++c;
+    const float fl = floorf(est);
+    if (est < (float)H && est - fl > eps && (fl + 1.0f) - est > eps) {
+#ifdef PT_DEBUG
+        if (half_gap_search(tab, H, u, (int)fl) != (int)fl) atomicCAS(&g_pt_debug_code, 0u, 8u);
+#endif
+        return (int)fl;
     }
-    return c;
+    const float start = (32.0f - __log2f((float)u)) * xhint_sm[p];
+    return half_gap_search(tab, H, u, start <= 0.0f ? 0 : (start >= (float)H ? H : (int)start));
 }
 
 struct CellRegs {
@@ -300,65 +335,81 @@ __device__ __forceinline__ int exchange_chain(int32_t* Es, uint8_t* perm, uint8_
     return m;
 }
 
-// The same exchange sweep run by all 32 lanes of one warp (NT <= 64).  Only
-// the carried energy is serial: the warp runs that recurrence uniformly (an
-// instruction issues once for all lanes) and records the accepted pairs as a
-// bit mask.  The slot contents then follow from the mask in parallel: after
-// the pass slot s holds the old content of slot s+1 when pair s was accepted,
-// and otherwise the configuration carried into s, which started at the lowest
-// slot of the run of accepted pairs ending at pair s-1 (s itself when pair s-1
-// was rejected).  The pair criteria cc of this sweep are overwritten with the
-// acceptance bounds E_{p+1} - 2 c_p.  Returns the lowest slot energy.
+// The same exchange sweep run by all 32 lanes of one warp (NT <= 64; lane l
+// holds slots l and l + 32), with no serial recurrence.  A chain of accepted
+// swaps that starts at slot i carries the energy E_i upward and ends at the
+// first pair p >= i whose bound E_{p+1} - 2 c_p exceeds E_i (that pair is
+// rejected, and the next chain starts at slot p + 1).  Each lane finds that
+// end for its own slots from a bit mask of the bounds above its energy
+// (independent compares); pointer doubling over "next start = end + 1" then
+// collects the ends met from slot 0 on, which are exactly the pairs the
+// ascending pass rejects.  The slot contents follow from the accepted-pair
+// mask: after the pass slot s holds the old content of slot s+1 when pair s
+// was accepted, and otherwise the configuration carried into s, which
+// started at the lowest slot of the run of accepted pairs ending at pair s-1
+// (s itself when pair s-1 was rejected).  The pair criteria cc of this sweep
+// are overwritten with the bounds.  Returns the lowest slot energy.
 template <bool INV>
 __device__ __forceinline__ int exchange_chain_warp(int32_t* Es, uint8_t* perm, uint8_t* inv, uint32_t* xacc,
                                                    int32_t* cc, int NT, int lane)
 {
-    constexpr int B = 4;
     const int np = NT - 1;
-    int m = INT_MAX;
-    for (int t = lane; t < NT; t += 32) {
-        const int e = Es[t];
-        m = min(m, e);
-        if (t >= 1) cc[t - 1] = e - 2 * cc[t - 1];
-    }
-    m = __reduce_min_sync(FULL, m);
+    const bool two = NT > 32;                      // warp-uniform
+    const int s1 = lane + 32;
+    const int e0 = lane < NT ? Es[lane] : INT_MAX;
+    const int e1 = (two && s1 < NT) ? Es[s1] : INT_MAX;
+    const int m = __reduce_min_sync(FULL, min(e0, e1));
+    if (lane < np) cc[lane] = Es[lane + 1] - 2 * cc[lane];
+    if (two && s1 < np) cc[s1] = Es[s1 + 1] - 2 * cc[s1];
     __syncwarp();
-    // serial recurrence of the carried energy, bounds and energies read ahead
-    int ce = Es[0];
-    uint32_t lo = 0u, hi = 0u;
-    int nxe[B], nxt[B];
+    // pairs whose bound exceeds this lane's slot energies (slot s1 >= 32 needs
+    // only pairs >= 32)
+    uint32_t r0lo = 0u, r0hi = 0u, r1hi = 0u;
 #pragma unroll
-    for (int i = 0; i < B; ++i) {
-        nxe[i] = i < np ? Es[i + 1] : 0;
-        nxt[i] = i < np ? cc[i] : 0;
-    }
-    for (int p0 = 0; p0 < np; p0 += B) {
-        int ne[B], tt[B];
+    for (int p = 0; p < 32; ++p)
+        if (p < np) r0lo |= (uint32_t)(cc[p] > e0) << p;
+    if (two) {
 #pragma unroll
-        for (int i = 0; i < B; ++i) {
-            ne[i] = nxe[i];
-            tt[i] = nxt[i];
-        }
-#pragma unroll
-        for (int i = 0; i < B; ++i) {
-            const int q = p0 + B + i;
-            nxe[i] = q < np ? Es[q + 1] : 0;
-            nxt[i] = q < np ? cc[q] : 0;
-        }
-        uint32_t nib = 0u;
-#pragma unroll
-        for (int i = 0; i < B; ++i) {
-            if (p0 + i < np) {
-                const bool a = tt[i] <= ce;          // E_{p+1} - E_carried <= 2 c_p
-                ce = a ? ce : ne[i];
-                nib |= (uint32_t)a << i;
+        for (int p = 32; p < 63; ++p)
+            if (p < np) {
+                const int t = cc[p];
+                r0hi |= (uint32_t)(t > e0) << (p - 32);
+                r1hi |= (uint32_t)(t > e1) << (p - 32);
             }
-        }
-        if (p0 < 32) lo |= nib << p0;
-        else hi |= nib << (p0 - 32);
     }
+    // end of a chain starting at each slot (np: it carries to the top slot);
+    // J = next chain start, R = the rejected pair as a bit (slots >= NT: none)
+    const unsigned long long q0 = (((unsigned long long)r0hi << 32) | r0lo) & (~0ull << lane);
+    const unsigned long long q1 = ((unsigned long long)r1hi << 32) & (~0ull << (s1 & 63));
+    const int end0 = q0 ? __ffsll((long long)q0) - 1 : np;
+    const int end1 = (two && s1 < NT && q1) ? __ffsll((long long)q1) - 1 : np;
+    int J0 = lane < NT ? end0 + 1 : NT;
+    int J1 = (two && s1 < NT) ? end1 + 1 : NT;
+    unsigned long long R0 = (lane < NT && end0 < np) ? 1ull << end0 : 0ull;
+    unsigned long long R1 = (two && s1 < NT && end1 < np) ? 1ull << end1 : 0ull;
+    // doubling: after k rounds R holds the rejections of the next 2^k chains
+    for (int k = 0; (1 << k) < NT; ++k) {
+        const int a = J0 < NT ? J0 : 0, b = J1 < NT ? J1 : 0;
+        unsigned long long Ra, Rb = 0ull;
+        int Ja, Jb = NT;
+        if (two) {
+            const unsigned long long Ra0 = __shfl_sync(FULL, R0, a & 31), Ra1 = __shfl_sync(FULL, R1, a & 31);
+            const unsigned long long Rb0 = __shfl_sync(FULL, R0, b & 31), Rb1 = __shfl_sync(FULL, R1, b & 31);
+            const int Ja0 = __shfl_sync(FULL, J0, a & 31), Ja1 = __shfl_sync(FULL, J1, a & 31);
+            const int Jb0 = __shfl_sync(FULL, J0, b & 31), Jb1 = __shfl_sync(FULL, J1, b & 31);
+            Ra = a >= 32 ? Ra1 : Ra0;
+            Rb = b >= 32 ? Rb1 : Rb0;
+            Ja = a >= 32 ? Ja1 : Ja0;
+            Jb = b >= 32 ? Jb1 : Jb0;
+        } else {                                   // NT <= 32: one slot per lane, pairs < 32
+            Ra = (unsigned long long)__shfl_sync(FULL, (uint32_t)R0, a);
+            Ja = __shfl_sync(FULL, J0, a);
+        }
+        if (J0 < NT) { R0 |= Ra; J0 = Ja; }
+        if (J1 < NT) { R1 |= Rb; J1 = Jb; }
+    }
+    const unsigned long long mask = ~__shfl_sync(FULL, R0, 0) & ((1ull << np) - 1ull);
     // every slot's new content from the mask, gathered before any slot is rewritten
-    const unsigned long long mask = ((unsigned long long)hi << 32) | lo;
     int e_new[2] = {0, 0}, b_new[2] = {0, 0};
 #pragma unroll
     for (int h = 0; h < 2; ++h) {

@@ -6,8 +6,10 @@ runs the main paths on small valid cases -- both sweep mappings, a doubling
 TTS evaluation, a speculative RAO batch, a planted instance whose couplers
 exceed +-3 (larger Metropolis table), a graph-launched batch and the
 allocation-free evaluation -- and must report no failed check and results
-equal to the oracle's.  It runs in a child process because a process loads
-one build of the library.
+equal to the oracle's.  Two long runs with an exchange pass every sweep (48
+temperatures on a wide ladder, 64 on a narrow one) also re-derive every
+closed-form exchange criterion from the table (code 8 on a difference).  It
+runs in a child process because a process loads one build of the library.
 """
 import os
 import subprocess
@@ -66,6 +68,12 @@ t = ctypes.c_int32()
 assert lib.pt_tts_eval_noalloc(L, J.ctypes.data_as(ctypes.c_void_p), len(J), betas.ctypes.data_as(ctypes.c_void_p),
                                NT, R, seed, 7, 64, 1, 1, None, ctypes.byref(t), None, None) == 0
 assert t.value == oracle.tts_eval(L, J, betas, R, seed, 7, 64, 1, 1)[0]
+# exchange every sweep over many criteria: the debug build recomputes each
+# closed-form critical gap by the table search (code 8 on any difference)
+for (l, nt, lo, hi, runs, n) in ((4, 48, 0.05, 5.0, 64, 1500), (2, 64, 0.30, 0.35, 64, 1500)):
+    with P.PTHandle(l, W.random_couplers(l, seed, 9), W.beta_ladder(nt, lo, hi), runs, seed, 9) as h:
+        h.sweep(n, 1)
+        assert P.debug_status() == 0, "closed-form exchange criterion differs from the table search"
 code = P.debug_status()
 assert code == 0, f"bounds check {code} failed"
 print("debug build: no failed bounds check")

@@ -74,6 +74,7 @@ SHAPES = [
     (4, 1, 4, 150, 1, None),                    # one temperature: no exchange
     (4, 2, 4, 150, 1, None),
     (4, 64, 2, 40, 1, None),                    # maximum slots
+    (4, 33, 3, 90, 1, None),                    # first slot count with two slots per exchange lane
 ]
 
 
@@ -105,6 +106,7 @@ SLOT_MAJOR = [
     (5, 8, 2, 100, 1, (4, 8, 1)),
     (4, 1, 4, 150, 1, (32, 1, 1)),              # one temperature
     (4, 64, 2, 40, 1, (2, 64, 2)),              # maximum slots
+    (4, 33, 3, 90, 1, (4, 32, 1)),              # two slots per exchange lane, 33 buffers on 32 teams
 ]
 
 
@@ -153,6 +155,23 @@ def test_standalone_exchange(P):
         ref.sweeps(3, 0)
         ref.exchange()
     _assert_state_equal(h.state(), ref, "standalone exchange")
+
+
+def test_narrow_ladder_exchange_bit_exact(P):
+    """Close temperatures (64 slots in beta [0.30, 0.35]) make exchange tables of
+    about 15,000 entries per pair, so the critical gaps reach the thousands and
+    the float estimate of each gap carries its largest absolute error.  Every
+    exchange decision must still equal the oracle's table search, in both
+    mappings."""
+    for mapping in (None, (2, 64, 2)):
+        h, ref, _, _ = _pair(P, 2, 64, 4, seed=31, uid=5, bmin=0.30, bmax=0.35)
+        if mapping:
+            h.set_mapping(*mapping)
+        h.sweep(300, 1)
+        ref.sweeps(300, 1)
+        _assert_state_equal(h.state(), ref, f"narrow ladder, mapping {mapping}")
+        assert ref.xacc.sum() > 0
+        h.close()
 
 
 def test_set_spins_and_gauge(P):
