@@ -232,8 +232,9 @@ __device__ __forceinline__ void colour_phase(const CellRegs& cr, uint32_t* sw, i
 }
 
 // Exchange critical gaps of every pair of this run for sweep counter s
-// (called by one group of 32 threads; lane l handles pairs 4l..4l+3 from one
-// Philox call).  Table offsets and search hints come from shared memory.
+// (called by one group of 32 threads; lane l handles pairs l and l + 32, the
+// four lanes of pairs 4c..4c+3 each forming the Philox call c and taking its
+// own word).  Table offsets and search hints come from shared memory.
 __device__ __forceinline__ void exchange_prepare(const InstDesc& in, const uint32_t* thr_sm, int lane,
                                                  uint32_t s, uint32_t runbits, uint32_t k0, uint32_t k1,
                                                  int NT, int32_t* cc)
@@ -242,14 +243,11 @@ __device__ __forceinline__ void exchange_prepare(const InstDesc& in, const uint3
     const int32_t* xoff_sm = reinterpret_cast<const int32_t*>(thr_sm + NT * in.kt);
     const float* xhint_sm = reinterpret_cast<const float*>(thr_sm + NT * in.kt + NT);
     const int npairs = NT - 1;
-    for (int call = lane; call * 4 < npairs; call += 32) {
-        const uint4 w = philox10(s, runbits, (uint32_t)call, 1u, k0, k1);
-        const uint32_t wv[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int p = call * 4 + e;
-            if (p < npairs) cc[p] = critical_half_gap(in, xoff_sm, xhint_sm, p, wv[e]);
-        }
+    for (int p = lane; p < npairs; p += 32) {
+        const uint4 w = philox10(s, runbits, (uint32_t)(p >> 2), 1u, k0, k1);
+        const int e = p & 3;
+        const uint32_t u = e == 0 ? w.x : e == 1 ? w.y : e == 2 ? w.z : w.w;
+        cc[p] = critical_half_gap(in, xoff_sm, xhint_sm, p, u);
     }
 }
 
