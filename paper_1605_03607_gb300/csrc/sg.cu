@@ -119,9 +119,11 @@ constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;
 constexpr int TC_ROWS = 128;
 // CTAs of 256 threads: all 8 warps stage a tile; in the epilogue warps w and
 // w + 4 read the same 32 tensor-memory lanes (a warp reaches lanes
-// 32 (w mod 4) .. + 31) and split the columns.  Dynamic shared memory:
-// forward A 32 KB + W 16 KB = 48 KB, input gradient dZ 16 KB + W^T 16 KB
-// padded to 48 KB (4 CTAs per SM, 64 or 128 tensor-memory columns each);
+// 32 (w mod 4) .. + 31) and split the columns, and each warp's stores pass
+// through a 4 KB slice of the consumed operand buffer (warp_store_*).
+// Dynamic shared memory: forward A 32 KB + W 16 KB = 48 KB, input gradient
+// dZ 16 KB + staging 16 KB + W^T 16 KB = 48 KB (4 CTAs per SM, 64 or 128
+// tensor-memory columns each);
 // weight gradient two stages of 24 KB (the next chunk loads while the
 // current one is multiplied) + ones 16 KB = 64 KB (3 CTAs, 128 columns).  The
 // shared memory bounds the resident CTAs, so their tensor memory never
@@ -215,6 +217,58 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
 
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// Epilogue stores of one warp's 32 accumulator rows (lane l holds row l),
+// staged through a 4 KB slice of shared memory so that each global store
+// instruction writes whole rows: 4 rows x 128 bytes (32 FP32 columns) or 8
+// rows x 64 bytes (32 BF16 columns) instead of one 16-byte piece of each of
+// 32 rows.  Row l's 16-byte chunk c sits at slot c ^ (l & 7) (FP32) or
+// c ^ ((l >> 1) & 3) (BF16) of its row, so neither the row-wise writes nor
+// the chunk-wise reads of a warp meet a bank conflict.  flush_* writes the
+// staged block: g points at the warp's first row and first column, ld is the
+// row pitch in elements, and only rows < nvalid are written.
+__device__ __forceinline__ void stage_f32(unsigned char* stage, int lane, int c, float4 v)
+{
+    *reinterpret_cast<float4*>(stage + lane * 128 + ((c ^ (lane & 7)) << 4)) = v;
+}
+
+__device__ __forceinline__ void flush_f32x32(const unsigned char* stage, float* g, int ld, int nvalid, int lane)
+{
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int row = k * 4 + (lane >> 3), c = lane & 7;
+        const float4 x = *reinterpret_cast<const float4*>(stage + row * 128 + ((c ^ (row & 7)) << 4));
+        if (row < nvalid) *reinterpret_cast<float4*>(g + (size_t)row * ld + c * 4) = x;
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ void stage_bf16(unsigned char* stage, int lane, int c, uint4 v)
+{
+    *reinterpret_cast<uint4*>(stage + lane * 64 + ((c ^ ((lane >> 1) & 3)) << 4)) = v;
+}
+
+__device__ __forceinline__ void flush_bf16x32(const unsigned char* stage, bf16* g, int ld, int nvalid, int lane)
+{
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int row = k * 8 + (lane >> 2), c = lane & 3;
+        const uint4 x = *reinterpret_cast<const uint4*>(stage + row * 64 + ((c ^ ((row >> 1) & 3)) << 4));
+        if (row < nvalid) *reinterpret_cast<uint4*>(g + (size_t)row * ld + c * 8) = x;
+    }
+    __syncwarp();
+}
+
+// A 32-column BF16 block packed in 16 words (2 per column pair) through the staging slice.
+__device__ __forceinline__ void store_bf16x32(unsigned char* stage, const uint32_t (&w)[16], bf16* g, int ld,
+                                              int nvalid, int lane)
+{
+#pragma unroll
+    for (int c = 0; c < 4; ++c) stage_bf16(stage, lane, c, make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]));
+    flush_bf16x32(stage, g, ld, nvalid, lane);
+}
+
 // Common prologue: tensor memory (ncols columns, warp 0), the two mbarriers,
 // and the packed weights (bytes) by one bulk copy.  Returns false (for every
 // thread) if the weights did not arrive within the wait limit.
@@ -258,7 +312,7 @@ __device__ __forceinline__ void tc_teardown(uint32_t tmem, uint32_t ncols, bool 
 // (messages): Z -> Zout (BF16), relu(Z) -> Rout (FP32).  EPI 1 (residual):
 // Z -> Zout, Yout = P0 row + relu(Z) (BF16).
 template <int EPI>
-__global__ void __launch_bounds__(TC_THREADS) lin_fwd_tc_kernel(int rows, RowSrc src, const bf16* __restrict__ Wpk,
+__global__ void __launch_bounds__(TC_THREADS, TC_CTAS_FWD) lin_fwd_tc_kernel(int rows, RowSrc src, const bf16* __restrict__ Wpk,
                                                                 const float* __restrict__ bias, bf16* __restrict__ Zout,
                                                                 float* __restrict__ Rout, bf16* __restrict__ Yout,
                                                                 int* err)
@@ -308,48 +362,52 @@ __global__ void __launch_bounds__(TC_THREADS) lin_fwd_tc_kernel(int rows, RowSrc
             break;
         }
         tc_fence_after();
-        const int q = warp & 3, r = r0 + q * 32 + lane;    // TMEM lane q*32 + lane = this thread's row
+        // warp w: accumulator rows 32 (w mod 4) .. + 31 (TMEM lanes), columns 32 (w / 4) .. + 31, read
+        // 16 at a time; the operand tile is consumed (MMA complete), so its 32 KB hold the 8 warps'
+        // staging slices
+        const int q = warp & 3, cb = (warp >> 2) * (HD / 2), row0 = r0 + q * 32, row = q * 32 + lane;
         const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
+        unsigned char* stage = As + warp * 4096;
+        uint32_t zw[HD / 4], yw[EPI == 1 ? HD / 4 : 1];
 #pragma unroll
-        for (int c0 = (warp >> 2) * (HD / 2); c0 < (warp >> 2) * (HD / 2) + HD / 2; c0 += 16) {
+        for (int hh = 0; hh < 2; ++hh) {
+            const int c0 = cb + 16 * hh;
             float z[16];
             tmem_ld16(tl + c0, z);
             tmem_ld_wait();
-            if (r < rows) {
 #pragma unroll
-                for (int i = 0; i < 16; ++i) z[i] += bias_sm[c0 + i];
-                uint4 zp[2];
-                uint32_t* zw = reinterpret_cast<uint32_t*>(zp);
+            for (int i = 0; i < 16; ++i) z[i] += bias_sm[c0 + i];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) zw[i] = pack_bf2(z[2 * i], z[2 * i + 1]);
-                uint4* zo = reinterpret_cast<uint4*>(Zout + (size_t)r * HD + c0);
-                zo[0] = zp[0];
-                zo[1] = zp[1];
-                if (EPI == 0) {
-                    float4* ro = reinterpret_cast<float4*>(Rout + (size_t)r * HD + c0);
+            for (int i = 0; i < 8; ++i) zw[8 * hh + i] = pack_bf2(z[2 * i], z[2 * i + 1]);
+            if (EPI == 0) {
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
-                        ro[i] = make_float4(fmaxf(z[4 * i], 0.f), fmaxf(z[4 * i + 1], 0.f), fmaxf(z[4 * i + 2], 0.f),
-                                            fmaxf(z[4 * i + 3], 0.f));
-                } else {
-                    // the residual input is half 0 of this row, already staged: k-chunks c0/8 and c0/8 + 1
-                    const int row = q * 32 + lane;
-                    const unsigned char* sb = As + (((row >> 3) * 16 + (c0 >> 3)) * 128) + (row & 7) * 16;
-                    uint4 b4[2] = {*reinterpret_cast<const uint4*>(sb), *reinterpret_cast<const uint4*>(sb + 128)}, yp[2];
-                    const uint32_t* bw = reinterpret_cast<const uint32_t*>(b4);
-                    uint32_t* yw = reinterpret_cast<uint32_t*>(yp);
+                for (int c = 0; c < 4; ++c)
+                    stage_f32(stage, lane, 4 * hh + c,
+                              make_float4(fmaxf(z[4 * c], 0.f), fmaxf(z[4 * c + 1], 0.f), fmaxf(z[4 * c + 2], 0.f),
+                                          fmaxf(z[4 * c + 3], 0.f)));
+            } else {
+                // the residual input is half 0 of this row, already staged: k-chunks c0/8 and c0/8 + 1
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
+                for (int kc = 0; kc < 2; ++kc) {
+                    const uint4 b4 = *reinterpret_cast<const uint4*>(As + (((row >> 3) * 16 + (c0 >> 3) + kc) * 128) +
+                                                                     (row & 7) * 16);
+                    const uint32_t bw[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
                         const float2 bb = unpack_bf2(bw[i]);
-                        yw[i] = pack_bf2(bb.x + fmaxf(z[2 * i], 0.f), bb.y + fmaxf(z[2 * i + 1], 0.f));
+                        yw[(EPI == 1 ? 8 * hh + 4 * kc + i : 0)] =
+                            pack_bf2(bb.x + fmaxf(z[8 * kc + 2 * i], 0.f), bb.y + fmaxf(z[8 * kc + 2 * i + 1], 0.f));
                     }
-                    uint4* yo = reinterpret_cast<uint4*>(Yout + (size_t)r * HD + c0);
-                    yo[0] = yp[0];
-                    yo[1] = yp[1];
                 }
             }
         }
-        if (EPI == 1) __syncthreads();                     // the staged tile is read above before it is restaged
+        if constexpr (EPI == 0) {
+            flush_f32x32(stage, Rout + (size_t)row0 * HD + cb, HD, rows - row0, lane);
+        } else {
+            __syncthreads();                               // every residual read before any slice is overwritten
+            store_bf16x32(stage, yw, Yout + (size_t)row0 * HD + cb, HD, rows - row0, lane);
+        }
+        store_bf16x32(stage, zw, Zout + (size_t)row0 * HD + cb, HD, rows - row0, lane);
     }
     tc_teardown(tmem, 64, failed, err);
 }
@@ -359,14 +417,15 @@ __global__ void __launch_bounds__(TC_THREADS) lin_fwd_tc_kernel(int rows, RowSrc
 // updates): out0 = base + dX[:, :64] (base may be out0 or NULL) and
 // out1 = dX[:, 64:], both [rows][64] FP32.
 template <int EPI>
-__global__ void __launch_bounds__(TC_THREADS) lin_bwd_input_tc_kernel(int rows, const bf16* __restrict__ dZ,
+__global__ void __launch_bounds__(TC_THREADS, EPI == 0 ? TC_CTAS_BWD : 2) lin_bwd_input_tc_kernel(int rows, const bf16* __restrict__ dZ,
                                                                       const bf16* __restrict__ WTpk,
                                                                       float* __restrict__ dX, const float* base,
                                                                       float* out0, float* __restrict__ out1, int* err)
 {
     extern __shared__ __align__(128) unsigned char tc_smem[];
     unsigned char* As = tc_smem;                         // [16 row groups][8 k-chunks][8 rows][16 B]
-    unsigned char* Ws = tc_smem + TC_A_BWD;              // [16 input groups][8 k-chunks][8 inputs][16 B]
+    unsigned char* Ws = tc_smem + 2 * TC_A_BWD;          // [16 input groups][8 k-chunks][8 inputs][16 B]
+    // bytes [0, 2 * TC_A_BWD): the dZ tile, then (MMA complete) the epilogue's staging slices
     __shared__ __align__(8) uint64_t bar_w, bar_mma;
     __shared__ uint32_t tmem_sh;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -413,31 +472,40 @@ __global__ void __launch_bounds__(TC_THREADS) lin_bwd_input_tc_kernel(int rows, 
             break;
         }
         tc_fence_after();
+        // warp w: rows 32 (w mod 4) .. + 31, columns 64 (w / 4) .. + 63 of dX, in two passes of 32
+        // through its staging slice (the consumed dZ tile and the 16 KB above it)
         const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
+        const int row0 = r0 + q * 32;
+        unsigned char* stage = As + warp * 4096;
 #pragma unroll
-        for (int c0 = (warp >> 2) * HD; c0 < (warp >> 2) * HD + HD; c0 += 16) {
-            float d[16];
-            tmem_ld16(tl + c0, d);
-            tmem_ld_wait();
-            if (r < rows) {
-                if (EPI == 0) {
-                    float4* o = reinterpret_cast<float4*>(dX + (size_t)r * KIN + c0);
+        for (int pass = 0; pass < 2; ++pass) {
+            const int c0 = (warp >> 2) * HD + pass * 32;
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) o[i] = make_float4(d[4 * i], d[4 * i + 1], d[4 * i + 2], d[4 * i + 3]);
-                } else if (c0 < HD) {
-                    float4* o = reinterpret_cast<float4*>(out0 + (size_t)r * HD + c0);
+            for (int hh = 0; hh < 2; ++hh) {
+                float d[16];
+                tmem_ld16(tl + c0 + 16 * hh, d);
+                tmem_ld_wait();
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const float4 bb = bpre[(EPI == 1 ? (c0 >> 2) + i : 0)];
-                        o[i] = make_float4(d[4 * i] + bb.x, d[4 * i + 1] + bb.y, d[4 * i + 2] + bb.z, d[4 * i + 3] + bb.w);
+                for (int c = 0; c < 4; ++c) {
+                    float4 v = make_float4(d[4 * c], d[4 * c + 1], d[4 * c + 2], d[4 * c + 3]);
+                    if (EPI == 1 && c0 < HD) {
+                        const float4 bb = bpre[(EPI == 1 ? (c0 >> 2) + 4 * hh + c : 0)];
+                        v.x += bb.x;
+                        v.y += bb.y;
+                        v.z += bb.z;
+                        v.w += bb.w;
                     }
-                } else {
-                    float4* o = reinterpret_cast<float4*>(out1 + (size_t)r * HD + (c0 - HD));
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) o[i] = make_float4(d[4 * i], d[4 * i + 1], d[4 * i + 2], d[4 * i + 3]);
+                    stage_f32(stage, lane, 4 * hh + c, v);
                 }
             }
+            if (EPI == 0)
+                flush_f32x32(stage, dX + (size_t)row0 * KIN + c0, KIN, rows - row0, lane);
+            else if (c0 < HD)
+                flush_f32x32(stage, out0 + (size_t)row0 * HD + c0, HD, rows - row0, lane);
+            else
+                flush_f32x32(stage, out1 + (size_t)row0 * HD + (c0 - HD), HD, rows - row0, lane);
         }
+        __syncthreads();                                   // staging slices read before the next tile lands there
     }
     tc_teardown(tmem, 128, failed, err);
 }
