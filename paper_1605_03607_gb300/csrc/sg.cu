@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(TC_THREADS, TC_CTAS_FWD) lin_fwd_tc_kernel(int
     unsigned char* Ws = tc_smem + TC_A_FWD;              // [8 output groups][16 k-chunks][8 outputs][16 B]
     __shared__ __align__(8) uint64_t bar_w, bar_mma;
     __shared__ uint32_t tmem_sh;
-    __shared__ const unsigned char* rowp[2][TC_ROWS];    // this tile's gathered row halves (NULL past the end)
+    __shared__ const unsigned char* rowp[2][2][TC_ROWS]; // gathered row halves of this and the next tile (NULL past the end)
     __shared__ float bias_sm[HD];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid < HD) bias_sm[tid] = bias[tid];
@@ -331,18 +331,23 @@ __global__ void __launch_bounds__(TC_THREADS, TC_CTAS_FWD) lin_fwd_tc_kernel(int
     constexpr uint32_t IDESC = tc_idesc_bf16(TC_ROWS, HD);
     const int ntiles = (rows + TC_ROWS - 1) / TC_ROWS;
     uint32_t phase = 0;
-    for (int tile = blockIdx.x; !failed && tile < ntiles; tile += gridDim.x) {
+    // one index lookup per row half: thread tid looks up row tid mod 128, half tid / 128
+    auto lookup = [&](int t, int buf) {
+        const int row = tid & (TC_ROWS - 1), hf = tid >> 7, r = t * TC_ROWS + row;
+        rowp[buf][hf][row] = r < rows ? reinterpret_cast<const unsigned char*>(src.half(r, hf)) : nullptr;
+    };
+    if (blockIdx.x < ntiles) lookup(blockIdx.x, 0);
+    int buf = 0;
+    for (int tile = blockIdx.x; !failed && tile < ntiles; tile += gridDim.x, buf ^= 1) {
         const int r0 = tile * TC_ROWS;
-        {                                                  // one index lookup per row half
-            const int row = tid & (TC_ROWS - 1), hf = tid >> 7, r = r0 + row;
-            rowp[hf][row] = r < rows ? reinterpret_cast<const unsigned char*>(src.half(r, hf)) : nullptr;
-        }
-        __syncthreads();
+        __syncthreads();                                    // this tile's row pointers staged; the last epilogue done
         for (int i = tid; i < 16 * TC_ROWS; i += TC_THREADS) {   // chunk i: row (i >> 7) * 8 + (i & 7), k-chunk (i >> 3) & 15
             const int kc = (i >> 3) & 15, row = ((i >> 7) << 3) | (i & 7);
-            const unsigned char* p = rowp[kc >> 3][row];
+            const unsigned char* p = rowp[buf][kc >> 3][row];
             cp_async16(As + i * 16, p ? p + (kc & 7) * 16 : reinterpret_cast<const unsigned char*>(Wpk), p != nullptr);
         }
+        // the next tile's lookups overlap this gather (its buffer was last read by the previous gather)
+        if (tile + (int)gridDim.x < ntiles) lookup(tile + gridDim.x, buf ^ 1);
         asm volatile("cp.async.wait_all;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");     // visible to the tensor core
         tc_fence_before();
@@ -798,7 +803,9 @@ __global__ void readout_kernel(int N, const bf16* __restrict__ h, const float* _
     for (int n = 0; n < N; ++n) dh[((size_t)b * N + n) * HD + c] = dg;
 }
 
-// embedding gradients: per-block partial sums in shared memory, then atomics
+// Embedding gradients: dX[o] += sum of dh over the nodes of orientation o, dJt[v] += sum of de over
+// the edges of coupler value v.  A thread owns column c of a strided set of rows and keeps its 2 + 6
+// class sums in registers; they reach shared memory once per thread and global memory once per block.
 __global__ void embed_bwd_kernel(int B, int N, int E, const int* __restrict__ u, const int8_t* __restrict__ J,
                                  const float* __restrict__ dh, const float* __restrict__ de, float* dX, float* dJt)
 {
@@ -807,16 +814,25 @@ __global__ void embed_bwd_kernel(int B, int N, int E, const int* __restrict__ u,
     for (int i = threadIdx.x; i < 6 * HD; i += blockDim.x) sj[i] = 0.f;
     __syncthreads();
     const int c = threadIdx.x % HD, lanes = blockDim.x / HD;
-    const size_t nrows = (size_t)B * (N + E);
-    for (size_t row = blockIdx.x * (size_t)lanes + threadIdx.x / HD; row < nrows; row += (size_t)gridDim.x * lanes) {
-        if (row < (size_t)B * N) {
-            atomicAdd(&sx[u[row % N] * HD + c], dh[row * HD + c]);
-        } else {
-            const size_t re = row - (size_t)B * N;
-            const int j = J[re];
-            atomicAdd(&sj[(j < 0 ? j + 3 : j + 2) * HD + c], de[re * HD + c]);
-        }
+    const size_t nN = (size_t)B * N, nE = (size_t)B * E, stride = (size_t)gridDim.x * lanes;
+    const size_t first = blockIdx.x * (size_t)lanes + threadIdx.x / HD;
+    float ax0 = 0.f, ax1 = 0.f, aj[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (size_t row = first; row < nN; row += stride) {
+        const float v = dh[row * HD + c];
+        if (u[row % N]) ax1 += v;
+        else ax0 += v;
     }
+    for (size_t re = first; re < nE; re += stride) {
+        const int j = J[re];
+        const int k = j < 0 ? j + 3 : j + 2;                 // -3,-2,-1,1,2,3 -> 0..5
+        const float v = de[re * HD + c];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) aj[q] += k == q ? v : 0.f;
+    }
+    atomicAdd(&sx[c], ax0);
+    atomicAdd(&sx[HD + c], ax1);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) atomicAdd(&sj[q * HD + c], aj[q]);
     __syncthreads();
     for (int i = threadIdx.x; i < 2 * HD; i += blockDim.x) atomicAdd(&dX[i], sx[i]);
     for (int i = threadIdx.x; i < 6 * HD; i += blockDim.x) atomicAdd(&dJt[i], sj[i]);
@@ -1125,7 +1141,7 @@ int backward_all(sg_model* M, int B)
         edge_from_messages_kernel<<<grid_for(nE * HD), 256, 0, st>>>(B, E, M->dX, M->de);
         M->launches += 18;
     }
-    embed_bwd_kernel<<<256, 256, 0, st>>>(B, N, E, M->d_u, M->d_J, M->dh, M->de, G + M->oX, G + M->oJ);
+    embed_bwd_kernel<<<4 * M->sms, 256, 0, st>>>(B, N, E, M->d_u, M->d_J, M->dh, M->de, G + M->oX, G + M->oJ);
     M->launches++;
     return PT_OK;
 }
