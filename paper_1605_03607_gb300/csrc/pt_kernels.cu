@@ -616,7 +616,7 @@ __device__ void process_bundle(const InstDesc* __restrict__ insts, const Bundle 
 // cell record (dp4a over int8 couplers and spins), Metropolis test of each
 // spin against its uniform in `rn`, flips written back, energy change and
 // flip bits accumulated.
-__device__ __forceinline__ void sm_word(const uint32_t* rec, uint32_t meta, uint32_t* bw, int col, int L2, int q,
+__device__ __forceinline__ void sm_word(const uint32_t* rec, uint4 meta, uint32_t* bw, int col, int L2, int q,
                                         const uint4 rn, const uint32_t* th, int kt, int& dk, int& pc)
 {
     const uint4 jin = *reinterpret_cast<const uint4*>(rec);
@@ -624,7 +624,7 @@ __device__ __forceinline__ void sm_word(const uint32_t* rec, uint32_t meta, uint
     const int ow = col * L2 + q;
     const uint32_t own = bw[ow];
     const int opp = (int)bw[(1 - col) * L2 + q];
-    const uint32_t mw = bw[PT_IDX((int)((meta >> 10) & 1023u), 2 * L2, 5u)], pw = bw[PT_IDX((int)(meta >> 20), 2 * L2, 5u)];
+    const uint32_t mw = bw[PT_IDX((int)meta.y, 2 * L2, 5u)], pw = bw[PT_IDX((int)meta.z, 2 * L2, 5u)];
     const int x01 = (int)__byte_perm(mw, pw, 0x5140);
     const int x23 = (int)__byte_perm(mw, pw, 0x7362);
     const int h0 = __dp4a((int)jin.x, opp, __dp4a((int)jud.x, x01, 0));
@@ -704,7 +704,9 @@ __device__ void process_bundle_sm(const InstDesc* __restrict__ insts, const Bund
         const uint32_t gidx = (uint32_t)(2 * q + ((r + c + col) & 1));
         const uint32_t mn = (uint32_t)((1 - col) * L2 + in.nbr[w * 2 + 0]);
         const uint32_t pl = (uint32_t)((1 - col) * L2 + in.nbr[w * 2 + 1]);
-        rec_sm[(col * L2 + q) * CELL_REC + 8] = gidx | (mn << 10) | (pl << 20);
+        rec_sm[(col * L2 + q) * CELL_REC + 8] = gidx;
+        rec_sm[(col * L2 + q) * CELL_REC + 9] = mn;
+        rec_sm[(col * L2 + q) * CELL_REC + 10] = pl;
     }
     const size_t rep0 = (size_t)run * NT;
     if (active) {
@@ -767,8 +769,8 @@ __device__ void process_bundle_sm(const InstDesc* __restrict__ insts, const Bund
                 for (int col = 0; col < 2; ++col) {
                     for (int q = tl; q < L2; q += G) {
                         const uint32_t* rec = rec_sm + (col * L2 + q) * CELL_REC;
-                        const uint32_t meta = rec[8];
-                        const uint4 rn = philox_group(ps, c1, meta & 1023u, k0, k1);
+                        const uint4 meta = *reinterpret_cast<const uint4*>(rec + 8);   // group, minus, plus word
+                        const uint4 rn = philox_group(ps, c1, meta.x, k0, k1);
                         sm_word(rec, meta, bw, col, L2, q, rn, th, KTI, dk, pc);
                     }
                     __syncwarp(tmask);                  // colour 0 of this buffer done by the whole team
