@@ -614,8 +614,9 @@ __device__ void process_bundle(const InstDesc* __restrict__ insts, const Bundle 
 // One colour-`col` word (4 spins, cell q) of the slot-major update at the
 // temperature of the slot whose threshold row is `th`: local fields from the
 // cell record (dp4a over int8 couplers and spins), Metropolis test of each
-// spin against its uniform in `rn`, flips written back, energy change and
-// flip bits accumulated.
+// spin against its uniform in `rn`, the word written back (unchanged where
+// nothing flipped: in a colour phase only the other colour's words are
+// read), energy change and flip bits accumulated.
 __device__ __forceinline__ void sm_word(const uint32_t* rec, uint4 meta, uint32_t* bw, int col, int L2, int q,
                                         const uint4 rn, const uint32_t* th, int kt, int& dk, int& pc)
 {
@@ -644,7 +645,7 @@ __device__ __forceinline__ void sm_word(const uint32_t* rec, uint4 meta, uint32_
     if (a1) { flip |= 0x0000FE00u; dk += kk1; }
     if (a2) { flip |= 0x00FE0000u; dk += kk2; }
     if (a3) { flip |= 0xFE000000u; dk += kk3; }
-    if (flip) bw[ow] = own ^ flip;
+    bw[ow] = own ^ flip;                           // unconditional: one compare fewer per word
     pc += __popc(flip);
 }
 

@@ -13,7 +13,8 @@
 // node or edge row), their input gradients and their weight gradients run on
 // the 5th-generation tensor cores (tcgen05.mma, accumulators in tensor
 // memory).  Gradients are FP32 buffers; master weights and Adam moments are
-// FP32.
+// FP32.  Every reduction runs in a fixed order (no floating-point atomics), so
+// a training step is bit-reproducible.
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -764,8 +765,8 @@ __global__ void edge_from_messages_kernel(int B, int E, const float* __restrict_
 // readout forward + loss gradient (one block per graph, HD threads)
 __global__ void readout_kernel(int N, const bf16* __restrict__ h, const float* __restrict__ W1, const float* __restrict__ b1,
                                const float* __restrict__ w2, const float* __restrict__ b2, float* y, float* gbuf,
-                               float* zbuf, const float* __restrict__ target, float inv_B, float* loss,
-                               float* dh, float* dW1, float* db1, float* dw2, float* db2)
+                               float* zbuf, const float* __restrict__ target, float inv_B, float* dybuf,
+                               float* sqbuf, float* dh)
 {
     __shared__ float gs[HD], as[HD], red[HD], dz[HD];
     const int b = blockIdx.x, c = threadIdx.x;
@@ -788,34 +789,66 @@ __global__ void readout_kernel(int N, const bf16* __restrict__ h, const float* _
     if (c == 0) y[b] = yb;
     if (!target) return;
     const float dy = 2.f * (yb - target[b]) * inv_B;
-    if (c == 0) {
-        atomicAdd(loss, (yb - target[b]) * (yb - target[b]) * inv_B);
-        atomicAdd(db2, dy);
+    if (c == 0) {                                  // this graph's loss term and output gradient (summed in order
+        dybuf[b] = dy;                             // over graphs by readout_grad_kernel)
+        sqbuf[b] = (yb - target[b]) * (yb - target[b]) * inv_B;
     }
-    atomicAdd(&dw2[c], dy * as[c]);
     dz[c] = z > 0.f ? dy * w2[c] : 0.f;
-    atomicAdd(&db1[c], dz[c]);
     __syncthreads();
-    for (int k = 0; k < HD; ++k) atomicAdd(&dW1[c * HD + k], dz[c] * gs[k]);
     float dg = 0.f;
     for (int o = 0; o < HD; ++o) dg += dz[o] * W1[o * HD + c];
     dg /= (float)N;
     for (int n = 0; n < N; ++n) dh[((size_t)b * N + n) * HD + c] = dg;
 }
 
+// Readout parameter gradients and the loss, summed over the B graphs in graph
+// order (bit-reproducible): block c < 64, thread k: dW1[c][k] += sum_b dz_b[c]
+// g_b[k] with dz_b[c] = dy_b w2[c] where z_b[c] > 0, and (thread 0) db1[c],
+// dw2[c]; block 64: db2 and the loss.
+__global__ void readout_grad_kernel(int B, const float* __restrict__ gbuf, const float* __restrict__ zbuf,
+                                    const float* __restrict__ dybuf, const float* __restrict__ sqbuf,
+                                    const float* __restrict__ w2, float* loss, float* dW1, float* db1, float* dw2,
+                                    float* db2)
+{
+    const int c = blockIdx.x, k = threadIdx.x;
+    if (c < HD) {
+        const float w = w2[c];
+        float acc = 0.f, a1 = 0.f, a2 = 0.f;
+        for (int b = 0; b < B; ++b) {
+            const float z = zbuf[b * HD + c], dy = dybuf[b];
+            const float dz = z > 0.f ? dy * w : 0.f;
+            acc += dz * gbuf[b * HD + k];
+            a1 += dz;
+            a2 += dy * fmaxf(z, 0.f);
+        }
+        dW1[c * HD + k] += acc;
+        if (k == 0) {
+            db1[c] += a1;
+            dw2[c] += a2;
+        }
+    } else if (k == 0) {
+        float s2 = 0.f, l = 0.f;
+        for (int b = 0; b < B; ++b) {
+            s2 += dybuf[b];
+            l += sqbuf[b];
+        }
+        db2[0] += s2;
+        *loss += l;
+    }
+}
+
 // Embedding gradients: dX[o] += sum of dh over the nodes of orientation o, dJt[v] += sum of de over
 // the edges of coupler value v.  A thread owns column c of a strided set of rows and keeps its 2 + 6
-// class sums in registers; they reach shared memory once per thread and global memory once per block.
+// class sums in registers; the block adds its 4 lanes' sums in lane order and writes them as its
+// partial part[block][8][64] (classes: orientations 0, 1, coupler values -3..3 without 0), and
+// embed_bwd_reduce adds the partials in block order (bit-reproducible).  256 threads per block.
 __global__ void embed_bwd_kernel(int B, int N, int E, const int* __restrict__ u, const int8_t* __restrict__ J,
-                                 const float* __restrict__ dh, const float* __restrict__ de, float* dX, float* dJt)
+                                 const float* __restrict__ dh, const float* __restrict__ de, float* __restrict__ part)
 {
-    __shared__ float sx[2 * HD], sj[6 * HD];
-    for (int i = threadIdx.x; i < 2 * HD; i += blockDim.x) sx[i] = 0.f;
-    for (int i = threadIdx.x; i < 6 * HD; i += blockDim.x) sj[i] = 0.f;
-    __syncthreads();
-    const int c = threadIdx.x % HD, lanes = blockDim.x / HD;
+    __shared__ float sp[4][8][HD];
+    const int c = threadIdx.x % HD, lane = threadIdx.x / HD, lanes = blockDim.x / HD;
     const size_t nN = (size_t)B * N, nE = (size_t)B * E, stride = (size_t)gridDim.x * lanes;
-    const size_t first = blockIdx.x * (size_t)lanes + threadIdx.x / HD;
+    const size_t first = blockIdx.x * (size_t)lanes + lane;
     float ax0 = 0.f, ax1 = 0.f, aj[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (size_t row = first; row < nN; row += stride) {
         const float v = dh[row * HD + c];
@@ -829,13 +862,26 @@ __global__ void embed_bwd_kernel(int B, int N, int E, const int* __restrict__ u,
 #pragma unroll
         for (int q = 0; q < 6; ++q) aj[q] += k == q ? v : 0.f;
     }
-    atomicAdd(&sx[c], ax0);
-    atomicAdd(&sx[HD + c], ax1);
+    sp[lane][0][c] = ax0;
+    sp[lane][1][c] = ax1;
 #pragma unroll
-    for (int q = 0; q < 6; ++q) atomicAdd(&sj[q * HD + c], aj[q]);
+    for (int q = 0; q < 6; ++q) sp[lane][2 + q][c] = aj[q];
     __syncthreads();
-    for (int i = threadIdx.x; i < 2 * HD; i += blockDim.x) atomicAdd(&dX[i], sx[i]);
-    for (int i = threadIdx.x; i < 6 * HD; i += blockDim.x) atomicAdd(&dJt[i], sj[i]);
+    for (int i = threadIdx.x; i < 8 * HD; i += blockDim.x) {
+        float t = 0.f;
+        for (int l = 0; l < lanes; ++l) t += sp[l][i / HD][i % HD];
+        part[(size_t)blockIdx.x * 8 * HD + i] = t;
+    }
+}
+
+__global__ void embed_bwd_reduce(int nblocks, const float* __restrict__ part, float* dX, float* dJt)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 8 * HD) return;
+    float t = 0.f;
+    for (int b = 0; b < nblocks; ++b) t += part[(size_t)b * 8 * HD + i];
+    if (i < 2 * HD) dX[i] += t;
+    else dJt[i - 2 * HD] += t;
 }
 
 __global__ void adam_kernel(int64_t n, float* theta, const float* __restrict__ g, float* m, float* v, float lr,
@@ -889,6 +935,8 @@ struct sg_model {
         *d_inc = nullptr, *d_src = nullptr, *d_tgt = nullptr, *d_eid = nullptr, *d_iden = nullptr, *d_msg_edge = nullptr;
     int8_t* d_J = nullptr;
     float *d_t = nullptr, *d_y = nullptr, *d_g = nullptr, *d_z = nullptr;
+    float *d_dy = nullptr, *d_sq = nullptr;   // per graph: output gradient, loss term (readout)
+    float* d_epart = nullptr;                 // embedding-gradient block partials [4 x SMs][8][64]
     std::vector<bf16*> h, e, m, s, zm, zu, ze;
     float *R = nullptr, *dX = nullptr, *dh = nullptr, *dh2 = nullptr, *de = nullptr, *dm = nullptr, *ds = nullptr;
     bf16* dZ = nullptr;
@@ -928,7 +976,8 @@ void free_graph(sg_model* M)
                     &M->d_eid, &M->d_iden, &M->d_msg_edge};
     for (int** p : ints) { cudaFree(*p); *p = nullptr; }
     cudaFree(M->d_J); M->d_J = nullptr;
-    float** fl[] = {&M->d_t, &M->d_y, &M->d_g, &M->d_z, &M->R, &M->dX, &M->dh, &M->dh2, &M->de, &M->dm, &M->ds};
+    float** fl[] = {&M->d_t, &M->d_y, &M->d_g, &M->d_z, &M->d_dy, &M->d_sq, &M->d_epart, &M->R, &M->dX, &M->dh,
+                    &M->dh2, &M->de, &M->dm, &M->ds};
     for (float** p : fl) { cudaFree(*p); *p = nullptr; }
     cudaFree(M->dZ); M->dZ = nullptr;
     cudaFree(M->wpart); M->wpart = nullptr;
@@ -998,6 +1047,9 @@ int prepare(sg_model* M, int L, int B)
     SK(salloc(&M->d_y, (size_t)B), "cudaMalloc y");
     SK(salloc(&M->d_g, (size_t)B * HD), "cudaMalloc g");
     SK(salloc(&M->d_z, (size_t)B * HD), "cudaMalloc z");
+    SK(salloc(&M->d_dy, (size_t)B), "cudaMalloc dy");
+    SK(salloc(&M->d_sq, (size_t)B), "cudaMalloc sq");
+    SK(salloc(&M->d_epart, (size_t)4 * M->sms * 8 * HD), "cudaMalloc embedding partials");
     M->h.assign(M->layers + 1, nullptr);
     M->e.assign(M->layers + 1, nullptr);
     M->m.assign(M->layers, nullptr);
@@ -1109,9 +1161,11 @@ int backward_all(sg_model* M, int B)
     SK(cudaMemsetAsync(M->dloss, 0, sizeof(float), st), "zero loss");
     SK(cudaMemsetAsync(M->de, 0, sizeof(float) * (size_t)B * E * HD, st), "zero de");
     readout_kernel<<<B, HD, 0, st>>>(N, M->h[M->layers], M->theta + M->oW1, M->theta + M->ob1, M->theta + M->ow2,
-                                     M->theta + M->ob2, M->d_y, M->d_g, M->d_z, M->d_t, 1.f / (float)B, M->dloss,
-                                     M->dh, G + M->oW1, G + M->ob1, G + M->ow2, G + M->ob2);
-    M->launches++;
+                                     M->theta + M->ob2, M->d_y, M->d_g, M->d_z, M->d_t, 1.f / (float)B, M->d_dy,
+                                     M->d_sq, M->dh);
+    readout_grad_kernel<<<HD + 1, HD, 0, st>>>(B, M->d_g, M->d_z, M->d_dy, M->d_sq, M->theta + M->ow2, M->dloss,
+                                               G + M->oW1, G + M->ob1, G + M->ow2, G + M->ob2);
+    M->launches += 2;
     const size_t nN = (size_t)B * N, nE = (size_t)B * E;
     for (int l = M->layers - 1; l >= 0; --l) {
         // edge update: e' = e + relu(ze), ze = We [e | s] + be
@@ -1141,8 +1195,9 @@ int backward_all(sg_model* M, int B)
         edge_from_messages_kernel<<<grid_for(nE * HD), 256, 0, st>>>(B, E, M->dX, M->de);
         M->launches += 18;
     }
-    embed_bwd_kernel<<<4 * M->sms, 256, 0, st>>>(B, N, E, M->d_u, M->d_J, M->dh, M->de, G + M->oX, G + M->oJ);
-    M->launches++;
+    embed_bwd_kernel<<<4 * M->sms, 256, 0, st>>>(B, N, E, M->d_u, M->d_J, M->dh, M->de, M->d_epart);
+    embed_bwd_reduce<<<(8 * HD + 255) / 256, 256, 0, st>>>(4 * M->sms, M->d_epart, G + M->oX, G + M->oJ);
+    M->launches += 2;
     return PT_OK;
 }
 
@@ -1295,7 +1350,7 @@ int sg_forward(sg_model* M, int32_t L, int32_t B, const int8_t* J, float* y)
     if ((rc = forward(M, B, false))) return rc;
     readout_kernel<<<B, HD, 0, M->stream>>>(M->N, M->h[M->layers], M->theta + M->oW1, M->theta + M->ob1,
                                             M->theta + M->ow2, M->theta + M->ob2, M->d_y, M->d_g, M->d_z, nullptr,
-                                            0.f, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+                                            0.f, nullptr, nullptr, nullptr);
     M->launches++;
     SK(cudaGetLastError(), "forward kernels");
     SK(cudaMemcpyAsync(y, M->d_y, sizeof(float) * B, cudaMemcpyDeviceToHost, M->stream), "download y");

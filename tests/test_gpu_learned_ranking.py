@@ -8,10 +8,14 @@ measurements, 80 % train the GPU surrogate on differences
 and the rest are held out.  The repeat correlation of the two measurements
 bounds what any ranking can reach; the untrained network ranks at chance.
 
-The assertions: the trained network's rank correlation with the measured
-held-out differences is at least 0.25 and at least 0.2 above the untrained
-network's, it stays below the repeat correlation of the measurement itself,
-and picking the best-predicted 4 of 64 random proposals finds harder moves
+Training is bit-reproducible, but its result still depends on the order in
+which the pairs are visited: the held-out rank correlation of single runs
+ranges over about 0.15-0.35 across shuffles.  The test therefore trains
+three networks (shuffles 0, 1, 2) and asserts on their mean: the trained
+networks' rank correlation with the measured held-out differences is at
+least 0.25 and at least 0.2 above the untrained network's, it stays below
+the repeat correlation of the measurement itself, and picking the
+best-predicted 4 of 64 random proposals (first network) finds harder moves
 on average than taking 4 at random (the guided step's use of the ranking).
 """
 import numpy as np
@@ -55,22 +59,25 @@ def test_trained_ranking_beats_untrained_on_held_out_moves(P):
     repeat = _spearman(a, b)
     perm = np.random.default_rng(0).permutation(len(d))
     tr, va = perm[:1400], perm[1400:]
-    with P.Surrogate() as m, P.Surrogate() as u:
-        m.set_params(W.surrogate_init_params(1))
+    with P.Surrogate() as u:
         u.set_params(W.surrogate_init_params(1))
-        hist = G.train_pairs(m, L, nb[tr], np.repeat(J0[None], len(tr), 0), d[tr] / d[tr].std(), epochs=60,
-                             batch=64, lr=1e-3)
-        pt, pu = m.forward(L, nb[va]), u.forward(L, nb[va])
-        sp_t, sp_u = _spearman(pt, d[va]), _spearman(pu, d[va])
-        assert sp_t >= 0.25 and sp_t >= sp_u + 0.2, (sp_t, sp_u, repeat)
-        # training (float atomics in two gradient kernels: not bit-reproducible) reduced the pair loss
-        assert hist[-1] < 0.8 * hist[0], hist
-        assert sp_t < repeat
-        rng = np.random.default_rng(1)
-        guided, plain = [], []
-        for _ in range(200):
-            cand = rng.choice(va, 64, replace=False)
-            pc = m.forward(L, nb[cand])
-            guided.append(d[cand[np.argsort(-pc, kind="stable")[:4]]].max())
-            plain.append(d[cand[:4]].max())
-        assert np.mean(guided) > np.mean(plain), (np.mean(guided), np.mean(plain))
+        sp_u = _spearman(u.forward(L, nb[va]), d[va])
+    sps, guided, plain = [], [], []
+    for shuffle in range(3):
+        with P.Surrogate() as m:
+            m.set_params(W.surrogate_init_params(1))
+            hist = G.train_pairs(m, L, nb[tr], np.repeat(J0[None], len(tr), 0), d[tr] / d[tr].std(), epochs=60,
+                                 batch=64, lr=1e-3, seed=shuffle)
+            assert hist[-1] < 0.8 * hist[0], hist          # training reduced the pair loss
+            sps.append(_spearman(m.forward(L, nb[va]), d[va]))
+            if shuffle == 0:                               # the guided step's use of the ranking
+                rng = np.random.default_rng(1)
+                for _ in range(200):
+                    cand = rng.choice(va, 64, replace=False)
+                    pc = m.forward(L, nb[cand])
+                    guided.append(d[cand[np.argsort(-pc, kind="stable")[:4]]].max())
+                    plain.append(d[cand[:4]].max())
+    sp_t = float(np.mean(sps))
+    assert sp_t >= 0.25 and sp_t >= sp_u + 0.2, (sps, sp_u, repeat)
+    assert sp_t < repeat
+    assert np.mean(guided) > np.mean(plain), (np.mean(guided), np.mean(plain))

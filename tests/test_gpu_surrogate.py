@@ -143,6 +143,23 @@ def test_training_reduces_loss(P):
     assert last < 0.2 * first, (first, last)
 
 
+def test_training_is_bit_reproducible(P):
+    """Every reduction of a training step runs in a fixed order (no floating-point
+    atomics), so two models trained from the same parameters on the same batches
+    end bit-identical, at a batch large enough for many CTAs per kernel."""
+    L, B = 4, 96
+    rng = np.random.default_rng(5)
+    batches = [(_J(L, B, rng), 2.0 + 0.3 * rng.standard_normal(B)) for _ in range(3)]
+    thetas, losses = [], []
+    for _ in range(2):
+        with P.Surrogate() as m:
+            m.set_params(W.surrogate_init_params(1))
+            losses.append([m.train_step(L, J, t, 1e-3) for J, t in batches * 2])
+            thetas.append(m.params())
+    assert losses[0] == losses[1]
+    assert np.array_equal(thetas[0], thetas[1])
+
+
 def test_rejects_zero_couplers(P):
     J = _J(2, 1, np.random.default_rng(1))
     J[0, 3] = 0
