@@ -184,7 +184,8 @@ int pt_get_tables(const pt_handle *h, uint32_t *thr, int64_t *xoff, uint32_t *xt
  * release build).  Codes: 1 Metropolis table row, 2 slot map, 3 exchange
  * table range, 4 run index, 5 neighbour word, 6 more than 1024 runs in a
  * TTS reduction, 7 slot map in the energy kernel, 8 a closed-form exchange
- * criterion that differs from the table search (debug builds evaluate both). */
+ * criterion that differs from the table search (debug builds evaluate both),
+ * 9 a bundle whose lattice side differs from its kernel's compile-time side. */
 int pt_debug_enabled(void);
 int pt_debug_status(uint32_t *code);
 

@@ -287,7 +287,8 @@ int run_graph(pt_batch* b, int nsweeps, int xevery)
             e = cudaStreamWaitEvent(g.st, b->ev_fork, 0);
             if (e == cudaSuccess)
                 e = launch_sweeps(b->d_desc, g.d_bundles, (int)g.bundles.size(), g.grid, g.block, g.smem,
-                                  (uint32_t)b->sweep, nsweeps, xevery, 0, b->d_queue + k, g.st, g.s.team > 0);
+                                  (uint32_t)b->sweep, nsweeps, xevery, 0, b->d_queue + k, g.st, g.s.team > 0, false,
+                                  g.L);
             if (e == cudaSuccess) e = cudaEventRecord(g.ev, g.st);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, g.ev, 0);
         }
@@ -756,7 +757,7 @@ int pt_batch_autotune(pt_batch* b, int32_t trial_sweeps, int32_t* block_out)
                 if (e == cudaSuccess) e = cudaMemsetAsync(b->d_queue + k, 0, sizeof(int), b->stream);
                 if (e == cudaSuccess)
                     e = launch_sweeps(b->d_desc, g.d_bundles, (int)g.bundles.size(), g.grid, g.block, g.smem, 0u,
-                                      trial_sweeps, 1, 0, b->d_queue + k, b->stream, g.s.team > 0);
+                                      trial_sweeps, 1, 0, b->d_queue + k, b->stream, g.s.team > 0, false, g.L);
                 if (e == cudaSuccess) e = cudaEventRecord(b->e1, b->stream);
                 if (e == cudaSuccess) e = cudaEventSynchronize(b->e1);
                 float t = 0.f;

@@ -339,7 +339,7 @@ int group_sweeps(pt_handle* h, Group& g, int64_t n, int xevery, const Bundle* ds
         const int chunk = (int)std::min<int64_t>(h->spl, n - done);
         if (h->timing) CK(cudaEventRecord(h->ev[2 * li], h->stream), "event");
         CK(launch_sweeps(g.d_desc, db, nb, nb, g.block, g.smem, (uint32_t)g.sweep, chunk, xevery, 0, nullptr,
-                         h->stream, h->team > 0, g.walk),
+                         h->stream, h->team > 0, g.walk, g.L),
            "sweep kernel");
         if (g.walk && g.NT > 1 && xevery > 0)
             g.walk_passes += (g.sweep + chunk) / (uint64_t)xevery - g.sweep / (uint64_t)xevery;
@@ -957,7 +957,7 @@ int pt_exchange(pt_handle* h)
     if (!h) return PT_ERR_ARG;
     Group& g = h->main;
     CK(launch_sweeps(g.d_desc, g.d_bundles, (int)g.bundles.size(), (int)g.bundles.size(), g.block,
-                     g.smem, (uint32_t)g.sweep, 0, 0, 1, nullptr, h->stream, h->team > 0, g.walk),
+                     g.smem, (uint32_t)g.sweep, 0, 0, 1, nullptr, h->stream, h->team > 0, g.walk, g.L),
        "exchange kernel");
     ++h->launches;
     if (g.walk && g.NT > 1) g.walk_passes += 1;

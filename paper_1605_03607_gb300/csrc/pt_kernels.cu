@@ -42,6 +42,7 @@ namespace ptg {
 //   5 neighbour spin word outside the buffer    6 TTS over more than 1024 runs
 //   7 energy kernel: slot map entry >= n_temps
 //   8 closed-form exchange criterion differs from the table search
+//   9 a bundle's lattice side differs from the kernel's compile-time side
 // Release builds compile the checks away.
 #ifdef PT_DEBUG
 __device__ unsigned int g_pt_debug_code;
@@ -660,14 +661,23 @@ __device__ __forceinline__ void sm_word(const uint32_t* rec, uint4 meta, uint32_
 // Bank layout: buffer strides are congruent to G modulo 32 and the cell
 // records are colour-major with a 48-byte stride, so a warp's own/opposite
 // spin words and coupler records come without bank conflicts.
-template <bool WALK>
+template <bool WALK, int LT>
 __device__ void process_bundle_sm(const InstDesc* __restrict__ insts, const Bundle bd,
                                   uint32_t sweep0, int nsweeps, int xevery, int mode,
                                   unsigned char* smem)
 {
     const InstDesc& in = insts[bd.inst];
     const int G = bd.team, NTEAM = bd.sp, TPI = G * NTEAM;
-    const int L = in.L, NT = in.NT, L2 = L * L, N = 8 * L2, NW = N / 4, NWP = NW + sm_pad(L, G);
+    // LT > 0: the lattice side is a compile-time constant (the launcher picks the
+    // instantiation from the one L of every bundle in the launch), so every
+    // offset derived from L folds into the instructions
+#ifdef PT_DEBUG
+    if (LT && in.L != LT) {                     // uniform per CTA: the whole CTA skips the bundle
+        if (threadIdx.x == 0) atomicCAS(&g_pt_debug_code, 0u, 9u);
+        return;
+    }
+#endif
+    const int L = LT ? LT : in.L, NT = in.NT, L2 = L * L, N = 8 * L2, NW = N / 4, NWP = NW + sm_pad(L, G);
     const int tid = threadIdx.x;
     const int item = tid / TPI, j = tid - item * TPI;
     const bool active = item < bd.nitems;
@@ -845,7 +855,7 @@ __device__ void process_bundle_sm(const InstDesc* __restrict__ insts, const Bund
 // kernels carry no walk code).  Both slot-major kernels are bounded to 72
 // registers (as if for 896 threads), which keeps 7 CTAs of 128 threads per SM;
 // the host still caps slot-major CTAs at 768 threads.
-template <bool SLOT_MAJOR, bool WALK>
+template <bool SLOT_MAJOR, bool WALK, int LT = 0>
 __global__ void __launch_bounds__(SLOT_MAJOR ? 896 : MAX_THREADS)
 pt_sweep_kernel(const InstDesc* __restrict__ insts, const Bundle* __restrict__ bundles,
                 int nbundles, uint32_t sweep0, int nsweeps, int xevery, int mode,
@@ -862,7 +872,7 @@ pt_sweep_kernel(const InstDesc* __restrict__ insts, const Bundle* __restrict__ b
     while (b < nbundles) {
         const Bundle bd = bundles[b];
         if (SLOT_MAJOR)
-            process_bundle_sm<WALK>(insts, bd, sweep0, nsweeps, xevery, mode, smem);
+            process_bundle_sm<WALK, LT>(insts, bd, sweep0, nsweeps, xevery, mode, smem);
         else
             process_bundle<WALK>(insts, bd, sweep0, nsweeps, xevery, mode, smem);
         if (!queue) break;
@@ -1056,8 +1066,10 @@ cudaError_t sweep_smem_capacity(int* bytes)
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
     size_t stat = 0;
-    const void* ks[4] = {(const void*)pt_sweep_kernel<false, false>, (const void*)pt_sweep_kernel<true, false>,
-                         (const void*)pt_sweep_kernel<false, true>, (const void*)pt_sweep_kernel<true, true>};
+    const void* ks[8] = {(const void*)pt_sweep_kernel<false, false>, (const void*)pt_sweep_kernel<true, false>,
+                         (const void*)pt_sweep_kernel<false, true>, (const void*)pt_sweep_kernel<true, true>,
+                         (const void*)pt_sweep_kernel<true, false, 4>, (const void*)pt_sweep_kernel<true, false, 8>,
+                         (const void*)pt_sweep_kernel<true, false, 12>, (const void*)pt_sweep_kernel<true, false, 16>};
     for (const void* k : ks) {
         cudaFuncAttributes fa;
         e = cudaFuncGetAttributes(&fa, k);
@@ -1077,8 +1089,10 @@ cudaError_t sweep_occupancy(int block, int smem_bytes, int* blocks_per_sm, bool 
 
 cudaError_t set_sweep_smem_limit(int bytes)
 {
-    const void* ks[4] = {(const void*)pt_sweep_kernel<false, false>, (const void*)pt_sweep_kernel<true, false>,
-                         (const void*)pt_sweep_kernel<false, true>, (const void*)pt_sweep_kernel<true, true>};
+    const void* ks[8] = {(const void*)pt_sweep_kernel<false, false>, (const void*)pt_sweep_kernel<true, false>,
+                         (const void*)pt_sweep_kernel<false, true>, (const void*)pt_sweep_kernel<true, true>,
+                         (const void*)pt_sweep_kernel<true, false, 4>, (const void*)pt_sweep_kernel<true, false, 8>,
+                         (const void*)pt_sweep_kernel<true, false, 12>, (const void*)pt_sweep_kernel<true, false, 16>};
     for (const void* k : ks) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         if (e != cudaSuccess) return e;
@@ -1104,15 +1118,26 @@ cudaError_t launch_energy(const InstDesc* insts, const int2* items, int nitems, 
 
 cudaError_t launch_sweeps(const InstDesc* insts, const Bundle* bundles, int nbundles, int grid,
                           int block, int smem_bytes, uint32_t sweep0, int nsweeps, int xevery,
-                          int mode, int* queue, cudaStream_t st, bool slot_major, bool walk)
+                          int mode, int* queue, cudaStream_t st, bool slot_major, bool walk, int L)
 {
     if (nbundles <= 0) return cudaSuccess;
+#define PT_SM_LAUNCH(LT)                                                                                         \
+    pt_sweep_kernel<true, false, LT><<<grid, block, smem_bytes, st>>>(insts, bundles, nbundles, sweep0, nsweeps, \
+                                                                      xevery, mode, queue)
     if (slot_major && walk)
         pt_sweep_kernel<true, true><<<grid, block, smem_bytes, st>>>(insts, bundles, nbundles, sweep0, nsweeps,
                                                                      xevery, mode, queue);
+    else if (slot_major && L == 4)
+        PT_SM_LAUNCH(4);
+    else if (slot_major && L == 8)
+        PT_SM_LAUNCH(8);
+    else if (slot_major && L == 12)
+        PT_SM_LAUNCH(12);
+    else if (slot_major && L == 16)
+        PT_SM_LAUNCH(16);
     else if (slot_major)
-        pt_sweep_kernel<true, false><<<grid, block, smem_bytes, st>>>(insts, bundles, nbundles, sweep0, nsweeps,
-                                                                      xevery, mode, queue);
+        PT_SM_LAUNCH(0);
+#undef PT_SM_LAUNCH
     else if (walk)
         pt_sweep_kernel<false, true><<<grid, block, smem_bytes, st>>>(insts, bundles, nbundles, sweep0, nsweeps,
                                                                       xevery, mode, queue);

@@ -20,10 +20,13 @@ cudaError_t launch_energy(const InstDesc* insts, const int2* items, int nitems, 
 // slot_major: every bundle uses the slot-major mapping (Bundle::team > 0),
 // otherwise the cell-major one (Bundle::team == 0).  walk: the instances carry
 // walk arrays (InstDesc::whot, wtrips, wstate) and the launch updates them.
+// L: the lattice side of every instance in the launch (0 if unknown or mixed);
+// the untracked slot-major kernel has instantiations for L = 4, 8, 12 and 16
+// with the side as a compile-time constant.
 cudaError_t launch_sweeps(const InstDesc* insts, const Bundle* bundles, int nbundles, int grid,
                           int block, int smem_bytes, uint32_t sweep0, int nsweeps, int xevery,
                           int mode, int* queue, cudaStream_t st, bool slot_major = false,
-                          bool walk = false);
+                          bool walk = false, int L = 0);
 // dist [n][n]: spins differing between sampled configurations of instance 0
 // (sample k: run run[k], slot slot[k]; device arrays).
 cudaError_t launch_hamming(const InstDesc* insts, int n, const int32_t* run, const int32_t* slot, int32_t* dist,
