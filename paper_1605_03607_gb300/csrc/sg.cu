@@ -244,6 +244,30 @@ __device__ __forceinline__ void flush_f32x32(const unsigned char* stage, float* 
     __syncwarp();
 }
 
+// Adds the sums of staged row pairs (2p, 2p + 1), in that order, to row p of g
+// (16 pairs x 32 FP32 columns; only pairs < npairs).
+__device__ __forceinline__ void flush_pairs_add_f32x32(const unsigned char* stage, float* g, int ld, int npairs,
+                                                       int lane)
+{
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int p = k * 4 + (lane >> 3), c = lane & 7, ra = 2 * p, rb = ra + 1;
+        const float4 a = *reinterpret_cast<const float4*>(stage + ra * 128 + ((c ^ (ra & 7)) << 4));
+        const float4 b = *reinterpret_cast<const float4*>(stage + rb * 128 + ((c ^ (rb & 7)) << 4));
+        if (p < npairs) {
+            float4* gp = reinterpret_cast<float4*>(g + (size_t)p * ld + c * 4);
+            float4 o = *gp;
+            o.x += a.x + b.x;
+            o.y += a.y + b.y;
+            o.z += a.z + b.z;
+            o.w += a.w + b.w;
+            *gp = o;
+        }
+    }
+    __syncwarp();
+}
+
 __device__ __forceinline__ void stage_bf16(unsigned char* stage, int lane, int c, uint4 v)
 {
     *reinterpret_cast<uint4*>(stage + lane * 64 + ((c ^ ((lane >> 1) & 3)) << 4)) = v;
@@ -419,9 +443,11 @@ __global__ void __launch_bounds__(TC_THREADS, TC_CTAS_FWD) lin_fwd_tc_kernel(int
 }
 
 // Input gradient: dX = dZ W over `rows` rows of dZ [rows][64] (BF16), with
-// W^T pre-packed.  EPI 0: dX [rows][128] FP32.  EPI 1 (node and edge
-// updates): out0 = base + dX[:, :64] (base may be out0 or NULL) and
-// out1 = dX[:, 64:], both [rows][64] FP32.
+// W^T pre-packed.  EPI 0 (messages; rows 2e and 2e+1 are the two directions
+// of edge e): dX[:, :64] -> dX [rows][64] FP32, and the edge half of each
+// pair, dX[2e][64:] + dX[2e+1][64:], added to out1[e] ([rows / 2][64]).
+// EPI 1 (node and edge updates): out0 = base + dX[:, :64] (base may be out0
+// or NULL) and out1 = dX[:, 64:], both [rows][64] FP32.
 template <int EPI>
 __global__ void __launch_bounds__(TC_THREADS, EPI == 0 ? TC_CTAS_BWD : 2) lin_bwd_input_tc_kernel(int rows, const bf16* __restrict__ dZ,
                                                                       const bf16* __restrict__ WTpk,
@@ -504,8 +530,10 @@ __global__ void __launch_bounds__(TC_THREADS, EPI == 0 ? TC_CTAS_BWD : 2) lin_bw
                     stage_f32(stage, lane, 4 * hh + c, v);
                 }
             }
-            if (EPI == 0)
-                flush_f32x32(stage, dX + (size_t)row0 * KIN + c0, KIN, rows - row0, lane);
+            if (EPI == 0 && c0 < HD)
+                flush_f32x32(stage, dX + (size_t)row0 * HD + c0, HD, rows - row0, lane);
+            else if (EPI == 0)                             // a warp's 32 rows are 16 whole edges (row0 is even)
+                flush_pairs_add_f32x32(stage, out1 + (size_t)(row0 / 2) * HD + (c0 - HD), HD, (rows - row0) / 2, lane);
             else if (c0 < HD)
                 flush_f32x32(stage, out0 + (size_t)row0 * HD + c0, HD, rows - row0, lane);
             else
@@ -746,19 +774,6 @@ __global__ void gather_add_kernel(int B, int N, int Rsrc, const int* __restrict_
             if (r >= 0) acc += src[((size_t)b * Rsrc + r) * w + off + c];
         }
         out[i] += acc;
-    }
-}
-
-// de[b][e] += dXm[b][2e][64..] + dXm[b][2e+1][64..]
-__global__ void edge_from_messages_kernel(int B, int E, const float* __restrict__ dXm, float* de)
-{
-    const size_t total = (size_t)B * E * HD;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t be = i / HD;
-        const int c = (int)(i % HD);
-        const int b = (int)(be / E), e = (int)(be % E);
-        const size_t r0 = (size_t)b * 2 * E + 2 * e;
-        de[i] += dXm[r0 * KIN + HD + c] + dXm[(r0 + 1) * KIN + HD + c];
     }
 }
 
@@ -1069,7 +1084,7 @@ int prepare(sg_model* M, int L, int B)
         SK(salloc(&M->ze[l], nE * HD), "cudaMalloc ze");
     }
     SK(salloc(&M->R, nM * HD), "cudaMalloc R");
-    SK(salloc(&M->dX, nM * KIN), "cudaMalloc dX");
+    SK(salloc(&M->dX, nM * HD), "cudaMalloc dX");           // message rows' node half of the input gradient
     SK(salloc(&M->dZ, nM * HD), "cudaMalloc dZ");
     {
         int dev = 0, sms = 0;
@@ -1187,13 +1202,12 @@ int backward_all(sg_model* M, int B)
         // messages: m_i = sum relu(zm) over rows into i
         relu_mask_kernel<<<grid_for(nE * 2 * HD / 2), 256, 0, st>>>(B * 2 * E, M->dm, M->d_tgt, 2 * E, N, M->zm[l], M->dZ);
         lin_bwd_input_tc_kernel<0><<<tc_grid(M, B * 2 * E, TC_CTAS_BWD), TC_THREADS, TC_SMEM_BWD, st>>>(B * 2 * E, M->dZ, wpk_bwd(M, l, 0),
-                                                                                 M->dX, nullptr, nullptr, nullptr,
+                                                                                 M->dX, nullptr, nullptr, M->de,
                                                                                  M->d_err);
         const RowSrc ms = rows_of(M->h[l], M->d_src, N, M->e[l], M->d_eid, E, 2 * E);
         lin_wgrad(M, B * 2 * E, ms, G + M->oWm[l], G + M->obm[l]);
-        gather_add_kernel<<<grid_for(nN * HD), 256, 0, st>>>(B, N, 2 * E, M->d_out_rows, M->dX, KIN, 0, M->dh);
-        edge_from_messages_kernel<<<grid_for(nE * HD), 256, 0, st>>>(B, E, M->dX, M->de);
-        M->launches += 18;
+        gather_add_kernel<<<grid_for(nN * HD), 256, 0, st>>>(B, N, 2 * E, M->d_out_rows, M->dX, HD, 0, M->dh);
+        M->launches += 17;
     }
     embed_bwd_kernel<<<4 * M->sms, 256, 0, st>>>(B, N, E, M->d_u, M->d_J, M->dh, M->de, M->d_epart);
     embed_bwd_reduce<<<(8 * HD + 255) / 256, 256, 0, st>>>(4 * M->sms, M->d_epart, G + M->oX, G + M->oJ);
