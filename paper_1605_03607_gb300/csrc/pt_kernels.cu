@@ -1066,10 +1066,12 @@ cudaError_t sweep_smem_capacity(int* bytes)
     e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
     size_t stat = 0;
-    const void* ks[8] = {(const void*)pt_sweep_kernel<false, false>, (const void*)pt_sweep_kernel<true, false>,
-                         (const void*)pt_sweep_kernel<false, true>, (const void*)pt_sweep_kernel<true, true>,
-                         (const void*)pt_sweep_kernel<true, false, 4>, (const void*)pt_sweep_kernel<true, false, 8>,
-                         (const void*)pt_sweep_kernel<true, false, 12>, (const void*)pt_sweep_kernel<true, false, 16>};
+    const void* ks[12] = {(const void*)pt_sweep_kernel<false, false>, (const void*)pt_sweep_kernel<true, false>,
+                          (const void*)pt_sweep_kernel<false, true>, (const void*)pt_sweep_kernel<true, true>,
+                          (const void*)pt_sweep_kernel<true, false, 4>, (const void*)pt_sweep_kernel<true, false, 8>,
+                          (const void*)pt_sweep_kernel<true, false, 12>, (const void*)pt_sweep_kernel<true, false, 16>,
+                          (const void*)pt_sweep_kernel<true, true, 4>, (const void*)pt_sweep_kernel<true, true, 8>,
+                          (const void*)pt_sweep_kernel<true, true, 12>, (const void*)pt_sweep_kernel<true, true, 16>};
     for (const void* k : ks) {
         cudaFuncAttributes fa;
         e = cudaFuncGetAttributes(&fa, k);
@@ -1089,10 +1091,12 @@ cudaError_t sweep_occupancy(int block, int smem_bytes, int* blocks_per_sm, bool 
 
 cudaError_t set_sweep_smem_limit(int bytes)
 {
-    const void* ks[8] = {(const void*)pt_sweep_kernel<false, false>, (const void*)pt_sweep_kernel<true, false>,
-                         (const void*)pt_sweep_kernel<false, true>, (const void*)pt_sweep_kernel<true, true>,
-                         (const void*)pt_sweep_kernel<true, false, 4>, (const void*)pt_sweep_kernel<true, false, 8>,
-                         (const void*)pt_sweep_kernel<true, false, 12>, (const void*)pt_sweep_kernel<true, false, 16>};
+    const void* ks[12] = {(const void*)pt_sweep_kernel<false, false>, (const void*)pt_sweep_kernel<true, false>,
+                          (const void*)pt_sweep_kernel<false, true>, (const void*)pt_sweep_kernel<true, true>,
+                          (const void*)pt_sweep_kernel<true, false, 4>, (const void*)pt_sweep_kernel<true, false, 8>,
+                          (const void*)pt_sweep_kernel<true, false, 12>, (const void*)pt_sweep_kernel<true, false, 16>,
+                          (const void*)pt_sweep_kernel<true, true, 4>, (const void*)pt_sweep_kernel<true, true, 8>,
+                          (const void*)pt_sweep_kernel<true, true, 12>, (const void*)pt_sweep_kernel<true, true, 16>};
     for (const void* k : ks) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         if (e != cudaSuccess) return e;
@@ -1121,22 +1125,22 @@ cudaError_t launch_sweeps(const InstDesc* insts, const Bundle* bundles, int nbun
                           int mode, int* queue, cudaStream_t st, bool slot_major, bool walk, int L)
 {
     if (nbundles <= 0) return cudaSuccess;
-#define PT_SM_LAUNCH(LT)                                                                                         \
-    pt_sweep_kernel<true, false, LT><<<grid, block, smem_bytes, st>>>(insts, bundles, nbundles, sweep0, nsweeps, \
-                                                                      xevery, mode, queue)
+#define PT_SM_LAUNCH(W, LT)                                                                                   \
+    pt_sweep_kernel<true, W, LT><<<grid, block, smem_bytes, st>>>(insts, bundles, nbundles, sweep0, nsweeps, \
+                                                                  xevery, mode, queue)
+#define PT_SM_LAUNCH_L(W)                                                                                     \
+    do {                                                                                                      \
+        if (L == 4) PT_SM_LAUNCH(W, 4);                                                                       \
+        else if (L == 8) PT_SM_LAUNCH(W, 8);                                                                  \
+        else if (L == 12) PT_SM_LAUNCH(W, 12);                                                                \
+        else if (L == 16) PT_SM_LAUNCH(W, 16);                                                                \
+        else PT_SM_LAUNCH(W, 0);                                                                              \
+    } while (0)
     if (slot_major && walk)
-        pt_sweep_kernel<true, true><<<grid, block, smem_bytes, st>>>(insts, bundles, nbundles, sweep0, nsweeps,
-                                                                     xevery, mode, queue);
-    else if (slot_major && L == 4)
-        PT_SM_LAUNCH(4);
-    else if (slot_major && L == 8)
-        PT_SM_LAUNCH(8);
-    else if (slot_major && L == 12)
-        PT_SM_LAUNCH(12);
-    else if (slot_major && L == 16)
-        PT_SM_LAUNCH(16);
+        PT_SM_LAUNCH_L(true);
     else if (slot_major)
-        PT_SM_LAUNCH(0);
+        PT_SM_LAUNCH_L(false);
+#undef PT_SM_LAUNCH_L
 #undef PT_SM_LAUNCH
     else if (walk)
         pt_sweep_kernel<false, true><<<grid, block, smem_bytes, st>>>(insts, bundles, nbundles, sweep0, nsweeps,

@@ -21,8 +21,8 @@ cudaError_t launch_energy(const InstDesc* insts, const int2* items, int nitems, 
 // otherwise the cell-major one (Bundle::team == 0).  walk: the instances carry
 // walk arrays (InstDesc::whot, wtrips, wstate) and the launch updates them.
 // L: the lattice side of every instance in the launch (0 if unknown or mixed);
-// the untracked slot-major kernel has instantiations for L = 4, 8, 12 and 16
-// with the side as a compile-time constant.
+// both slot-major kernels (walk tracked or not) have instantiations for
+// L = 4, 8, 12 and 16 with the side as a compile-time constant.
 cudaError_t launch_sweeps(const InstDesc* insts, const Bundle* bundles, int nbundles, int grid,
                           int block, int smem_bytes, uint32_t sweep0, int nsweeps, int xevery,
                           int mode, int* queue, cudaStream_t st, bool slot_major = false,
