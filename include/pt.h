@@ -279,10 +279,15 @@ int engineer_begin(pt_handle *h, const pt_rule *rule, uint32_t base_uid, int32_t
 int engineer_step(pt_handle *h, uint32_t step, pt_step_result *out);
 
 /* n_steps consecutive steps t = step0 .. step0+n_steps-1 with results
- * identical to n_steps engineer_step calls.  Up to `speculation` (1..16)
+ * identical to n_steps engineer_step calls.  `speculation` (1..16)
  * candidates are drawn against the current couplers and evaluated in one
  * batched launch; every candidate after the first kept one is discarded and
- * redrawn.  out: n_steps results (may be NULL). */
+ * redrawn.  A batch is always evaluated in full, also when fewer steps remain
+ * in the call; the evaluated candidates of the steps past the call's end are
+ * kept and used by the next engineer_run call if it starts at the next step
+ * and the couplers, runs per evaluation, pt_rule and base uid are unchanged
+ * (engineer_begin, engineer_set_adaptive, pt_set_coupler, lao_*, the guided
+ * step and pt_restore drop them).  out: n_steps results (may be NULL). */
 int engineer_run(pt_handle *h, uint32_t step0, int32_t n_steps, int32_t speculation,
                  pt_step_result *out);
 

@@ -109,6 +109,19 @@ struct pt_handle {
     int64_t cost_max = 0;
     double beta_per_run = 0.0;
     std::vector<int32_t> last_levels;   // deciding levels of the last doubling evaluation of candidates
+    // Evaluated candidates of RAO steps past the end of the last engineer_run call (each batch is
+    // evaluated in full, spec candidates), kept with everything their evaluation depends on; the
+    // next call uses them only if it starts at `step` and all of it is unchanged.
+    struct SpecCache {
+        bool valid = false;
+        uint32_t step = 0;             // RAO step of entry 0
+        int32_t n_runs = 0;
+        uint32_t base_uid = 0;
+        pt_rule rule{};
+        std::vector<int8_t> J;
+        std::vector<int32_t> e, v, res, level;   // res: tts, hits, target per entry
+        std::vector<uint32_t> cu, ua;
+    } spec_cache;
     std::string err = "no error";
 };
 
@@ -1080,6 +1093,7 @@ int pt_set_coupler(pt_handle* h, int32_t edge, int8_t value)
     if (edge < 0 || edge >= h->n_edges || value < -J_ABS_MAX)
         return fail(h, PT_ERR_ARG, "edge out of range or |value| > 127");
     const int8_t prev = h->J[edge];
+    h->spec_cache.valid = false;
     h->J[edge] = value;
     if (int rc0 = ensure_table_rows(h, coupler_kmax(h->L, h->J.data()))) {
         h->J[edge] = prev;
@@ -1140,6 +1154,7 @@ int engineer_begin(pt_handle* h, const pt_rule* rule, uint32_t base_uid, int32_t
         return fail(h, PT_ERR_ARG, "max_sweeps must be S * 2^k <= 2^30 with pass_mult 1");
     h->rule = *rule;
     h->base_uid = base_uid;
+    h->spec_cache.valid = false;
     int32_t t, nh;
     int rc = rule->max_sweeps > 0
                  ? pt_tts_eval_doubling(h, base_uid, rule->S, rule->max_sweeps, rule->exchange_every, &t, &nh,
@@ -1162,30 +1177,47 @@ int engineer_run(pt_handle* h, uint32_t step0, int32_t n_steps, int32_t spec, pt
     int rc = ensure_candidates(h, spec);
     if (rc) return rc;
     std::vector<int8_t> Jc((size_t)spec * h->n_edges);
-    std::vector<int32_t> e(spec), v(spec);
+    std::vector<int32_t> e(spec), v(spec), res, lv;
     std::vector<uint32_t> cu(spec), ua(spec);
+    pt_handle::SpecCache& c = h->spec_cache;
     int32_t done = 0;
     bool changed = false;
     while (done < n_steps) {
-        const int k = std::min<int>(spec, n_steps - done);
-        for (int j = 0; j < k; ++j) {
-            engineer_draw(h, h->J.data(), step0 + (uint32_t)(done + j), 0u, e[j], v[j], cu[j], ua[j]);
-            int8_t* Jj = Jc.data() + (size_t)j * h->n_edges;
-            std::memcpy(Jj, h->J.data(), h->n_edges);
-            Jj[e[j]] = (int8_t)v[j];
-        }
-        // every candidate of the batch uses the runs of the step it stands for;
-        // the batch is cut after a candidate that is kept or that halves them
+        const uint32_t s0 = step0 + (uint32_t)done;
         const int n = h->adapt ? h->n_cur : h->R;
-        std::vector<int32_t> res;
-        rc = eval_candidates(h, k, Jc.data(), cu.data(), res, PT_TARGET_BEST, nullptr, n);
-        if (rc) return rc;
+        // candidates of steps s0, s0+1, ...: evaluated by the previous call past its end, if nothing
+        // their evaluation depends on has changed since; otherwise a full batch of spec is evaluated
+        // now, so that the GPU holds spec candidates' runs even when fewer steps remain in this call
+        int k;
+        if (c.valid && c.step == s0 && c.n_runs == n && c.base_uid == h->base_uid && c.rule.S == h->rule.S &&
+            c.rule.pass_mult == h->rule.pass_mult && c.rule.exchange_every == h->rule.exchange_every &&
+            c.rule.max_sweeps == h->rule.max_sweeps && c.J == h->J) {
+            k = (int)c.e.size();
+            e = c.e; v = c.v; cu = c.cu; ua = c.ua; res = c.res; lv = c.level;
+        } else {
+            k = spec;
+            e.resize(k); v.resize(k); cu.resize(k); ua.resize(k);
+            for (int j = 0; j < k; ++j) {
+                engineer_draw(h, h->J.data(), s0 + (uint32_t)j, 0u, e[j], v[j], cu[j], ua[j]);
+                int8_t* Jj = Jc.data() + (size_t)j * h->n_edges;
+                std::memcpy(Jj, h->J.data(), h->n_edges);
+                Jj[e[j]] = (int8_t)v[j];
+            }
+            // every candidate of the batch uses the runs of the step it stands for
+            rc = eval_candidates(h, k, Jc.data(), cu.data(), res, PT_TARGET_BEST, nullptr, n);
+            if (rc) return rc;
+            lv.assign(h->last_levels.begin(), h->last_levels.begin() + k);
+        }
+        c.valid = false;
         pt_rule rule = h->rule;
         if (h->adapt && h->beta_per_run > 0.0) rule.beta_rao = h->beta_per_run * (double)n;
-        int used = k;
-        for (int j = 0; j < k; ++j) {
+        // decisions in step order; the batch is cut after a candidate that is kept or that halves the runs
+        const int kuse = std::min<int>(k, n_steps - done);
+        int used = kuse;
+        bool stop = false;
+        for (int j = 0; j < kuse && !stop; ++j) {
             const int32_t tn = res[(size_t)j * 3];
-            const int32_t level = h->last_levels[(size_t)j];
+            const int32_t level = lv[(size_t)j];
             const bool acc = engineer_accept(rule, h->tts_cur, tn, ua[j]);
             if (out) {
                 pt_step_result& o = out[done + j];
@@ -1193,7 +1225,6 @@ int engineer_run(pt_handle* h, uint32_t step0, int32_t n_steps, int32_t spec, pt
                 o.tts_old = h->tts_cur; o.tts_new = tn; o.accepted = acc ? 1 : 0; o.cand_uid = cu[j];
                 o.n_runs = n; o.level = level;
             }
-            bool stop = false;
             if (acc) {
                 h->J[e[j]] = (int8_t)v[j];
                 h->tts_cur = tn;
@@ -1205,10 +1236,21 @@ int engineer_run(pt_handle* h, uint32_t step0, int32_t n_steps, int32_t spec, pt
                 h->n_cur = std::max(h->n_min, n / 2);
                 stop = true;
             }
-            if (stop) {
-                used = j + 1;
-                break;
-            }
+            if (stop) used = j + 1;
+        }
+        if (!stop && kuse < k) {               // steps past this call's end: kept for the next call
+            c.valid = true;
+            c.step = s0 + (uint32_t)kuse;
+            c.n_runs = n;
+            c.base_uid = h->base_uid;
+            c.rule = h->rule;
+            c.J = h->J;
+            c.e.assign(e.begin() + kuse, e.begin() + k);
+            c.v.assign(v.begin() + kuse, v.begin() + k);
+            c.cu.assign(cu.begin() + kuse, cu.begin() + k);
+            c.ua.assign(ua.begin() + kuse, ua.begin() + k);
+            c.res.assign(res.begin() + (size_t)kuse * 3, res.begin() + (size_t)k * 3);
+            c.level.assign(lv.begin() + kuse, lv.begin() + k);
         }
         done += used;
     }
@@ -1255,6 +1297,7 @@ int lao_begin(pt_handle* h, const pt_rule* rule, uint32_t uid, int32_t n_loops, 
     int32_t eg = 0;
     if (lao_plant(h->L, h->seed, uid, n_loops, w_max, planted.data(), loops.data(), J.data(), &eg) != PT_OK)
         return fail(h, PT_ERR_ARG, pt_last_error(nullptr));
+    h->spec_cache.valid = false;
     h->rule = *rule;
     h->rule.pass_mult = 1;                   // the target is known: no longer pass
     h->rule.max_sweeps = 0;                  // one pass of S sweeps against E_GS
@@ -1280,6 +1323,7 @@ int lao_begin(pt_handle* h, const pt_rule* rule, uint32_t uid, int32_t n_loops, 
 int lao_run(pt_handle* h, uint32_t step0, int32_t n_steps, int32_t spec, pt_lao_result* out)
 {
     if (!h) return PT_ERR_ARG;
+    h->spec_cache.valid = false;           // the couplers change outside engineer_run
     if (!h->lao) return fail(h, PT_ERR_STATE, "lao_begin not called");
     if (step0 < 1 || n_steps < 0 || spec < 1 || spec > 16)
         return fail(h, PT_ERR_ARG, "need step0 >= 1, n_steps >= 0, speculation in [1, 16]");
@@ -1430,6 +1474,7 @@ int engineer_guided_step(pt_handle* h, sg_model* m, uint32_t step, int32_t n_pro
                          pt_step_result* out, float* pred, int32_t* ranked)
 {
     if (!h) return fail(h, PT_ERR_ARG, "NULL argument");
+    h->spec_cache.valid = false;           // the couplers change outside engineer_run
     if (!h->eng) return fail(h, PT_ERR_STATE, "engineer_begin not called");
     if (n_prop < 1 || n_prop > 1024 || top < 1 || top > 16 || top > n_prop)
         return fail(h, PT_ERR_ARG, "need 1 <= top <= min(n_prop, 16), n_prop <= 1024");
@@ -1498,11 +1543,13 @@ int engineer_set_adaptive(pt_handle* h, int32_t n0, int32_t n_min, int64_t cost_
 {
     if (!h) return PT_ERR_ARG;
     if (n0 == 0) {
+        h->spec_cache.valid = false;
         h->adapt = false;
         return PT_OK;
     }
     if (n_min < 1 || n0 < n_min || n0 > h->R || cost_max < 1 || !(beta_per_run >= 0.0) || !std::isfinite(beta_per_run))
         return fail(h, PT_ERR_ARG, "need 1 <= n_min <= n0 <= n_runs, cost_max >= 1, beta_per_run >= 0");
+    h->spec_cache.valid = false;
     h->adapt = true;
     h->n_cur = n0;
     h->n_min = n_min;
@@ -1554,6 +1601,7 @@ int pt_checkpoint(pt_handle* h, void* buf, size_t* len)
 int pt_restore(pt_handle* h, const void* buf, size_t len)
 {
     if (!h || !buf) return fail(h, PT_ERR_ARG, "NULL argument");
+    h->spec_cache.valid = false;
     size_t need = 0;
     pt_checkpoint(h, nullptr, &need);
     if (len != need) return fail(h, PT_ERR_ARG, "checkpoint size does not match this handle");

@@ -195,3 +195,75 @@ def test_adaptive_budget_matches_oracle(P, spec, max_sweeps):
     assert list(res["tts_new"]) == list(log["tts"]) and list(res["accepted"]) == list(log["accept"])
     assert n_after == n2 and t_gpu == tf and np.array_equal(J_gpu, Jf)
     assert len(set(log["n"])) >= 2                    # the run count did change
+
+
+def _split_run(h, step0, lengths, spec):
+    """engineer_run over consecutive calls of the given lengths; results concatenated."""
+    parts, step = [], step0
+    for n in lengths:
+        parts.append(h.engineer_run(step, n, spec))
+        step += n
+    return {k: np.concatenate([p[k] for p in parts]) for k in parts[0]}
+
+
+@pytest.mark.parametrize("beta_rao,direction", [(-1.0, 1), (0.02, 1), (-1.0, -1)])
+def test_engineer_run_split_calls_match_one_call_and_oracle(P, beta_rao, direction):
+    """Each speculative batch is evaluated in full and the candidates past a
+    call's end are kept for the next call: splitting 30 steps into calls of
+    3, 5, 1, 7, 8, 6 with speculation 8 gives every decision of one 30-step
+    call with speculation 1 and of the oracle's sequential loop."""
+    L, NT, R, S, seed = 4, 8, 4, 128, 51
+    J = W.random_couplers(L, seed, 0)
+    betas = W.beta_ladder(NT, 0.1, 3.0)
+    out = []
+    for lengths, spec in (([30], 1), ([3, 5, 1, 7, 8, 6], 8), ([16, 14], 16)):
+        with P.PTHandle(L, J, betas, R, seed, 0) as h:
+            h.engineer_begin(S=S, pass_mult=2, exchange_every=1, base_uid=0, beta_rao=beta_rao, direction=direction)
+            r = _split_run(h, 0, lengths, spec)
+            out.append((r, h.engineer_tts(), h.couplers()))
+    for r, t, Jc in out[1:]:
+        assert all(np.array_equal(r[k], out[0][0][k]) for k in r)
+        assert t == out[0][1] and np.array_equal(Jc, out[0][2])
+    Jo, to, lo = oracle.engineer_run(L, J, betas, R, seed, 0, S, 2, 1, 0, 30, beta_rao=beta_rao, direction=direction)
+    assert list(out[0][0]["accepted"]) == list(lo["accept"]) and out[0][1] == to and np.array_equal(out[0][2], Jo)
+
+
+def test_engineer_run_kept_candidates_dropped_on_coupler_change(P):
+    """A coupler set between two calls drops the candidates the first call
+    evaluated past its end: the second call equals a fresh loop from the new
+    couplers (same TTS baseline), not the kept evaluations."""
+    L, NT, R, S, seed = 4, 8, 4, 128, 53
+    J = W.random_couplers(L, seed, 0)
+    betas = W.beta_ladder(NT, 0.1, 3.0)
+    with P.PTHandle(L, J, betas, R, seed, 0) as h:
+        h.engineer_begin(S=S, pass_mult=2, exchange_every=1, base_uid=0)
+        h.engineer_run(0, 2, 8)                      # evaluates steps 0..7, keeps those past step 1
+        Jm = h.couplers().copy()
+        Jm[5] = -Jm[5]
+        h.set_coupler(5, int(Jm[5]))
+        tts = h.engineer_tts()
+        r = h.engineer_run(2, 6, 8)
+        got = (r, h.engineer_tts(), h.couplers())
+    Jo, to, lo = oracle.engineer_run(L, Jm, betas, R, seed, 0, S, 2, 1, 2, 6, tts_cur=tts)
+    assert list(got[0]["accepted"]) == list(lo["accept"]) and got[1] == to and np.array_equal(got[2], Jo)
+
+
+def test_adaptive_budget_split_calls_match_oracle(P):
+    """The adaptive budget with calls of 2, 3, 5 steps at speculation 4: run
+    counts, TTS values, decisions and halvings equal the oracle's."""
+    L, seed, base, NT = 2, 101, 0, 4
+    J0 = W.random_couplers(L, seed, 0)
+    betas = W.beta_ladder(NT, 0.5, 3.0)
+    S, pm, n0, nmin = 16, 2, 32, 4
+    cost_max = 10 * S * pm
+    with P.PTHandle(L, J0, betas, n0, seed, base) as h:
+        t0 = h.engineer_begin(S=S, pass_mult=pm, base_uid=base)
+        h.set_adaptive(n0, nmin, cost_max, beta_per_run=0.05)
+        res = _split_run(h, 0, [2, 3, 5], 4)
+        n_after = h.adaptive_runs()
+        J_gpu, t_gpu = h.couplers(), h.engineer_tts()
+    Jf, tf, n2, log = oracle.engineer_run_adaptive(L, J0, betas, seed, base, S, pm, 1, 0, 10, n0, nmin, cost_max, t0,
+                                                   beta_per_run=0.05)
+    assert list(res["n_runs"]) == list(log["n"]) and list(res["tts_new"]) == list(log["tts"])
+    assert list(res["accepted"]) == list(log["accept"])
+    assert n_after == n2 and t_gpu == tf and np.array_equal(J_gpu, Jf)
