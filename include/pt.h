@@ -368,8 +368,11 @@ int lao_begin(pt_handle *h, const pt_rule *rule, uint32_t uid, int32_t n_loops, 
  * floor(w0 M / 2^32), puts in loop (t, 0xFFFFFFFF) drawn against the
  * remaining couplers, evaluates the candidate against its own E_GS with PT
  * key w2, and keeps it under Algorithm 1's rule (Boltzmann uniform w1); w0..w2
- * come from counter (t, 0xFFFFFFFE, 0, 4).  Candidates are PT-evaluated up to
- * `speculation` (1..16) at a time; results equal the step-by-step loop.
+ * come from counter (t, 0xFFFFFFFE, 0, 4).  Candidates are PT-evaluated
+ * `speculation` (1..16) at a time; results equal the step-by-step loop.  As in
+ * engineer_run, a batch is always evaluated in full and the evaluations of
+ * steps past the call's end are used by the next lao_run call if it starts at
+ * the next step with the couplers, loops, E_GS and pt_rule unchanged.
  * out: n_steps records (may be NULL). */
 int lao_run(pt_handle *h, uint32_t step0, int32_t n_steps, int32_t speculation, pt_lao_result *out);
 

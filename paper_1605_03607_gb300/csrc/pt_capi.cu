@@ -122,6 +122,19 @@ struct pt_handle {
         std::vector<int32_t> e, v, res, level;   // res: tts, hits, target per entry
         std::vector<uint32_t> cu, ua;
     } spec_cache;
+    // The same for lao_run: candidates also depend on the loop list and E_GS, and an accepted one
+    // replaces the couplers and one loop record.
+    struct LaoCache {
+        bool valid = false;
+        uint32_t step = 0;
+        pt_rule rule{};
+        std::vector<int8_t> J;
+        std::vector<int32_t> loops;
+        int32_t E_gs = 0;
+        std::vector<int8_t> Jc;                        // candidates' couplers [count][n_edges]
+        std::vector<int32_t> rem, egs, recs, res;      // recs [count][PT_LOOP_WORDS], res 3 per entry
+        std::vector<uint32_t> cu, ua;
+    } lao_cache;
     std::string err = "no error";
 };
 
@@ -1094,6 +1107,7 @@ int pt_set_coupler(pt_handle* h, int32_t edge, int8_t value)
         return fail(h, PT_ERR_ARG, "edge out of range or |value| > 127");
     const int8_t prev = h->J[edge];
     h->spec_cache.valid = false;
+    h->lao_cache.valid = false;
     h->J[edge] = value;
     if (int rc0 = ensure_table_rows(h, coupler_kmax(h->L, h->J.data()))) {
         h->J[edge] = prev;
@@ -1155,6 +1169,7 @@ int engineer_begin(pt_handle* h, const pt_rule* rule, uint32_t base_uid, int32_t
     h->rule = *rule;
     h->base_uid = base_uid;
     h->spec_cache.valid = false;
+    h->lao_cache.valid = false;
     int32_t t, nh;
     int rc = rule->max_sweeps > 0
                  ? pt_tts_eval_doubling(h, base_uid, rule->S, rule->max_sweeps, rule->exchange_every, &t, &nh,
@@ -1180,6 +1195,7 @@ int engineer_run(pt_handle* h, uint32_t step0, int32_t n_steps, int32_t spec, pt
     std::vector<int32_t> e(spec), v(spec), res, lv;
     std::vector<uint32_t> cu(spec), ua(spec);
     pt_handle::SpecCache& c = h->spec_cache;
+    h->lao_cache.valid = false;                // LAO's kept evaluations assume the LAO state
     int32_t done = 0;
     bool changed = false;
     while (done < n_steps) {
@@ -1298,6 +1314,7 @@ int lao_begin(pt_handle* h, const pt_rule* rule, uint32_t uid, int32_t n_loops, 
     if (lao_plant(h->L, h->seed, uid, n_loops, w_max, planted.data(), loops.data(), J.data(), &eg) != PT_OK)
         return fail(h, PT_ERR_ARG, pt_last_error(nullptr));
     h->spec_cache.valid = false;
+    h->lao_cache.valid = false;
     h->rule = *rule;
     h->rule.pass_mult = 1;                   // the target is known: no longer pass
     h->rule.max_sweeps = 0;                  // one pass of S sweeps against E_GS
@@ -1336,42 +1353,57 @@ int lao_run(pt_handle* h, uint32_t step0, int32_t n_steps, int32_t spec, pt_lao_
     std::vector<uint32_t> cu(spec), ua(spec);
     int32_t done = 0;
     bool changed = false;
+    pt_handle::LaoCache& c = h->lao_cache;
     while (done < n_steps) {
-        // k candidates drawn against the current instance: after the first
-        // accepted one the rest are stale and redrawn (same results as one by one)
-        const int k = std::min<int>(spec, n_steps - done);
-        for (int j = 0; j < k; ++j) {
-            const uint32_t t = step0 + (uint32_t)(done + j);
-            uint32_t ctl[3];
-            for (int w = 0; w < 3; ++w) ctl[w] = lao_word(h->seed, h->lao_uid, t, 0xFFFFFFFEu, 0u, w);
-            rem[j] = (int)mulhi(ctl[0], (uint32_t)M);
-            ua[j] = ctl[1];
-            cu[j] = ctl[2];
-            const int32_t* old = h->loops.data() + (size_t)rem[j] * PT_LOOP_WORDS;
-            int8_t* Jj = Jc.data() + (size_t)j * h->n_edges;
-            int32_t* rec = recs.data() + (size_t)j * PT_LOOP_WORDS;
-            std::memcpy(Jj, h->J.data(), h->n_edges);
-            loop_apply(g, h->planted.data(), old, Jj, -1);
-            if (!lao_draw_loop(g, h->planted.data(), Jj, h->seed, h->lao_uid, t, 0xFFFFFFFFu, h->lao_w_max, rec))
-                return fail(h, PT_ERR_STATE, "no admissible replacement loop");
-            loop_apply(g, h->planted.data(), rec, Jj, 1);
-            egs[j] = h->E_gs + old[1] * (old[0] - 2) - rec[1] * (rec[0] - 2);
-        }
-        // one batched evaluation, each candidate against its own ground-state energy
+        const uint32_t s0 = step0 + (uint32_t)done;
+        // candidates drawn against the current instance: after the first accepted one the rest are stale
+        // and redrawn (same results as one by one).  Evaluations the previous call made for steps past
+        // its end are used if the instance, its loops and E_GS are unchanged; otherwise a full batch of
+        // spec is evaluated, also when fewer steps remain in this call.
+        int k;
         std::vector<int32_t> res;
-        if ((rc = eval_candidates(h, k, Jc.data(), cu.data(), res, PT_TARGET_BEST, egs.data()))) return rc;
-        std::vector<int32_t> tts(k);
-        for (int j = 0; j < k; ++j) tts[j] = res[(size_t)j * 3];
-        int used = k;
-        for (int j = 0; j < k; ++j) {
-            const bool acc = engineer_accept(h->rule, h->tts_cur, tts[j], ua[j]);
+        if (c.valid && c.step == s0 && c.rule.S == h->rule.S && c.rule.exchange_every == h->rule.exchange_every &&
+            c.E_gs == h->E_gs && c.J == h->J && c.loops == h->loops) {
+            k = (int)c.rem.size();
+            Jc = c.Jc; rem = c.rem; egs = c.egs; recs = c.recs; res = c.res; cu = c.cu; ua = c.ua;
+        } else {
+            k = spec;
+            Jc.resize((size_t)k * h->n_edges);
+            rem.resize(k); egs.resize(k); recs.resize((size_t)k * PT_LOOP_WORDS); cu.resize(k); ua.resize(k);
+            for (int j = 0; j < k; ++j) {
+                const uint32_t t = s0 + (uint32_t)j;
+                uint32_t ctl[3];
+                for (int w = 0; w < 3; ++w) ctl[w] = lao_word(h->seed, h->lao_uid, t, 0xFFFFFFFEu, 0u, w);
+                rem[j] = (int)mulhi(ctl[0], (uint32_t)M);
+                ua[j] = ctl[1];
+                cu[j] = ctl[2];
+                const int32_t* old = h->loops.data() + (size_t)rem[j] * PT_LOOP_WORDS;
+                int8_t* Jj = Jc.data() + (size_t)j * h->n_edges;
+                int32_t* rec = recs.data() + (size_t)j * PT_LOOP_WORDS;
+                std::memcpy(Jj, h->J.data(), h->n_edges);
+                loop_apply(g, h->planted.data(), old, Jj, -1);
+                if (!lao_draw_loop(g, h->planted.data(), Jj, h->seed, h->lao_uid, t, 0xFFFFFFFFu, h->lao_w_max, rec))
+                    return fail(h, PT_ERR_STATE, "no admissible replacement loop");
+                loop_apply(g, h->planted.data(), rec, Jj, 1);
+                egs[j] = h->E_gs + old[1] * (old[0] - 2) - rec[1] * (rec[0] - 2);
+            }
+            // one batched evaluation, each candidate against its own ground-state energy
+            if ((rc = eval_candidates(h, k, Jc.data(), cu.data(), res, PT_TARGET_BEST, egs.data()))) return rc;
+        }
+        c.valid = false;
+        const int kuse = std::min<int>(k, n_steps - done);
+        int used = kuse;
+        bool kept = false;
+        for (int j = 0; j < kuse; ++j) {
+            const int32_t tn = res[(size_t)j * 3];
+            const bool acc = engineer_accept(h->rule, h->tts_cur, tn, ua[j]);
             if (out) {
                 pt_lao_result& o = out[done + j];
                 o.removed = rem[j];
                 std::memcpy(o.loop, recs.data() + (size_t)j * PT_LOOP_WORDS, sizeof(o.loop));
                 o.E_gs_new = egs[j];
                 o.tts_old = h->tts_cur;
-                o.tts_new = tts[j];
+                o.tts_new = tn;
                 o.accepted = acc ? 1 : 0;
                 o.cand_uid = cu[j];
             }
@@ -1380,12 +1412,28 @@ int lao_run(pt_handle* h, uint32_t step0, int32_t n_steps, int32_t spec, pt_lao_
                 std::memcpy(h->loops.data() + (size_t)rem[j] * PT_LOOP_WORDS, recs.data() + (size_t)j * PT_LOOP_WORDS,
                             sizeof(int32_t) * PT_LOOP_WORDS);
                 h->E_gs = egs[j];
-                h->tts_cur = tts[j];
+                h->tts_cur = tn;
                 h->hits_cur = res[(size_t)j * 3 + 1];
                 changed = true;
+                kept = true;
                 used = j + 1;
                 break;
             }
+        }
+        if (!kept && kuse < k) {               // steps past this call's end: kept for the next call
+            c.valid = true;
+            c.step = s0 + (uint32_t)kuse;
+            c.rule = h->rule;
+            c.J = h->J;
+            c.loops = h->loops;
+            c.E_gs = h->E_gs;
+            c.Jc.assign(Jc.begin() + (size_t)kuse * h->n_edges, Jc.begin() + (size_t)k * h->n_edges);
+            c.rem.assign(rem.begin() + kuse, rem.begin() + k);
+            c.egs.assign(egs.begin() + kuse, egs.begin() + k);
+            c.recs.assign(recs.begin() + (size_t)kuse * PT_LOOP_WORDS, recs.begin() + (size_t)k * PT_LOOP_WORDS);
+            c.res.assign(res.begin() + (size_t)kuse * 3, res.begin() + (size_t)k * 3);
+            c.cu.assign(cu.begin() + kuse, cu.begin() + k);
+            c.ua.assign(ua.begin() + kuse, ua.begin() + k);
         }
         done += used;
     }
@@ -1475,6 +1523,7 @@ int engineer_guided_step(pt_handle* h, sg_model* m, uint32_t step, int32_t n_pro
 {
     if (!h) return fail(h, PT_ERR_ARG, "NULL argument");
     h->spec_cache.valid = false;           // the couplers change outside engineer_run
+    h->lao_cache.valid = false;
     if (!h->eng) return fail(h, PT_ERR_STATE, "engineer_begin not called");
     if (n_prop < 1 || n_prop > 1024 || top < 1 || top > 16 || top > n_prop)
         return fail(h, PT_ERR_ARG, "need 1 <= top <= min(n_prop, 16), n_prop <= 1024");
@@ -1544,12 +1593,14 @@ int engineer_set_adaptive(pt_handle* h, int32_t n0, int32_t n_min, int64_t cost_
     if (!h) return PT_ERR_ARG;
     if (n0 == 0) {
         h->spec_cache.valid = false;
+    h->lao_cache.valid = false;
         h->adapt = false;
         return PT_OK;
     }
     if (n_min < 1 || n0 < n_min || n0 > h->R || cost_max < 1 || !(beta_per_run >= 0.0) || !std::isfinite(beta_per_run))
         return fail(h, PT_ERR_ARG, "need 1 <= n_min <= n0 <= n_runs, cost_max >= 1, beta_per_run >= 0");
     h->spec_cache.valid = false;
+    h->lao_cache.valid = false;
     h->adapt = true;
     h->n_cur = n0;
     h->n_min = n_min;
@@ -1602,6 +1653,7 @@ int pt_restore(pt_handle* h, const void* buf, size_t len)
 {
     if (!h || !buf) return fail(h, PT_ERR_ARG, "NULL argument");
     h->spec_cache.valid = false;
+    h->lao_cache.valid = false;
     size_t need = 0;
     pt_checkpoint(h, nullptr, &need);
     if (len != need) return fail(h, PT_ERR_ARG, "checkpoint size does not match this handle");

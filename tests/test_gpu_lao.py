@@ -81,3 +81,27 @@ def test_overlaps_match_oracle(P, planted):
     ref = oracle.overlaps(st["spins"], st["E"], E_gs)
     assert r == ref
     assert r["n_gs"] >= 1 and r["n_es"] >= 1
+
+
+@pytest.mark.parametrize("beta,spec,lengths", [(-1.0, 8, [3, 5, 1, 5]), (0.05, 16, [7, 7])])
+def test_lao_split_calls_match_oracle(P, beta, spec, lengths):
+    """lao_run evaluates every batch in full and keeps the evaluations past a
+    call's end for the next call: uneven calls give the oracle's decisions,
+    loops, couplers and E_GS."""
+    L, NT, R, M, S, w = 4, 8, 8, 40, 256, 5
+    seed, uid, steps = 20160516, 23, sum(lengths)
+    betas = W.beta_ladder(NT, 0.1, 3.0)
+    ref = oracle.LAOState(L, betas, R, seed, uid, M, w_max=w, S=S, beta_rao=beta)
+    log = ref.run(1, steps)
+    with P.PTHandle(L, np.zeros(W.chimera_n_edges(L), np.int8), betas, R, seed, 0) as h:
+        h.lao_begin(S, uid, M, w, 1, beta)
+        parts, step = [], 1
+        for n in lengths:
+            parts.append(h.lao_run(step, n, spec))
+            step += n
+        st = h.lao_state()
+    res = {k: np.concatenate([p[k] for p in parts]) for k in ("removed", "tts_new", "E_gs_new", "accepted")}
+    assert np.array_equal(res["removed"], log["removed"]) and np.array_equal(res["tts_new"], log["tts"])
+    assert np.array_equal(res["E_gs_new"], log["E_gs"]) and np.array_equal(res["accepted"], log["accepted"])
+    assert np.array_equal(st["loops"], ref.loops) and np.array_equal(st["J"], ref.J)
+    assert st["E_gs"] == ref.E_gs and st["tts"] == ref.tts
