@@ -126,10 +126,11 @@ __host__ __device__ inline int64_t table_bytes(int NT, int kt) { return pad16(4L
 void set_global_error(const char* msg);
 
 // Slot-major mapping only: one 12-word record per (colour, cell), colour-major:
-// in-cell couplers (4 words), inter-cell couplers (4 words), the group index,
-// the minus- and plus-neighbour spin word (each its own word, read together by
-// one 16-byte load with no unpacking) and 1 unused word.  The 48-byte stride
-// puts the records a team reads at once into distinct banks.
+// in-cell couplers (4 words), inter-cell couplers (4 words), then one 16-byte
+// word group read by a single load with no unpacking: the high half of the
+// Philox round-0 product M1 * (group index), the minus- and plus-neighbour
+// spin word, the low half of that product.  The 48-byte stride puts the
+// records a team reads at once into distinct banks.
 constexpr int CELL_REC = 12;
 __host__ __device__ inline int64_t cell_table_bytes(int L) { return 4LL * CELL_REC * 2 * L * L; }
 

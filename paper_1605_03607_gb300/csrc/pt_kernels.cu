@@ -617,7 +617,7 @@ __device__ void process_bundle(const InstDesc* __restrict__ insts, const Bundle 
 // cell record (dp4a over int8 couplers and spins), Metropolis test of each
 // spin against its uniform in `rn`, the word written back (unchanged where
 // nothing flipped: in a colour phase only the other colour's words are
-// read), energy change and flip bits accumulated.
+// read), energy change and flip count accumulated (pc: -2 per flipped spin).
 __device__ __forceinline__ void sm_word(const uint32_t* rec, uint4 meta, uint32_t* bw, int col, int L2, int q,
                                         const uint4 rn, const uint32_t* th, int kt, int& dk, int& pc)
 {
@@ -633,10 +633,11 @@ __device__ __forceinline__ void sm_word(const uint32_t* rec, uint4 meta, uint32_
     const int h1 = __dp4a((int)jin.y, opp, __dp4a((int)jud.y, x01, 0));
     const int h2 = __dp4a((int)jin.z, opp, __dp4a((int)jud.z, x23, 0));
     const int h3 = __dp4a((int)jin.w, opp, __dp4a((int)jud.w, x23, 0));
-    const int kk0 = (int)(int8_t)(own) * h0;
-    const int kk1 = (int)(int8_t)(own >> 8) * h1;
-    const int kk2 = (int)(int8_t)(own >> 16) * h2;
-    const int kk3 = (int)(int8_t)(own >> 24) * h3;
+    // spin i of the word as dp4a(own, 1 << 8i): integer multiply-adds, off the ALU pipe
+    const int kk0 = __dp4a((int)own, 0x00000001, 0) * h0;
+    const int kk1 = __dp4a((int)own, 0x00000100, 0) * h1;
+    const int kk2 = __dp4a((int)own, 0x00010000, 0) * h2;
+    const int kk3 = __dp4a((int)own, 0x01000000, 0) * h3;
     const bool a0 = (kk0 <= 0) | (rn.x < th[PT_IDX(max(kk0, 0), kt, 1u)]);
     const bool a1 = (kk1 <= 0) | (rn.y < th[PT_IDX(max(kk1, 0), kt, 1u)]);
     const bool a2 = (kk2 <= 0) | (rn.z < th[PT_IDX(max(kk2, 0), kt, 1u)]);
@@ -647,7 +648,7 @@ __device__ __forceinline__ void sm_word(const uint32_t* rec, uint4 meta, uint32_
     if (a2) { flip |= 0x00FE0000u; dk += kk2; }
     if (a3) { flip |= 0xFE000000u; dk += kk3; }
     bw[ow] = own ^ flip;                           // unconditional: one compare fewer per word
-    pc += __popc(flip);
+    pc = __dp4a((int)flip, 0x01010101, pc);        // -2 per flipped spin (a flipped byte is 0xFE)
 }
 
 // Slot-major mapping: a team of G lanes (a power of two, inside one warp)
@@ -713,11 +714,13 @@ __device__ void process_bundle_sm(const InstDesc* __restrict__ insts, const Bund
     for (int w = tid; w < L2 * 2; w += blockDim.x) {
         const int q = w >> 1, col = w & 1, r = q / L, c = q - r * L;
         const uint32_t gidx = (uint32_t)(2 * q + ((r + c + col) & 1));
+        const uint64_t gprod = (uint64_t)PHILOX_M1 * gidx;   // Philox round 0, word 2: fixed per cell
         const uint32_t mn = (uint32_t)((1 - col) * L2 + in.nbr[w * 2 + 0]);
         const uint32_t pl = (uint32_t)((1 - col) * L2 + in.nbr[w * 2 + 1]);
-        rec_sm[(col * L2 + q) * CELL_REC + 8] = gidx;
+        rec_sm[(col * L2 + q) * CELL_REC + 8] = (uint32_t)(gprod >> 32);
         rec_sm[(col * L2 + q) * CELL_REC + 9] = mn;
         rec_sm[(col * L2 + q) * CELL_REC + 10] = pl;
+        rec_sm[(col * L2 + q) * CELL_REC + 11] = (uint32_t)gprod;
     }
     const size_t rep0 = (size_t)run * NT;
     if (active) {
@@ -780,8 +783,9 @@ __device__ void process_bundle_sm(const InstDesc* __restrict__ insts, const Bund
                 for (int col = 0; col < 2; ++col) {
                     for (int q = tl; q < L2; q += G) {
                         const uint32_t* rec = rec_sm + (col * L2 + q) * CELL_REC;
-                        const uint4 meta = *reinterpret_cast<const uint4*>(rec + 8);   // group, minus, plus word
-                        const uint4 rn = philox_group(ps, c1, meta.x, k0, k1);
+                        // group product high half, minus word, plus word, group product low half
+                        const uint4 meta = *reinterpret_cast<const uint4*>(rec + 8);
+                        const uint4 rn = philox_group_prod(ps, c1, meta.x, meta.w, k0, k1);
                         sm_word(rec, meta, bw, col, L2, q, rn, th, KTI, dk, pc);
                     }
                     __syncwarp(tmask);                  // colour 0 of this buffer done by the whole team
@@ -792,7 +796,7 @@ __device__ void process_bundle_sm(const InstDesc* __restrict__ insts, const Bund
                 }
                 if (tl == 0) {
                     Es[t] += 2 * dk;
-                    macc[t] += (uint32_t)(pc / 7);
+                    macc[t] += (uint32_t)(-pc >> 1);
                 }
             }
         }

@@ -101,8 +101,9 @@ __host__ __device__ __forceinline__ uint4 philox_slot(const PhiloxPre& p, uint32
 }
 
 // The same counter (s, c1, g, 0) when a thread keeps the slot word c1 and
-// walks over groups g: only the products of round 0 word 0 and round 1 word 2
-// are independent of g; they are formed once per sweep.
+// walks over groups g: the products of round 0 word 0 and round 1 word 2
+// depend on neither g nor c1 and are formed once per sweep; round 0's word-2
+// product depends on g alone and comes from the caller.
 struct PhiloxSweep {
     uint32_t y0k;   // round-1 high product of word 2, xor round-1 key word 0
     uint32_t y1;    // round-1 low product of word 2
@@ -121,14 +122,15 @@ __host__ __device__ __forceinline__ PhiloxSweep philox_sweep_pre(uint32_t s, uin
     return p;
 }
 
-// Output of philox10(s, c1, g, 0, k0, k1) given philox_sweep_pre(s, k0, k1).
-__host__ __device__ __forceinline__ uint4 philox_group(const PhiloxSweep& p, uint32_t c1, uint32_t g, uint32_t k0,
-                                                       uint32_t k1)
+// Output of philox10(s, c1, g, 0, k0, k1) given philox_sweep_pre(s, k0, k1) and
+// round 0's word-2 product M1 * g as its high and low halves (bh, bl): a
+// thread that visits the same groups every sweep can keep that product.
+__host__ __device__ __forceinline__ uint4 philox_group_prod(const PhiloxSweep& p, uint32_t c1, uint32_t bh,
+                                                            uint32_t bl, uint32_t k0, uint32_t k1)
 {
-    const uint64_t B = (uint64_t)PHILOX_M1 * g;            // round 0, word 2
-    const uint32_t x0 = (uint32_t)(B >> 32) ^ c1 ^ k0;
+    const uint32_t x0 = bh ^ c1 ^ k0;
     const uint64_t C = (uint64_t)PHILOX_M0 * x0;           // round 1, word 0
-    uint32_t a0 = p.y0k ^ (uint32_t)B;
+    uint32_t a0 = p.y0k ^ bl;
     uint32_t a1 = p.y1;
     uint32_t a2 = (uint32_t)(C >> 32) ^ p.x3k;
     uint32_t a3 = (uint32_t)C;
