@@ -633,11 +633,10 @@ __device__ __forceinline__ void sm_word(const uint32_t* rec, uint4 meta, uint32_
     const int h1 = __dp4a((int)jin.y, opp, __dp4a((int)jud.y, x01, 0));
     const int h2 = __dp4a((int)jin.z, opp, __dp4a((int)jud.z, x23, 0));
     const int h3 = __dp4a((int)jin.w, opp, __dp4a((int)jud.w, x23, 0));
-    // spin i of the word as dp4a(own, 1 << 8i): integer multiply-adds, off the ALU pipe
-    const int kk0 = __dp4a((int)own, 0x00000001, 0) * h0;
-    const int kk1 = __dp4a((int)own, 0x00000100, 0) * h1;
-    const int kk2 = __dp4a((int)own, 0x00010000, 0) * h2;
-    const int kk3 = __dp4a((int)own, 0x01000000, 0) * h3;
+    const int kk0 = (int)(int8_t)(own) * h0;
+    const int kk1 = (int)(int8_t)(own >> 8) * h1;
+    const int kk2 = (int)(int8_t)(own >> 16) * h2;
+    const int kk3 = (int)(int8_t)(own >> 24) * h3;
     const bool a0 = (kk0 <= 0) | (rn.x < th[PT_IDX(max(kk0, 0), kt, 1u)]);
     const bool a1 = (kk1 <= 0) | (rn.y < th[PT_IDX(max(kk1, 0), kt, 1u)]);
     const bool a2 = (kk2 <= 0) | (rn.z < th[PT_IDX(max(kk2, 0), kt, 1u)]);
